@@ -1,0 +1,216 @@
+/*
+ * hdd.h — C ABI of the GB300 Helmholtz domain-decomposition solver.
+ *
+ * Problem (§2, Eq. 1): -Δu - k²u = f on (0,1)², u = 0 on ∂Ω, P1 finite elements on a uniform
+ * mesh of N intervals per side with every cell split along one diagonal (Eq. 2).  The unknowns
+ * are the (N-1)² interior nodes, index (i-1) + (j-1)(N-1) for node (i/N, j/N), x fastest.
+ *
+ * Solver (§3): flexible GMRES, right-preconditioned by one-level restricted additive Schwarz
+ * M⁻¹ = Σ_j R_jᵀ D_j A_j⁻¹ R_j (Eq. 3) on an overlapping Cartesian partition; every local
+ * system A_j ũ_j = f̃_j is solved inexactly by GMRES on P_j A_j ũ = P_j f̃ with the two-level
+ * deflation P_j = I - A_j Z_j E_j⁻¹ Z_jᵀ, E_j = Z_jᵀ A_j Z_j (Eq. 4), Z_j = Z_jʸ ⊗ Z_jˣ built from
+ * the quadratic rational Bézier stencil (1/8)[1 4 6 4 1] (Eq. 5).  All subdomain solves (and all
+ * right-hand sides) run at once on the GPU.
+ *
+ * Conventions for every entry point:
+ *  - Vectors passed as `*_dev` are caller-owned DEVICE pointers of interleaved complex128
+ *    (re, im doubles), one vector of (N-1)² entries per right-hand side, stored RHS-major.
+ *    They must be 16-byte aligned and live on the context's device.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is enqueued on it; calls
+ *    that return statistics synchronise it before returning.
+ *  - Every call returns an hdd_status and never aborts the process; after an error the context
+ *    can still be destroyed.  hdd_last_error() gives a one-line description.
+ *  - The library owns all of its internal device memory (allocated in the setup calls and in
+ *    hdd_solve when larger work buffers are needed; freed by hdd_destroy).
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - Required call order: hdd_create → hdd_assemble → hdd_setup_dd → hdd_setup_deflation
+ *    (and/or hdd_setup_exact) → hdd_solve / test hooks.  Out-of-order calls return
+ *    HDD_ERR_STATE.  Calling a setup step again invalidates the later ones.
+ */
+#ifndef HDD_H
+#define HDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdd_ctx hdd_ctx;
+
+typedef enum {
+    HDD_OK = 0,
+    HDD_ERR_INVALID_ARG = 1,     /* NULL pointer, size out of range, misaligned pointer      */
+    HDD_ERR_STATE = 2,           /* call order violated                                      */
+    HDD_ERR_OOM = 3,             /* device allocation failed                                 */
+    HDD_ERR_CUDA = 4,            /* a CUDA runtime call failed                               */
+    HDD_ERR_SINGULAR_COARSE = 5, /* zero pivot in the LU of some E_j (Eq. 4)                 */
+    HDD_ERR_SINGULAR_LOCAL = 6,  /* zero pivot in the LU of some A_j (direct local solve)    */
+    HDD_ERR_NO_CONVERGENCE = 7,  /* outer FGMRES reached outer_maxit above the tolerance     */
+    HDD_ERR_BREAKDOWN = 8,       /* reserved                                                 */
+    HDD_ERR_NONFINITE = 9,       /* NaN/Inf met in a residual                                */
+    HDD_ERR_TIMEOUT = 10         /* reserved for bounded device-side waits                   */
+} hdd_status;
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+hdd_status hdd_create(hdd_ctx **out, int device);
+
+/* Free every device and host resource of the context (NULL is accepted). */
+void hdd_destroy(hdd_ctx *ctx);
+
+/* Static string naming a status code. */
+const char *hdd_status_str(hdd_status s);
+
+/* Description of the most recent error on this context ("" if none). */
+const char *hdd_last_error(const hdd_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Assembly (§2, Eq. 2).  The matrix is never stored: with constant k and a uniform mesh the */
+/* assembled P1 operator is the 7-point stencil                                              */
+/*   centre 4 - k²h²/2, edge neighbours -1 - k²h²/12, the two corners joined by the cell      */
+/*   diagonals -k²h²/12 (SW/NE for diag = 0, NW/SE for diag = 1),                            */
+/* which every kernel applies matrix-free.                                                   */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    double k;   /* wave number                                            */
+    int N;      /* intervals per side, h = 1/N, 4 <= N <= 65536            */
+    int diag;   /* 0: cells split along SW-NE, 1: along NW-SE              */
+} hdd_assemble_params;
+
+hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *prm);
+
+/* Load vector on the device (§3): point sources F += amp·e_c at the interior node nearest to
+ * (x, y) (clamped into the interior), and Gaussian bumps F += M g with g the nodal values of
+ * amp·exp(-|x - c|²/(2σ²)) at the interior nodes (the interpolant in V^h) and M the P1 mass
+ * matrix.  points: npoints triples (x, y, amp); bumps: nbumps quadruples (cx, cy, σ, amp), both
+ * host arrays.  f_dev: one complex128 vector of (N-1)², overwritten. */
+hdd_status hdd_build_rhs(hdd_ctx *ctx, int npoints, const double *points, int nbumps,
+                         const double *bumps, void *f_dev, void *stream);
+
+/* y = A x for nrhs global complex128 vectors (x_dev, y_dev distinct). */
+hdd_status hdd_apply_A(hdd_ctx *ctx, const void *x_dev, void *y_dev, int nrhs, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Decomposition (Eq. 3, §3).  Sx x Sy Cartesian subdomains with interfaces                  */
+/* 0 = a_0 < a_1 < ... < a_S = N (node indices; NULL = uniform round(pN/S)).  Subdomain      */
+/* (p, q) owns the interior nodes a_p <= i < a_{p+1}, a_q <= j < a_{q+1} (D_j = ownership    */
+/* indicator) and its local box, after appending `overlap` element layers, is               */
+/* max(1, a_p - δ + 1) <= i <= min(N-1, a_{p+1} + δ - 1) (same in y).  Subdomain index        */
+/* s = p + q·Sx.  A_j = R_j A R_jᵀ is the stencil on the box with zero Dirichlet values      */
+/* outside it.                                                                               */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int Sx, Sy;       /* 1 <= Sx, Sy <= 4096                                 */
+    int overlap;      /* δ >= 1 element layers                                */
+    const int *ifx;   /* host array of Sx+1 interfaces in x, or NULL          */
+    const int *ify;   /* host array of Sy+1 interfaces in y, or NULL          */
+} hdd_dd_params;
+
+hdd_status hdd_setup_dd(hdd_ctx *ctx, const hdd_dd_params *prm);
+
+/* Number of subdomains and, for subdomain s, the 12 ints
+ * {ix0, ix1, iy0, iy1, ox0, ox1, oy0, oy1, nx, ny, mx, my}: local box, owned range,
+ * box size, coarse size (mx = floor(nx/2)). */
+hdd_status hdd_get_subdomain(const hdd_ctx *ctx, int s, int *info12);
+int hdd_num_subdomains(const hdd_ctx *ctx);
+
+/* Packed local layout used by the local test hooks: subdomain s occupies
+ * [fine_off[s], fine_off[s] + nx·ny) of a packed fine vector (box x fastest) and
+ * [coarse_off[s], coarse_off[s] + mx·my) of a packed coarse vector.  Host arrays of nsub+1. */
+hdd_status hdd_get_offsets(const hdd_ctx *ctx, long long *fine_off, long long *coarse_off);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Deflation set-up (Eq. 4, Eq. 5).  For every distinct box shape: E = Zᵀ A Z (5x5 coarse   */
+/* stencil, half-bandwidth 2·mx+2) is formed and LU-factorised with partial pivoting in FP64 */
+/* on the device; subdomains with equal shape share one factor.                             */
+/* ---------------------------------------------------------------------------------------- */
+hdd_status hdd_setup_deflation(hdd_ctx *ctx, void *stream);
+
+/* Banded LU (FP64, partial pivoting) of every distinct A_j for the direct local solve
+ * (inner_tol <= 0, the benchmark of §3.1). */
+hdd_status hdd_setup_exact(hdd_ctx *ctx, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Solve (§3).                                                                               */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    double outer_tol;    /* stop when ||f - A x|| <= outer_tol ||f|| (true residual)        */
+    int outer_restart;   /* FGMRES restart length (>= outer_maxit means unrestarted)         */
+    int outer_maxit;     /* total outer iterations                                          */
+    double inner_tol;    /* relative deflated residual ||P(f̃ - A ũ)|| <= tol ||P f̃||;        */
+                         /* <= 0 selects the direct (banded LU) local solve                 */
+    int inner_restart;   /* GMRES restart length, 1..64                                      */
+    int inner_maxit;     /* total inner iterations per local solve                          */
+    int inner_prec;      /* 64: complex64 inner solves with FP32 accumulation;              */
+                         /* 128: complex128 inner solves.  Coarse E and outer: FP64 always  */
+} hdd_solve_params;
+
+typedef struct {
+    int outer_its;               /* outer FGMRES iterations (preconditioner applications)     */
+    int status;                  /* hdd_status of the solve                                   */
+    double rel_res_true;         /* ||f - A x|| / ||f|| recomputed at exit                    */
+    long long inner_its_total;   /* Arnoldi steps summed over every local solve              */
+    double inner_its_avg;        /* inner_its_total / (outer_its x #subdomains), as in §3    */
+    int inner_its_max;           /* largest step count of one local solve                     */
+    long long inner_maxit_hits;  /* local solves stopped by inner_maxit                       */
+    double t_solve_ms;           /* wall time of the solve (host clock, stream synchronised) */
+    int n_history;               /* entries in res_history                                    */
+    const double *res_history;   /* |g_{j+1}|/||f|| per outer iteration; library-owned, valid */
+                                 /* until the next hdd_solve or hdd_destroy                   */
+} hdd_solve_stats;
+
+/* Solve A x = f for one right-hand side (f_dev → x_dev, complex128, distinct buffers).
+ * stats may be NULL.  Returns HDD_ERR_NO_CONVERGENCE (x holds the last iterate) when
+ * outer_maxit is reached. */
+hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_solve_params *prm,
+                     hdd_solve_stats *stats, void *stream);
+
+/* One application of the RAS preconditioner z = Σ_j R_jᵀ D_j ũ_j with ũ_j the inexact (or,
+ * for inner_tol <= 0, direct) solution of A_j ũ_j = R_j v (Eq. 3): the inner-solve hot path on
+ * its own.  v_dev, z_dev: global complex128.  inner_its (may be NULL): host array of nsub
+ * receiving each local solve's Arnoldi step count. */
+hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev,
+                         const hdd_solve_params *prm, int *inner_its, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Local test hooks on packed local vectors (layout of hdd_get_offsets), complex128.         */
+/*   op 0: out = A_j in        (fine → fine, every subdomain)                                */
+/*   op 1: out = Z_j in        (coarse → fine)                                               */
+/*   op 2: out = Z_jᵀ in       (fine → coarse)                                               */
+/*   op 3: out = E_j⁻¹ in      (coarse → coarse, FP64 factors)                               */
+/*   op 4: out = P_j A_j in    (fine → fine)                                                 */
+/*   op 5: out = R_j in        (global → fine; `in` is a global vector)                      */
+/*   op 6: out = A_j⁻¹ in      (fine → fine, direct solve; needs hdd_setup_exact)            */
+/* prec: 64 runs the fine arithmetic of ops 0, 1, 2, 4 in complex64 (inputs rounded to FP32, */
+/* outputs widened back), 128 in complex128. */
+hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void *out_dev,
+                        void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Profiling.  With profiling on, every kernel launch is bracketed by a pair of CUDA events on */
+/* the launching stream; durations are summed per kernel family together with the family's   */
+/* algorithmic bytes (data the step must read and write once) and floating-point operations. */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    char name[40];       /* family, e.g. "coarse_solve_fp64"                          */
+    long long launches;
+    double ms;           /* sum of per-launch event durations                         */
+    double bytes;        /* algorithmic bytes, summed over launches                   */
+    double flops;        /* algorithmic floating-point operations, summed            */
+    int bound;           /* 0: memory-bandwidth bound, 1: FP64-arithmetic bound        */
+} hdd_kernel_stat;
+
+/* Synchronise the device, clear the counters and switch event timing on (1) or off (0). */
+hdd_status hdd_profile(hdd_ctx *ctx, int enable);
+/* Number of kernel families (entries readable with hdd_profile_get). */
+int hdd_profile_count(const hdd_ctx *ctx);
+/* Synchronise the device and read family i. */
+hdd_status hdd_profile_get(hdd_ctx *ctx, int i, hdd_kernel_stat *out);
+/* Kernel launches made by this context since creation (counted whether or not profiling is on). */
+long long hdd_launch_count(const hdd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDD_H */

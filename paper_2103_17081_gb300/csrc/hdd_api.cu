@@ -1,0 +1,952 @@
+// hdd_api.cu — context, set-up and solve driver behind the C ABI declared in include/hdd.h.
+//
+// Host code only orchestrates: every arithmetic step of assembly, deflation set-up, inner and
+// outer solves runs in the kernels of kernels_local.cu, kernels_coarse.cu and kernels_outer.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "hdd.h"
+#include "hdd_common.cuh"
+
+using namespace hdd;
+
+namespace {
+
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevMem() { if (p) cudaFree(p); }
+    cudaError_t ensure(size_t b) {
+        if (b <= bytes && p) return cudaSuccess;
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        cudaError_t e = cudaMalloc(&p, b > 0 ? b : 16);
+        if (e == cudaSuccess) bytes = b;
+        return e;
+    }
+    void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+    template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct SubBox {
+    int ix0, ix1, iy0, iy1, ox0, ox1, oy0, oy1, nx, ny, mx, my;
+};
+
+struct FactorSet {            // banded FP64 factors of one matrix per shape
+    DevMem L, U, I, Rr, table;
+    std::vector<BandFactor> h;
+    std::vector<double> fma_col;    // FP64 FMAs of one real column solve, per shape
+    int kmax = 0;                   // most band entries in one column of L or Û
+    int max_m = 0;
+    bool ready = false;
+    void clear() { L.release(); U.release(); I.release(); Rr.release(); table.release(); h.clear(); max_m = 0; ready = false; }
+};
+
+template <typename R> struct InnerWork {   // inner GMRES buffers for one precision
+    int restart = 0;
+    DevMem f, u, x, t, V, y, s, p1, p2, p3;
+    DevMem H, cs, sn, g, ref, its, kcols, conv, rsf;
+    DevMem act0, act1, flagA, flagB;
+};
+
+// Kernel families timed by the profiler (CUDA events around every launch on the launching
+// stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
+enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, NFAM };
+const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
+                              "local_cgs2_update", "local_givens_normalize", "local_misc",
+                              "outer_cgs2_fp64", "outer_misc_fp64"};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0};
+
+struct Prof {
+    bool on = false;
+    long long launches = 0;
+    long long cnt[NFAM] = {};
+    double ms[NFAM] = {}, bytes[NFAM] = {}, flops[NFAM] = {};
+    struct P { int f; cudaEvent_t a, b; double by, fl; };
+    std::vector<P> pend;
+    std::vector<cudaEvent_t> pool;
+    ~Prof() {
+        for (auto &p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+    void reset() {
+        launches = 0;
+        for (int f = 0; f < NFAM; f++) { cnt[f] = 0; ms[f] = bytes[f] = flops[f] = 0; }
+    }
+    cudaEvent_t get() {
+        if (pool.empty()) { cudaEvent_t e; cudaEventCreate(&e); return e; }
+        cudaEvent_t e = pool.back(); pool.pop_back(); return e;
+    }
+    // after a stream synchronisation every pending event pair is complete
+    void harvest() {
+        for (auto &p : pend) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.f] += t;
+            cnt[p.f]++; bytes[p.f] += p.by; flops[p.f] += p.fl;
+            pool.push_back(p.a); pool.push_back(p.b);
+        }
+        pend.clear();
+    }
+};
+
+struct OuterWork {
+    int R = 0;
+    long long n = 0;
+    DevMem V, Z, w, r, H, cs, sn, g, h1, h2, part, npart, hn, flag, hist, beta, y;
+};
+
+}  // namespace
+
+struct hdd_ctx {
+    int device = 0;
+    std::string err;
+    bool assembled = false, dd = false;
+    // problem
+    int N = 0, diag = 0;
+    double k = 0, h = 0;
+    Stencil st{};
+    long long nglob = 0;
+    // decomposition
+    int Sx = 0, Sy = 0, overlap = 0;
+    std::vector<SubBox> subs;
+    std::vector<int> sub_shape;
+    std::vector<std::pair<int, int>> shapes;   // (nx, ny)
+    std::vector<Task> h_tasks;
+    std::vector<Tile> h_ftiles, h_ctiles;
+    DevMem d_tasks, d_ftiles, d_ctiles, d_ones;
+    long long ld = 0, ldc = 0;
+    int max_nx = 0, max_n = 0;
+    std::vector<long long> foffs, coffs;
+    // factors
+    FactorSet E, Aex;
+    // work
+    InnerWork<float> w32;
+    InnerWork<double> w64;
+    OuterWork ow;
+    DevMem tmp_a, tmp_b, tmp_c;                // staging for test hooks
+    int *h_counter = nullptr;                  // pinned
+    DevMem d_counter;
+    std::vector<double> hist;
+    std::vector<int> h_its;
+    Prof prof;
+    ~hdd_ctx() { if (h_counter) cudaFreeHost(h_counter); }
+};
+
+#define FAIL(code, ...)                                                                            \
+    do {                                                                                           \
+        char _b[512];                                                                              \
+        snprintf(_b, sizeof(_b), __VA_ARGS__);                                                     \
+        ctx->err = _b;                                                                             \
+        return code;                                                                               \
+    } while (0)
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t _e = (call);                                                                   \
+        if (_e != cudaSuccess) {                                                                   \
+            if (_e == cudaErrorMemoryAllocation) FAIL(HDD_ERR_OOM, "%s: %s", #call, cudaGetErrorString(_e)); \
+            FAIL(HDD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e));                           \
+        }                                                                                          \
+    } while (0)
+
+#define CKL() CK(cudaGetLastError())
+
+namespace {
+
+// Counts every kernel launch; with profiling on, brackets it with a CUDA event pair on the
+// launching stream.  Use: { Launch L(ctx, family, bytes, flops, stream); launch(...); }
+struct Launch {
+    hdd_ctx *c; int f; double by, fl; cudaStream_t s; cudaEvent_t a = nullptr;
+    Launch(hdd_ctx *ctx, int fam, double bytes, double flops, cudaStream_t st)
+        : c(ctx), f(fam), by(bytes), fl(flops), s(st) {
+        c->prof.launches++;
+        if (c->prof.on) { a = c->prof.get(); cudaEventRecord(a, s); }
+    }
+    ~Launch() {
+        if (a) {
+            cudaEvent_t b = c->prof.get();
+            cudaEventRecord(b, s);
+            c->prof.pend.push_back(Prof::P{f, a, b, by, fl});
+        }
+    }
+};
+#define KL(fam, by, fl, stmt) do { Launch _l(ctx, fam, (double)(by), (double)(fl), s); stmt; } while (0)
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <typename R> LocalArgs<R> local_args(hdd_ctx *ctx) {
+    LocalArgs<R> a;
+    a.tasks = ctx->d_tasks.as<Task>();
+    a.ftiles = ctx->d_ftiles.as<Tile>();
+    a.ctiles = ctx->d_ctiles.as<Tile>();
+    a.ntasks = (int)ctx->h_tasks.size();
+    a.nftiles = (int)ctx->h_ftiles.size();
+    a.nctiles = (int)ctx->h_ctiles.size();
+    a.st = ctx->st;
+    a.ld = ctx->ld;
+    a.ldc = ctx->ldc;
+    a.max_nx = ctx->max_nx;
+    a.gw = ctx->N - 1;
+    return a;
+}
+
+hdd_status read_counter(hdd_ctx *ctx, cudaStream_t s, int *out) {
+    CK(cudaMemcpyAsync(ctx->h_counter, ctx->d_counter.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->prof.harvest();
+    *out = *ctx->h_counter;
+    return HDD_OK;
+}
+
+// E_j (or A_j) factors for every distinct shape, FP64, on the device.
+hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s) {
+    F.clear();
+    const int ns = (int)ctx->shapes.size();
+    std::vector<int> m(ns), kl(ns), ku(ns);
+    long long totL = 0, totU = 0, totM = 0;
+    F.h.resize(ns);
+    for (int q = 0; q < ns; q++) {
+        int nx = ctx->shapes[q].first, ny = ctx->shapes[q].second;
+        if (coarse) { m[q] = (nx / 2) * (ny / 2); kl[q] = ku[q] = 2 * (nx / 2) + 2; }
+        else { m[q] = nx * ny; kl[q] = ku[q] = nx + 1; }
+        F.h[q] = BandFactor{m[q], kl[q], ku[q], totL, totU, totM};
+        totL += (long long)m[q] * kl[q];
+        totU += (long long)m[q] * (kl[q] + ku[q]);
+        totM += m[q];
+        F.max_m = std::max(F.max_m, m[q]);
+    }
+    std::vector<DevMem> ab(ns), piv(ns);
+    std::vector<double *> abp(ns);
+    std::vector<int *> pivp(ns);
+    for (int q = 0; q < ns; q++) {
+        size_t W = 2 * kl[q] + ku[q] + 1;
+        CK(ab[q].ensure((size_t)m[q] * W * sizeof(double)));
+        CK(cudaMemsetAsync(ab[q].p, 0, (size_t)m[q] * W * sizeof(double), s));
+        CK(piv[q].ensure((size_t)m[q] * sizeof(int)));
+        abp[q] = ab[q].as<double>();
+        pivp[q] = piv[q].as<int>();
+        int nx = ctx->shapes[q].first, ny = ctx->shapes[q].second;
+        if (coarse) launch_assemble_E(ctx->st, nx, ny, kl[q], ku[q], abp[q], s);
+        else launch_assemble_Aloc(ctx->st, nx, ny, kl[q], ku[q], abp[q], s);
+        CKL();
+    }
+    DevMem dm, dkl, dku, dab, dpiv, dinfo;
+    CK(dm.ensure(ns * sizeof(int))); CK(dkl.ensure(ns * sizeof(int))); CK(dku.ensure(ns * sizeof(int)));
+    CK(dab.ensure(ns * sizeof(double *))); CK(dpiv.ensure(ns * sizeof(int *))); CK(dinfo.ensure(ns * sizeof(int)));
+    CK(cudaMemcpyAsync(dm.p, m.data(), ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dkl.p, kl.data(), ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dku.p, ku.data(), ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dab.p, abp.data(), ns * sizeof(double *), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dpiv.p, pivp.data(), ns * sizeof(int *), cudaMemcpyHostToDevice, s));
+    launch_band_lu(ns, dm.as<int>(), dkl.as<int>(), dku.as<int>(), dab.as<double *>(), dpiv.as<int *>(),
+                   dinfo.as<int>(), s);
+    CKL();
+    std::vector<int> info(ns);
+    CK(cudaMemcpyAsync(info.data(), dinfo.p, ns * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < ns; q++)
+        if (info[q] != 0)
+            FAIL(coarse ? HDD_ERR_SINGULAR_COARSE : HDD_ERR_SINGULAR_LOCAL,
+                 "zero pivot in column %d of the %s factor of box %dx%d", info[q] - 1,
+                 coarse ? "E" : "A_j", ctx->shapes[q].first, ctx->shapes[q].second);
+    CK(F.L.ensure((size_t)std::max(totL, 1LL) * sizeof(double)));
+    CK(F.U.ensure((size_t)std::max(totU, 1LL) * sizeof(double)));
+    CK(F.I.ensure((size_t)std::max(2 * totM, 1LL) * sizeof(int)));
+    CK(F.Rr.ensure((size_t)std::max(totM, 1LL) * sizeof(double)));
+    for (int q = 0; q < ns; q++) {
+        const BandFactor &b = F.h[q];
+        launch_band_convert(b.m, b.kl, b.ku, abp[q], pivp[q], F.L.as<double>() + b.l_off,
+                            F.U.as<double>() + b.u_off, F.I.as<int>() + 2 * b.p_off + b.m,
+                            F.Rr.as<double>() + b.p_off, F.I.as<int>() + 2 * b.p_off, s);
+        CKL();
+    }
+    F.fma_col.assign(ns, 0.0);
+    F.kmax = 0;
+    for (int q = 0; q < ns; q++) {
+        const BandFactor &b = F.h[q];
+        std::vector<int> ue(b.m);
+        CK(cudaMemcpy(ue.data(), F.I.as<int>() + 2 * b.p_off + b.m, b.m * sizeof(int), cudaMemcpyDeviceToHost));
+        double fm = 0;
+        for (int j = 0; j < b.m; j++) { fm += std::min(b.kl, b.m - 1 - j) + ue[j]; F.kmax = std::max(F.kmax, ue[j]); }
+        F.kmax = std::max(F.kmax, b.kl);
+        F.fma_col[q] = fm;
+    }
+    CK(F.table.ensure(ns * sizeof(BandFactor)));
+    CK(cudaMemcpyAsync(F.table.p, F.h.data(), ns * sizeof(BandFactor), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    if (set_band_solve_smem(F.max_m, F.kmax) != cudaSuccess)
+        FAIL(HDD_ERR_INVALID_ARG, "factor of order %d with %d band entries per column exceeds the shared-memory solve",
+             F.max_m, F.kmax);
+    F.ready = true;
+    return HDD_OK;
+}
+
+// FP64 banded solve of every flagged task; `nact` tasks are expected to be flagged (profiling).
+void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *out, bool fine,
+                const int *flag, cudaStream_t s, int nact = -1) {
+    const int nt = (int)ctx->h_tasks.size();
+    double fl = 0;
+    for (int q = 0; q < nt; q++) fl += F.fma_col[ctx->h_tasks[q].shape];
+    fl = 4.0 * fl * (nact < 0 ? 1.0 : (double)nact / nt);      // 2 columns x 2 flops per FMA
+    Launch L(ctx, F_COARSE, fl * 2.0, fl, s);                      // factor bytes ~ 8 B per FMA / 4
+    launch_band_solve(ctx->d_tasks.as<Task>(), (int)ctx->h_tasks.size(), F.table.as<BandFactor>(),
+                      F.L.as<double>(), F.U.as<double>(), F.I.as<int>(), F.Rr.as<double>(), in, out,
+                      fine ? 1 : 0, flag, F.max_m, F.kmax, s);
+}
+
+template <typename R> InnerWork<R> &work(hdd_ctx *ctx);
+template <> InnerWork<float> &work<float>(hdd_ctx *ctx) { return ctx->w32; }
+template <> InnerWork<double> &work<double>(hdd_ctx *ctx) { return ctx->w64; }
+
+template <typename R> hdd_status ensure_inner(hdd_ctx *ctx, int R_) {
+    InnerWork<R> &W = work<R>(ctx);
+    const size_t cs = sizeof(c2<R>);
+    const long long ld = ctx->ld, ldc = ctx->ldc, nt = (long long)ctx->h_tasks.size();
+    const long long nft = (long long)ctx->h_ftiles.size();
+    CK(W.f.ensure(ld * cs)); CK(W.u.ensure(ld * cs)); CK(W.x.ensure(ld * cs)); CK(W.t.ensure(ld * cs));
+    CK(W.V.ensure((size_t)(R_ + 1) * ld * cs));
+    CK(W.y.ensure(ldc * sizeof(double2))); CK(W.s.ensure((size_t)(R_ + 2) * ldc * sizeof(double2)));
+    CK(W.p1.ensure(nft * LOCAL_LDP * cs)); CK(W.p2.ensure(nft * LOCAL_LDP * cs)); CK(W.p3.ensure(nft * LOCAL_LDP * cs));
+    CK(W.H.ensure((size_t)nt * (R_ + 1) * R_ * cs));
+    CK(W.cs.ensure((size_t)nt * R_ * sizeof(R)));
+    CK(W.sn.ensure((size_t)nt * R_ * cs));
+    CK(W.g.ensure((size_t)nt * (R_ + 1) * cs));
+    CK(W.ref.ensure(nt * sizeof(R)));
+    CK(W.its.ensure(nt * sizeof(int))); CK(W.kcols.ensure(nt * sizeof(int)));
+    CK(W.conv.ensure(nt * sizeof(int))); CK(W.rsf.ensure(nt * sizeof(int)));
+    CK(W.act0.ensure(nt * sizeof(int))); CK(W.act1.ensure(nt * sizeof(int)));
+    CK(W.flagA.ensure(nt * sizeof(int))); CK(W.flagB.ensure(nt * sizeof(int)));
+    W.restart = R_;
+    size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)cs);
+    if (smem > 48 * 1024) CK(set_local_smem_limits<R>(smem));
+    return HDD_OK;
+}
+
+template <typename R> InnerState<R> inner_state(InnerWork<R> &W) {
+    InnerState<R> S;
+    S.H = W.H.template as<c2<R>>(); S.cs = W.cs.template as<R>(); S.sn = W.sn.template as<c2<R>>();
+    S.g = W.g.template as<c2<R>>(); S.ref = W.ref.template as<R>(); S.its = W.its.template as<int>();
+    S.kcols = W.kcols.template as<int>(); S.conv = W.conv.template as<int>(); S.restart = W.rsf.template as<int>();
+    return S;
+}
+
+// All local solves of one RAS application (Eq. 3): z = Σ_j R_jᵀ D_j ũ_j, ũ_j from deflated
+// GMRES on P_j A_j ũ = P_j R_j v (Eq. 4), then completed by ũ += Q_j (f̃ - A_j ũ).
+template <typename R>
+hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve_params *prm,
+                     cudaStream_t s, long long *its_total, int *its_max, long long *hits,
+                     int *its_out) {
+    const int RST = prm->inner_restart;
+    hdd_status st = ensure_inner<R>(ctx, RST);
+    if (st != HDD_OK) return st;
+    InnerWork<R> &W = work<R>(ctx);
+    InnerState<R> S = inner_state<R>(W);
+    LocalArgs<R> a = local_args<R>(ctx);
+    const long long ld = ctx->ld, ldc = ctx->ldc;
+    const double cs = (double)sizeof(c2<R>);
+    const int nt = (int)ctx->h_tasks.size();
+    c2<R> *f = W.f.template as<c2<R>>(), *u = W.u.template as<c2<R>>(), *x = W.x.template as<c2<R>>();
+    c2<R> *t = W.t.template as<c2<R>>(), *V = W.V.template as<c2<R>>();
+    double2 *y = W.y.template as<double2>(), *sc = W.s.template as<double2>();
+    c2<R> *p1 = W.p1.template as<c2<R>>(), *p2 = W.p2.template as<c2<R>>(), *p3 = W.p3.template as<c2<R>>();
+    int *act[2] = {W.act0.template as<int>(), W.act1.template as<int>()};
+    int *cyc = W.flagA.template as<int>(), *rs = W.flagB.template as<int>();
+    int *cnt = ctx->d_counter.as<int>();
+    const int *ones = ctx->d_ones.as<int>();
+    const R tol = (R)prm->inner_tol;
+    const int maxit = prm->inner_maxit;
+
+    KL(F_LMISC, ld * (16 + cs), 0, launch_restrict<R>(a, v, ctx->nglob, f, nullptr, s));
+    CK(cudaMemsetAsync(W.its.p, 0, nt * sizeof(int), s));
+    CK(cudaMemsetAsync(W.conv.p, 0, nt * sizeof(int), s));
+    CK(cudaMemsetAsync(W.kcols.p, 0, nt * sizeof(int), s));
+    CK(cudaMemsetAsync(act[0], 0, nt * sizeof(int), s));
+    CK(cudaMemsetAsync(act[1], 0, nt * sizeof(int), s));
+    CK(cudaMemsetAsync(u, 0, ld * sizeof(c2<R>), s));
+    // first cycle from ũ = 0: r0 = P f̃ = f̃ - A Z E⁻¹ Zᵀ f̃, and ref = ||P f̃||
+    KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, y, 0, nullptr, s));
+    band_solve(ctx, ctx->E, y, sc, false, nullptr, s);
+    KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, V, nullptr, 0, p3, nullptr, s));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+    KL(F_LMISC, 2 * ld * cs, 0, launch_init_cycle<R>(a, S, RST, V, p3, ones, act[0], cnt, tol, maxit, 1, s));
+    CKL();
+    CK(cudaMemcpyAsync(cyc, ones, nt * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    int cur = 0, nact = 0;
+    st = read_counter(ctx, s, &nact);
+    if (st != HDD_OK) return st;
+    for (;;) {
+        for (int i = 0; i < RST && nact > 0; i++) {
+            const int *ain = act[cur];
+            int *aout = act[cur ^ 1];
+            c2<R> *vi = V + (long long)i * ld, *vn = V + (long long)(i + 1) * ld;
+            const double fa = (double)nact / nt;            // fraction of tasks still iterating
+            KL(F_ZT, fa * (ld * cs + ldc * 16), 0, launch_zt<R>(a, vi, y, 1, ain, s));
+            double2 *si = sc + (long long)(i + 1) * ldc;  // E⁻¹ Zᵀ A v_i, kept for the completion
+            band_solve(ctx, ctx->E, y, si, false, ain, s, nact);
+            KL(F_PS, fa * ((i + 3) * ld * cs + ldc * 16), fa * 8.0 * (i + 1) * ld,
+               launch_prolong_stencil<R>(a, 0, vi, si, vn, V, i + 1, p1, ain, s));
+            KL(F_CGS, fa * (i + 3) * ld * cs, fa * 16.0 * (i + 1) * ld,
+               launch_cgs_update<R>(a, 2, vn, V, i + 1, p1, p2, ain, s));
+            KL(F_CGS, fa * (i + 3) * ld * cs, fa * 8.0 * (i + 1) * ld,
+               launch_cgs_update<R>(a, 3, vn, V, i + 1, p2, p3, ain, s));
+            CK(cudaMemsetAsync(aout, 0, nt * sizeof(int), s));
+            CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+            KL(F_GIVENS, fa * 2 * ld * cs, 0,
+               launch_givens_normalize<R>(a, S, RST, i, vn, p1, p2, p3, ain, aout, cnt, tol, maxit, s));
+            CKL();
+            cur ^= 1;
+            st = read_counter(ctx, s, &nact);
+            if (st != HDD_OK) return st;
+        }
+        // end of cycle: ũ += V y for the tasks of this cycle; flag the ones needing a restart
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+        CK(cudaMemsetAsync(rs, 0, nt * sizeof(int), s));
+        KL(F_LMISC, 0, 0, launch_update_u<R>(a, S, RST, u, V, cyc, rs, cnt, maxit, s));
+        CKL();
+        int nrs = 0;
+        st = read_counter(ctx, s, &nrs);
+        if (st != HDD_OK) return st;
+        if (nrs == 0) break;
+        // restart: r = P(f̃ - A ũ) → v0
+        KL(F_LMISC, 0, 0, launch_local_A<R>(a, u, t, f, rs, s));
+        KL(F_ZT, 0, 0, launch_zt<R>(a, t, y, 0, rs, s));
+        band_solve(ctx, ctx->E, y, sc, false, rs, s, nrs);
+        KL(F_PS, 0, 0, launch_prolong_stencil<R>(a, 1, t, sc, V, nullptr, 0, p3, rs, s));
+        CK(cudaMemsetAsync(act[cur], 0, nt * sizeof(int), s));
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+        KL(F_LMISC, 0, 0, launch_init_cycle<R>(a, S, RST, V, p3, rs, act[cur], cnt, tol, maxit, 0, s));
+        CKL();
+        std::swap(cyc, rs);
+        st = read_counter(ctx, s, &nact);
+        if (st != HDD_OK) return st;
+    }
+    // completion x = ũ + Z E⁻¹ Zᵀ (f̃ - A ũ) with E⁻¹ Zᵀ (f̃ - A ũ) = s₀ - Σ y_i s_{i+1}
+    // (linearity; every term was solved during the last cycle), then z = Σ R_jᵀ D_j x_j
+    double2 *scomp = sc + (long long)(RST + 1) * ldc;
+    KL(F_LMISC, (RST + 2) * ldc * 16.0, 0, launch_coarse_combine<R>(a, S, RST, sc, scomp, s));
+    KL(F_LMISC, 2 * ld * cs + ldc * 16, 0, launch_z<R>(a, scomp, u, x, nullptr, s));
+    KL(F_LMISC, ld * (cs + 16), 0, launch_scatter<R>(a, x, z, ctx->nglob, s));
+    CKL();
+    ctx->h_its.resize(nt);
+    CK(cudaMemcpyAsync(ctx->h_its.data(), W.its.p, nt * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->prof.harvest();
+    long long tot = 0, nh = 0;
+    int mx = 0;
+    for (int q = 0; q < nt; q++) {
+        tot += ctx->h_its[q];
+        mx = std::max(mx, ctx->h_its[q]);
+        if (ctx->h_its[q] >= maxit) nh++;
+    }
+    if (its_total) *its_total = tot;
+    if (its_max) *its_max = mx;
+    if (hits) *hits = nh;
+    if (its_out) std::copy(ctx->h_its.begin(), ctx->h_its.end(), its_out);
+    return HDD_OK;
+}
+
+hdd_status exact_ras(hdd_ctx *ctx, const double2 *v, double2 *z, cudaStream_t s) {
+    if (!ctx->Aex.ready) FAIL(HDD_ERR_STATE, "direct local solves need hdd_setup_exact");
+    hdd_status st = ensure_inner<double>(ctx, 1);
+    if (st != HDD_OK) return st;
+    InnerWork<double> &W = ctx->w64;
+    LocalArgs<double> a = local_args<double>(ctx);
+    KL(F_LMISC, ctx->ld * 32, 0, launch_restrict<double>(a, v, ctx->nglob, W.f.as<double2>(), nullptr, s));
+    band_solve(ctx, ctx->Aex, W.f.as<double2>(), W.x.as<double2>(), true, nullptr, s);
+    KL(F_LMISC, ctx->ld * 32, 0, launch_scatter<double>(a, W.x.as<double2>(), z, ctx->nglob, s));
+    CKL();
+    return HDD_OK;
+}
+
+hdd_status ras_apply(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve_params *prm,
+                     cudaStream_t s, long long *tot, int *mx, long long *hits, int *its_out) {
+    if (prm->inner_tol <= 0) {
+        if (tot) *tot = 0;
+        if (mx) *mx = 0;
+        if (hits) *hits = 0;
+        return exact_ras(ctx, v, z, s);
+    }
+    if (!ctx->E.ready) FAIL(HDD_ERR_STATE, "inexact local solves need hdd_setup_deflation");
+    if (prm->inner_prec == 64) return inner_ras<float>(ctx, v, z, prm, s, tot, mx, hits, its_out);
+    return inner_ras<double>(ctx, v, z, prm, s, tot, mx, hits, its_out);
+}
+
+hdd_status check_solve_params(hdd_ctx *ctx, const hdd_solve_params *p) {
+    if (!p) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->outer_tol > 0) || p->outer_maxit < 1 || p->outer_restart < 1)
+        FAIL(HDD_ERR_INVALID_ARG, "outer_tol must be > 0, outer_maxit and outer_restart >= 1");
+    if (p->inner_tol > 0 && (p->inner_restart < 1 || p->inner_restart > MAX_RESTART || p->inner_maxit < 1))
+        FAIL(HDD_ERR_INVALID_ARG, "inner_restart must be in 1..%d and inner_maxit >= 1", MAX_RESTART);
+    if (p->inner_prec != 64 && p->inner_prec != 128)
+        FAIL(HDD_ERR_INVALID_ARG, "inner_prec must be 64 or 128");
+    return HDD_OK;
+}
+
+double host_norm(hdd_ctx *ctx, const double *dpart, long long n, cudaStream_t s, hdd_status *st) {
+    std::vector<double> h(outer_grid(n));
+    *st = HDD_OK;
+    if (cudaMemcpyAsync(h.data(), dpart, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        ctx->err = "norm read-back failed";
+        *st = HDD_ERR_CUDA;
+        return 0;
+    }
+    double a = 0;
+    for (double v : h) a += v;
+    return std::sqrt(a);
+}
+
+}  // namespace
+
+// ===========================================================================================
+// C ABI
+// ===========================================================================================
+extern "C" {
+
+const char *hdd_status_str(hdd_status s) {
+    switch (s) {
+        case HDD_OK: return "HDD_OK";
+        case HDD_ERR_INVALID_ARG: return "HDD_ERR_INVALID_ARG";
+        case HDD_ERR_STATE: return "HDD_ERR_STATE";
+        case HDD_ERR_OOM: return "HDD_ERR_OOM";
+        case HDD_ERR_CUDA: return "HDD_ERR_CUDA";
+        case HDD_ERR_SINGULAR_COARSE: return "HDD_ERR_SINGULAR_COARSE";
+        case HDD_ERR_SINGULAR_LOCAL: return "HDD_ERR_SINGULAR_LOCAL";
+        case HDD_ERR_NO_CONVERGENCE: return "HDD_ERR_NO_CONVERGENCE";
+        case HDD_ERR_BREAKDOWN: return "HDD_ERR_BREAKDOWN";
+        case HDD_ERR_NONFINITE: return "HDD_ERR_NONFINITE";
+        case HDD_ERR_TIMEOUT: return "HDD_ERR_TIMEOUT";
+    }
+    return "HDD_UNKNOWN";
+}
+
+const char *hdd_last_error(const hdd_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+hdd_status hdd_create(hdd_ctx **out, int device) {
+    if (!out) return HDD_ERR_INVALID_ARG;
+    *out = nullptr;
+    int nd = 0;
+    if (cudaGetDeviceCount(&nd) != cudaSuccess || device < 0 || device >= nd) return HDD_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return HDD_ERR_CUDA;
+    hdd_ctx *ctx = new hdd_ctx();
+    ctx->device = device;
+    if (cudaMallocHost(&ctx->h_counter, sizeof(int)) != cudaSuccess || ctx->d_counter.ensure(sizeof(int)) != cudaSuccess) {
+        delete ctx;
+        return HDD_ERR_OOM;
+    }
+    *out = ctx;
+    return HDD_OK;
+}
+
+void hdd_destroy(hdd_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    delete ctx;
+}
+
+hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *p) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!p) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
+    if (p->N < 4 || p->N > 65536) FAIL(HDD_ERR_INVALID_ARG, "N must be in 4..65536");
+    if (!std::isfinite(p->k) || p->k < 0) FAIL(HDD_ERR_INVALID_ARG, "k must be finite and >= 0");
+    if (p->diag != 0 && p->diag != 1) FAIL(HDD_ERR_INVALID_ARG, "diag must be 0 or 1");
+    CK(cudaSetDevice(ctx->device));
+    ctx->N = p->N; ctx->k = p->k; ctx->diag = p->diag; ctx->h = 1.0 / p->N;
+    ctx->nglob = (long long)(p->N - 1) * (p->N - 1);
+    const double kh2 = p->k * p->k * ctx->h * ctx->h;
+    // element-by-element P1 assembly on the uniform mesh reduces to this 7-point stencil
+    // (stiffness [4; -1 x4], consistent mass h²/12 [6; 1 x6]); see the header comment.
+    ctx->st.c0 = 4.0 - kh2 / 2.0;
+    ctx->st.c1 = -1.0 - kh2 / 12.0;
+    ctx->st.c2 = -kh2 / 12.0;
+    ctx->st.diag = p->diag;
+    ctx->assembled = true;
+    ctx->dd = false;
+    ctx->E.clear(); ctx->Aex.clear();
+    return HDD_OK;
+}
+
+hdd_status hdd_build_rhs(hdd_ctx *ctx, int npoints, const double *points, int nbumps,
+                         const double *bumps, void *f_dev, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->assembled) FAIL(HDD_ERR_STATE, "hdd_assemble first");
+    if (!f_dev || !aligned16(f_dev) || npoints < 0 || nbumps < 0 || (npoints && !points) || (nbumps && !bumps))
+        FAIL(HDD_ERR_INVALID_ARG, "bad rhs arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<double> buf(3 * npoints + 4 * nbumps + 1);
+    for (int q = 0; q < 3 * npoints; q++) buf[q] = points[q];
+    for (int q = 0; q < 4 * nbumps; q++) buf[3 * npoints + q] = bumps[q];
+    CK(ctx->tmp_c.ensure(buf.size() * sizeof(double)));
+    CK(cudaMemcpyAsync(ctx->tmp_c.p, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_build_rhs(ctx->N, ctx->h, ctx->diag, npoints, ctx->tmp_c.as<double>(), nbumps,
+                     ctx->tmp_c.as<double>() + 3 * npoints, (double2 *)f_dev, s);
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    return HDD_OK;
+}
+
+hdd_status hdd_apply_A(hdd_ctx *ctx, const void *x_dev, void *y_dev, int nrhs, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->assembled) FAIL(HDD_ERR_STATE, "hdd_assemble first");
+    if (!x_dev || !y_dev || nrhs < 1 || x_dev == y_dev || !aligned16(x_dev) || !aligned16(y_dev))
+        FAIL(HDD_ERR_INVALID_ARG, "bad apply_A arguments");
+    CK(cudaSetDevice(ctx->device));
+    for (int r = 0; r < nrhs; r++)
+        launch_gstencil(ctx->st, ctx->N, (const double2 *)x_dev + r * ctx->nglob,
+                        (double2 *)y_dev + r * ctx->nglob, nullptr, (cudaStream_t)stream);
+    CKL();
+    return HDD_OK;
+}
+
+hdd_status hdd_setup_dd(hdd_ctx *ctx, const hdd_dd_params *p) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->assembled) FAIL(HDD_ERR_STATE, "hdd_assemble first");
+    if (!p) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
+    if (p->Sx < 1 || p->Sy < 1 || p->Sx > 4096 || p->Sy > 4096 || p->overlap < 1)
+        FAIL(HDD_ERR_INVALID_ARG, "need 1 <= Sx, Sy <= 4096 and overlap >= 1");
+    CK(cudaSetDevice(ctx->device));
+    const int N = ctx->N;
+    auto interfaces = [&](int S, const int *given, std::vector<int> &a) -> bool {
+        a.resize(S + 1);
+        for (int q = 0; q <= S; q++) a[q] = given ? given[q] : (int)std::floor((double)q * N / S + 0.5);
+        if (a[0] != 0 || a[S] != N) return false;
+        for (int q = 0; q < S; q++) if (a[q + 1] - a[q] < 2) return false;
+        return true;
+    };
+    std::vector<int> ax, ay;
+    if (!interfaces(p->Sx, p->ifx, ax) || !interfaces(p->Sy, p->ify, ay))
+        FAIL(HDD_ERR_INVALID_ARG, "interfaces must run 0 = a_0 < ... < a_S = N with gaps >= 2");
+    ctx->Sx = p->Sx; ctx->Sy = p->Sy; ctx->overlap = p->overlap;
+    ctx->subs.clear(); ctx->shapes.clear(); ctx->sub_shape.clear();
+    std::map<std::pair<int, int>, int> shape_id;
+    const int d = p->overlap;
+    for (int qy = 0; qy < p->Sy; qy++)
+        for (int qx = 0; qx < p->Sx; qx++) {
+            SubBox b;
+            b.ix0 = std::max(1, ax[qx] - d + 1); b.ix1 = std::min(N - 1, ax[qx + 1] + d - 1);
+            b.iy0 = std::max(1, ay[qy] - d + 1); b.iy1 = std::min(N - 1, ay[qy + 1] + d - 1);
+            b.ox0 = std::max(1, ax[qx]); b.ox1 = ax[qx + 1] - 1;
+            b.oy0 = std::max(1, ay[qy]); b.oy1 = ay[qy + 1] - 1;
+            b.nx = b.ix1 - b.ix0 + 1; b.ny = b.iy1 - b.iy0 + 1;
+            b.mx = b.nx / 2; b.my = b.ny / 2;
+            if (b.nx > 256) FAIL(HDD_ERR_INVALID_ARG, "subdomain box %d nodes wide exceeds 256", b.nx);
+            auto key = std::make_pair(b.nx, b.ny);
+            auto it = shape_id.find(key);
+            int sid;
+            if (it == shape_id.end()) { sid = (int)ctx->shapes.size(); shape_id[key] = sid; ctx->shapes.push_back(key); }
+            else sid = it->second;
+            ctx->subs.push_back(b);
+            ctx->sub_shape.push_back(sid);
+        }
+    // one task per subdomain; fine tiles of FINE_ROWS rows, coarse tiles of COARSE_ROWS rows
+    ctx->h_tasks.clear(); ctx->h_ftiles.clear(); ctx->h_ctiles.clear();
+    ctx->foffs.assign(1, 0); ctx->coffs.assign(1, 0);
+    long long fo = 0, co = 0;
+    ctx->max_nx = 0; ctx->max_n = 0;
+    for (size_t q = 0; q < ctx->subs.size(); q++) {
+        const SubBox &b = ctx->subs[q];
+        Task T{};
+        T.nx = b.nx; T.ny = b.ny; T.mx = b.mx; T.my = b.my;
+        T.ix0 = b.ix0; T.iy0 = b.iy0; T.ox0 = b.ox0; T.ox1 = b.ox1; T.oy0 = b.oy0; T.oy1 = b.oy1;
+        T.shape = ctx->sub_shape[q]; T.sub = (int)q; T.rhs = 0;
+        T.foff = fo; T.coff = co;
+        T.tile0 = (int)ctx->h_ftiles.size();
+        for (int r = 0; r < b.ny; r += FINE_ROWS)
+            ctx->h_ftiles.push_back(Tile{(int)q, r, std::min(FINE_ROWS, b.ny - r)});
+        T.ntiles = (int)ctx->h_ftiles.size() - T.tile0;
+        for (int r = 0; r < b.my; r += COARSE_ROWS)
+            ctx->h_ctiles.push_back(Tile{(int)q, r, std::min(COARSE_ROWS, b.my - r)});
+        fo += (long long)b.nx * b.ny;
+        co += (long long)b.mx * b.my;
+        ctx->foffs.push_back(fo); ctx->coffs.push_back(co);
+        ctx->max_nx = std::max(ctx->max_nx, b.nx);
+        ctx->max_n = std::max(ctx->max_n, b.nx * b.ny);
+        ctx->h_tasks.push_back(T);
+    }
+    ctx->ld = fo; ctx->ldc = co;
+    const int nt = (int)ctx->h_tasks.size();
+    CK(ctx->d_tasks.ensure(nt * sizeof(Task)));
+    CK(ctx->d_ftiles.ensure(ctx->h_ftiles.size() * sizeof(Tile)));
+    CK(ctx->d_ctiles.ensure(ctx->h_ctiles.size() * sizeof(Tile)));
+    CK(ctx->d_ones.ensure(nt * sizeof(int)));
+    std::vector<int> ones(nt, 1);
+    CK(cudaMemcpy(ctx->d_tasks.p, ctx->h_tasks.data(), nt * sizeof(Task), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_ftiles.p, ctx->h_ftiles.data(), ctx->h_ftiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_ctiles.p, ctx->h_ctiles.data(), ctx->h_ctiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_ones.p, ones.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+    ctx->E.clear(); ctx->Aex.clear();
+    ctx->dd = true;
+    return HDD_OK;
+}
+
+int hdd_num_subdomains(const hdd_ctx *ctx) { return ctx && ctx->dd ? (int)ctx->subs.size() : 0; }
+
+hdd_status hdd_get_subdomain(const hdd_ctx *ctx_, int s, int *info) {
+    hdd_ctx *ctx = const_cast<hdd_ctx *>(ctx_);
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (s < 0 || s >= (int)ctx->subs.size() || !info) FAIL(HDD_ERR_INVALID_ARG, "bad subdomain index");
+    const SubBox &b = ctx->subs[s];
+    int v[12] = {b.ix0, b.ix1, b.iy0, b.iy1, b.ox0, b.ox1, b.oy0, b.oy1, b.nx, b.ny, b.mx, b.my};
+    std::memcpy(info, v, sizeof(v));
+    return HDD_OK;
+}
+
+hdd_status hdd_get_offsets(const hdd_ctx *ctx_, long long *fine_off, long long *coarse_off) {
+    hdd_ctx *ctx = const_cast<hdd_ctx *>(ctx_);
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (fine_off) std::copy(ctx->foffs.begin(), ctx->foffs.end(), fine_off);
+    if (coarse_off) std::copy(ctx->coffs.begin(), ctx->coffs.end(), coarse_off);
+    return HDD_OK;
+}
+
+hdd_status hdd_setup_deflation(hdd_ctx *ctx, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    CK(cudaSetDevice(ctx->device));
+    return build_factors(ctx, ctx->E, true, (cudaStream_t)stream);
+}
+
+hdd_status hdd_setup_exact(hdd_ctx *ctx, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    CK(cudaSetDevice(ctx->device));
+    return build_factors(ctx, ctx->Aex, false, (cudaStream_t)stream);
+}
+
+hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev, const hdd_solve_params *prm,
+                         int *inner_its, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (!v_dev || !z_dev || v_dev == z_dev || !aligned16(v_dev) || !aligned16(z_dev))
+        FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
+    hdd_status st = check_solve_params(ctx, prm);
+    if (st != HDD_OK) return st;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(z_dev, 0, ctx->nglob * sizeof(double2), s));
+    st = ras_apply(ctx, (const double2 *)v_dev, (double2 *)z_dev, prm, s, nullptr, nullptr, nullptr, inner_its);
+    if (st != HDD_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    return HDD_OK;
+}
+
+hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_solve_params *prm,
+                     hdd_solve_stats *stats, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (!f_dev || !x_dev || f_dev == x_dev || !aligned16(f_dev) || !aligned16(x_dev))
+        FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
+    hdd_status st = check_solve_params(ctx, prm);
+    if (st != HDD_OK) return st;
+    if (prm->inner_tol > 0 && !ctx->E.ready) FAIL(HDD_ERR_STATE, "hdd_setup_deflation first");
+    if (prm->inner_tol <= 0 && !ctx->Aex.ready) FAIL(HDD_ERR_STATE, "hdd_setup_exact first");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const long long n = ctx->nglob;
+    const int R = std::min(prm->outer_restart, prm->outer_maxit);
+    OuterWork &O = ctx->ow;
+    const int G = outer_grid(n);
+    const int ldp = R + 1;
+    CK(O.V.ensure((size_t)(R + 1) * n * sizeof(double2)));
+    CK(O.Z.ensure((size_t)R * n * sizeof(double2)));
+    CK(O.w.ensure(n * sizeof(double2))); CK(O.r.ensure(n * sizeof(double2)));
+    CK(O.H.ensure((size_t)(R + 1) * R * sizeof(double2)));
+    CK(O.cs.ensure(R * sizeof(double))); CK(O.sn.ensure(R * sizeof(double2)));
+    CK(O.g.ensure((R + 1) * sizeof(double2)));
+    CK(O.h1.ensure((R + 1) * sizeof(double2))); CK(O.h2.ensure((R + 1) * sizeof(double2)));
+    CK(O.y.ensure((R + 1) * sizeof(double2)));
+    CK(O.part.ensure((size_t)G * ldp * sizeof(double2)));
+    CK(O.npart.ensure(G * sizeof(double)));
+    CK(O.hn.ensure(sizeof(double))); CK(O.flag.ensure(sizeof(int))); CK(O.beta.ensure(sizeof(double)));
+    CK(O.hist.ensure((size_t)(prm->outer_maxit + 1) * sizeof(double)));
+    const size_t osm = (size_t)(R + 1) * sizeof(double2);   // dynamic: h (update), y (axpy, trisolve)
+    if (osm + 40 * 1024 > 227 * 1024) FAIL(HDD_ERR_INVALID_ARG, "outer restart %d too long", R);
+    CK(set_outer_smem_limits(osm));
+    double2 *V = O.V.as<double2>(), *Zb = O.Z.as<double2>(), *w = O.w.as<double2>(), *r = O.r.as<double2>();
+    const double2 *f = (const double2 *)f_dev;
+    double2 *x = (double2 *)x_dev;
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+    KL(F_OMISC, n * 16, 0, launch_onorm(f, n, O.npart.as<double>(), s));
+    CKL();
+    const double fn = host_norm(ctx, O.npart.as<double>(), n, s, &st);
+    if (st != HDD_OK) return st;
+    hdd_solve_stats loc{};
+    hdd_solve_stats &S = stats ? *stats : loc;
+    std::memset(&S, 0, sizeof(S));
+    ctx->hist.clear();
+    if (!std::isfinite(fn)) FAIL(HDD_ERR_NONFINITE, "right-hand side is not finite");
+    if (fn == 0.0) { S.rel_res_true = 0; S.status = HDD_OK; return HDD_OK; }
+    int total = 0;
+    long long inner_tot = 0, hits = 0;
+    int inner_mx = 0;
+    hdd_status result = HDD_OK;
+    double relres = 1.0;
+    for (;;) {
+        KL(F_OMISC, 3 * n * 16, 0, launch_gstencil(ctx->st, ctx->N, x, r, f, s));   // r = f - A x
+        KL(F_OMISC, n * 16, 0, launch_onorm(r, n, O.npart.as<double>(), s));
+        KL(F_OMISC, 2 * n * 16, 0, launch_oinit(r, n, O.npart.as<double>(), V, O.g.as<double2>(), R, O.beta.as<double>(), s));
+        CKL();
+        double beta = 0;
+        CK(cudaMemcpyAsync(&beta, O.beta.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ctx->prof.harvest();
+        relres = beta / fn;
+        if (!std::isfinite(beta)) { result = HDD_ERR_NONFINITE; ctx->err = "non-finite outer residual"; break; }
+        if (relres <= prm->outer_tol) break;
+        if (total >= prm->outer_maxit) { result = HDD_ERR_NO_CONVERGENCE; ctx->err = "outer_maxit reached"; break; }
+        int kcols = 0;
+        for (int j = 0; j < R; j++) {
+            double2 *vj = V + (long long)j * n, *zj = Zb + (long long)j * n;
+            long long it_tot = 0, it_hits = 0;
+            int it_mx = 0;
+            st = ras_apply(ctx, vj, zj, prm, s, &it_tot, &it_mx, &it_hits, nullptr);
+            if (st != HDD_OK) return st;
+            inner_tot += it_tot; hits += it_hits; inner_mx = std::max(inner_mx, it_mx);
+            const double nv = j + 1;
+            KL(F_OMISC, 2 * n * 16, 0, launch_gstencil(ctx->st, ctx->N, zj, w, nullptr, s));     // w = A z_j
+            KL(F_OCGS, (nv + 1) * n * 16, 8 * nv * n,
+               launch_odots(V, n, j + 1, w, n, O.part.as<double2>(), ldp, s));                 // h1 = V^H w
+            KL(F_OMISC, 0, 0, launch_oreduce(O.part.as<double2>(), G, ldp, j + 1, O.h1.as<double2>(), s));
+            KL(F_OCGS, (nv + 2) * n * 16, 16 * nv * n,
+               launch_oupdate(V, n, j + 1, O.h1.as<double2>(), w, n, O.part.as<double2>(), ldp, nullptr, s));
+            KL(F_OMISC, 0, 0, launch_oreduce(O.part.as<double2>(), G, ldp, j + 1, O.h2.as<double2>(), s));
+            KL(F_OCGS, (nv + 2) * n * 16, 8 * nv * n,
+               launch_oupdate(V, n, j + 1, O.h2.as<double2>(), w, n, nullptr, ldp, O.npart.as<double>(), s));
+            KL(F_OMISC, 0, 0,
+               launch_ogivens(O.H.as<double2>(), R + 1, O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(), j,
+                              O.h1.as<double2>(), O.h2.as<double2>(), O.npart.as<double>(), G, prm->outer_tol * fn,
+                              O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>() + total, fn, s));
+            KL(F_OMISC, 2 * n * 16, 0, launch_oscale(V + (long long)(j + 1) * n, w, O.hn.as<double>(), n, s));
+            CKL();
+            total++;
+            kcols = j + 1;
+            int more = 0;
+            CK(cudaMemcpyAsync(ctx->h_counter, O.flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            ctx->prof.harvest();
+            more = *ctx->h_counter;
+            if (!more || total >= prm->outer_maxit) break;
+        }
+        KL(F_OMISC, 0, 0, launch_otrisolve(O.H.as<double2>(), R + 1, O.g.as<double2>(), kcols, O.y.as<double2>(), s));
+        KL(F_OMISC, (kcols + 2.0) * n * 16, 8.0 * kcols * n, launch_oaxpy(O.y.as<double2>(), kcols, Zb, n, x, n, s));
+        CKL();
+    }
+    CK(cudaStreamSynchronize(s));
+    ctx->prof.harvest();
+    auto t1 = std::chrono::steady_clock::now();
+    ctx->hist.resize(total);
+    if (total) CK(cudaMemcpy(ctx->hist.data(), O.hist.p, total * sizeof(double), cudaMemcpyDeviceToHost));
+    S.outer_its = total;
+    S.status = result;
+    S.rel_res_true = relres;
+    S.inner_its_total = inner_tot;
+    S.inner_its_avg = total ? (double)inner_tot / ((double)total * ctx->subs.size()) : 0.0;
+    S.inner_its_max = inner_mx;
+    S.inner_maxit_hits = hits;
+    S.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    S.n_history = total;
+    S.res_history = ctx->hist.data();
+    return result;
+}
+
+hdd_status hdd_profile(hdd_ctx *ctx, int enable) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    ctx->prof.harvest();
+    ctx->prof.reset();
+    ctx->prof.on = enable != 0;
+    return HDD_OK;
+}
+
+int hdd_profile_count(const hdd_ctx *ctx) { return ctx ? (int)NFAM : 0; }
+
+hdd_status hdd_profile_get(hdd_ctx *ctx, int i, hdd_kernel_stat *out) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (i < 0 || i >= NFAM || !out) FAIL(HDD_ERR_INVALID_ARG, "bad profile index");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    ctx->prof.harvest();
+    std::memset(out, 0, sizeof(*out));
+    std::snprintf(out->name, sizeof(out->name), "%s", kFamName[i]);
+    out->launches = ctx->prof.cnt[i];
+    out->ms = ctx->prof.ms[i];
+    out->bytes = ctx->prof.bytes[i];
+    out->flops = ctx->prof.flops[i];
+    out->bound = kFamBound[i];
+    return HDD_OK;
+}
+
+long long hdd_launch_count(const hdd_ctx *ctx) { return ctx ? ctx->prof.launches : 0; }
+
+hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void *out_dev, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (op < 0 || op > 6 || (prec != 64 && prec != 128) || !in_dev || !out_dev || in_dev == out_dev ||
+        !aligned16(in_dev) || !aligned16(out_dev))
+        FAIL(HDD_ERR_INVALID_ARG, "bad local_op arguments");
+    if ((op == 3 || op == 4) && !ctx->E.ready) FAIL(HDD_ERR_STATE, "hdd_setup_deflation first");
+    if (op == 6 && !ctx->Aex.ready) FAIL(HDD_ERR_STATE, "hdd_setup_exact first");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long ld = ctx->ld, ldc = ctx->ldc;
+    const double2 *in = (const double2 *)in_dev;
+    double2 *out = (double2 *)out_dev;
+    if (op == 3) { band_solve(ctx, ctx->E, in, out, false, nullptr, s); CKL(); CK(cudaStreamSynchronize(s)); return HDD_OK; }
+    if (op == 6) { band_solve(ctx, ctx->Aex, in, out, true, nullptr, s); CKL(); CK(cudaStreamSynchronize(s)); return HDD_OK; }
+    auto run = [&](auto tag) -> hdd_status {
+        using R = decltype(tag);
+        LocalArgs<R> a = local_args<R>(ctx);
+        size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(c2<R>));
+        if (smem > 48 * 1024) CK(set_local_smem_limits<R>(smem));
+        CK(ctx->tmp_a.ensure(std::max(ld, ldc) * sizeof(c2<R>)));
+        CK(ctx->tmp_b.ensure(std::max(ld, ldc) * sizeof(c2<R>)));
+        CK(ctx->tmp_c.ensure((std::max(ld, ldc) + 64) * sizeof(double2)));
+        c2<R> *ta = ctx->tmp_a.as<c2<R>>(), *tb = ctx->tmp_b.as<c2<R>>();
+        const int is_d = sizeof(R) == 8;
+        switch (op) {
+            case 0:
+                launch_cast(ld, in, 1, ta, is_d, s);
+                launch_local_A<R>(a, ta, tb, nullptr, nullptr, s);
+                launch_cast(ld, tb, is_d, out, 1, s);
+                break;
+            case 1:
+                launch_z<R>(a, in, nullptr, tb, nullptr, s);
+                launch_cast(ld, tb, is_d, out, 1, s);
+                break;
+            case 2:
+                launch_cast(ld, in, 1, ta, is_d, s);
+                launch_zt<R>(a, ta, out, 0, nullptr, s);
+                break;
+            case 4: {                                   // P A v = A (v - Z E⁻¹ Zᵀ A v)
+                double2 *y = ctx->tmp_c.as<double2>();      // ld + 64 >= 2·ldc + 32 entries
+                double2 *s2 = y + ldc + 32;
+                launch_cast(ld, in, 1, ta, is_d, s);
+                launch_zt<R>(a, ta, y, 1, nullptr, s);
+                band_solve(ctx, ctx->E, y, s2, false, nullptr, s);
+                launch_prolong_stencil<R>(a, 0, ta, s2, tb, nullptr, 0, ta /*unused: nv = 0*/, nullptr, s);
+                launch_cast(ld, tb, is_d, out, 1, s);
+                break;
+            }
+            case 5:
+                launch_restrict<R>(a, in, ctx->nglob, tb, nullptr, s);
+                launch_cast(ld, tb, is_d, out, 1, s);
+                break;
+        }
+        CKL();
+        CK(cudaStreamSynchronize(s));
+        return HDD_OK;
+    };
+    return prec == 64 ? run(float{}) : run(double{});
+}
+
+}  // extern "C"

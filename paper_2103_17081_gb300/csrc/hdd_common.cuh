@@ -1,0 +1,191 @@
+// hdd_common.cuh — shared definitions of the GB300 solver library (device + host launchers).
+//
+// Layout in HBM
+//  * global vectors: complex128, (N-1)² interior nodes, x fastest;
+//  * packed local vectors: every (subdomain, right-hand side) "task" owns a contiguous slab of
+//    nx·ny fine entries (box, x fastest) at Task::foff and mx·my coarse entries at Task::coff;
+//  * Krylov bases: basis vector k of every task at base + k·ld (ld = total packed length), so
+//    one kernel sweeps the same vector of all tasks with coalesced accesses;
+//  * FP64 banded factors (one per distinct box shape): L stored by column (kl multipliers per
+//    column), U stored by column above the diagonal with its true extent, reciprocal pivots.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hdd {
+
+// ------------------------------------------------------------------------------------------
+// complex helpers (storage as float2 / double2)
+// ------------------------------------------------------------------------------------------
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+template <typename R> using c2 = typename C2<R>::T;
+
+template <typename R> __host__ __device__ __forceinline__ c2<R> mk(R re, R im) {
+    c2<R> z; z.x = re; z.y = im; return z;
+}
+template <typename R> __device__ __forceinline__ c2<R> cadd(c2<R> a, c2<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ c2<R> csub(c2<R> a, c2<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R> __device__ __forceinline__ c2<R> cscale(R s, c2<R> a) { return mk<R>(s * a.x, s * a.y); }
+template <typename R> __device__ __forceinline__ c2<R> cmul(c2<R> a, c2<R> b) {
+    return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += conj(a) * b
+template <typename R> __device__ __forceinline__ void cdotc_acc(c2<R> &acc, c2<R> a, c2<R> b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc -= h * v
+template <typename R> __device__ __forceinline__ void caxpy_neg(c2<R> &acc, c2<R> h, c2<R> v) {
+    acc.x = fma(-h.x, v.x, acc.x); acc.x = fma(h.y, v.y, acc.x);
+    acc.y = fma(-h.x, v.y, acc.y); acc.y = fma(-h.y, v.x, acc.y);
+}
+// acc += h * v
+template <typename R> __device__ __forceinline__ void caxpy(c2<R> &acc, c2<R> h, c2<R> v) {
+    acc.x = fma(h.x, v.x, acc.x); acc.x = fma(-h.y, v.y, acc.x);
+    acc.y = fma(h.x, v.y, acc.y); acc.y = fma(h.y, v.x, acc.y);
+}
+
+template <typename R> __device__ __forceinline__ R shfl_xor(R v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+
+// ------------------------------------------------------------------------------------------
+// problem description shared with the kernels
+// ------------------------------------------------------------------------------------------
+struct Stencil {           // P1 operator K - k²M on the uniform mesh (Eq. 2), 7-point form
+    double c0;             // centre
+    double c1;             // E, W, N, S
+    double c2;             // the two corners joined by the cell diagonals
+    int diag;              // 0: diagonal pair (+1,+1)/(-1,-1); 1: (+1,-1)/(-1,+1)
+};
+
+struct Task {              // one local solve: subdomain `sub` for right-hand side `rhs`
+    int nx, ny, mx, my;    // box and coarse sizes
+    int ix0, iy0;          // global node (1-based) of the box's local (0,0)
+    int ox0, ox1, oy0, oy1;// owned nodes (global, inclusive)
+    int shape;             // index of the shared factor of E (and of A_j)
+    int sub, rhs;
+    int tile0, ntiles;     // fine tiles of this task
+    long long foff, coff;  // packed fine / coarse offsets
+};
+
+struct Tile {              // a block of fine rows (fine tiles) or coarse rows (coarse tiles)
+    int task, r0, nr;
+};
+
+struct BandFactor {        // FP64 banded LU with partial pivoting, solve-friendly layout
+    int m, kl, ku;         // order and bandwidths of the unfactored matrix
+    long long l_off;       // Lcol: m x kl doubles, L(j+1+q, j) at l_off + j·kl + q
+    long long u_off;       // Ucol: m x (kl+ku), U(c-1-q, c) at u_off + c·(kl+ku) + q
+    long long p_off;       // piv / uext / rinv: m entries each
+};
+
+constexpr int MAX_RESTART = 64;       // inner GMRES restart bound (Hessenberg in registers/smem)
+constexpr int FINE_ROWS = 8;          // fine rows per fine tile
+constexpr int COARSE_ROWS = 4;        // coarse rows per coarse tile
+constexpr int LOCAL_THREADS = 256;    // threads per tile CTA
+
+// per-task inner GMRES state (precision R)
+template <typename R> struct InnerState {
+    c2<R> *H;        // [task][(restart+1) * restart], column i holds rows 0..i+1
+    R *cs;           // [task][restart]
+    c2<R> *sn;       // [task][restart]
+    c2<R> *g;        // [task][restart+1]
+    R *ref;          // ||P f̃||
+    int *its;        // Arnoldi steps so far (whole solve)
+    int *kcols;      // columns in the current cycle
+    int *conv;       // 1 once converged / finished
+    int *restart;    // 1 if the task needs another cycle
+};
+
+// ------------------------------------------------------------------------------------------
+// host-side launchers (defined in the kernel translation units)
+// ------------------------------------------------------------------------------------------
+template <typename R> struct LocalArgs {
+    const Task *tasks; const Tile *ftiles; const Tile *ctiles;
+    int ntasks, nftiles, nctiles;
+    Stencil st;
+    long long ld;      // packed fine length (all tasks): stride between basis vectors
+    long long ldc;     // packed coarse length
+    int max_nx;        // largest box width (shared-memory sizing), <= 256
+    int gw;            // global grid width N-1
+};
+
+// local (batched over tasks), R = float or double
+template <typename R> void launch_restrict(const LocalArgs<R> &a, const double2 *glob, long long nglob,
+                                           c2<R> *out, const int *flag, cudaStream_t s);
+template <typename R> void launch_scatter(const LocalArgs<R> &a, const c2<R> *x, double2 *glob,
+                                          long long nglob, cudaStream_t s);
+template <typename R> void launch_local_A(const LocalArgs<R> &a, const c2<R> *in, c2<R> *out,
+                                          const c2<R> *f, const int *flag, cudaStream_t s);
+template <typename R> void launch_zt(const LocalArgs<R> &a, const c2<R> *in, double2 *y, int apply_A,
+                                     const int *flag, cudaStream_t s);
+template <typename R> void launch_z(const LocalArgs<R> &a, const double2 *sc, const c2<R> *add,
+                                    c2<R> *out, const int *flag, cudaStream_t s);
+template <typename R> void launch_prolong_stencil(const LocalArgs<R> &a, int mode, const c2<R> *in,
+                                                  const double2 *sc, c2<R> *out, const c2<R> *V,
+                                                  int nv, c2<R> *part, const int *flag,
+                                                  cudaStream_t s);
+template <typename R> void launch_cgs_update(const LocalArgs<R> &a, int pass, c2<R> *w, const c2<R> *V,
+                                             int nv, const c2<R> *part_in, c2<R> *part_out,
+                                             const int *flag, cudaStream_t s);
+template <typename R> void launch_givens_normalize(const LocalArgs<R> &a, const InnerState<R> &S,
+                                                   int restart, int i, c2<R> *w, const c2<R> *p1,
+                                                   const c2<R> *p2, const c2<R> *p3,
+                                                   const int *act_in, int *act_out, int *counter,
+                                                   R tol, int maxit, cudaStream_t s);
+template <typename R> void launch_init_cycle(const LocalArgs<R> &a, const InnerState<R> &S, int restart,
+                                             c2<R> *v0, const c2<R> *p3, const int *flag,
+                                             int *act_out, int *counter, R tol, int maxit,
+                                             int set_ref, cudaStream_t s);
+template <typename R> void launch_update_u(const LocalArgs<R> &a, const InnerState<R> &S, int restart,
+                                           c2<R> *u, const c2<R> *V, const int *flag, int *rs_out,
+                                           int *counter, int maxit, cudaStream_t s);
+template <typename R> cudaError_t set_local_smem_limits(size_t bytes);
+template <typename R> void launch_coarse_combine(const LocalArgs<R> &a, const InnerState<R> &S,
+                                                 int restart, const double2 *sbuf, double2 *sc,
+                                                 cudaStream_t s);
+size_t local_max_dynamic_smem(int max_nx, int bytes_per_c);
+void launch_cast(long long n, const void *in, int in_double, void *out, int out_double, cudaStream_t s);
+constexpr int LOCAL_LDP = MAX_RESTART + 2;   // partial-sum slots per fine tile
+
+// coarse / banded FP64
+void launch_assemble_E(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s);
+void launch_assemble_Aloc(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s);
+void launch_band_lu(int nmat, const int *m, const int *kl, const int *ku, double *const *ab,
+                    int *const *piv, int *info, cudaStream_t s);
+void launch_band_convert(int m, int kl, int ku, const double *ab, const int *piv, double *Lcol,
+                         double *Ucol, int *uext, double *rinv, int *pivout, cudaStream_t s);
+void launch_band_solve(const Task *tasks, int ntasks, const BandFactor *shapes, const double *Lall,
+                       const double *Uall, const int *Iall, const double *Rall, const double2 *in,
+                       double2 *out, int use_fine_offsets, const int *flag, int max_m,
+                       int kmax_entries, cudaStream_t s);
+cudaError_t set_band_solve_smem(int max_m, int kmax_entries);
+
+// global FP64 (outer FGMRES)
+int outer_grid(long long n);
+void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f,
+                     cudaStream_t s);
+void launch_build_rhs(int N, double h, int diag, int npts, const double *pts, int nb,
+                      const double *bumps, double2 *f, cudaStream_t s);
+void launch_odots(const double2 *V, long long ld, int nv, const double2 *w, long long n,
+                  double2 *part, int ldp, cudaStream_t s);
+void launch_oupdate(const double2 *V, long long ld, int nv, const double2 *h, double2 *w, long long n,
+                    double2 *part_dots, int ldp, double *part_norm, cudaStream_t s);
+void launch_onorm(const double2 *x, long long n, double *part, cudaStream_t s);
+void launch_oreduce(const double2 *part, int nparts, int ldp, int nv, double2 *out, cudaStream_t s);
+void launch_ogivens(double2 *H, long long ldh, double *cs, double2 *sn, double2 *g, int j,
+                    const double2 *h1, const double2 *h2, const double *npart, int nparts,
+                    double tol_abs, double *hn_out, int *flag, double *hist, double fnorm,
+                    cudaStream_t s);
+void launch_oscale(double2 *out, const double2 *w, const double *hn, long long n, cudaStream_t s);
+void launch_otrisolve(const double2 *H, long long ldh, const double2 *g, int k, double2 *y,
+                      cudaStream_t s);
+void launch_oaxpy(const double2 *y, int k, const double2 *Zb, long long ld, double2 *x, long long n,
+                  cudaStream_t s);
+void launch_oinit(const double2 *r, long long n, const double *npart, double2 *v0, double2 *g, int R,
+                  double *beta_out, cudaStream_t s);
+cudaError_t set_outer_smem_limits(size_t bytes);
+
+}  // namespace hdd

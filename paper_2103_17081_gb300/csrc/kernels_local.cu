@@ -1,0 +1,728 @@
+// kernels_local.cu — batched kernels of the inner deflated GMRES (§2 Eq. 4–5, §3), one CTA per
+// tile of one task, every task of every subdomain (and right-hand side) in one launch.
+//
+// Fine tiles cover FINE_ROWS box rows of one task; coarse tiles cover COARSE_ROWS coarse rows.
+// Reductions are two-stage and deterministic: each tile writes its partial sums to a slot of
+// its own, and every consumer adds the partials of a task in tile order.
+#include "hdd_common.cuh"
+
+namespace hdd {
+
+constexpr int LDP = MAX_RESTART + 2;     // partial-sum slots per tile
+constexpr int EPT = 8;                   // fine elements per thread (FINE_ROWS*max_nx <= 2048)
+constexpr int NWARP = LOCAL_THREADS / 32;
+
+// 1D Bézier deflation weight (Eq. 5 factor): fine node f, coarse node c (0-based); column c is
+// centred on fine node 2c+1 with weights (1,4,6,4,1)/8 on f = 2c-1 .. 2c+3.
+__device__ __forceinline__ float zw_f(int t) {
+    return t == 0 || t == 4 ? 0.125f : (t == 2 ? 0.75f : 0.5f);
+}
+template <typename R> __device__ __forceinline__ R zw(int t) { return (R)zw_f(t); }
+
+template <typename R> __device__ __forceinline__ c2<R> load_c(const c2<R> *p) { return *p; }
+
+// w = A u at local (x, y) from a shared-memory row buffer u[rows][nx] whose row 0 is box row
+// `ybase`; rows outside [0, ny) and columns outside [0, nx) are zero (Dirichlet around the box).
+template <typename R>
+__device__ __forceinline__ c2<R> stencil_smem(const Stencil &st, const c2<R> *u, int ybase,
+                                              int nrows, int nx, int ny, int x, int y) {
+    const R c0 = (R)st.c0, c1 = (R)st.c1, c2v = (R)st.c2;
+    auto U = [&](int xx, int yy) -> c2<R> {
+        if (xx < 0 || xx >= nx || yy < 0 || yy >= ny) return mk<R>(0, 0);
+        int r = yy - ybase;
+        if (r < 0 || r >= nrows) return mk<R>(0, 0);
+        return u[r * nx + xx];
+    };
+    c2<R> cc = U(x, y);
+    c2<R> e = U(x + 1, y), wv = U(x - 1, y), n = U(x, y + 1), s = U(x, y - 1);
+    c2<R> d1, d2;
+    if (st.diag == 0) { d1 = U(x + 1, y + 1); d2 = U(x - 1, y - 1); }
+    else { d1 = U(x + 1, y - 1); d2 = U(x - 1, y + 1); }
+    c2<R> r;
+    r.x = c0 * cc.x + c1 * (((e.x + wv.x) + n.x) + s.x) + c2v * (d1.x + d2.x);
+    r.y = c0 * cc.y + c1 * (((e.y + wv.y) + n.y) + s.y) + c2v * (d1.y + d2.y);
+    return r;
+}
+
+// Block reduction of `nv` complex partial sums held by every thread (acc computed per l by
+// the caller through `get`), written to out[0..nv).
+template <typename R, typename F>
+__device__ void block_reduce_many(int nv, F get, c2<R> *red /*[NWARP][LDP]*/, c2<R> *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = 0; l < nv; l++) {
+        c2<R> a = get(l);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) { a.x += shfl_xor(a.x, o); a.y += shfl_xor(a.y, o); }
+        if (lane == 0) red[warp * LDP + l] = a;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < nv; l += blockDim.x) {
+        c2<R> s = mk<R>(0, 0);
+        for (int q = 0; q < NWARP; q++) s = cadd<R>(s, red[q * LDP + l]);
+        out[l] = s;
+    }
+}
+
+template <typename R> __device__ R block_sum(R v, R *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    R s = 0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < NWARP; q++) s += red[q];
+    return s;
+}
+
+// ------------------------------------------------------------------------------------------
+// restriction f̃_j = R_j v (Eq. 3), global complex128 → packed local precision R
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_restrict(LocalArgs<R> a, int gw, long long nglob, const double2 *__restrict__ glob,
+           c2<R> *__restrict__ out, const int *__restrict__ flag) {
+    const Tile tl = a.ftiles[blockIdx.x];
+    if (flag && !flag[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    const int cnt = tl.nr * T.nx;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int y = tl.r0 + e / T.nx, x = e % T.nx;
+        long long gi = (long long)(T.ix0 + x - 1) + (long long)(T.iy0 + y - 1) * gw +
+                       (long long)T.rhs * nglob;
+        double2 v = glob[gi];
+        out[T.foff + (long long)y * T.nx + x] = mk<R>((R)v.x, (R)v.y);
+    }
+}
+
+// z = Σ_j R_jᵀ D_j x_j: every owned node is written by exactly one task (no atomics).
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_scatter(LocalArgs<R> a, int gw, long long nglob, const c2<R> *__restrict__ x,
+          double2 *__restrict__ glob) {
+    const Tile tl = a.ftiles[blockIdx.x];
+    const Task T = a.tasks[tl.task];
+    const int cnt = tl.nr * T.nx;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int y = tl.r0 + e / T.nx, xx = e % T.nx;
+        int gx = T.ix0 + xx, gy = T.iy0 + y;
+        if (gx < T.ox0 || gx > T.ox1 || gy < T.oy0 || gy > T.oy1) continue;
+        c2<R> v = x[T.foff + (long long)y * T.nx + xx];
+        glob[(long long)(gx - 1) + (long long)(gy - 1) * gw + (long long)T.rhs * nglob] =
+            make_double2((double)v.x, (double)v.y);
+    }
+}
+
+// out = A_j in   or   out = f - A_j in   (fine tiles, neighbours read through L1)
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_local_A(LocalArgs<R> a, const c2<R> *__restrict__ in, c2<R> *__restrict__ out,
+          const c2<R> *__restrict__ f, const int *__restrict__ flag) {
+    extern __shared__ unsigned char smem_raw[];
+    c2<R> *u = reinterpret_cast<c2<R> *>(smem_raw);
+    const Tile tl = a.ftiles[blockIdx.x];
+    if (flag && !flag[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    const int y0 = tl.r0 - 1, nrows = tl.nr + 2;
+    for (int e = threadIdx.x; e < nrows * T.nx; e += blockDim.x) {
+        int yy = y0 + e / T.nx, xx = e % T.nx;
+        u[e] = (yy >= 0 && yy < T.ny) ? in[T.foff + (long long)yy * T.nx + xx] : mk<R>(0, 0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tl.nr * T.nx; e += blockDim.x) {
+        int y = tl.r0 + e / T.nx, x = e % T.nx;
+        c2<R> w = stencil_smem<R>(a.st, u, y0, nrows, T.nx, T.ny, x, y);
+        long long gi = T.foff + (long long)y * T.nx + x;
+        if (f) w = csub<R>(f[gi], w);
+        out[gi] = w;
+    }
+}
+
+// y = Z_jᵀ t (coarse tiles), with t = A_j in (apply_A) or t = in; y in FP64.
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_zt(LocalArgs<R> a, const c2<R> *__restrict__ in, double2 *__restrict__ yout, int apply_A,
+     const int *__restrict__ flag) {
+    extern __shared__ unsigned char smem_raw[];
+    const Tile tl = a.ctiles[blockIdx.x];
+    if (flag && !flag[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    const int nx = T.nx, ny = T.ny, mx = T.mx;
+    // fine rows feeding coarse rows [r0, r0+nr): 2c-1 .. 2c+3
+    const int F0 = 2 * tl.r0 - 1, F1 = 2 * (tl.r0 + tl.nr - 1) + 3;
+    const int nF = F1 - F0 + 1;                    // 2*nr + 3
+    const int V0 = F0 - 1, nV = nF + 2;            // input rows for the stencil
+    c2<R> *vin = reinterpret_cast<c2<R> *>(smem_raw);
+    c2<R> *t = vin + (apply_A ? nV * nx : 0);
+    c2<R> *sx = t + nF * nx;
+    if (apply_A) {
+        for (int e = threadIdx.x; e < nV * nx; e += blockDim.x) {
+            int yy = V0 + e / nx, xx = e % nx;
+            vin[e] = (yy >= 0 && yy < ny) ? in[T.foff + (long long)yy * nx + xx] : mk<R>(0, 0);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nF * nx; e += blockDim.x) {
+            int yy = F0 + e / nx, xx = e % nx;
+            t[e] = (yy >= 0 && yy < ny) ? stencil_smem<R>(a.st, vin, V0, nV, nx, ny, xx, yy)
+                                        : mk<R>(0, 0);
+        }
+    } else {
+        for (int e = threadIdx.x; e < nF * nx; e += blockDim.x) {
+            int yy = F0 + e / nx, xx = e % nx;
+            t[e] = (yy >= 0 && yy < ny) ? in[T.foff + (long long)yy * nx + xx] : mk<R>(0, 0);
+        }
+    }
+    __syncthreads();
+    // x-direction: sx[f][cx] = Σ_a w_a t[f][2cx-1+a]
+    for (int e = threadIdx.x; e < nF * mx; e += blockDim.x) {
+        int fr = e / mx, cx = e % mx;
+        c2<R> s = mk<R>(0, 0);
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+            int fx = 2 * cx - 1 + q;
+            if (fx >= 0 && fx < nx) {
+                c2<R> v = t[fr * nx + fx];
+                s.x = fma(zw<R>(q), v.x, s.x);
+                s.y = fma(zw<R>(q), v.y, s.y);
+            }
+        }
+        sx[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tl.nr * mx; e += blockDim.x) {
+        int cy = tl.r0 + e / mx, cx = e % mx;
+        c2<R> s = mk<R>(0, 0);
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+            int fy = 2 * cy - 1 + q;
+            if (fy >= 0 && fy < ny) {
+                c2<R> v = sx[(fy - F0) * mx + cx];
+                s.x = fma(zw<R>(q), v.x, s.x);
+                s.y = fma(zw<R>(q), v.y, s.y);
+            }
+        }
+        yout[T.coff + (long long)cy * mx + cx] = make_double2((double)s.x, (double)s.y);
+    }
+}
+
+// Z s for box rows [F0, F0+nF): s (FP64 coarse) → px (x-interpolated coarse rows) → zs.
+// Shared buffers: sc[ncy*mx], px[ncy*nx].  Returns via zs[nF*nx].
+template <typename R>
+__device__ void prolong_rows(const Task &T, const double2 *__restrict__ s, int F0, int nF,
+                             c2<R> *sc, c2<R> *px, c2<R> *zs) {
+    const int nx = T.nx, ny = T.ny, mx = T.mx, my = T.my;
+    // coarse rows cy with 2cy-1 <= f <= 2cy+3 for some f in [F0, F0+nF)
+    int C0 = (F0 - 3) >= 0 ? (F0 - 3 + 1) / 2 : -((3 - F0) / 2);
+    int C1 = (F0 + nF - 1 + 1) / 2;
+    if (C0 < 0) C0 = 0;
+    if (C1 > my - 1) C1 = my - 1;
+    const int ncy = C1 - C0 + 1;
+    for (int e = threadIdx.x; e < ncy * mx; e += blockDim.x) {
+        double2 v = s[T.coff + (long long)(C0 + e / mx) * mx + (e % mx)];
+        sc[e] = mk<R>((R)v.x, (R)v.y);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ncy * nx; e += blockDim.x) {
+        int r = e / nx, fx = e % nx;
+        c2<R> acc = mk<R>(0, 0);
+        int cx0 = (fx - 3) >= 0 ? (fx - 3 + 1) / 2 : 0;
+        int cx1 = (fx + 1) / 2;
+        if (cx1 > mx - 1) cx1 = mx - 1;
+        for (int cx = cx0; cx <= cx1; cx++) {
+            R wgt = zw<R>(fx - 2 * cx + 1);
+            c2<R> v = sc[r * mx + cx];
+            acc.x = fma(wgt, v.x, acc.x);
+            acc.y = fma(wgt, v.y, acc.y);
+        }
+        px[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nF * nx; e += blockDim.x) {
+        int fy = F0 + e / nx, fx = e % nx;
+        c2<R> acc = mk<R>(0, 0);
+        if (fy >= 0 && fy < ny) {
+            int cy0 = (fy - 3) >= 0 ? (fy - 3 + 1) / 2 : 0;
+            int cy1 = (fy + 1) / 2;
+            if (cy1 > my - 1) cy1 = my - 1;
+            for (int cy = cy0; cy <= cy1; cy++) {
+                R wgt = zw<R>(fy - 2 * cy + 1);
+                c2<R> v = px[(cy - C0) * nx + fx];
+                acc.x = fma(wgt, v.x, acc.x);
+                acc.y = fma(wgt, v.y, acc.y);
+            }
+        }
+        zs[e] = acc;
+    }
+    __syncthreads();
+}
+
+__host__ __device__ inline int prolong_max_cy(int nrows_fine) { return nrows_fine / 2 + 4; }
+
+// out = add + Z s on fine tiles (add may be null)
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_z(LocalArgs<R> a, const double2 *__restrict__ s, const c2<R> *__restrict__ add,
+    c2<R> *__restrict__ out, const int *__restrict__ flag) {
+    extern __shared__ unsigned char smem_raw[];
+    const Tile tl = a.ftiles[blockIdx.x];
+    if (flag && !flag[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    const int maxc = prolong_max_cy(tl.nr);
+    c2<R> *sc = reinterpret_cast<c2<R> *>(smem_raw);
+    c2<R> *px = sc + maxc * T.mx;
+    c2<R> *zs = px + maxc * T.nx;
+    prolong_rows<R>(T, s, tl.r0, tl.nr, sc, px, zs);
+    for (int e = threadIdx.x; e < tl.nr * T.nx; e += blockDim.x) {
+        long long gi = T.foff + (long long)tl.r0 * T.nx + e;
+        c2<R> v = zs[e];
+        if (add) v = cadd<R>(add[gi], v);
+        out[gi] = v;
+    }
+}
+
+// Arnoldi (mode 0): out = A (in - Z s), partial dots V_l^H out (l < nv);
+// residual (mode 1): out = in - A (Z s), partial ||out||².
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_prolong_stencil(LocalArgs<R> a, int mode, const c2<R> *__restrict__ in,
+                  const double2 *__restrict__ s, c2<R> *__restrict__ out,
+                  const c2<R> *__restrict__ V, int nv, c2<R> *__restrict__ part,
+                  const int *__restrict__ flag) {
+    extern __shared__ unsigned char smem_raw[];
+    const Tile tl = a.ftiles[blockIdx.x];
+    if (flag && !flag[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    const int nx = T.nx, ny = T.ny;
+    const int F0 = tl.r0 - 1, nF = tl.nr + 2;
+    const int maxc = prolong_max_cy(nF);
+    c2<R> *sc = reinterpret_cast<c2<R> *>(smem_raw);
+    c2<R> *px = sc + maxc * T.mx;
+    c2<R> *u = px + maxc * nx;                     // nF*nx
+    c2<R> *red = u + nF * nx;                      // NWARP*LDP
+    prolong_rows<R>(T, s, F0, nF, sc, px, u);      // u = Z s on rows F0..F0+nF-1
+    if (mode == 0) {
+        for (int e = threadIdx.x; e < nF * nx; e += blockDim.x) {
+            int yy = F0 + e / nx;
+            if (yy >= 0 && yy < ny) u[e] = csub<R>(in[T.foff + (long long)yy * nx + e % nx], u[e]);
+        }
+        __syncthreads();
+    }
+    c2<R> wv[EPT];
+    const int cnt = tl.nr * nx;
+    R nrm = 0;
+#pragma unroll
+    for (int k = 0; k < EPT; k++) {
+        int e = threadIdx.x + k * LOCAL_THREADS;
+        wv[k] = mk<R>(0, 0);
+        if (e < cnt) {
+            int y = tl.r0 + e / nx, x = e % nx;
+            c2<R> w = stencil_smem<R>(a.st, u, F0, nF, nx, ny, x, y);
+            long long gi = T.foff + (long long)y * nx + x;
+            if (mode == 1) w = csub<R>(in[gi], w);
+            out[gi] = w;
+            wv[k] = w;
+            nrm = fma(w.x, w.x, fma(w.y, w.y, nrm));
+        }
+    }
+    c2<R> *mypart = part + (long long)blockIdx.x * LDP;
+    if (mode == 0) {
+        const long long base = T.foff + (long long)tl.r0 * nx;
+        block_reduce_many<R>(nv, [&](int l) {
+            c2<R> acc = mk<R>(0, 0);
+            const c2<R> *vl = V + (long long)l * a.ld + base;
+#pragma unroll
+            for (int k = 0; k < EPT; k++) {
+                int e = threadIdx.x + k * LOCAL_THREADS;
+                if (e < cnt) cdotc_acc<R>(acc, vl[e], wv[k]);
+            }
+            return acc;
+        }, red, mypart);
+    } else {
+        R *redr = reinterpret_cast<R *>(red);
+        R tot = block_sum<R>(nrm, redr);
+        if (threadIdx.x == 0) mypart[LDP - 1] = mk<R>(tot, 0);
+    }
+}
+
+// Sum over the task's tiles of partial slot l (fixed order → deterministic).
+template <typename R>
+__device__ __forceinline__ c2<R> task_sum(const c2<R> *part, const Task &T, int l) {
+    c2<R> s = mk<R>(0, 0);
+    for (int q = 0; q < T.ntiles; q++) s = cadd<R>(s, part[(long long)(T.tile0 + q) * LDP + l]);
+    return s;
+}
+
+// Classical Gram-Schmidt passes 2 and 3 (CGS2): w -= V h (h = task sum of part_in);
+// pass 2 also forms the partial dots V^H w, pass 3 the partial ||w||².
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_cgs_update(LocalArgs<R> a, int pass, c2<R> *__restrict__ w, const c2<R> *__restrict__ V, int nv,
+             const c2<R> *__restrict__ part_in, c2<R> *__restrict__ part_out,
+             const int *__restrict__ flag) {
+    __shared__ c2<R> hv[LDP];
+    __shared__ c2<R> red[NWARP * LDP];
+    const Tile tl = a.ftiles[blockIdx.x];
+    if (flag && !flag[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    for (int l = threadIdx.x; l < nv; l += blockDim.x) hv[l] = task_sum<R>(part_in, T, l);
+    __syncthreads();
+    const int cnt = tl.nr * T.nx;
+    const long long base = T.foff + (long long)tl.r0 * T.nx;
+    c2<R> wv[EPT];
+    R nrm = 0;
+#pragma unroll
+    for (int k = 0; k < EPT; k++) {
+        int e = threadIdx.x + k * LOCAL_THREADS;
+        wv[k] = mk<R>(0, 0);
+        if (e < cnt) {
+            c2<R> x = w[base + e];
+            for (int l = 0; l < nv; l++) caxpy_neg<R>(x, hv[l], V[(long long)l * a.ld + base + e]);
+            w[base + e] = x;
+            wv[k] = x;
+            nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+        }
+    }
+    c2<R> *mypart = part_out + (long long)blockIdx.x * LDP;
+    if (pass == 2) {
+        block_reduce_many<R>(nv, [&](int l) {
+            c2<R> acc = mk<R>(0, 0);
+            const c2<R> *vl = V + (long long)l * a.ld + base;
+#pragma unroll
+            for (int k = 0; k < EPT; k++) {
+                int e = threadIdx.x + k * LOCAL_THREADS;
+                if (e < cnt) cdotc_acc<R>(acc, vl[e], wv[k]);
+            }
+            return acc;
+        }, red, mypart);
+    } else {
+        R tot = block_sum<R>(nrm, reinterpret_cast<R *>(red));
+        if (threadIdx.x == 0) mypart[LDP - 1] = mk<R>(tot, 0);
+    }
+}
+
+// Complex Givens rotation G = [c s; -conj(s) c], c real, with G [a; b] = [r; 0] (the standard
+// complex form, cf. Bindel, Demmel, Kahan & Marques, ACM TOMS 2002), magnitudes by hypot.
+template <typename R>
+__device__ void givens(c2<R> a, c2<R> b, R &c, c2<R> &s, c2<R> &r) {
+    R aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+    if (bb == (R)0) { c = 1; s = mk<R>(0, 0); r = a; return; }
+    if (aa == (R)0) { c = 0; s = mk<R>(b.x / bb, -b.y / bb); r = mk<R>(bb, 0); return; }
+    R t = hypot(aa, bb);
+    c2<R> ph = mk<R>(a.x / aa, a.y / aa);
+    c = aa / t;
+    c2<R> cb = mk<R>(b.x / t, -b.y / t);       // conj(b)/t
+    s = cmul<R>(ph, cb);
+    r = mk<R>(ph.x * t, ph.y * t);
+}
+
+// End of Arnoldi step i: normalise v_{i+1} = w/||w|| (every tile of the task) and, on the
+// task's first tile, rotate the new Hessenberg column, update g and test |g_{i+1}| <= tol·ref.
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_givens_normalize(LocalArgs<R> a, InnerState<R> S, int restart, int i, c2<R> *__restrict__ w,
+                   const c2<R> *__restrict__ p1, const c2<R> *__restrict__ p2,
+                   const c2<R> *__restrict__ p3, const int *__restrict__ act_in,
+                   int *__restrict__ act_out, int *__restrict__ counter, R tol, int maxit) {
+    __shared__ R hn_s;
+    const Tile tl = a.ftiles[blockIdx.x];
+    if (!act_in[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    if (threadIdx.x == 0) {
+        R s = 0;
+        for (int q = 0; q < T.ntiles; q++) s += p3[(long long)(T.tile0 + q) * LDP + LDP - 1].x;
+        hn_s = sqrt(s);
+    }
+    __syncthreads();
+    const R hn = hn_s;
+    if (hn > (R)0) {
+        const R inv = (R)1 / hn;
+        const long long base = T.foff + (long long)tl.r0 * T.nx;
+        for (int e = threadIdx.x; e < tl.nr * T.nx; e += blockDim.x) {
+            c2<R> v = w[base + e];
+            w[base + e] = mk<R>(v.x * inv, v.y * inv);
+        }
+    }
+    if (blockIdx.x != T.tile0 || threadIdx.x != 0) return;
+    const int t = tl.task;
+    c2<R> *H = S.H + (long long)t * (restart + 1) * restart;
+    c2<R> *hc = H + (long long)i * (restart + 1);
+    R *cs = S.cs + (long long)t * restart;
+    c2<R> *sn = S.sn + (long long)t * restart;
+    c2<R> *g = S.g + (long long)t * (restart + 1);
+    for (int l = 0; l <= i; l++) hc[l] = cadd<R>(task_sum<R>(p1, T, l), task_sum<R>(p2, T, l));
+    for (int l = 0; l < i; l++) {
+        c2<R> x = hc[l], y = hc[l + 1];
+        c2<R> sx = sn[l];
+        // [c s; -conj(s) c] [x; y]
+        hc[l] = cadd<R>(cscale<R>(cs[l], x), cmul<R>(sx, y));
+        hc[l + 1] = csub<R>(cscale<R>(cs[l], y), cmul<R>(mk<R>(sx.x, -sx.y), x));
+    }
+    R c; c2<R> s, r;
+    givens<R>(hc[i], mk<R>(hn, 0), c, s, r);
+    cs[i] = c; sn[i] = s;
+    hc[i] = r;
+    hc[i + 1] = mk<R>(0, 0);
+    c2<R> gi = g[i];
+    g[i + 1] = mk<R>(-(s.x * gi.x + s.y * gi.y), -(s.x * gi.y - s.y * gi.x));   // -conj(s) g_i
+    g[i] = cscale<R>(c, gi);
+    const int its = S.its[t] + 1;
+    S.its[t] = its;
+    S.kcols[t] = i + 1;
+    const R res = hypot(g[i + 1].x, g[i + 1].y);
+    const bool conv = res <= tol * S.ref[t] || !(hn > (R)0);
+    const bool stop = conv || its >= maxit || i + 1 >= restart;
+    if (conv || its >= maxit) S.conv[t] = 1;
+    act_out[t] = stop ? 0 : 1;
+    if (!stop) atomicAdd(counter, 1);
+}
+
+// Start of a cycle: r = P(f̃ - A u) was written into v0 by k_prolong_stencil (mode 1) with its
+// partial norms in p3; normalise, set g = [β, 0, ...] and decide whether Arnoldi is needed.
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_init_cycle(LocalArgs<R> a, InnerState<R> S, int restart, c2<R> *__restrict__ v0,
+             const c2<R> *__restrict__ p3, const int *__restrict__ flag, int *__restrict__ act_out,
+             int *__restrict__ counter, R tol, int maxit, int set_ref) {
+    __shared__ R beta_s;
+    const Tile tl = a.ftiles[blockIdx.x];
+    if (!flag[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    if (threadIdx.x == 0) {
+        R s = 0;
+        for (int q = 0; q < T.ntiles; q++) s += p3[(long long)(T.tile0 + q) * LDP + LDP - 1].x;
+        beta_s = sqrt(s);
+    }
+    __syncthreads();
+    const R beta = beta_s;
+    if (beta > (R)0) {
+        const R inv = (R)1 / beta;
+        const long long base = T.foff + (long long)tl.r0 * T.nx;
+        for (int e = threadIdx.x; e < tl.nr * T.nx; e += blockDim.x) {
+            c2<R> v = v0[base + e];
+            v0[base + e] = mk<R>(v.x * inv, v.y * inv);
+        }
+    }
+    if (blockIdx.x != T.tile0 || threadIdx.x != 0) return;
+    const int t = tl.task;
+    if (set_ref) S.ref[t] = beta;
+    c2<R> *g = S.g + (long long)t * (restart + 1);
+    g[0] = mk<R>(beta, 0);
+    for (int l = 1; l <= restart; l++) g[l] = mk<R>(0, 0);
+    S.kcols[t] = 0;
+    const bool done = !(beta > tol * S.ref[t]) || S.its[t] >= maxit;
+    if (done) S.conv[t] = 1;
+    act_out[t] = done ? 0 : 1;
+    if (!done) atomicAdd(counter, 1);
+}
+
+// y = H(0:k,0:k)⁻¹ g(0:k) for task t, by one thread (k <= restart <= 64).
+template <typename R>
+__device__ void solve_small(const InnerState<R> &S, int restart, int t, int k, c2<R> *y) {
+    const c2<R> *H = S.H + (long long)t * (restart + 1) * restart;
+    const c2<R> *g = S.g + (long long)t * (restart + 1);
+    for (int r = k - 1; r >= 0; r--) {
+        c2<R> sacc = g[r];
+        for (int l = r + 1; l < k; l++) sacc = csub<R>(sacc, cmul<R>(H[(long long)l * (restart + 1) + r], y[l]));
+        c2<R> d = H[(long long)r * (restart + 1) + r];
+        R den = d.x * d.x + d.y * d.y;
+        y[r] = mk<R>((sacc.x * d.x + sacc.y * d.y) / den, (sacc.y * d.x - sacc.x * d.y) / den);
+    }
+}
+
+// Coarse part of the completion x = ũ + Z E⁻¹ Zᵀ(f̃ - A ũ): with ũ = ũ₀ + V y, linearity gives
+// E⁻¹ Zᵀ(f̃ - A ũ) = s₀ - Σ_i y_i s_{i+1}, where s₀ = E⁻¹ Zᵀ(f̃ - A ũ₀) was solved at the start of
+// the cycle and s_{i+1} = E⁻¹ Zᵀ A v_i in Arnoldi step i (slots of sbuf, stride ldc).
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_coarse_combine(LocalArgs<R> a, InnerState<R> S, int restart, const double2 *__restrict__ sbuf,
+                 double2 *__restrict__ sc) {
+    __shared__ c2<R> y[MAX_RESTART];
+    const Tile tl = a.ctiles[blockIdx.x];
+    const Task T = a.tasks[tl.task];
+    const int k = S.kcols[tl.task];
+    if (threadIdx.x == 0) solve_small<R>(S, restart, tl.task, k, y);
+    __syncthreads();
+    for (int e = threadIdx.x; e < tl.nr * T.mx; e += blockDim.x) {
+        const long long idx = T.coff + (long long)tl.r0 * T.mx + e;
+        double2 acc = sbuf[idx];
+        for (int l = 0; l < k; l++) {
+            const double2 sv = sbuf[(long long)(l + 1) * a.ldc + idx];
+            const double yr = (double)y[l].x, yi = (double)y[l].y;
+            acc.x -= yr * sv.x - yi * sv.y;
+            acc.y -= yr * sv.y + yi * sv.x;
+        }
+        sc[idx] = acc;
+    }
+}
+
+// u += V y with y = H⁻¹ g (each tile solves the small triangle itself); the first tile of a
+// task flags it for another cycle when it neither converged nor ran out of iterations.
+template <typename R>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_update_u(LocalArgs<R> a, InnerState<R> S, int restart, c2<R> *__restrict__ u,
+           const c2<R> *__restrict__ V, const int *__restrict__ flag, int *__restrict__ rs_out,
+           int *__restrict__ counter, int maxit) {
+    __shared__ c2<R> y[MAX_RESTART];
+    const Tile tl = a.ftiles[blockIdx.x];
+    if (!flag[tl.task]) return;
+    const Task T = a.tasks[tl.task];
+    const int t = tl.task;
+    const int k = S.kcols[t];
+    if (threadIdx.x == 0) {
+        solve_small<R>(S, restart, t, k, y);
+        if (blockIdx.x == T.tile0) {
+            const bool again = !S.conv[t] && S.its[t] < maxit;
+            rs_out[t] = again ? 1 : 0;
+            if (again) atomicAdd(counter, 1);
+        }
+    }
+    __syncthreads();
+    if (k == 0) return;
+    const long long base = T.foff + (long long)tl.r0 * T.nx;
+    for (int e = threadIdx.x; e < tl.nr * T.nx; e += blockDim.x) {
+        c2<R> x = u[base + e];
+        for (int l = 0; l < k; l++) caxpy<R>(x, y[l], V[(long long)l * a.ld + base + e]);
+        u[base + e] = x;
+    }
+}
+
+template <typename RI, typename RO>
+__global__ void k_cast(long long n, const c2<RI> *__restrict__ in, c2<RO> *__restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = mk<RO>((RO)in[i].x, (RO)in[i].y);
+}
+
+// ------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------
+template <typename R> static size_t csz() { return sizeof(c2<R>); }
+
+template <typename R>
+void launch_restrict(const LocalArgs<R> &a, const double2 *glob, long long nglob, c2<R> *out,
+                     const int *flag, cudaStream_t s) {
+    k_restrict<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, a.gw, nglob, glob, out, flag);
+}
+template <typename R>
+void launch_scatter(const LocalArgs<R> &a, const c2<R> *x, double2 *glob, long long nglob,
+                    cudaStream_t s) {
+    k_scatter<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, a.gw, nglob, x, glob);
+}
+template <typename R>
+void launch_local_A(const LocalArgs<R> &a, const c2<R> *in, c2<R> *out, const c2<R> *f,
+                    const int *flag, cudaStream_t s) {
+    size_t sm = (size_t)(FINE_ROWS + 2) * a.max_nx * csz<R>();
+    k_local_A<R><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, in, out, f, flag);
+}
+template <typename R>
+size_t zt_smem(const LocalArgs<R> &a, int apply_A) {
+    int nF = 2 * COARSE_ROWS + 3, nV = nF + 2;
+    return ((size_t)(apply_A ? nV : 0) * a.max_nx + (size_t)nF * a.max_nx + (size_t)nF * (a.max_nx / 2 + 1)) * csz<R>();
+}
+template <typename R>
+void launch_zt(const LocalArgs<R> &a, const c2<R> *in, double2 *y, int apply_A, const int *flag,
+               cudaStream_t s) {
+    k_zt<R><<<a.nctiles, LOCAL_THREADS, zt_smem(a, apply_A), s>>>(a, in, y, apply_A, flag);
+}
+template <typename R>
+void launch_z(const LocalArgs<R> &a, const double2 *sc, const c2<R> *add, c2<R> *out,
+              const int *flag, cudaStream_t s) {
+    int maxc = prolong_max_cy(FINE_ROWS);
+    size_t sm = ((size_t)maxc * (a.max_nx / 2 + 1) + (size_t)maxc * a.max_nx + (size_t)FINE_ROWS * a.max_nx) * csz<R>();
+    k_z<R><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, sc, add, out, flag);
+}
+template <typename R>
+size_t ps_smem(const LocalArgs<R> &a) {
+    int nF = FINE_ROWS + 2, maxc = prolong_max_cy(nF);
+    return ((size_t)maxc * (a.max_nx / 2 + 1) + (size_t)maxc * a.max_nx + (size_t)nF * a.max_nx +
+            (size_t)NWARP * LDP) * csz<R>();
+}
+template <typename R>
+void launch_prolong_stencil(const LocalArgs<R> &a, int mode, const c2<R> *in, const double2 *sc,
+                            c2<R> *out, const c2<R> *V, int nv, c2<R> *part, const int *flag,
+                            cudaStream_t s) {
+    k_prolong_stencil<R><<<a.nftiles, LOCAL_THREADS, ps_smem(a), s>>>(a, mode, in, sc, out, V, nv,
+                                                                       part, flag);
+}
+template <typename R>
+void launch_cgs_update(const LocalArgs<R> &a, int pass, c2<R> *w, const c2<R> *V, int nv,
+                       const c2<R> *part_in, c2<R> *part_out, const int *flag, cudaStream_t s) {
+    k_cgs_update<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, pass, w, V, nv, part_in, part_out, flag);
+}
+template <typename R>
+void launch_givens_normalize(const LocalArgs<R> &a, const InnerState<R> &S, int restart, int i,
+                             c2<R> *w, const c2<R> *p1, const c2<R> *p2, const c2<R> *p3,
+                             const int *act_in, int *act_out, int *counter, R tol, int maxit,
+                             cudaStream_t s) {
+    k_givens_normalize<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, S, restart, i, w, p1, p2, p3, act_in,
+                                                               act_out, counter, tol, maxit);
+}
+template <typename R>
+void launch_init_cycle(const LocalArgs<R> &a, const InnerState<R> &S, int restart, c2<R> *v0,
+                       const c2<R> *p3, const int *flag, int *act_out, int *counter, R tol,
+                       int maxit, int set_ref, cudaStream_t s) {
+    k_init_cycle<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, S, restart, v0, p3, flag, act_out, counter,
+                                                         tol, maxit, set_ref);
+}
+template <typename R>
+void launch_update_u(const LocalArgs<R> &a, const InnerState<R> &S, int restart, c2<R> *u,
+                     const c2<R> *V, const int *flag, int *rs_out, int *counter, int maxit,
+                     cudaStream_t s) {
+    k_update_u<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, S, restart, u, V, flag, rs_out, counter, maxit);
+}
+template <typename R>
+void launch_coarse_combine(const LocalArgs<R> &a, const InnerState<R> &S, int restart,
+                           const double2 *sbuf, double2 *sc, cudaStream_t s) {
+    k_coarse_combine<R><<<a.nctiles, LOCAL_THREADS, 0, s>>>(a, S, restart, sbuf, sc);
+}
+void launch_cast(long long n, const void *in, int in_double, void *out, int out_double,
+                 cudaStream_t s) {
+    int grid = (int)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    if (grid < 1) grid = 1;
+    if (in_double && out_double)
+        k_cast<double, double><<<grid, 256, 0, s>>>(n, (const double2 *)in, (double2 *)out);
+    else if (in_double)
+        k_cast<double, float><<<grid, 256, 0, s>>>(n, (const double2 *)in, (float2 *)out);
+    else if (out_double)
+        k_cast<float, double><<<grid, 256, 0, s>>>(n, (const float2 *)in, (double2 *)out);
+    else
+        k_cast<float, float><<<grid, 256, 0, s>>>(n, (const float2 *)in, (float2 *)out);
+}
+
+size_t local_max_dynamic_smem(int max_nx, int bytes_per_c) {
+    int nF = FINE_ROWS + 2, maxc = prolong_max_cy(nF);
+    size_t ps = ((size_t)maxc * (max_nx / 2 + 1) + (size_t)maxc * max_nx + (size_t)nF * max_nx +
+                 (size_t)NWARP * LDP) * bytes_per_c;
+    int cF = 2 * COARSE_ROWS + 3;
+    size_t zt = ((size_t)(cF + 2) * max_nx + (size_t)cF * max_nx + (size_t)cF * (max_nx / 2 + 1)) * bytes_per_c;
+    return ps > zt ? ps : zt;
+}
+
+template <typename R> cudaError_t set_local_smem_limits(size_t bytes) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_prolong_stencil<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_zt<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_z<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_local_A<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+#define INST(R)                                                                                         \
+    template void launch_restrict<R>(const LocalArgs<R> &, const double2 *, long long, c2<R> *, const int *, cudaStream_t); \
+    template void launch_scatter<R>(const LocalArgs<R> &, const c2<R> *, double2 *, long long, cudaStream_t); \
+    template void launch_local_A<R>(const LocalArgs<R> &, const c2<R> *, c2<R> *, const c2<R> *, const int *, cudaStream_t); \
+    template void launch_zt<R>(const LocalArgs<R> &, const c2<R> *, double2 *, int, const int *, cudaStream_t); \
+    template void launch_z<R>(const LocalArgs<R> &, const double2 *, const c2<R> *, c2<R> *, const int *, cudaStream_t); \
+    template void launch_prolong_stencil<R>(const LocalArgs<R> &, int, const c2<R> *, const double2 *, c2<R> *, const c2<R> *, int, c2<R> *, const int *, cudaStream_t); \
+    template void launch_cgs_update<R>(const LocalArgs<R> &, int, c2<R> *, const c2<R> *, int, const c2<R> *, c2<R> *, const int *, cudaStream_t); \
+    template void launch_givens_normalize<R>(const LocalArgs<R> &, const InnerState<R> &, int, int, c2<R> *, const c2<R> *, const c2<R> *, const c2<R> *, const int *, int *, int *, R, int, cudaStream_t); \
+    template void launch_init_cycle<R>(const LocalArgs<R> &, const InnerState<R> &, int, c2<R> *, const c2<R> *, const int *, int *, int *, R, int, int, cudaStream_t); \
+    template void launch_update_u<R>(const LocalArgs<R> &, const InnerState<R> &, int, c2<R> *, const c2<R> *, const int *, int *, int *, int, cudaStream_t); \
+    template cudaError_t set_local_smem_limits<R>(size_t); \
+    template void launch_coarse_combine<R>(const LocalArgs<R> &, const InnerState<R> &, int, const double2 *, double2 *, cudaStream_t);
+
+INST(float)
+INST(double)
+
+}  // namespace hdd

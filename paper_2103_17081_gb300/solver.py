@@ -1,0 +1,192 @@
+"""Solver: an object wrapper over one hdd_ctx (include/hdd.h) with PyTorch device memory."""
+from __future__ import annotations
+
+import ctypes as C
+
+from ._binding import (AssembleParams, DDParams, HDDError, KernelStat, SolveParams, SolveStats,
+                       lib)
+
+LOCAL_OPS = {"A": 0, "Z": 1, "Zt": 2, "Einv": 3, "PA": 4, "R": 5, "Ainv": 6}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Solver:
+    """One problem on one GPU: assemble → setup_dd → setup_deflation → solve."""
+
+    def __init__(self, device: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2103_17081_gb300 needs a CUDA GPU (no CPU fallback)")
+        self.device = int(device)
+        torch.cuda.set_device(self.device)
+        self._L = lib()
+        h = C.c_void_p()
+        self._check(self._L.hdd_create(C.byref(h), self.device), "hdd_create", ctx=False)
+        self._h = h
+        self.N = None
+        self.k = None
+        self.nsub = 0
+
+    # -- plumbing ------------------------------------------------------------------------------
+    def _check(self, rc: int, where: str, ctx: bool = True):
+        if rc != 0:
+            msg = ""
+            if ctx and getattr(self, "_h", None):
+                msg = self._L.hdd_last_error(self._h).decode()
+            raise HDDError(rc, where, msg)
+
+    def _stream(self, stream=None):
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return C.c_void_p(s.cuda_stream)
+
+    def _vec(self, t, n=None, name="vector"):
+        torch = _torch()
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128
+                and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous complex128 CUDA tensor")
+        if n is not None and t.numel() < n:
+            raise ValueError(f"{name} has {t.numel()} entries, needs {n}")
+        return C.c_void_p(t.data_ptr())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.hdd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up --------------------------------------------------------------------------------
+    def assemble(self, k: float, N: int, diag: int = 0):
+        p = AssembleParams(float(k), int(N), int(diag))
+        self._check(self._L.hdd_assemble(self._h, C.byref(p)), "hdd_assemble")
+        self.N, self.k = int(N), float(k)
+        self.n = (self.N - 1) ** 2
+        return self
+
+    def setup_dd(self, Sx: int, Sy: int, overlap: int, ifx=None, ify=None):
+        ax = (C.c_int * (Sx + 1))(*ifx) if ifx is not None else None
+        ay = (C.c_int * (Sy + 1))(*ify) if ify is not None else None
+        p = DDParams(int(Sx), int(Sy), int(overlap),
+                     C.cast(ax, C.POINTER(C.c_int)) if ax is not None else None,
+                     C.cast(ay, C.POINTER(C.c_int)) if ay is not None else None)
+        self._check(self._L.hdd_setup_dd(self._h, C.byref(p)), "hdd_setup_dd")
+        self.nsub = self._L.hdd_num_subdomains(self._h)
+        return self
+
+    def setup_deflation(self, stream=None):
+        self._check(self._L.hdd_setup_deflation(self._h, self._stream(stream)), "hdd_setup_deflation")
+        return self
+
+    def setup_exact(self, stream=None):
+        self._check(self._L.hdd_setup_exact(self._h, self._stream(stream)), "hdd_setup_exact")
+        return self
+
+    @classmethod
+    def from_workload(cls, w, device: int = 0, deflation: bool = True, exact: bool = False):
+        s = cls(device).assemble(w.k, w.N)
+        s.setup_dd(w.Sx, w.Sy, w.overlap, w.ifx, w.ify)
+        if deflation:
+            s.setup_deflation()
+        if exact:
+            s.setup_exact()
+        return s
+
+    # -- queries -------------------------------------------------------------------------------
+    def subdomain(self, s: int) -> dict:
+        info = (C.c_int * 12)()
+        self._check(self._L.hdd_get_subdomain(self._h, int(s), info), "hdd_get_subdomain")
+        keys = ("ix0", "ix1", "iy0", "iy1", "ox0", "ox1", "oy0", "oy1", "nx", "ny", "mx", "my")
+        return dict(zip(keys, list(info)))
+
+    def offsets(self):
+        fo = (C.c_longlong * (self.nsub + 1))()
+        co = (C.c_longlong * (self.nsub + 1))()
+        self._check(self._L.hdd_get_offsets(self._h, fo, co), "hdd_get_offsets")
+        return list(fo), list(co)
+
+    # -- vectors -------------------------------------------------------------------------------
+    def empty(self, n=None):
+        torch = _torch()
+        return torch.empty(self.n if n is None else n, dtype=torch.complex128, device=f"cuda:{self.device}")
+
+    def build_rhs(self, spec, out=None, stream=None):
+        """Load vector of a workloads.RHSSpec (point sources and Gaussian bumps) on the device."""
+        pts = [v for p in spec.points for v in (p.x, p.y, p.amp)]
+        bps = [v for b in spec.bumps for v in (b.cx, b.cy, b.sigma, b.amp)]
+        f = self.empty() if out is None else out
+        P = (C.c_double * max(1, len(pts)))(*pts)
+        B = (C.c_double * max(1, len(bps)))(*bps)
+        self._check(self._L.hdd_build_rhs(self._h, len(spec.points), P, len(spec.bumps), B,
+                                          self._vec(f, self.n, "f"), self._stream(stream)),
+                    "hdd_build_rhs")
+        return f
+
+    def apply_A(self, x, out=None, stream=None):
+        nrhs = x.numel() // self.n
+        y = self.empty(x.numel()) if out is None else out
+        self._check(self._L.hdd_apply_A(self._h, self._vec(x), self._vec(y), nrhs, self._stream(stream)),
+                    "hdd_apply_A")
+        return y
+
+    # -- solves --------------------------------------------------------------------------------
+    @staticmethod
+    def params(outer_tol=1e-6, outer_restart=5000, outer_maxit=5000, inner_tol=1e-2,
+               inner_restart=30, inner_maxit=1000, inner_prec=64) -> SolveParams:
+        return SolveParams(outer_tol, outer_restart, outer_maxit, inner_tol, inner_restart,
+                           inner_maxit, inner_prec)
+
+    def solve(self, f, out=None, stream=None, raise_on_error=True, **kw):
+        prm = self.params(**kw)
+        x = self.empty() if out is None else out
+        st = SolveStats()
+        rc = self._L.hdd_solve(self._h, self._vec(f, self.n, "f"), self._vec(x, self.n, "x"),
+                               C.byref(prm), C.byref(st), self._stream(stream))
+        stats = {k: getattr(st, k) for k, _ in SolveStats._fields_ if k != "res_history"}
+        stats["res_history"] = [st.res_history[i] for i in range(st.n_history)]
+        stats["status_code"] = rc
+        if rc != 0 and raise_on_error:
+            self._check(rc, "hdd_solve")
+        return x, stats
+
+    def ras_apply(self, v, out=None, stream=None, **kw):
+        prm = self.params(**kw)
+        z = self.empty() if out is None else out
+        its = (C.c_int * max(1, self.nsub))()
+        self._check(self._L.hdd_ras_apply(self._h, self._vec(v, self.n, "v"), self._vec(z, self.n, "z"),
+                                          C.byref(prm), its, self._stream(stream)), "hdd_ras_apply")
+        return z, list(its)[: self.nsub]
+
+    def local_op(self, op: str, x, prec: int = 128, out_len=None, stream=None):
+        fo, co = self.offsets()
+        nout = {"A": fo[-1], "Z": fo[-1], "Zt": co[-1], "Einv": co[-1], "PA": fo[-1], "R": fo[-1],
+                "Ainv": fo[-1]}[op]
+        out = self.empty(nout if out_len is None else out_len)
+        self._check(self._L.hdd_local_op(self._h, LOCAL_OPS[op], int(prec), self._vec(x), self._vec(out),
+                                         self._stream(stream)), "hdd_local_op")
+        return out
+
+    # -- profiling -----------------------------------------------------------------------------
+    def profile(self, enable: bool = True):
+        """Clear the per-family counters and switch CUDA-event timing of every launch on/off."""
+        self._check(self._L.hdd_profile(self._h, 1 if enable else 0), "hdd_profile")
+
+    def profile_stats(self) -> list:
+        out = []
+        for i in range(self._L.hdd_profile_count(self._h)):
+            k = KernelStat()
+            self._check(self._L.hdd_profile_get(self._h, i, C.byref(k)), "hdd_profile_get")
+            out.append({"name": k.name.decode(), "launches": k.launches, "ms": k.ms,
+                        "bytes": k.bytes, "flops": k.flops, "bound": "fp64" if k.bound else "hbm"})
+        return out
+
+    def launch_count(self) -> int:
+        return int(self._L.hdd_launch_count(self._h))
