@@ -306,7 +306,7 @@ class Problem:
         return z, {"inner_its_total": tot.value, "inner_its_max": mx.value,
                    "inner_maxit_hits": hits.value}
 
-    def solve(self, f, outer_tol=1e-6, outer_restart=30, outer_maxit=5000, inner_tol=1e-2,
+    def solve(self, f, outer_tol=1e-6, outer_restart=2000, outer_maxit=2000, inner_tol=1e-2,
               inner_restart=30, inner_maxit=1000, raise_on_error=True):
         f = _c128(f)
         x = np.zeros_like(f)

@@ -823,7 +823,8 @@ int or_solve(const or_problem *p, const double *f_, double *x_, const or_solve_p
              or_stats *st, double *hist, int hcap) {
     const zc *f = (const zc *)f_;
     zc *x = (zc *)x_;
-    const int n = p->n, R = prm->outer_restart;
+    const int n = p->n;
+    const int R = prm->outer_restart < prm->outer_maxit ? prm->outer_restart : prm->outer_maxit;
     memset(st, 0, sizeof(*st));
     for (int t = 0; t < n; t++) x[t] = 0;
     double fn = nrm2(f, n);

@@ -139,7 +139,7 @@ class Solver:
 
     # -- solves --------------------------------------------------------------------------------
     @staticmethod
-    def params(outer_tol=1e-6, outer_restart=5000, outer_maxit=5000, inner_tol=1e-2,
+    def params(outer_tol=1e-6, outer_restart=2000, outer_maxit=2000, inner_tol=1e-2,
                inner_restart=30, inner_maxit=1000, inner_prec=64) -> SolveParams:
         return SolveParams(outer_tol, outer_restart, outer_maxit, inner_tol, inner_restart,
                            inner_maxit, inner_prec)
