@@ -37,14 +37,13 @@ struct SubBox {
     int ix0, ix1, iy0, iy1, ox0, ox1, oy0, oy1, nx, ny, mx, my;
 };
 
-struct FactorSet {            // banded FP64 factors of one matrix per shape
-    DevMem L, U, I, Rr, table;
-    std::vector<BandFactor> h;
-    std::vector<double> fma_col;    // FP64 FMAs of one real column solve, per shape
-    int kmax = 0;                   // most band entries in one column of L or Û
-    int max_m = 0;
+struct FactorSet {            // banded FP64 factors of one matrix per shape, blocked solve form
+    DevMem M, P, Meta, table;
+    std::vector<BlockFactor> h;
+    std::vector<double> fma_col;    // FP64 FMAs of one real column by banded substitution, per shape
+    int maxlen = 0, maxK = 0;       // shared-memory sizing of the blocked solve
     bool ready = false;
-    void clear() { L.release(); U.release(); I.release(); Rr.release(); table.release(); h.clear(); max_m = 0; ready = false; }
+    void clear() { M.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); maxlen = maxK = 0; ready = false; }
 };
 
 template <typename R> struct InnerWork {   // inner GMRES buffers for one precision
@@ -203,22 +202,16 @@ hdd_status read_counter(hdd_ctx *ctx, cudaStream_t s, int *out) {
     return HDD_OK;
 }
 
-// E_j (or A_j) factors for every distinct shape, FP64, on the device.
+// E_j (or A_j) factors for every distinct shape, FP64, on the device: banded LU with partial
+// pivoting, then the blocked solve operators.
 hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s) {
     F.clear();
     const int ns = (int)ctx->shapes.size();
     std::vector<int> m(ns), kl(ns), ku(ns);
-    long long totL = 0, totU = 0, totM = 0;
-    F.h.resize(ns);
     for (int q = 0; q < ns; q++) {
         int nx = ctx->shapes[q].first, ny = ctx->shapes[q].second;
         if (coarse) { m[q] = (nx / 2) * (ny / 2); kl[q] = ku[q] = 2 * (nx / 2) + 2; }
         else { m[q] = nx * ny; kl[q] = ku[q] = nx + 1; }
-        F.h[q] = BandFactor{m[q], kl[q], ku[q], totL, totU, totM};
-        totL += (long long)m[q] * kl[q];
-        totU += (long long)m[q] * (kl[q] + ku[q]);
-        totM += m[q];
-        F.max_m = std::max(F.max_m, m[q]);
     }
     std::vector<DevMem> ab(ns), piv(ns);
     std::vector<double *> abp(ns);
@@ -254,34 +247,82 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
             FAIL(coarse ? HDD_ERR_SINGULAR_COARSE : HDD_ERR_SINGULAR_LOCAL,
                  "zero pivot in column %d of the %s factor of box %dx%d", info[q] - 1,
                  coarse ? "E" : "A_j", ctx->shapes[q].first, ctx->shapes[q].second);
-    CK(F.L.ensure((size_t)std::max(totL, 1LL) * sizeof(double)));
-    CK(F.U.ensure((size_t)std::max(totU, 1LL) * sizeof(double)));
-    CK(F.I.ensure((size_t)std::max(2 * totM, 1LL) * sizeof(int)));
-    CK(F.Rr.ensure((size_t)std::max(totM, 1LL) * sizeof(double)));
+    // permuted L, extents, permutation; then the panel widths (index bookkeeping on the host)
+    F.h.resize(ns);
+    F.fma_col.assign(ns, 0.0);
+    long long totP = 0;
+    std::vector<DevMem> Lp(ns), lext(ns), uext(ns);
+    std::vector<int> KLW(ns);
+    DevMem perm_all, derr;
+    for (int q = 0; q < ns; q++) totP += m[q];
+    CK(F.P.ensure((size_t)std::max(totP, 1LL) * sizeof(int)));
+    CK(derr.ensure(sizeof(int)));
+    CK(cudaMemsetAsync(derr.p, 0, sizeof(int), s));
+    long long po = 0;
     for (int q = 0; q < ns; q++) {
-        const BandFactor &b = F.h[q];
-        launch_band_convert(b.m, b.kl, b.ku, abp[q], pivp[q], F.L.as<double>() + b.l_off,
-                            F.U.as<double>() + b.u_off, F.I.as<int>() + 2 * b.p_off + b.m,
-                            F.Rr.as<double>() + b.p_off, F.I.as<int>() + 2 * b.p_off, s);
+        KLW[q] = 3 * kl[q];
+        CK(Lp[q].ensure((size_t)m[q] * KLW[q] * sizeof(double)));
+        CK(lext[q].ensure(m[q] * sizeof(int)));
+        CK(uext[q].ensure(m[q] * sizeof(int)));
+        launch_factor_prepare(m[q], kl[q], ku[q], abp[q], pivp[q], KLW[q], Lp[q].as<double>(),
+                              lext[q].as<int>(), uext[q].as<int>(), F.P.as<int>() + po, derr.as<int>(), s);
+        CKL();
+        F.h[q].m = m[q];
+        F.h[q].perm_off = po;
+        po += m[q];
+    }
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr) FAIL(HDD_ERR_INVALID_ARG, "row interchanges carried a multiplier beyond 3·kl rows");
+    long long mo = 0;
+    std::vector<int4> meta;
+    for (int q = 0; q < ns; q++) {
+        std::vector<int> le(m[q]), ue(m[q]);
+        CK(cudaMemcpy(le.data(), lext[q].p, m[q] * sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ue.data(), uext[q].p, m[q] * sizeof(int), cudaMemcpyDeviceToHost));
+        const int nbk = (m[q] + BNB - 1) / BNB;
+        BlockFactor &b = F.h[q];
+        b.nblk = nbk; b.wl = 0; b.wu = 0;
+        b.meta_off = (long long)meta.size();
+        long long so = 0;                      // operator offset relative to this shape
+        const long long base = mo;
+        for (int J = 0; J < nbk; J++) {
+            const int r0 = J * BNB, r1 = std::min(m[q], r0 + BNB) - 1;
+            int wl = 0, wu = 0;
+            for (int c = std::max(0, r0 - KLW[q]); c < r0; c++)             // left panel
+                if (c + le[c] >= r0) { wl = r0 - c; break; }
+            for (int c = std::min(m[q] - 1, r1 + kl[q] + ku[q]); c > r1; c--)  // right panel
+                if (c - ue[c] <= r1) { wu = c - r1; break; }
+            wl += wl & 1; wu += wu & 1;
+            int4 e;
+            e.x = (int)(base + so); e.y = wl; so += (long long)BNB * (BNB + wl);
+            e.z = (int)(base + so); e.w = wu; so += (long long)BNB * (BNB + wu);
+            meta.push_back(e);
+            b.wl = std::max(b.wl, wl); b.wu = std::max(b.wu, wu);
+        }
+        mo += so;
+        double fm = 0;
+        for (int j = 0; j < m[q]; j++) fm += std::min(kl[q], m[q] - 1 - j) + ue[j];
+        F.fma_col[q] = fm;
+        F.maxlen = std::max(F.maxlen, nbk * BNB + std::max(b.wl, b.wu));
+        F.maxK = std::max(F.maxK, BNB + std::max(b.wl, b.wu));
+    }
+    if (mo >= (1LL << 31)) FAIL(HDD_ERR_INVALID_ARG, "blocked factors exceed 2^31 doubles");
+    CK(F.M.ensure((size_t)std::max(mo, 1LL) * sizeof(double)));
+    CK(F.Meta.ensure(meta.size() * sizeof(int4)));
+    CK(cudaMemcpy(F.Meta.p, meta.data(), meta.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    for (int q = 0; q < ns; q++) {
+        launch_block_operators(m[q], kl[q], ku[q], abp[q], KLW[q], Lp[q].as<double>(),
+                               F.Meta.as<int4>() + F.h[q].meta_off, F.M.as<double>(), s);
         CKL();
     }
-    F.fma_col.assign(ns, 0.0);
-    F.kmax = 0;
-    for (int q = 0; q < ns; q++) {
-        const BandFactor &b = F.h[q];
-        std::vector<int> ue(b.m);
-        CK(cudaMemcpy(ue.data(), F.I.as<int>() + 2 * b.p_off + b.m, b.m * sizeof(int), cudaMemcpyDeviceToHost));
-        double fm = 0;
-        for (int j = 0; j < b.m; j++) { fm += std::min(b.kl, b.m - 1 - j) + ue[j]; F.kmax = std::max(F.kmax, ue[j]); }
-        F.kmax = std::max(F.kmax, b.kl);
-        F.fma_col[q] = fm;
-    }
-    CK(F.table.ensure(ns * sizeof(BandFactor)));
-    CK(cudaMemcpyAsync(F.table.p, F.h.data(), ns * sizeof(BandFactor), cudaMemcpyHostToDevice, s));
+    CK(F.table.ensure(ns * sizeof(BlockFactor)));
+    CK(cudaMemcpyAsync(F.table.p, F.h.data(), ns * sizeof(BlockFactor), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
-    if (set_band_solve_smem(F.max_m, F.kmax) != cudaSuccess)
-        FAIL(HDD_ERR_INVALID_ARG, "factor of order %d with %d band entries per column exceeds the shared-memory solve",
-             F.max_m, F.kmax);
+    if (set_block_solve_smem(F.maxlen, F.maxK) != cudaSuccess)
+        FAIL(HDD_ERR_INVALID_ARG, "factor of order %d (panel %d) exceeds the shared-memory solve",
+             F.maxlen, F.maxK);
     F.ready = true;
     return HDD_OK;
 }
@@ -293,10 +334,10 @@ void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *ou
     double fl = 0;
     for (int q = 0; q < nt; q++) fl += F.fma_col[ctx->h_tasks[q].shape];
     fl = 4.0 * fl * (nact < 0 ? 1.0 : (double)nact / nt);      // 2 columns x 2 flops per FMA
-    Launch L(ctx, F_COARSE, fl * 2.0, fl, s);                      // factor bytes ~ 8 B per FMA / 4
-    launch_band_solve(ctx->d_tasks.as<Task>(), (int)ctx->h_tasks.size(), F.table.as<BandFactor>(),
-                      F.L.as<double>(), F.U.as<double>(), F.I.as<int>(), F.Rr.as<double>(), in, out,
-                      fine ? 1 : 0, flag, F.max_m, F.kmax, s);
+    Launch L(ctx, F_COARSE, fl * 2.0, fl, s);
+    launch_block_solve(ctx->d_tasks.as<Task>(), nt, F.table.as<BlockFactor>(), F.M.as<double>(),
+                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, F.maxlen,
+                       F.maxK, s);
 }
 
 template <typename R> InnerWork<R> &work(hdd_ctx *ctx);

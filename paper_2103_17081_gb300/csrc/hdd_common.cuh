@@ -74,12 +74,16 @@ struct Tile {              // a block of fine rows (fine tiles) or coarse rows (
     int task, r0, nr;
 };
 
-struct BandFactor {        // FP64 banded LU with partial pivoting, solve-friendly layout
-    int m, kl, ku;         // order and bandwidths of the unfactored matrix
-    long long l_off;       // Lcol: m x kl doubles, L(j+1+q, j) at l_off + j·kl + q
-    long long u_off;       // Ucol: m x (kl+ku), U(c-1-q, c) at u_off + c·(kl+ku) + q
-    long long p_off;       // piv / uext / rinv: m entries each
+struct BlockFactor {        // FP64 banded LU with partial pivoting in blocked solve form
+    int m;                 // order
+    int nblk;              // blocks of BNB rows
+    int wl, wu;            // widest left (L) / right (U) panel over the blocks, even
+    long long perm_off;    // int perm[m]: (P b)[i] = b[perm[i]]
+    long long meta_off;    // int4 per block: {forward operator offset, its panel width w_l,
+                           //                  backward operator offset, its panel width w_u}
+                           // offsets in doubles from the start of the operator array
 };
+constexpr int BNB = 16;    // rows per block of the blocked banded solve
 
 constexpr int MAX_RESTART = 64;       // inner GMRES restart bound (Hessenberg in registers/smem)
 constexpr int FINE_ROWS = 8;          // fine rows per fine tile
@@ -155,13 +159,14 @@ void launch_assemble_E(const Stencil &st, int nx, int ny, int kl, int ku, double
 void launch_assemble_Aloc(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s);
 void launch_band_lu(int nmat, const int *m, const int *kl, const int *ku, double *const *ab,
                     int *const *piv, int *info, cudaStream_t s);
-void launch_band_convert(int m, int kl, int ku, const double *ab, const int *piv, double *Lcol,
-                         double *Ucol, int *uext, double *rinv, int *pivout, cudaStream_t s);
-void launch_band_solve(const Task *tasks, int ntasks, const BandFactor *shapes, const double *Lall,
-                       const double *Uall, const int *Iall, const double *Rall, const double2 *in,
-                       double2 *out, int use_fine_offsets, const int *flag, int max_m,
-                       int kmax_entries, cudaStream_t s);
-cudaError_t set_band_solve_smem(int max_m, int kmax_entries);
+void launch_factor_prepare(int m, int kl, int ku, const double *ab, const int *piv, int KLW,
+                           double *Lp, int *lext, int *uext, int *perm, int *err, cudaStream_t s);
+void launch_block_operators(int m, int kl, int ku, const double *ab, int KLW, const double *Lp,
+                            const int4 *meta, double *Mall, cudaStream_t s);
+void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
+                        const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
+                        int use_fine, const int *flag, int maxlen, int maxK, cudaStream_t s);
+cudaError_t set_block_solve_smem(int maxlen, int maxK);
 
 // global FP64 (outer FGMRES)
 int outer_grid(long long n);

@@ -140,160 +140,280 @@ k_band_lu(const int *__restrict__ mv, const int *__restrict__ klv, const int *__
 #undef ABX
 }
 
-// Re-layout a factor for the solve: L by columns; U by columns above the diagonal, scaled to a
-// unit diagonal (Û = D⁻¹U, entry Û(r,c) = U(r,c)/U(r,r)), with the true extent of each column;
-// reciprocal pivots 1/U(r,r).
-__global__ void k_band_convert(int m, int kl, int ku, const double *__restrict__ ab,
-                               const int *__restrict__ piv, double *__restrict__ Lcol,
-                               double *__restrict__ Ucol, int *__restrict__ uext,
-                               double *__restrict__ rinv, int *__restrict__ pivout) {
-    const int W = 2 * kl + ku + 1, KU = kl + ku;
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    for (int q = 0; q < kl; q++) {
-        int r = j + 1 + q;
-        Lcol[(long long)j * kl + q] = r < m ? ab[(long long)r * W + (j - r + kl)] : 0.0;
+// ------------------------------------------------------------------------------------------
+// Blocked form of the banded LU factor for the solve.
+//
+// The factorisation records the interchange piv[j] and the multipliers of column j at the row
+// positions of step j.  Applying every later interchange to those multipliers gives the usual
+// P E = L U with a fully permuted unit lower L, whose column j may then reach beyond row j+kl.
+// The solve works on blocks of BNB rows: with L_JJ the diagonal block and L_J the panel of the
+// WL columns to its left (U_JJ, U_J: diagonal block and the WU columns to its right),
+//   y_J = L_JJ⁻¹ (Pb)_J - L_JJ⁻¹ L_J y_{J-WL..J}          (forward)
+//   x_J = U_JJ⁻¹ y_J   - U_JJ⁻¹ U_J x_{J+1..J+WU}          (backward)
+// so each block is one dense matrix–vector product with the precomputed operator
+// M_J = [L_JJ⁻¹ | -L_JJ⁻¹ L_J] (resp. [U_JJ⁻¹ | -U_JJ⁻¹ U_J]) instead of BNB dependent rows.
+// ------------------------------------------------------------------------------------------
+
+// perm: (P b)[i] = b[perm[i]], the interchanges applied in order to the identity.
+__global__ void k_perm(int m, const int *__restrict__ piv, int *__restrict__ perm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i < m; i++) perm[i] = i;
+    for (int j = 0; j < m; j++) {
+        int p = piv[j];
+        if (p != j) { int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
     }
-    int ext = 0;
-    for (int q = 0; q < KU; q++) {
-        int r = j - 1 - q;
-        double v = 0.0;
-        if (r >= 0) {
-            double u = ab[(long long)r * W + (j - r + kl)];
-            v = u / ab[(long long)r * W + kl];
-        }
-        Ucol[(long long)j * KU + q] = v;
-        if (v != 0.0) ext = q + 1;
-    }
-    uext[j] = ext;
-    rinv[j] = 1.0 / ab[(long long)j * W + kl];
-    pivout[j] = piv[j];
 }
 
-constexpr int BS_PF = 8;        // factor columns in flight ahead of the sweep (per warp ring)
-constexpr int BS_KMAX = 8;      // up to 8 x 32 = 256 band entries per column
+// Column j of the permuted L: multipliers of step j with every later interchange applied.
+// Lp[j*KLW + q] = L(j+1+q, j); lext[j] = 1 + last non-zero q.  err is set if a multiplier
+// would leave the KLW window.
+__global__ void k_lperm(int m, int kl, int ku, const double *__restrict__ ab, const int *__restrict__ piv,
+                        int KLW, double *__restrict__ Lp, int *__restrict__ lext, int *__restrict__ err) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int W = 2 * kl + ku + 1;
+    double *c = Lp + (long long)j * KLW;
+    for (int q = 0; q < KLW; q++) {
+        const int r = j + 1 + q;
+        c[q] = (q < kl && r < m) ? ab[(long long)r * W + (j - r + kl)] : 0.0;
+    }
+    const int jmax = min(m - 1, j + KLW);
+    for (int jp = j + 1; jp <= jmax; jp++) {
+        const int p = piv[jp];
+        if (p == jp) continue;
+        const int qa = jp - j - 1, qb = p - j - 1;
+        if (qb >= KLW) {
+            if (c[qa] != 0.0) atomicExch(err, 1);
+            c[qa] = 0.0;
+            continue;
+        }
+        const double t = c[qa]; c[qa] = c[qb]; c[qb] = t;
+    }
+    int e = 0;
+    for (int q = 0; q < KLW; q++) if (c[q] != 0.0) e = q + 1;
+    lext[j] = e;
+}
 
-__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+// U column extents above the diagonal (for the backward window).
+__global__ void k_uext(int m, int kl, int ku, const double *__restrict__ ab, int *__restrict__ uext) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    const int W = 2 * kl + ku + 1;
+    int e = 0;
+    for (int q = 0; q < kl + ku; q++) {
+        const int r = c - 1 - q;
+        if (r >= 0 && ab[(long long)r * W + (c - r + kl)] != 0.0) e = q + 1;
+    }
+    uext[c] = e;
+}
+
+// Forward block operators: one CTA per block J, M_J row-major BNB x (BNB + w_J) at meta[J].x,
+// w_J = meta[J].y the width of block J's left panel.
+__global__ void k_block_fwd(int m, int KLW, const double *__restrict__ Lp, const int4 *__restrict__ meta,
+                            double *__restrict__ Mall) {
+    __shared__ double Li[BNB][BNB];
+    const int J = blockIdx.x, r0 = J * BNB;
+    const int WL = meta[J].y, K = BNB + WL;
+    double *MJ = Mall + meta[J].x;
+    auto Lv = [&](int r, int c) -> double {            // permuted L(r, c), r > c
+        if (c < 0 || r >= m || c >= m) return 0.0;
+        const int q = r - c - 1;
+        return (q >= 0 && q < KLW) ? Lp[(long long)c * KLW + q] : 0.0;
+    };
+    // L_JJ⁻¹ column by column (unit lower triangular; rows past m are identity)
+    if (threadIdx.x < BNB) {
+        const int c = threadIdx.x;
+        double x[BNB];
+        for (int r = 0; r < BNB; r++) x[r] = (r == c) ? 1.0 : 0.0;
+        for (int r = c + 1; r < BNB; r++) {
+            double acc = 0.0;
+            for (int k = c; k < r; k++) acc = fma(Lv(r0 + r, r0 + k), x[k], acc);
+            x[r] = -acc;
+        }
+        for (int r = 0; r < BNB; r++) Li[r][c] = x[r];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < BNB * K; e += blockDim.x) {
+        const int r = e / K, cc = e % K;
+        double v;
+        if (cc < BNB) v = Li[r][cc];
+        else {
+            const int col = r0 - WL + (cc - BNB);          // global column of the panel entry
+            double acc = 0.0;
+            for (int k = 0; k <= r; k++) acc = fma(Li[r][k], Lv(r0 + k, col), acc);
+            v = -acc;
+        }
+        MJ[e] = (r0 + r < m) ? v : 0.0;
+    }
+}
+
+// Backward block operators from the row-band U: M_J = [U_JJ⁻¹ | -U_JJ⁻¹ U_J], BNB x (BNB + w_J)
+// at meta[J].z with w_J = meta[J].w.
+__global__ void k_block_bwd(int m, int kl, int ku, const double *__restrict__ ab,
+                            const int4 *__restrict__ meta, double *__restrict__ Mall) {
+    __shared__ double Ui[BNB][BNB];
+    const int J = blockIdx.x, r0 = J * BNB;
+    const int WU = meta[J].w, K = BNB + WU;
+    const int W = 2 * kl + ku + 1;
+    double *MJ = Mall + meta[J].z;
+    auto Uv = [&](int r, int c) -> double {            // U(r, c), c >= r
+        if (r >= m || c >= m || c < r || c - r > kl + ku) return 0.0;
+        return ab[(long long)r * W + (c - r + kl)];
+    };
+    if (threadIdx.x < BNB) {
+        const int c = threadIdx.x;
+        double x[BNB];
+        for (int r = 0; r < BNB; r++) x[r] = 0.0;
+        if (r0 + c < m) {
+            for (int r = c; r >= 0; r--) {
+                double acc = (r == c) ? 1.0 : 0.0;
+                for (int k = r + 1; k <= c; k++) acc = fma(-Uv(r0 + r, r0 + k), x[k], acc);
+                x[r] = acc / Uv(r0 + r, r0 + r);
+            }
+        }
+        for (int r = 0; r < BNB; r++) Ui[r][c] = x[r];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < BNB * K; e += blockDim.x) {
+        const int r = e / K, cc = e % K;
+        double v;
+        if (cc < BNB) v = Ui[r][cc];
+        else {
+            const int col = r0 + BNB + (cc - BNB);
+            double acc = 0.0;
+            for (int k = r; k < BNB; k++) acc = fma(Ui[r][k], Uv(r0 + k, col), acc);
+            v = -acc;
+        }
+        MJ[e] = (r0 + r < m) ? v : 0.0;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
     unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int BS_T = 128;                 // threads: BNB rows x (BS_T/BNB) lanes per row
+constexpr int BS_LPR = BS_T / BNB;        // lanes per row (8)
+
+// y = M_J [a ; window] for the BNB rows of block J: lane `part` of row r sums the columns
+// part, part + BS_LPR, ... of the row with four independent accumulators (operands loaded
+// ahead of the FMAs), then the row's lanes reduce by shuffles.
+__device__ __forceinline__ double block_row_dot(const double *__restrict__ Mrow, int K,
+                                                const double *__restrict__ a,
+                                                const double *__restrict__ win, int part) {
+    double s0 = Mrow[part] * a[part];
+    double s1 = Mrow[part + BS_LPR] * a[part + BS_LPR];
+    double s2 = 0.0, s3 = 0.0;
+    const int WL = K - BNB;
+    int c = part;
+    for (; c + 3 * BS_LPR < WL; c += 4 * BS_LPR) {
+        const double m0 = Mrow[BNB + c], m1 = Mrow[BNB + c + BS_LPR];
+        const double m2 = Mrow[BNB + c + 2 * BS_LPR], m3 = Mrow[BNB + c + 3 * BS_LPR];
+        const double w0 = win[c], w1 = win[c + BS_LPR], w2 = win[c + 2 * BS_LPR], w3 = win[c + 3 * BS_LPR];
+        s0 = fma(m0, w0, s0); s1 = fma(m1, w1, s1); s2 = fma(m2, w2, s2); s3 = fma(m3, w3, s3);
+    }
+    for (; c < WL; c += BS_LPR) s0 = fma(Mrow[BNB + c], win[c], s0);
+    s0 = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int o = BS_LPR / 2; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    return s0;
 }
 
-// x = F⁻¹ b for the real banded factor F of the task's shape.  One WARP per (task, component)
-// chain, so a step needs only warp-level synchronisation: lane ℓ updates rows j+1+ℓ+32k.
-// The warp's vector sits in shared memory; the factor columns stream through a per-warp ring
-// filled by cp.async BS_PF steps ahead (each lane copies, and later reads, its own entries).
-// Forward: interchange b_j ↔ b_piv(j), then b_{j+1..j+kl} -= L(:,j) b_j; backward: unit upper
-// sweep on D⁻¹y with the true extent of every column of Û.
-template <int K>
-__global__ void __launch_bounds__(128)
-k_band_solve(const Task *__restrict__ tasks, int ntasks, const BandFactor *__restrict__ shapes,
-             const double *__restrict__ Lall, const double *__restrict__ Uall,
-             const int *__restrict__ Iall, const double *__restrict__ Rall,
-             const double2 *__restrict__ in, double2 *__restrict__ out, int use_fine,
-             const int *__restrict__ flag, int max_m) {
-    extern __shared__ double bsm[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int chain = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (chain >= 2 * ntasks) return;
-    const int t = chain >> 1, comp = chain & 1;
+template <int N> __device__ __forceinline__ void cp_async_wait_n() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+constexpr int BS_RING = 4;                // operator buffers; BS_RING-1 blocks in flight
+
+// x = F⁻¹ b with the blocked operators, one CTA per (task, component).  The operators stream
+// through a ring of BS_RING shared-memory buffers by cp.async, BS_RING-1 blocks ahead of the
+// block being applied (they are usually evicted from L2 between solves); one barrier per block.
+__global__ void __launch_bounds__(BS_T)
+k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ shapes,
+              const double *__restrict__ Mall, const int *__restrict__ Pall,
+              const int4 *__restrict__ Meta, const double2 *__restrict__ in,
+              double2 *__restrict__ out, int use_fine, const int *__restrict__ flag, int maxlen,
+              int maxK) {
+    extern __shared__ double sm[];
+    const int t = blockIdx.x >> 1, comp = blockIdx.x & 1;
     if (flag && !flag[t]) return;
-    // per-warp shared memory: b[max_m] | piv[max_m] | uext[max_m] | ring[BS_PF][32K]
-    const size_t per_warp = (size_t)max_m * 16 + (size_t)BS_PF * 32 * K * 8;
-    double *b = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(bsm) + per_warp * warp);
-    int *piv = reinterpret_cast<int *>(b + max_m);
-    int *uext = piv + max_m;
-    double *ring = reinterpret_cast<double *>(uext + max_m);
     const Task T = tasks[t];
-    const BandFactor F = shapes[T.shape];
+    const BlockFactor F = shapes[T.shape];
     const long long off = use_fine ? T.foff : T.coff;
-    const int m = F.m, kl = F.kl, KU = F.kl + F.ku;
-    const double *L = Lall + F.l_off;
-    const double *U = Uall + F.u_off;
-    const int *piv_g = Iall + 2 * F.p_off;
-    const int *uext_g = piv_g + m;
-    const double *rinv = Rall + F.p_off;
+    const int m = F.m, nbk = F.nblk, WL = F.wl, WU = F.wu;
+    double *Y = sm;                         // WL zeros, then y (nbk*BNB)
+    double *X = sm + maxlen;                // Pb during the forward sweep; x (+ WU zeros) after
+    double *Mb = sm + 2 * maxlen;           // BS_RING x BNB x maxK
+    const int *perm = Pall + F.perm_off;
+    const int4 *meta = Meta + F.meta_off;
     const double *inr = reinterpret_cast<const double *>(in + off) + comp;
+    const int tid = threadIdx.x, row = tid / BS_LPR, part = tid % BS_LPR;
+    auto load_block = [&](long long src_off, int K, int buf) {
+        const int nchunk = BNB * K / 2;                 // 16-byte chunks
+        const double *src = Mall + src_off;
+        double *dst = Mb + buf * BNB * maxK;
+        for (int q = tid; q < nchunk; q += BS_T) cp_async16(dst + 2 * q, src + 2 * q);
+    };
+    // forward operators of blocks 0 .. BS_RING-2 in flight while the right-hand side is gathered
+#pragma unroll
+    for (int u = 0; u < BS_RING - 1; u++) {
+        if (u < nbk) { const int4 mt = meta[u]; load_block(mt.x, BNB + mt.y, u); }
+        cp_async_commit();
+    }
+    for (int i = tid; i < WL; i += BS_T) Y[i] = 0.0;
+    for (int i0 = 0; i0 < nbk * BNB; i0 += 4 * BS_T) {      // (P b): four gathers in flight
+        int pi[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) { const int i = i0 + u * BS_T + tid; pi[u] = i < m ? perm[i] : -1; }
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = pi[u] >= 0 ? inr[2 * (long long)pi[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) { const int i = i0 + u * BS_T + tid; if (i < nbk * BNB) X[i] = v[u]; }
+    }
+    // ---- forward: y_J = M_J [(Pb)_J ; y_{J-w_J..J}] ----
+    for (int J = 0; J < nbk; J++) {
+        const int wJ = meta[J].y;
+        cp_async_wait_n<BS_RING - 2>();
+        __syncthreads();
+        if (J + BS_RING - 1 < nbk) {
+            const int4 mt = meta[J + BS_RING - 1];
+            load_block(mt.x, BNB + mt.y, (J + BS_RING - 1) % BS_RING);
+        }
+        cp_async_commit();
+        const double *Mrow = Mb + (J % BS_RING) * BNB * maxK + row * (BNB + wJ);
+        const double v = block_row_dot(Mrow, BNB + wJ, X + J * BNB, Y + WL + J * BNB - wJ, part);
+        if (part == 0) Y[WL + J * BNB + row] = v;
+    }
+    cp_async_wait_n<0>();
+    __syncthreads();
+    // ---- backward: x_J = M_J [y_J ; x_{J+1..J+w_J}] ----
+#pragma unroll
+    for (int u = 0; u < BS_RING - 1; u++) {
+        const int J = nbk - 1 - u;
+        if (J >= 0) { const int4 mt = meta[J]; load_block(mt.z, BNB + mt.w, u); }
+        cp_async_commit();
+    }
+    for (int i = tid; i < nbk * BNB + WU; i += BS_T) X[i] = 0.0;
+    for (int J = nbk - 1; J >= 0; J--) {
+        const int k = nbk - 1 - J;                          // sweep position
+        const int wJ = meta[J].w;
+        cp_async_wait_n<BS_RING - 2>();
+        __syncthreads();
+        if (J - (BS_RING - 1) >= 0) {
+            const int4 mt = meta[J - (BS_RING - 1)];
+            load_block(mt.z, BNB + mt.w, (k + BS_RING - 1) % BS_RING);
+        }
+        cp_async_commit();
+        const double *Mrow = Mb + (k % BS_RING) * BNB * maxK + row * (BNB + wJ);
+        const double v = block_row_dot(Mrow, BNB + wJ, Y + WL + J * BNB, X + (J + 1) * BNB, part);
+        if (part == 0) X[J * BNB + row] = v;
+    }
+    __syncthreads();
     double *outr = reinterpret_cast<double *>(out + off) + comp;
-    for (int i = lane; i < m; i += 32) {
-        b[i] = inr[2 * (long long)i];
-        piv[i] = piv_g[i];
-        uext[i] = uext_g[i];
-    }
-    // ---- forward ----
-    auto issue_L = [&](int j) {          // column min(j, m-1) of L, entries lane + 32k (clamped)
-        const double *col = L + (long long)min(j, m - 1) * kl;
-        double *slot = ring + (j % BS_PF) * 32 * K;
-#pragma unroll
-        for (int k = 0; k < K; k++) cp_async8(slot + k * 32 + lane, col + min(lane + 32 * k, kl - 1));
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int u = 0; u < BS_PF - 1; u++) issue_L(u);
-    __syncwarp();
-    for (int j = 0; j < m; j++) {
-        issue_L(j + BS_PF - 1);
-        cp_async_wait<BS_PF - 1>();                  // column j of L is in this lane's slots
-        const int p = piv[j];
-        const double sj = b[j], sp = b[p];
-        const int nq = min(kl, m - 1 - j);
-        const double *lc = ring + (j % BS_PF) * 32 * K;
-        double nv[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const int q = lane + 32 * k, r = j + 1 + q;
-            nv[k] = 0.0;
-            if (q < nq) nv[k] = fma(-lc[k * 32 + lane], sp, (r == p) ? sj : b[r]);
-        }
-        __syncwarp();                                 // every lane has read b[j], b[p]
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const int q = lane + 32 * k;
-            if (q < nq) b[j + 1 + q] = nv[k];
-        }
-        if (lane == 0) b[j] = sp;                     // y_j
-        __syncwarp();
-    }
-    cp_async_wait<0>();
-    // ---- D⁻¹ y ----
-    for (int i = lane; i < m; i += 32) b[i] *= rinv[i];
-    __syncwarp();
-    // ---- backward ----
-    auto issue_U = [&](int c) {          // column max(c, 0) of Û, entries lane + 32k (clamped)
-        const double *col = U + (long long)max(c, 0) * KU;
-        double *slot = ring + (((c % BS_PF) + BS_PF) % BS_PF) * 32 * K;
-#pragma unroll
-        for (int k = 0; k < K; k++) cp_async8(slot + k * 32 + lane, col + min(lane + 32 * k, KU - 1));
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int u = 0; u < BS_PF - 1; u++) issue_U(m - 1 - u);
-    for (int c = m - 1; c >= 0; c--) {
-        issue_U(c - (BS_PF - 1));
-        cp_async_wait<BS_PF - 1>();
-        const double xc = b[c];
-        const int ne = uext[c];
-        const double *uc = ring + (c % BS_PF) * 32 * K;
-        double nv[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const int q = lane + 32 * k;
-            nv[k] = 0.0;
-            if (q < ne) nv[k] = fma(-uc[k * 32 + lane], xc, b[c - 1 - q]);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const int q = lane + 32 * k;
-            if (q < ne) b[c - 1 - q] = nv[k];
-        }
-        if (lane == 0) outr[2 * (long long)c] = xc;
-        __syncwarp();
-    }
-    cp_async_wait<0>();
+    for (int i = tid; i < m; i += BS_T) outr[2 * (long long)i] = X[i];
 }
 
 void launch_assemble_E(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s) {
@@ -308,57 +428,31 @@ void launch_band_lu(int nmat, const int *m, const int *kl, const int *ku, double
                     int *const *piv, int *info, cudaStream_t s) {
     k_band_lu<<<nmat, 512, 0, s>>>(m, kl, ku, ab, piv, info);
 }
-void launch_band_convert(int m, int kl, int ku, const double *ab, const int *piv, double *Lcol,
-                         double *Ucol, int *uext, double *rinv, int *pivout, cudaStream_t s) {
-    k_band_convert<<<(m + 127) / 128, 128, 0, s>>>(m, kl, ku, ab, piv, Lcol, Ucol, uext, rinv, pivout);
+void launch_factor_prepare(int m, int kl, int ku, const double *ab, const int *piv, int KLW,
+                           double *Lp, int *lext, int *uext, int *perm, int *err, cudaStream_t s) {
+    k_perm<<<1, 32, 0, s>>>(m, piv, perm);
+    k_lperm<<<(m + 127) / 128, 128, 0, s>>>(m, kl, ku, ab, piv, KLW, Lp, lext, err);
+    k_uext<<<(m + 127) / 128, 128, 0, s>>>(m, kl, ku, ab, uext);
 }
-// warps per CTA and dynamic shared memory of the banded solve for factors up to order max_m
-// whose columns hold at most kmax_entries band entries
-static int bs_k(int kmax_entries) { return (kmax_entries + 31) / 32; }
-static size_t bs_per_warp(int max_m, int K) { return (size_t)max_m * 16 + (size_t)BS_PF * 32 * K * 8; }
-static int bs_wpc(int max_m, int K) {
-    size_t pw = bs_per_warp(max_m, K);
-    int w = (int)((200 * 1024) / pw);
-    return w < 1 ? 1 : (w > 4 ? 4 : w);
+void launch_block_operators(int m, int kl, int ku, const double *ab, int KLW, const double *Lp,
+                            const int4 *meta, double *Mall, cudaStream_t s) {
+    const int nbk = (m + BNB - 1) / BNB;
+    k_block_fwd<<<nbk, 128, 0, s>>>(m, KLW, Lp, meta, Mall);
+    k_block_bwd<<<nbk, 128, 0, s>>>(m, kl, ku, ab, meta, Mall);
 }
-
-template <int K>
-static void bs_launch(const Task *tasks, int ntasks, const BandFactor *shapes, const double *Lall,
-                      const double *Uall, const int *Iall, const double *Rall, const double2 *in,
-                      double2 *out, int use_fine, const int *flag, int max_m, cudaStream_t s) {
-    const int wpc = bs_wpc(max_m, K);
-    const int grid = (2 * ntasks + wpc - 1) / wpc;
-    k_band_solve<K><<<grid, 32 * wpc, bs_per_warp(max_m, K) * wpc, s>>>(
-        tasks, ntasks, shapes, Lall, Uall, Iall, Rall, in, out, use_fine, flag, max_m);
+static size_t bs_smem(int maxlen, int maxK) {
+    return (2 * (size_t)maxlen + (size_t)BS_RING * BNB * maxK) * sizeof(double);
 }
-
-void launch_band_solve(const Task *tasks, int ntasks, const BandFactor *shapes, const double *Lall,
-                       const double *Uall, const int *Iall, const double *Rall, const double2 *in,
-                       double2 *out, int use_fine_offsets, const int *flag, int max_m,
-                       int kmax_entries, cudaStream_t s) {
-    switch (bs_k(kmax_entries)) {
-        case 1: bs_launch<1>(tasks, ntasks, shapes, Lall, Uall, Iall, Rall, in, out, use_fine_offsets, flag, max_m, s); break;
-        case 2: bs_launch<2>(tasks, ntasks, shapes, Lall, Uall, Iall, Rall, in, out, use_fine_offsets, flag, max_m, s); break;
-        case 3: bs_launch<3>(tasks, ntasks, shapes, Lall, Uall, Iall, Rall, in, out, use_fine_offsets, flag, max_m, s); break;
-        case 4: bs_launch<4>(tasks, ntasks, shapes, Lall, Uall, Iall, Rall, in, out, use_fine_offsets, flag, max_m, s); break;
-        case 5: case 6: bs_launch<6>(tasks, ntasks, shapes, Lall, Uall, Iall, Rall, in, out, use_fine_offsets, flag, max_m, s); break;
-        default: bs_launch<8>(tasks, ntasks, shapes, Lall, Uall, Iall, Rall, in, out, use_fine_offsets, flag, max_m, s); break;
-    }
+void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
+                        const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
+                        int use_fine, const int *flag, int maxlen, int maxK, cudaStream_t s) {
+    k_block_solve<<<2 * ntasks, BS_T, bs_smem(maxlen, maxK), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
+                                                                 use_fine, flag, maxlen, maxK);
 }
-// Opt the solve kernels into the shared memory they need; returns an error if one warp's
-// share does not fit.
-cudaError_t set_band_solve_smem(int max_m, int kmax_entries) {
-    const int K = bs_k(kmax_entries);
-    if (K > BS_KMAX) return cudaErrorInvalidValue;
-    const size_t bytes = bs_per_warp(max_m, K) * bs_wpc(max_m, K);
+cudaError_t set_block_solve_smem(int maxlen, int maxK) {
+    const size_t bytes = bs_smem(maxlen, maxK);
     if (bytes > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_band_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_band_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_band_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_band_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaFuncSetAttribute(k_block_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace hdd

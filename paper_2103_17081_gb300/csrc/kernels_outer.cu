@@ -177,13 +177,15 @@ __global__ void __launch_bounds__(OT) k_onorm(const double2 *__restrict__ x, lon
     }
 }
 
-// out[l] = Σ_q part[q][l] (fixed order).
+// out[l] = Σ_q part[q][l]: one warp per l, lane i adds q = i, i+32, ... in order, then a fixed
+// shuffle tree (deterministic).
 __global__ void k_oreduce(const double2 *__restrict__ part, int nparts, int ldp, int nv, double2 *__restrict__ out) {
-    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (l >= nv) return;
     double2 s = make_double2(0.0, 0.0);
-    for (int q = 0; q < nparts; q++) { double2 v = part[(long long)q * ldp + l]; s.x += v.x; s.y += v.y; }
-    out[l] = s;
+    for (int q = lane; q < nparts; q += 32) { double2 v = part[(long long)q * ldp + l]; s.x += v.x; s.y += v.y; }
+    for (int o = 16; o > 0; o >>= 1) { s.x += shfl_xor(s.x, o); s.y += shfl_xor(s.y, o); }
+    if (lane == 0) out[l] = s;
 }
 
 __device__ void zgivens(double2 a, double2 b, double &c, double2 &s, double2 &r) {
@@ -320,7 +322,7 @@ void launch_onorm(const double2 *x, long long n, double *part, cudaStream_t s) {
     k_onorm<<<outer_grid(n), OT, 0, s>>>(x, n, part);
 }
 void launch_oreduce(const double2 *part, int nparts, int ldp, int nv, double2 *out, cudaStream_t s) {
-    k_oreduce<<<(nv + 127) / 128, 128, 0, s>>>(part, nparts, ldp, nv, out);
+    k_oreduce<<<(nv + 7) / 8, 256, 0, s>>>(part, nparts, ldp, nv, out);
 }
 void launch_ogivens(double2 *H, long long ldh, double *cs, double2 *sn, double2 *g, int j, const double2 *h1,
                     const double2 *h2, const double *npart, int nparts, double tol_abs, double *hn_out, int *flag,

@@ -134,8 +134,10 @@ def test_tiny_solve_matches_oracle(oracle_mod, prec):
     assert _rel(xg, xo) < 1e-5
     if prec == 128:
         assert abs(st["outer_its"] - so["outer_its"]) <= 1
-        n = min(len(st["res_history"]), len(so["res_history"])) - 2
-        assert np.allclose(st["res_history"][:n], so["res_history"][:n], rtol=1e-4, atol=0)
+        hg, ho = np.array(st["res_history"]), np.array(so["res_history"])
+        assert np.allclose(hg[:10], ho[:10], rtol=1e-6, atol=0)
+        n = min(len(hg), len(ho)) - 2
+        assert np.allclose(hg[:n], ho[:n], rtol=1e-2, atol=0), np.max(np.abs(hg[:n] / ho[:n] - 1))
     else:
         # this workload is specified in complex128; complex64 inner solves are allowed a wider
         # margin here (at k=100 and k=200 their outer counts match the oracle within 1)
