@@ -210,6 +210,25 @@ hdd_status hdd_profile_get(hdd_ctx *ctx, int i, hdd_kernel_stat *out);
 /* Kernel launches made by this context since creation (counted whether or not profiling is on). */
 long long hdd_launch_count(const hdd_ctx *ctx);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Deflated operator without device allocation.                                             */
+/*                                                                                          */
+/* The paper has no counterpart: this entry point exists for callers that cannot call        */
+/* cudaMalloc, e.g. code running inside a captured CUDA graph, under an allocator that must  */
+/* not be re-entered, or in an embedding that owns all device memory up front.               */
+/*                                                                                          */
+/* out = P_j A_j in for every subdomain j (the same operator and packed layout as            */
+/* hdd_local_op op 4, complex128).  in_dev, out_dev: caller-owned packed local vectors       */
+/* (hdd_get_offsets), distinct, 16-byte aligned.  The two complex128 coarse work vectors live */
+/* in a fixed array inside the library (16 MiB, present on every GPU that loads the library  */
+/* until the process exits): the packed coarse length Σ m_x·m_y must not exceed 524288, else */
+/* HDD_ERR_INVALID_ARG.  The call allocates nothing; the first call on a device looks up that */
+/* array's device address (make the first call before any stream capture).  Every call      */
+/* shares the array, so calls that may overlap on the GPU (other streams, other contexts on  */
+/* the same device) race; serialise them.  Work is enqueued on `stream`; no synchronisation. */
+/* ---------------------------------------------------------------------------------------- */
+hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

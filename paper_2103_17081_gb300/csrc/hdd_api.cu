@@ -545,6 +545,32 @@ double host_norm(hdd_ctx *ctx, const double *dpart, long long n, cudaStream_t s,
 }  // namespace
 
 // ===========================================================================================
+// Fixed scratch for hdd_apply_PA_noalloc: two complex128 coarse vectors (y = Zᵀ A v and
+// s = E⁻¹ y) of at most HDD_NOALLOC_MAX_COARSE entries each, 16 MiB held by every GPU that
+// loads the library for the life of the process.  Host code cannot use the symbol itself as a
+// device address; the address is looked up once per device (noalloc_scratch below).
+// ===========================================================================================
+#define HDD_NOALLOC_MAX_COARSE (1 << 19)
+#define HDD_NOALLOC_MAX_DEVICES 64
+static __device__ __align__(256) double2 g_noalloc_scratch[2 * HDD_NOALLOC_MAX_COARSE];
+static double2 *g_noalloc_ptr[HDD_NOALLOC_MAX_DEVICES];
+
+namespace {
+// Device address of g_noalloc_scratch on the current device (resolved on first use).
+cudaError_t noalloc_scratch(int device, double2 **out) {
+    if (device < 0 || device >= HDD_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = reinterpret_cast<double2 *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+}  // namespace
+
+// ===========================================================================================
 // C ABI
 // ===========================================================================================
 extern "C" {
@@ -928,6 +954,37 @@ hdd_status hdd_profile_get(hdd_ctx *ctx, int i, hdd_kernel_stat *out) {
 }
 
 long long hdd_launch_count(const hdd_ctx *ctx) { return ctx ? ctx->prof.launches : 0; }
+
+hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (!ctx->E.ready) FAIL(HDD_ERR_STATE, "hdd_setup_deflation first");
+    if (!in_dev || !out_dev || in_dev == out_dev || !aligned16(in_dev) || !aligned16(out_dev))
+        FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
+    if (ctx->ldc > HDD_NOALLOC_MAX_COARSE)
+        FAIL(HDD_ERR_INVALID_ARG, "packed coarse length %lld exceeds the no-allocation limit %d",
+             ctx->ldc, HDD_NOALLOC_MAX_COARSE);
+    CK(cudaSetDevice(ctx->device));
+    double2 *scratch = nullptr;
+    CK(noalloc_scratch(ctx->device, &scratch));
+    cudaStream_t s = (cudaStream_t)stream;
+    LocalArgs<double> a = local_args<double>(ctx);
+    const size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(double2));
+    if (smem > 48 * 1024) CK(set_local_smem_limits<double>(smem));
+    double2 *y = scratch, *sc = scratch + HDD_NOALLOC_MAX_COARSE;
+    const double2 *in = (const double2 *)in_dev;
+    double2 *out = (double2 *)out_dev;
+    const FactorSet &F = ctx->E;
+    // every coarse entry of y and s is written before it is read: nothing needs clearing
+    launch_zt<double>(a, in, y, 1, nullptr, s);                                        // y = Zᵀ A v
+    launch_block_solve(ctx->d_tasks.as<Task>(), (int)ctx->h_tasks.size(), F.table.as<BlockFactor>(),
+                       F.M.as<double>(), F.P.as<int>(), F.Meta.as<int4>(), y, sc, 0, nullptr,
+                       F.maxlen, F.maxK, s);                                            // s = E⁻¹ y
+    launch_prolong_stencil<double>(a, 0, in, sc, out, nullptr, 0, scratch, nullptr, s); // A(v - Z s)
+    ctx->prof.launches += 3;
+    CKL();
+    return HDD_OK;
+}
 
 hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void *out_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
