@@ -210,3 +210,28 @@ def test_errors_are_status_codes(oracle_mod):
     assert st["status_code"] == 7 and st["outer_its"] == 3
     x, st = s.solve(torch.zeros_like(f))
     assert st["outer_its"] == 0 and float(x.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("prec", [64, 128])
+def test_k200_full_solve_against_stored_oracle(prec):
+    """k=200, N=640, 8x8 subdomains (the bench workload), whole solve at outer tolerance 1e-6,
+    compared with the oracle's solve stored by tests/golden/make_k200_reference.py: outer
+    iterations within +10 %, solution at 256 seeded nodes within 1e-5 relative, same ||x||."""
+    import json
+    import os
+    torch = _torch()
+    from paper_2103_17081_gb300 import Solver
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "k200_oracle.json")))
+    w = W.make("k200")
+    s = Solver.from_workload(w)
+    f = s.build_rhs(w.rhs[0])
+    x, st = s.solve(f, outer_tol=w.outer_tol, inner_tol=w.inner_tol, inner_prec=prec)
+    r = f - s.apply_A(x)
+    assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(f)) <= 1.0001e-6
+    assert st["outer_its"] <= 1.1 * ref["outer_its"]
+    idx = torch.tensor(ref["sample_index"], device=x.device)
+    xs = x[idx].cpu().numpy()
+    xr = np.array(ref["sample_re"])
+    assert np.linalg.norm(xs - xr) <= 1e-5 * np.linalg.norm(xr)
+    assert abs(float(torch.linalg.vector_norm(x)) - ref["x_norm2"]) <= 1e-5 * ref["x_norm2"]
+    assert float(x.imag.abs().max()) == 0.0
