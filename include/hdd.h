@@ -120,6 +120,14 @@ int hdd_num_subdomains(const hdd_ctx *ctx);
  * [coarse_off[s], coarse_off[s] + mx·my) of a packed coarse vector.  Host arrays of nsub+1. */
 hdd_status hdd_get_offsets(const hdd_ctx *ctx, long long *fine_off, long long *coarse_off);
 
+/* Batch nrhs independent right-hand sides (1..4096; default 1 after hdd_setup_dd): every
+ * subsequent hdd_solve / hdd_ras_apply takes nrhs global vectors (RHS-major) and runs the local
+ * solves of every (subdomain, RHS) pair in the same launches; the outer FGMRES iterations of the
+ * right-hand sides run in lockstep, each with its own Krylov basis and stopping test.  The
+ * packed local layout (hdd_get_offsets) then repeats per RHS.  Factors are kept. */
+hdd_status hdd_setup_batch(hdd_ctx *ctx, int nrhs);
+int hdd_num_rhs(const hdd_ctx *ctx);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Deflation set-up (Eq. 4, Eq. 5).  For every distinct box shape: E = Zᵀ A Z (5x5 coarse   */
 /* stencil, half-bandwidth 2·mx+2) is formed and LU-factorised with partial pivoting in FP64 */
@@ -160,16 +168,18 @@ typedef struct {
                                  /* until the next hdd_solve or hdd_destroy                   */
 } hdd_solve_stats;
 
-/* Solve A x = f for one right-hand side (f_dev → x_dev, complex128, distinct buffers).
- * stats may be NULL.  Returns HDD_ERR_NO_CONVERGENCE (x holds the last iterate) when
- * outer_maxit is reached. */
+/* Solve A x = f for the batched right-hand sides (f_dev → x_dev: nrhs complex128 vectors,
+ * distinct buffers).  stats may be NULL; outer_its counts lockstep iterations (the largest over
+ * the right-hand sides), rel_res_true is the largest true relative residual, inner_its_avg the
+ * average over all local solves, res_history that of the first RHS.  Returns
+ * HDD_ERR_NO_CONVERGENCE (x holds the last iterates) when outer_maxit is reached. */
 hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_solve_params *prm,
                      hdd_solve_stats *stats, void *stream);
 
 /* One application of the RAS preconditioner z = Σ_j R_jᵀ D_j ũ_j with ũ_j the inexact (or,
  * for inner_tol <= 0, direct) solution of A_j ũ_j = R_j v (Eq. 3): the inner-solve hot path on
- * its own.  v_dev, z_dev: global complex128.  inner_its (may be NULL): host array of nsub
- * receiving each local solve's Arnoldi step count. */
+ * its own.  v_dev, z_dev: nrhs global complex128 vectors.  inner_its (may be NULL): host array
+ * of nsub x nrhs receiving each local solve's Arnoldi step count (task r·nsub + s). */
 hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev,
                          const hdd_solve_params *prm, int *inner_its, void *stream);
 

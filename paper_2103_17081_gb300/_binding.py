@@ -16,7 +16,8 @@ SYMBOLS = ["hdd_create", "hdd_destroy", "hdd_status_str", "hdd_last_error", "hdd
            "hdd_build_rhs", "hdd_apply_A", "hdd_setup_dd", "hdd_get_subdomain",
            "hdd_num_subdomains", "hdd_get_offsets", "hdd_setup_deflation", "hdd_setup_exact",
            "hdd_solve", "hdd_ras_apply", "hdd_local_op", "hdd_profile", "hdd_profile_count",
-           "hdd_profile_get", "hdd_launch_count", "hdd_apply_PA_noalloc"]
+           "hdd_profile_get", "hdd_launch_count", "hdd_apply_PA_noalloc", "hdd_setup_batch",
+           "hdd_num_rhs"]
 
 
 def status_name(code: int) -> str:
@@ -112,6 +113,10 @@ def lib(build_if_missing: bool = True):
     L.hdd_profile_get.restype = I
     L.hdd_launch_count.argtypes = [P]
     L.hdd_launch_count.restype = C.c_longlong
+    L.hdd_setup_batch.argtypes = [P, I]
+    L.hdd_setup_batch.restype = I
+    L.hdd_num_rhs.argtypes = [P]
+    L.hdd_num_rhs.restype = I
     L.hdd_apply_PA_noalloc.argtypes = [P, V, V, V]
     L.hdd_apply_PA_noalloc.restype = I
     _lib = L

@@ -94,9 +94,7 @@ struct Prof {
 };
 
 struct OuterWork {
-    int R = 0;
-    long long n = 0;
-    DevMem V, Z, w, r, H, cs, sn, g, h1, h2, part, npart, hn, flag, hist, beta, y;
+    DevMem V, Z, w, r, H, cs, sn, g, h1, h2, part, npart, hn, flag, hist, beta, y, fnorm, act, kcols;
 };
 
 }  // namespace
@@ -115,9 +113,10 @@ struct hdd_ctx {
     std::vector<SubBox> subs;
     std::vector<int> sub_shape;
     std::vector<std::pair<int, int>> shapes;   // (nx, ny)
-    std::vector<Task> h_tasks;
+    int nrhs = 1;                               // right-hand sides batched per solve
+    std::vector<Task> h_tasks;                  // task t = r·nsub + s
     std::vector<Tile> h_ftiles, h_ctiles;
-    DevMem d_tasks, d_ftiles, d_ctiles, d_ones;
+    DevMem d_tasks, d_ftiles, d_ctiles, d_ones, d_mask;
     long long ld = 0, ldc = 0;
     int max_nx = 0, max_n = 0;
     std::vector<long long> foffs, coffs;
@@ -378,10 +377,11 @@ template <typename R> InnerState<R> inner_state(InnerWork<R> &W) {
 
 // All local solves of one RAS application (Eq. 3): z = Σ_j R_jᵀ D_j ũ_j, ũ_j from deflated
 // GMRES on P_j A_j ũ = P_j R_j v (Eq. 4), then completed by ũ += Q_j (f̃ - A_j ũ).
+// mask (may be null = every task): tasks whose RHS takes part; the others are left untouched.
 template <typename R>
 hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve_params *prm,
                      cudaStream_t s, long long *its_total, int *its_max, long long *hits,
-                     int *its_out) {
+                     int *its_out, const int *mask) {
     const int RST = prm->inner_restart;
     hdd_status st = ensure_inner<R>(ctx, RST);
     if (st != HDD_OK) return st;
@@ -402,7 +402,8 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     const R tol = (R)prm->inner_tol;
     const int maxit = prm->inner_maxit;
 
-    KL(F_LMISC, ld * (16 + cs), 0, launch_restrict<R>(a, v, ctx->nglob, f, nullptr, s));
+    const int *all = mask ? mask : ones;
+    KL(F_LMISC, ld * (16 + cs), 0, launch_restrict<R>(a, v, ctx->nglob, f, mask, s));
     CK(cudaMemsetAsync(W.its.p, 0, nt * sizeof(int), s));
     CK(cudaMemsetAsync(W.conv.p, 0, nt * sizeof(int), s));
     CK(cudaMemsetAsync(W.kcols.p, 0, nt * sizeof(int), s));
@@ -410,13 +411,13 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     CK(cudaMemsetAsync(act[1], 0, nt * sizeof(int), s));
     CK(cudaMemsetAsync(u, 0, ld * sizeof(c2<R>), s));
     // first cycle from ũ = 0: r0 = P f̃ = f̃ - A Z E⁻¹ Zᵀ f̃, and ref = ||P f̃||
-    KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, y, 0, nullptr, s));
-    band_solve(ctx, ctx->E, y, sc, false, nullptr, s);
-    KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, V, nullptr, 0, p3, nullptr, s));
+    KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, y, 0, mask, s));
+    band_solve(ctx, ctx->E, y, sc, false, mask, s);
+    KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, V, nullptr, 0, p3, mask, s));
     CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
-    KL(F_LMISC, 2 * ld * cs, 0, launch_init_cycle<R>(a, S, RST, V, p3, ones, act[0], cnt, tol, maxit, 1, s));
+    KL(F_LMISC, 2 * ld * cs, 0, launch_init_cycle<R>(a, S, RST, V, p3, all, act[0], cnt, tol, maxit, 1, s));
     CKL();
-    CK(cudaMemcpyAsync(cyc, ones, nt * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(cyc, all, nt * sizeof(int), cudaMemcpyDeviceToDevice, s));
     int cur = 0, nact = 0;
     st = read_counter(ctx, s, &nact);
     if (st != HDD_OK) return st;
@@ -469,9 +470,9 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     // completion x = ũ + Z E⁻¹ Zᵀ (f̃ - A ũ) with E⁻¹ Zᵀ (f̃ - A ũ) = s₀ - Σ y_i s_{i+1}
     // (linearity; every term was solved during the last cycle), then z = Σ R_jᵀ D_j x_j
     double2 *scomp = sc + (long long)(RST + 1) * ldc;
-    KL(F_LMISC, (RST + 2) * ldc * 16.0, 0, launch_coarse_combine<R>(a, S, RST, sc, scomp, s));
-    KL(F_LMISC, 2 * ld * cs + ldc * 16, 0, launch_z<R>(a, scomp, u, x, nullptr, s));
-    KL(F_LMISC, ld * (cs + 16), 0, launch_scatter<R>(a, x, z, ctx->nglob, s));
+    KL(F_LMISC, (RST + 2) * ldc * 16.0, 0, launch_coarse_combine<R>(a, S, RST, sc, scomp, mask, s));
+    KL(F_LMISC, 2 * ld * cs + ldc * 16, 0, launch_z<R>(a, scomp, u, x, mask, s));
+    KL(F_LMISC, ld * (cs + 16), 0, launch_scatter<R>(a, x, z, ctx->nglob, mask, s));
     CKL();
     ctx->h_its.resize(nt);
     CK(cudaMemcpyAsync(ctx->h_its.data(), W.its.p, nt * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -491,30 +492,31 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     return HDD_OK;
 }
 
-hdd_status exact_ras(hdd_ctx *ctx, const double2 *v, double2 *z, cudaStream_t s) {
+hdd_status exact_ras(hdd_ctx *ctx, const double2 *v, double2 *z, cudaStream_t s, const int *mask) {
     if (!ctx->Aex.ready) FAIL(HDD_ERR_STATE, "direct local solves need hdd_setup_exact");
     hdd_status st = ensure_inner<double>(ctx, 1);
     if (st != HDD_OK) return st;
     InnerWork<double> &W = ctx->w64;
     LocalArgs<double> a = local_args<double>(ctx);
-    KL(F_LMISC, ctx->ld * 32, 0, launch_restrict<double>(a, v, ctx->nglob, W.f.as<double2>(), nullptr, s));
-    band_solve(ctx, ctx->Aex, W.f.as<double2>(), W.x.as<double2>(), true, nullptr, s);
-    KL(F_LMISC, ctx->ld * 32, 0, launch_scatter<double>(a, W.x.as<double2>(), z, ctx->nglob, s));
+    KL(F_LMISC, ctx->ld * 32, 0, launch_restrict<double>(a, v, ctx->nglob, W.f.as<double2>(), mask, s));
+    band_solve(ctx, ctx->Aex, W.f.as<double2>(), W.x.as<double2>(), true, mask, s);
+    KL(F_LMISC, ctx->ld * 32, 0, launch_scatter<double>(a, W.x.as<double2>(), z, ctx->nglob, mask, s));
     CKL();
     return HDD_OK;
 }
 
 hdd_status ras_apply(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve_params *prm,
-                     cudaStream_t s, long long *tot, int *mx, long long *hits, int *its_out) {
+                     cudaStream_t s, long long *tot, int *mx, long long *hits, int *its_out,
+                     const int *mask = nullptr) {
     if (prm->inner_tol <= 0) {
         if (tot) *tot = 0;
         if (mx) *mx = 0;
         if (hits) *hits = 0;
-        return exact_ras(ctx, v, z, s);
+        return exact_ras(ctx, v, z, s, mask);
     }
     if (!ctx->E.ready) FAIL(HDD_ERR_STATE, "inexact local solves need hdd_setup_deflation");
-    if (prm->inner_prec == 64) return inner_ras<float>(ctx, v, z, prm, s, tot, mx, hits, its_out);
-    return inner_ras<double>(ctx, v, z, prm, s, tot, mx, hits, its_out);
+    if (prm->inner_prec == 64) return inner_ras<float>(ctx, v, z, prm, s, tot, mx, hits, its_out, mask);
+    return inner_ras<double>(ctx, v, z, prm, s, tot, mx, hits, its_out, mask);
 }
 
 hdd_status check_solve_params(hdd_ctx *ctx, const hdd_solve_params *p) {
@@ -526,20 +528,6 @@ hdd_status check_solve_params(hdd_ctx *ctx, const hdd_solve_params *p) {
     if (p->inner_prec != 64 && p->inner_prec != 128)
         FAIL(HDD_ERR_INVALID_ARG, "inner_prec must be 64 or 128");
     return HDD_OK;
-}
-
-double host_norm(hdd_ctx *ctx, const double *dpart, long long n, cudaStream_t s, hdd_status *st) {
-    std::vector<double> h(outer_grid(n));
-    *st = HDD_OK;
-    if (cudaMemcpyAsync(h.data(), dpart, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        ctx->err = "norm read-back failed";
-        *st = HDD_ERR_CUDA;
-        return 0;
-    }
-    double a = 0;
-    for (double v : h) a += v;
-    return std::sqrt(a);
 }
 
 }  // namespace
@@ -567,6 +555,51 @@ cudaError_t noalloc_scratch(int device, double2 **out) {
     }
     *out = g_noalloc_ptr[device];
     return cudaSuccess;
+}
+}  // namespace
+
+namespace {
+// Task and tile tables for nrhs right-hand sides: task t = r·nsub + s solves subdomain s for
+// RHS r; fine tiles of FINE_ROWS box rows, coarse tiles of COARSE_ROWS coarse rows.
+hdd_status build_tasks(hdd_ctx *ctx, int nrhs) {
+    const int ns = (int)ctx->subs.size();
+    ctx->h_tasks.clear(); ctx->h_ftiles.clear(); ctx->h_ctiles.clear();
+    ctx->foffs.assign(1, 0); ctx->coffs.assign(1, 0);
+    long long fo = 0, co = 0;
+    for (int r = 0; r < nrhs; r++)
+        for (int q = 0; q < ns; q++) {
+            const SubBox &b = ctx->subs[q];
+            const int t = r * ns + q;
+            Task T{};
+            T.nx = b.nx; T.ny = b.ny; T.mx = b.mx; T.my = b.my;
+            T.ix0 = b.ix0; T.iy0 = b.iy0; T.ox0 = b.ox0; T.ox1 = b.ox1; T.oy0 = b.oy0; T.oy1 = b.oy1;
+            T.shape = ctx->sub_shape[q]; T.sub = q; T.rhs = r;
+            T.foff = fo; T.coff = co;
+            T.tile0 = (int)ctx->h_ftiles.size();
+            for (int y = 0; y < b.ny; y += FINE_ROWS)
+                ctx->h_ftiles.push_back(Tile{t, y, std::min(FINE_ROWS, b.ny - y)});
+            T.ntiles = (int)ctx->h_ftiles.size() - T.tile0;
+            for (int y = 0; y < b.my; y += COARSE_ROWS)
+                ctx->h_ctiles.push_back(Tile{t, y, std::min(COARSE_ROWS, b.my - y)});
+            fo += (long long)b.nx * b.ny;
+            co += (long long)b.mx * b.my;
+            if (r == 0) { ctx->foffs.push_back(fo); ctx->coffs.push_back(co); }
+            ctx->h_tasks.push_back(T);
+        }
+    ctx->ld = fo; ctx->ldc = co;
+    const int nt = (int)ctx->h_tasks.size();
+    CK(ctx->d_tasks.ensure(nt * sizeof(Task)));
+    CK(ctx->d_ftiles.ensure(ctx->h_ftiles.size() * sizeof(Tile)));
+    CK(ctx->d_ctiles.ensure(ctx->h_ctiles.size() * sizeof(Tile)));
+    CK(ctx->d_ones.ensure(nt * sizeof(int)));
+    CK(ctx->d_mask.ensure(nt * sizeof(int)));
+    std::vector<int> ones(nt, 1);
+    CK(cudaMemcpy(ctx->d_tasks.p, ctx->h_tasks.data(), nt * sizeof(Task), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_ftiles.p, ctx->h_ftiles.data(), ctx->h_ftiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_ctiles.p, ctx->h_ctiles.data(), ctx->h_ctiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_ones.p, ones.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+    ctx->nrhs = nrhs;
+    return HDD_OK;
 }
 }  // namespace
 
@@ -664,9 +697,8 @@ hdd_status hdd_apply_A(hdd_ctx *ctx, const void *x_dev, void *y_dev, int nrhs, v
     if (!x_dev || !y_dev || nrhs < 1 || x_dev == y_dev || !aligned16(x_dev) || !aligned16(y_dev))
         FAIL(HDD_ERR_INVALID_ARG, "bad apply_A arguments");
     CK(cudaSetDevice(ctx->device));
-    for (int r = 0; r < nrhs; r++)
-        launch_gstencil(ctx->st, ctx->N, (const double2 *)x_dev + r * ctx->nglob,
-                        (double2 *)y_dev + r * ctx->nglob, nullptr, (cudaStream_t)stream);
+    launch_gstencil(ctx->st, ctx->N, (const double2 *)x_dev, (double2 *)y_dev, nullptr, nrhs, nullptr,
+                    (cudaStream_t)stream);
     CKL();
     return HDD_OK;
 }
@@ -711,42 +743,13 @@ hdd_status hdd_setup_dd(hdd_ctx *ctx, const hdd_dd_params *p) {
             ctx->subs.push_back(b);
             ctx->sub_shape.push_back(sid);
         }
-    // one task per subdomain; fine tiles of FINE_ROWS rows, coarse tiles of COARSE_ROWS rows
-    ctx->h_tasks.clear(); ctx->h_ftiles.clear(); ctx->h_ctiles.clear();
-    ctx->foffs.assign(1, 0); ctx->coffs.assign(1, 0);
-    long long fo = 0, co = 0;
     ctx->max_nx = 0; ctx->max_n = 0;
-    for (size_t q = 0; q < ctx->subs.size(); q++) {
-        const SubBox &b = ctx->subs[q];
-        Task T{};
-        T.nx = b.nx; T.ny = b.ny; T.mx = b.mx; T.my = b.my;
-        T.ix0 = b.ix0; T.iy0 = b.iy0; T.ox0 = b.ox0; T.ox1 = b.ox1; T.oy0 = b.oy0; T.oy1 = b.oy1;
-        T.shape = ctx->sub_shape[q]; T.sub = (int)q; T.rhs = 0;
-        T.foff = fo; T.coff = co;
-        T.tile0 = (int)ctx->h_ftiles.size();
-        for (int r = 0; r < b.ny; r += FINE_ROWS)
-            ctx->h_ftiles.push_back(Tile{(int)q, r, std::min(FINE_ROWS, b.ny - r)});
-        T.ntiles = (int)ctx->h_ftiles.size() - T.tile0;
-        for (int r = 0; r < b.my; r += COARSE_ROWS)
-            ctx->h_ctiles.push_back(Tile{(int)q, r, std::min(COARSE_ROWS, b.my - r)});
-        fo += (long long)b.nx * b.ny;
-        co += (long long)b.mx * b.my;
-        ctx->foffs.push_back(fo); ctx->coffs.push_back(co);
+    for (const SubBox &b : ctx->subs) {
         ctx->max_nx = std::max(ctx->max_nx, b.nx);
         ctx->max_n = std::max(ctx->max_n, b.nx * b.ny);
-        ctx->h_tasks.push_back(T);
     }
-    ctx->ld = fo; ctx->ldc = co;
-    const int nt = (int)ctx->h_tasks.size();
-    CK(ctx->d_tasks.ensure(nt * sizeof(Task)));
-    CK(ctx->d_ftiles.ensure(ctx->h_ftiles.size() * sizeof(Tile)));
-    CK(ctx->d_ctiles.ensure(ctx->h_ctiles.size() * sizeof(Tile)));
-    CK(ctx->d_ones.ensure(nt * sizeof(int)));
-    std::vector<int> ones(nt, 1);
-    CK(cudaMemcpy(ctx->d_tasks.p, ctx->h_tasks.data(), nt * sizeof(Task), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_ftiles.p, ctx->h_ftiles.data(), ctx->h_ftiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_ctiles.p, ctx->h_ctiles.data(), ctx->h_ctiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_ones.p, ones.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+    hdd_status bst = build_tasks(ctx, 1);
+    if (bst != HDD_OK) return bst;
     ctx->E.clear(); ctx->Aex.clear();
     ctx->dd = true;
     return HDD_OK;
@@ -798,7 +801,7 @@ hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev, const hdd
     if (st != HDD_OK) return st;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaMemsetAsync(z_dev, 0, ctx->nglob * sizeof(double2), s));
+    CK(cudaMemsetAsync(z_dev, 0, (size_t)ctx->nrhs * ctx->nglob * sizeof(double2), s));
     st = ras_apply(ctx, (const double2 *)v_dev, (double2 *)z_dev, prm, s, nullptr, nullptr, nullptr, inner_its);
     if (st != HDD_OK) return st;
     CK(cudaStreamSynchronize(s));
@@ -819,111 +822,178 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     const long long n = ctx->nglob;
+    const int nr = ctx->nrhs, ns = (int)ctx->subs.size();
     const int R = std::min(prm->outer_restart, prm->outer_maxit);
     OuterWork &O = ctx->ow;
     const int G = outer_grid(n);
     const int ldp = R + 1;
-    CK(O.V.ensure((size_t)(R + 1) * n * sizeof(double2)));
-    CK(O.Z.ensure((size_t)R * n * sizeof(double2)));
-    CK(O.w.ensure(n * sizeof(double2))); CK(O.r.ensure(n * sizeof(double2)));
-    CK(O.H.ensure((size_t)(R + 1) * R * sizeof(double2)));
-    CK(O.cs.ensure(R * sizeof(double))); CK(O.sn.ensure(R * sizeof(double2)));
-    CK(O.g.ensure((R + 1) * sizeof(double2)));
-    CK(O.h1.ensure((R + 1) * sizeof(double2))); CK(O.h2.ensure((R + 1) * sizeof(double2)));
-    CK(O.y.ensure((R + 1) * sizeof(double2)));
-    CK(O.part.ensure((size_t)G * ldp * sizeof(double2)));
-    CK(O.npart.ensure(G * sizeof(double)));
-    CK(O.hn.ensure(sizeof(double))); CK(O.flag.ensure(sizeof(int))); CK(O.beta.ensure(sizeof(double)));
-    CK(O.hist.ensure((size_t)(prm->outer_maxit + 1) * sizeof(double)));
+    OuterBatch B{nr, n, (long long)nr * n, ldp, G, R, nullptr};
+    CK(O.V.ensure((size_t)(R + 1) * nr * n * sizeof(double2)));
+    CK(O.Z.ensure((size_t)R * nr * n * sizeof(double2)));
+    CK(O.w.ensure((size_t)nr * n * sizeof(double2))); CK(O.r.ensure((size_t)nr * n * sizeof(double2)));
+    CK(O.H.ensure((size_t)nr * (R + 1) * R * sizeof(double2)));
+    CK(O.cs.ensure((size_t)nr * R * sizeof(double))); CK(O.sn.ensure((size_t)nr * R * sizeof(double2)));
+    CK(O.g.ensure((size_t)nr * (R + 1) * sizeof(double2)));
+    CK(O.h1.ensure((size_t)nr * ldp * sizeof(double2))); CK(O.h2.ensure((size_t)nr * ldp * sizeof(double2)));
+    CK(O.y.ensure((size_t)nr * ldp * sizeof(double2)));
+    CK(O.part.ensure((size_t)nr * G * ldp * sizeof(double2)));
+    CK(O.npart.ensure((size_t)nr * G * sizeof(double)));
+    CK(O.hn.ensure(nr * sizeof(double))); CK(O.flag.ensure(nr * sizeof(int))); CK(O.beta.ensure(nr * sizeof(double)));
+    CK(O.fnorm.ensure(nr * sizeof(double))); CK(O.act.ensure(nr * sizeof(int))); CK(O.kcols.ensure(nr * sizeof(int)));
+    CK(O.hist.ensure((size_t)nr * (prm->outer_maxit + 1) * sizeof(double)));
     const size_t osm = (size_t)(R + 1) * sizeof(double2);   // dynamic: h (update), y (axpy, trisolve)
     if (osm + 40 * 1024 > 227 * 1024) FAIL(HDD_ERR_INVALID_ARG, "outer restart %d too long", R);
     CK(set_outer_smem_limits(osm));
-    double2 *V = O.V.as<double2>(), *Zb = O.Z.as<double2>(), *w = O.w.as<double2>(), *r = O.r.as<double2>();
+    double2 *V = O.V.as<double2>(), *Zb = O.Z.as<double2>(), *w = O.w.as<double2>(), *rv = O.r.as<double2>();
     const double2 *f = (const double2 *)f_dev;
     double2 *x = (double2 *)x_dev;
-    CK(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
-    KL(F_OMISC, n * 16, 0, launch_onorm(f, n, O.npart.as<double>(), s));
-    CKL();
-    const double fn = host_norm(ctx, O.npart.as<double>(), n, s, &st);
-    if (st != HDD_OK) return st;
+    const int hstride = prm->outer_maxit + 1;
     hdd_solve_stats loc{};
     hdd_solve_stats &S = stats ? *stats : loc;
     std::memset(&S, 0, sizeof(S));
     ctx->hist.clear();
-    if (!std::isfinite(fn)) FAIL(HDD_ERR_NONFINITE, "right-hand side is not finite");
-    if (fn == 0.0) { S.rel_res_true = 0; S.status = HDD_OK; return HDD_OK; }
+    CK(cudaMemsetAsync(x, 0, (size_t)nr * n * sizeof(double2), s));
+    // ||f_r|| for every RHS (host sums the per-CTA partials in CTA order)
+    std::vector<double> fn(nr), part((size_t)nr * G), beta(nr);
+    KL(F_OMISC, (double)nr * n * 16, 0, launch_onorm(B, f, O.npart.as<double>(), s));
+    CKL();
+    CK(cudaMemcpyAsync(part.data(), O.npart.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->prof.harvest();
+    for (int r = 0; r < nr; r++) {
+        double a = 0;
+        for (int q = 0; q < G; q++) a += part[(size_t)r * G + q];
+        fn[r] = std::sqrt(a);
+        if (!std::isfinite(fn[r])) FAIL(HDD_ERR_NONFINITE, "right-hand side %d is not finite", r);
+    }
+    CK(cudaMemcpyAsync(O.fnorm.p, fn.data(), nr * sizeof(double), cudaMemcpyHostToDevice, s));
+    // per-RHS state: done[r] once its true residual meets the tolerance (zero RHS: at once)
+    std::vector<int> done(nr), act(nr), kcols(nr), its(nr, 0), tmask((size_t)nr * ns);
+    std::vector<double> relres(nr, 0.0);
+    for (int r = 0; r < nr; r++) done[r] = fn[r] == 0.0;
     int total = 0;
     long long inner_tot = 0, hits = 0;
     int inner_mx = 0;
     hdd_status result = HDD_OK;
-    double relres = 1.0;
+    const int *dact = O.act.as<int>();
+    auto push_active = [&]() -> hdd_status {
+        for (int r = 0; r < nr; r++)
+            for (int q = 0; q < ns; q++) tmask[(size_t)r * ns + q] = act[r];
+        CK(cudaMemcpyAsync(O.act.p, act.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->d_mask.p, tmask.data(), tmask.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        return HDD_OK;
+    };
     for (;;) {
-        KL(F_OMISC, 3 * n * 16, 0, launch_gstencil(ctx->st, ctx->N, x, r, f, s));   // r = f - A x
-        KL(F_OMISC, n * 16, 0, launch_onorm(r, n, O.npart.as<double>(), s));
-        KL(F_OMISC, 2 * n * 16, 0, launch_oinit(r, n, O.npart.as<double>(), V, O.g.as<double2>(), R, O.beta.as<double>(), s));
+        // true residuals r = f - A x of the RHS still running, β_r, v_{r,0}, g_r
+        for (int r = 0; r < nr; r++) act[r] = !done[r];
+        if ((st = push_active()) != HDD_OK) return st;
+        B.active = dact;
+        KL(F_OMISC, 3.0 * nr * n * 16, 0, launch_gstencil(ctx->st, ctx->N, x, rv, f, nr, dact, s));
+        KL(F_OMISC, (double)nr * n * 16, 0, launch_onorm(B, rv, O.npart.as<double>(), s));
+        KL(F_OMISC, 2.0 * nr * n * 16, 0, launch_oinit(B, rv, O.npart.as<double>(), V, O.g.as<double2>(), O.beta.as<double>(), s));
         CKL();
-        double beta = 0;
-        CK(cudaMemcpyAsync(&beta, O.beta.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(beta.data(), O.beta.p, nr * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         ctx->prof.harvest();
-        relres = beta / fn;
-        if (!std::isfinite(beta)) { result = HDD_ERR_NONFINITE; ctx->err = "non-finite outer residual"; break; }
-        if (relres <= prm->outer_tol) break;
+        bool any = false;
+        for (int r = 0; r < nr; r++) {
+            if (done[r]) continue;
+            if (!std::isfinite(beta[r])) { result = HDD_ERR_NONFINITE; ctx->err = "non-finite outer residual"; done[r] = 1; continue; }
+            relres[r] = beta[r] / fn[r];
+            if (relres[r] <= prm->outer_tol) { done[r] = 1; continue; }
+            any = true;
+        }
+        if (!any) break;
         if (total >= prm->outer_maxit) { result = HDD_ERR_NO_CONVERGENCE; ctx->err = "outer_maxit reached"; break; }
-        int kcols = 0;
+        for (int r = 0; r < nr; r++) { act[r] = !done[r]; kcols[r] = 0; }
+        if ((st = push_active()) != HDD_OK) return st;
         for (int j = 0; j < R; j++) {
-            double2 *vj = V + (long long)j * n, *zj = Zb + (long long)j * n;
+            double2 *vj = V + (long long)j * B.ld, *zj = Zb + (long long)j * B.ld;
             long long it_tot = 0, it_hits = 0;
             int it_mx = 0;
-            st = ras_apply(ctx, vj, zj, prm, s, &it_tot, &it_mx, &it_hits, nullptr);
+            st = ras_apply(ctx, vj, zj, prm, s, &it_tot, &it_mx, &it_hits, nullptr, ctx->d_mask.as<int>());
             if (st != HDD_OK) return st;
             inner_tot += it_tot; hits += it_hits; inner_mx = std::max(inner_mx, it_mx);
-            const double nv = j + 1;
-            KL(F_OMISC, 2 * n * 16, 0, launch_gstencil(ctx->st, ctx->N, zj, w, nullptr, s));     // w = A z_j
-            KL(F_OCGS, (nv + 1) * n * 16, 8 * nv * n,
-               launch_odots(V, n, j + 1, w, n, O.part.as<double2>(), ldp, s));                 // h1 = V^H w
-            KL(F_OMISC, 0, 0, launch_oreduce(O.part.as<double2>(), G, ldp, j + 1, O.h1.as<double2>(), s));
-            KL(F_OCGS, (nv + 2) * n * 16, 16 * nv * n,
-               launch_oupdate(V, n, j + 1, O.h1.as<double2>(), w, n, O.part.as<double2>(), ldp, nullptr, s));
-            KL(F_OMISC, 0, 0, launch_oreduce(O.part.as<double2>(), G, ldp, j + 1, O.h2.as<double2>(), s));
-            KL(F_OCGS, (nv + 2) * n * 16, 8 * nv * n,
-               launch_oupdate(V, n, j + 1, O.h2.as<double2>(), w, n, nullptr, ldp, O.npart.as<double>(), s));
+            int nact = 0;
+            for (int r = 0; r < nr; r++) nact += act[r];
+            const double nv = j + 1, fa = nact;
+            KL(F_OMISC, 2.0 * fa * n * 16, 0, launch_gstencil(ctx->st, ctx->N, zj, w, nullptr, nr, dact, s));  // w = A z_j
+            KL(F_OCGS, fa * (nv + 1) * n * 16, fa * 8 * nv * n,
+               launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                              // h1 = V^H w
+            KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
+            KL(F_OCGS, fa * (nv + 2) * n * 16, fa * 16 * nv * n,
+               launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), nullptr, s));
+            KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
+            KL(F_OCGS, fa * (nv + 2) * n * 16, fa * 8 * nv * n,
+               launch_oupdate(B, V, j + 1, O.h2.as<double2>(), w, nullptr, O.npart.as<double>(), s));
             KL(F_OMISC, 0, 0,
-               launch_ogivens(O.H.as<double2>(), R + 1, O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(), j,
-                              O.h1.as<double2>(), O.h2.as<double2>(), O.npart.as<double>(), G, prm->outer_tol * fn,
-                              O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>() + total, fn, s));
-            KL(F_OMISC, 2 * n * 16, 0, launch_oscale(V + (long long)(j + 1) * n, w, O.hn.as<double>(), n, s));
+               launch_ogivens(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(), j,
+                              O.h1.as<double2>(), O.h2.as<double2>(), O.npart.as<double>(), O.fnorm.as<double>(),
+                              prm->outer_tol, O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>(), hstride,
+                              total, s));
+            KL(F_OMISC, 2.0 * fa * n * 16, 0,
+               launch_oscale(B, V + (long long)(j + 1) * B.ld, w, O.hn.as<double>(), s));
             CKL();
             total++;
-            kcols = j + 1;
-            int more = 0;
-            CK(cudaMemcpyAsync(ctx->h_counter, O.flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            std::vector<int> flags(nr);
+            CK(cudaMemcpyAsync(flags.data(), O.flag.p, nr * sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             ctx->prof.harvest();
-            more = *ctx->h_counter;
+            bool changed = false, more = false;
+            for (int r = 0; r < nr; r++) {
+                if (!act[r]) continue;
+                its[r]++;
+                kcols[r] = j + 1;
+                if (!flags[r]) { act[r] = 0; changed = true; } else more = true;
+            }
             if (!more || total >= prm->outer_maxit) break;
+            if (changed && (st = push_active()) != HDD_OK) return st;
         }
-        KL(F_OMISC, 0, 0, launch_otrisolve(O.H.as<double2>(), R + 1, O.g.as<double2>(), kcols, O.y.as<double2>(), s));
-        KL(F_OMISC, (kcols + 2.0) * n * 16, 8.0 * kcols * n, launch_oaxpy(O.y.as<double2>(), kcols, Zb, n, x, n, s));
-        CKL();
+        // x_r += Z_r y_r, y_r = H_r⁻¹ g_r, for every RHS that ran in this cycle
+        int kmax = 0;
+        for (int r = 0; r < nr; r++) kmax = std::max(kmax, kcols[r]);
+        CK(cudaMemcpyAsync(O.kcols.p, kcols.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (kmax > 0) {
+            KL(F_OMISC, 0, 0, launch_otrisolve(B, O.H.as<double2>(), O.g.as<double2>(), O.kcols.as<int>(), kmax,
+                                               O.y.as<double2>(), s));
+            KL(F_OMISC, (kmax + 2.0) * nr * n * 16, 8.0 * kmax * nr * n,
+               launch_oaxpy(B, O.y.as<double2>(), O.kcols.as<int>(), kmax, Zb, x, s));
+            CKL();
+        }
     }
     CK(cudaStreamSynchronize(s));
     ctx->prof.harvest();
     auto t1 = std::chrono::steady_clock::now();
-    ctx->hist.resize(total);
-    if (total) CK(cudaMemcpy(ctx->hist.data(), O.hist.p, total * sizeof(double), cudaMemcpyDeviceToHost));
+    // residual history of the first RHS (per-RHS histories stay on the device)
+    const int n0 = its[0];
+    ctx->hist.resize(n0);
+    if (n0) CK(cudaMemcpy(ctx->hist.data(), O.hist.p, n0 * sizeof(double), cudaMemcpyDeviceToHost));
+    double worst = 0;
+    for (int r = 0; r < nr; r++) worst = std::max(worst, relres[r]);
     S.outer_its = total;
     S.status = result;
-    S.rel_res_true = relres;
+    S.rel_res_true = worst;
     S.inner_its_total = inner_tot;
-    S.inner_its_avg = total ? (double)inner_tot / ((double)total * ctx->subs.size()) : 0.0;
+    long long solves = 0;
+    for (int r = 0; r < nr; r++) solves += (long long)its[r] * ns;
+    S.inner_its_avg = solves ? (double)inner_tot / (double)solves : 0.0;
     S.inner_its_max = inner_mx;
     S.inner_maxit_hits = hits;
     S.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    S.n_history = total;
+    S.n_history = n0;
     S.res_history = ctx->hist.data();
     return result;
 }
+
+hdd_status hdd_setup_batch(hdd_ctx *ctx, int nrhs) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (nrhs < 1 || nrhs > 4096) FAIL(HDD_ERR_INVALID_ARG, "nrhs must be in 1..4096");
+    CK(cudaSetDevice(ctx->device));
+    return build_tasks(ctx, nrhs);
+}
+
+int hdd_num_rhs(const hdd_ctx *ctx) { return ctx && ctx->dd ? ctx->nrhs : 0; }
 
 hdd_status hdd_profile(hdd_ctx *ctx, int enable) {
     if (!ctx) return HDD_ERR_INVALID_ARG;

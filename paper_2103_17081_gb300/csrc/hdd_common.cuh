@@ -120,7 +120,7 @@ template <typename R> struct LocalArgs {
 template <typename R> void launch_restrict(const LocalArgs<R> &a, const double2 *glob, long long nglob,
                                            c2<R> *out, const int *flag, cudaStream_t s);
 template <typename R> void launch_scatter(const LocalArgs<R> &a, const c2<R> *x, double2 *glob,
-                                          long long nglob, cudaStream_t s);
+                                          long long nglob, const int *flag, cudaStream_t s);
 template <typename R> void launch_local_A(const LocalArgs<R> &a, const c2<R> *in, c2<R> *out,
                                           const c2<R> *f, const int *flag, cudaStream_t s);
 template <typename R> void launch_zt(const LocalArgs<R> &a, const c2<R> *in, double2 *y, int apply_A,
@@ -149,7 +149,7 @@ template <typename R> void launch_update_u(const LocalArgs<R> &a, const InnerSta
 template <typename R> cudaError_t set_local_smem_limits(size_t bytes);
 template <typename R> void launch_coarse_combine(const LocalArgs<R> &a, const InnerState<R> &S,
                                                  int restart, const double2 *sbuf, double2 *sc,
-                                                 cudaStream_t s);
+                                                 const int *flag, cudaStream_t s);
 size_t local_max_dynamic_smem(int max_nx, int bytes_per_c);
 void launch_cast(long long n, const void *in, int in_double, void *out, int out_double, cudaStream_t s);
 constexpr int LOCAL_LDP = MAX_RESTART + 2;   // partial-sum slots per fine tile
@@ -168,28 +168,37 @@ void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes
                         int use_fine, const int *flag, int maxlen, int maxK, cudaStream_t s);
 cudaError_t set_block_solve_smem(int maxlen, int maxK);
 
-// global FP64 (outer FGMRES)
+// global FP64 (outer FGMRES), batched over right-hand sides
+struct OuterBatch {
+    int nrhs;              // independent right-hand sides
+    long long n;           // entries per global vector
+    long long ld;          // stride between basis vectors of one RHS (= nrhs·n)
+    int ldp;               // reduction slots per CTA and per RHS (>= R+1)
+    int G;                 // CTAs per RHS of the chunked reductions
+    int R;                 // Hessenberg columns (restart length)
+    const int *active;     // per-RHS flag, or null for all
+};
 int outer_grid(long long n);
-void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f,
-                     cudaStream_t s);
+void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f, int nrhs,
+                     const int *active, cudaStream_t s);
 void launch_build_rhs(int N, double h, int diag, int npts, const double *pts, int nb,
                       const double *bumps, double2 *f, cudaStream_t s);
-void launch_odots(const double2 *V, long long ld, int nv, const double2 *w, long long n,
-                  double2 *part, int ldp, cudaStream_t s);
-void launch_oupdate(const double2 *V, long long ld, int nv, const double2 *h, double2 *w, long long n,
-                    double2 *part_dots, int ldp, double *part_norm, cudaStream_t s);
-void launch_onorm(const double2 *x, long long n, double *part, cudaStream_t s);
-void launch_oreduce(const double2 *part, int nparts, int ldp, int nv, double2 *out, cudaStream_t s);
-void launch_ogivens(double2 *H, long long ldh, double *cs, double2 *sn, double2 *g, int j,
-                    const double2 *h1, const double2 *h2, const double *npart, int nparts,
-                    double tol_abs, double *hn_out, int *flag, double *hist, double fnorm,
-                    cudaStream_t s);
-void launch_oscale(double2 *out, const double2 *w, const double *hn, long long n, cudaStream_t s);
-void launch_otrisolve(const double2 *H, long long ldh, const double2 *g, int k, double2 *y,
-                      cudaStream_t s);
-void launch_oaxpy(const double2 *y, int k, const double2 *Zb, long long ld, double2 *x, long long n,
+void launch_odots(const OuterBatch &B, const double2 *V, int nv, const double2 *w, double2 *part,
                   cudaStream_t s);
-void launch_oinit(const double2 *r, long long n, const double *npart, double2 *v0, double2 *g, int R,
+void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2 *h, double2 *w,
+                    double2 *part_dots, double *part_norm, cudaStream_t s);
+void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s);
+void launch_oreduce(const OuterBatch &B, const double2 *part, int nv, double2 *out, cudaStream_t s);
+void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, int j,
+                    const double2 *h1, const double2 *h2, const double *npart, const double *fnorm,
+                    double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
+                    cudaStream_t s);
+void launch_oscale(const OuterBatch &B, double2 *out, const double2 *w, const double *hn, cudaStream_t s);
+void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, const int *kcols, int kmax,
+                      double2 *y, cudaStream_t s);
+void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int kmax, const double2 *Zb,
+                  double2 *x, cudaStream_t s);
+void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, double2 *g,
                   double *beta_out, cudaStream_t s);
 cudaError_t set_outer_smem_limits(size_t bytes);
 

@@ -99,8 +99,9 @@ k_restrict(LocalArgs<R> a, int gw, long long nglob, const double2 *__restrict__ 
 template <typename R>
 __global__ void __launch_bounds__(LOCAL_THREADS)
 k_scatter(LocalArgs<R> a, int gw, long long nglob, const c2<R> *__restrict__ x,
-          double2 *__restrict__ glob) {
+          double2 *__restrict__ glob, const int *__restrict__ flag) {
     const Tile tl = a.ftiles[blockIdx.x];
+    if (flag && !flag[tl.task]) return;
     const Task T = a.tasks[tl.task];
     const int cnt = tl.nr * T.nx;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -535,9 +536,10 @@ __device__ void solve_small(const InnerState<R> &S, int restart, int t, int k, c
 template <typename R>
 __global__ void __launch_bounds__(LOCAL_THREADS)
 k_coarse_combine(LocalArgs<R> a, InnerState<R> S, int restart, const double2 *__restrict__ sbuf,
-                 double2 *__restrict__ sc) {
+                 double2 *__restrict__ sc, const int *__restrict__ flag) {
     __shared__ c2<R> y[MAX_RESTART];
     const Tile tl = a.ctiles[blockIdx.x];
+    if (flag && !flag[tl.task]) return;
     const Task T = a.tasks[tl.task];
     const int k = S.kcols[tl.task];
     if (threadIdx.x == 0) solve_small<R>(S, restart, tl.task, k, y);
@@ -605,8 +607,8 @@ void launch_restrict(const LocalArgs<R> &a, const double2 *glob, long long nglob
 }
 template <typename R>
 void launch_scatter(const LocalArgs<R> &a, const c2<R> *x, double2 *glob, long long nglob,
-                    cudaStream_t s) {
-    k_scatter<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, a.gw, nglob, x, glob);
+                    const int *flag, cudaStream_t s) {
+    k_scatter<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, a.gw, nglob, x, glob, flag);
 }
 template <typename R>
 void launch_local_A(const LocalArgs<R> &a, const c2<R> *in, c2<R> *out, const c2<R> *f,
@@ -672,8 +674,8 @@ void launch_update_u(const LocalArgs<R> &a, const InnerState<R> &S, int restart,
 }
 template <typename R>
 void launch_coarse_combine(const LocalArgs<R> &a, const InnerState<R> &S, int restart,
-                           const double2 *sbuf, double2 *sc, cudaStream_t s) {
-    k_coarse_combine<R><<<a.nctiles, LOCAL_THREADS, 0, s>>>(a, S, restart, sbuf, sc);
+                           const double2 *sbuf, double2 *sc, const int *flag, cudaStream_t s) {
+    k_coarse_combine<R><<<a.nctiles, LOCAL_THREADS, 0, s>>>(a, S, restart, sbuf, sc, flag);
 }
 void launch_cast(long long n, const void *in, int in_double, void *out, int out_double,
                  cudaStream_t s) {
@@ -710,7 +712,7 @@ template <typename R> cudaError_t set_local_smem_limits(size_t bytes) {
 
 #define INST(R)                                                                                         \
     template void launch_restrict<R>(const LocalArgs<R> &, const double2 *, long long, c2<R> *, const int *, cudaStream_t); \
-    template void launch_scatter<R>(const LocalArgs<R> &, const c2<R> *, double2 *, long long, cudaStream_t); \
+    template void launch_scatter<R>(const LocalArgs<R> &, const c2<R> *, double2 *, long long, const int *, cudaStream_t); \
     template void launch_local_A<R>(const LocalArgs<R> &, const c2<R> *, c2<R> *, const c2<R> *, const int *, cudaStream_t); \
     template void launch_zt<R>(const LocalArgs<R> &, const c2<R> *, double2 *, int, const int *, cudaStream_t); \
     template void launch_z<R>(const LocalArgs<R> &, const double2 *, const c2<R> *, c2<R> *, const int *, cudaStream_t); \
@@ -720,7 +722,7 @@ template <typename R> cudaError_t set_local_smem_limits(size_t bytes) {
     template void launch_init_cycle<R>(const LocalArgs<R> &, const InnerState<R> &, int, c2<R> *, const c2<R> *, const int *, int *, int *, R, int, int, cudaStream_t); \
     template void launch_update_u<R>(const LocalArgs<R> &, const InnerState<R> &, int, c2<R> *, const c2<R> *, const int *, int *, int *, int, cudaStream_t); \
     template cudaError_t set_local_smem_limits<R>(size_t); \
-    template void launch_coarse_combine<R>(const LocalArgs<R> &, const InnerState<R> &, int, const double2 *, double2 *, cudaStream_t);
+    template void launch_coarse_combine<R>(const LocalArgs<R> &, const InnerState<R> &, int, const double2 *, double2 *, const int *, cudaStream_t);
 
 INST(float)
 INST(double)

@@ -17,11 +17,16 @@ int outer_grid(long long n) {
     return (int)(g > OUTER_CTAS ? g : OUTER_CTAS);
 }
 
-// y = A x (f == nullptr) or y = f - A x on the (N-1)² interior grid, zero Dirichlet values.
+// y = A x (f == nullptr) or y = f - A x on the (N-1)² interior grid, zero Dirichlet values;
+// blockIdx.y selects the right-hand side (vectors of n entries, consecutive).
 __global__ void k_gstencil(Stencil st, int N, const double2 *__restrict__ x, double2 *__restrict__ y,
-                           const double2 *__restrict__ f) {
+                           const double2 *__restrict__ f, const int *__restrict__ active) {
+    if (active && !active[blockIdx.y]) return;
     const int w = N - 1;
     const long long n = (long long)w * w;
+    x += blockIdx.y * n;
+    y += blockIdx.y * n;
+    if (f) f += blockIdx.y * n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int ix = (int)(i % w), iy = (int)(i / w);
@@ -80,10 +85,16 @@ __device__ __forceinline__ void chunk_of(long long n, long long &b, long long &e
     e = b + per < n ? b + per : n;
 }
 
+// ------------------------------------------------------------------------------------------
+// Outer FGMRES kernels, batched over independent right-hand sides (blockIdx.y = r).  Layout
+// (OuterBatch): basis vector l of RHS r at V + l·ld + r·n (ld = nrhs·n), per-RHS work vectors at
+// w + r·n, per-RHS reduction partials at part + r·G·ldp, Hessenberg of RHS r at
+// H + r·(R+1)·R (column-major, leading dimension R+1).  A RHS with active[r] == 0 is skipped.
+// ------------------------------------------------------------------------------------------
+
 // Each CTA owns one contiguous chunk of the vectors (at most OCH entries).  The chunk of w is
 // staged in shared memory once; then warp q of the CTA forms the partial dots of vectors
 // l = q, q + 8, ... over the chunk with shuffle reductions only (no block barrier per vector).
-
 __device__ __forceinline__ void warp_dots(const double2 *__restrict__ V, long long ld, int nv,
                                           const double2 *__restrict__ ws, long long b, int len,
                                           double2 *__restrict__ part, int ldp) {
@@ -103,29 +114,34 @@ __device__ __forceinline__ void warp_dots(const double2 *__restrict__ V, long lo
     }
 }
 
-// Partial dots part[cta][l] = Σ_{chunk} conj(V_l) w, l < nv.
+// Partial dots part[r][cta][l] = Σ_{chunk} conj(V_{r,l}) w_r, l < nv.
 __global__ void __launch_bounds__(OT)
-k_odots(const double2 *__restrict__ V, long long ld, int nv, const double2 *__restrict__ w,
-        long long n, double2 *__restrict__ part, int ldp) {
+k_odots(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__restrict__ w,
+        double2 *__restrict__ part) {
     __shared__ double2 ws[OCH];
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    V += r * B.n; w += r * B.n; part += (long long)r * B.G * B.ldp;
     long long b, e;
-    chunk_of(n, b, e);
+    chunk_of(B.n, b, e);
     const int len = (int)(e > b ? e - b : 0);
     for (int i = threadIdx.x; i < len; i += OT) ws[i] = w[b + i];
     __syncthreads();
-    warp_dots(V, ld, nv, ws, b, len, part, ldp);
+    warp_dots(V, B.ld, nv, ws, b, len, part, B.ldp);
 }
 
-// w -= Σ_l h_l V_l; then (part_dots != null) partial dots V^H w, else partial ||w||².
+// w_r -= Σ_l h_{r,l} V_{r,l}; then (part_dots != null) partial dots V_r^H w_r, else ||w_r||².
 __global__ void __launch_bounds__(OT)
-k_oupdate(const double2 *__restrict__ V, long long ld, int nv, const double2 *__restrict__ h,
-          double2 *__restrict__ w, long long n, double2 *__restrict__ part_dots, int ldp,
-          double *__restrict__ part_norm) {
+k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__restrict__ h,
+          double2 *__restrict__ w, double2 *__restrict__ part_dots, double *__restrict__ part_norm) {
     extern __shared__ double2 hs[];
     __shared__ double2 ws[OCH];
     __shared__ double red[OT / 32];
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    V += r * B.n; w += r * B.n; h += (long long)r * B.ldp;
     long long b, e;
-    chunk_of(n, b, e);
+    chunk_of(B.n, b, e);
     const int len = (int)(e > b ? e - b : 0);
     for (int l = threadIdx.x; l < nv; l += OT) hs[l] = h[l];
     __syncthreads();
@@ -135,10 +151,10 @@ k_oupdate(const double2 *__restrict__ V, long long ld, int nv, const double2 *__
         const double2 *vp = V + b + i;
         int l = 0;
         for (; l + 1 < nv; l += 2) {                // two independent accumulation chains
-            caxpy_neg<double>(x0, hs[l], vp[(long long)l * ld]);
-            caxpy_neg<double>(x1, hs[l + 1], vp[(long long)(l + 1) * ld]);
+            caxpy_neg<double>(x0, hs[l], vp[(long long)l * B.ld]);
+            caxpy_neg<double>(x1, hs[l + 1], vp[(long long)(l + 1) * B.ld]);
         }
-        if (l < nv) caxpy_neg<double>(x0, hs[l], vp[(long long)l * ld]);
+        if (l < nv) caxpy_neg<double>(x0, hs[l], vp[(long long)l * B.ld]);
         x0.x += x1.x; x0.y += x1.y;
         w[b + i] = x0;
         ws[i] = x0;
@@ -146,7 +162,7 @@ k_oupdate(const double2 *__restrict__ V, long long ld, int nv, const double2 *__
     }
     if (part_dots) {
         __syncthreads();
-        warp_dots(V, ld, nv, ws, b, len, part_dots, ldp);
+        warp_dots(V, B.ld, nv, ws, b, len, part_dots + (long long)r * B.G * B.ldp, B.ldp);
     } else {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int o = 16; o > 0; o >>= 1) nrm += shfl_xor(nrm, o);
@@ -155,16 +171,19 @@ k_oupdate(const double2 *__restrict__ V, long long ld, int nv, const double2 *__
         if (threadIdx.x == 0) {
             double s = 0.0;
             for (int q = 0; q < OT / 32; q++) s += red[q];
-            part_norm[blockIdx.x] = s;
+            part_norm[(long long)r * B.G + blockIdx.x] = s;
         }
     }
 }
 
-// Partial ||x||² per CTA.
-__global__ void __launch_bounds__(OT) k_onorm(const double2 *__restrict__ x, long long n, double *__restrict__ part) {
+// Partial ||x_r||² per CTA: part[r][cta].
+__global__ void __launch_bounds__(OT) k_onorm(OuterBatch B, const double2 *__restrict__ x, double *__restrict__ part) {
     __shared__ double red[OT / 32];
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    x += r * B.n;
     long long b, e;
-    chunk_of(n, b, e);
+    chunk_of(B.n, b, e);
     double s = 0.0;
     for (long long i = b + threadIdx.x; i < e; i += OT) s = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, s));
     for (int o = 16; o > 0; o >>= 1) s += shfl_xor(s, o);
@@ -173,19 +192,22 @@ __global__ void __launch_bounds__(OT) k_onorm(const double2 *__restrict__ x, lon
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int q = 0; q < OT / 32; q++) t += red[q];
-        part[blockIdx.x] = t;
+        part[(long long)r * B.G + blockIdx.x] = t;
     }
 }
 
-// out[l] = Σ_q part[q][l]: one warp per l, lane i adds q = i, i+32, ... in order, then a fixed
-// shuffle tree (deterministic).
-__global__ void k_oreduce(const double2 *__restrict__ part, int nparts, int ldp, int nv, double2 *__restrict__ out) {
+// out[r][l] = Σ_q part[r][q][l]: one warp per l, lane i adds q = i, i+32, ... in order, then a
+// fixed shuffle tree (deterministic).
+__global__ void k_oreduce(OuterBatch B, const double2 *__restrict__ part, int nv, double2 *__restrict__ out) {
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
     const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (l >= nv) return;
+    part += (long long)r * B.G * B.ldp;
     double2 s = make_double2(0.0, 0.0);
-    for (int q = lane; q < nparts; q += 32) { double2 v = part[(long long)q * ldp + l]; s.x += v.x; s.y += v.y; }
+    for (int q = lane; q < B.G; q += 32) { double2 v = part[(long long)q * B.ldp + l]; s.x += v.x; s.y += v.y; }
     for (int o = 16; o > 0; o >>= 1) { s.x += shfl_xor(s.x, o); s.y += shfl_xor(s.y, o); }
-    if (lane == 0) out[l] = s;
+    if (lane == 0) out[(long long)r * B.ldp + l] = s;
 }
 
 __device__ void zgivens(double2 a, double2 b, double &c, double2 &s, double2 &r) {
@@ -200,19 +222,26 @@ __device__ void zgivens(double2 a, double2 b, double &c, double2 &s, double2 &r)
     r = make_double2(ph.x * t, ph.y * t);
 }
 
-// Outer Arnoldi column j: h = h1 + h2 (CGS2), h_{j+1,j} = sqrt(Σ norm partials); rotate with the
-// previous rotations, form rotation j, update g; flag = 1 while |g_{j+1}| > tol_abs and hn > 0.
-__global__ void k_ogivens(double2 *__restrict__ H, long long ldh, double *__restrict__ cs,
+// Outer Arnoldi column j of every active RHS (one thread each): h = h1 + h2 (CGS2),
+// h_{j+1,j} = sqrt(Σ norm partials); previous rotations, rotation j, g update.
+// flag[r] = 1 while |g_{j+1}| > tol·||f_r|| and h_{j+1,j} > 0; hist[r·hstride + it] records
+// |g_{j+1}|/||f_r||.
+__global__ void k_ogivens(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs,
                           double2 *__restrict__ sn, double2 *__restrict__ g, int j,
                           const double2 *__restrict__ h1, const double2 *__restrict__ h2,
-                          const double *__restrict__ npart, int nparts, double tol_abs,
-                          double *__restrict__ hn_out, int *__restrict__ flag,
-                          double *__restrict__ hist, double fnorm) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                          const double *__restrict__ npart, const double *__restrict__ fnorm,
+                          double tol, double *__restrict__ hn_out, int *__restrict__ flag,
+                          double *__restrict__ hist, int hstride, int it) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= B.nrhs || (B.active && !B.active[r])) return;
+    const int R = B.R;
+    H += (long long)r * (R + 1) * R; cs += (long long)r * R; sn += (long long)r * R;
+    g += (long long)r * (R + 1); h1 += (long long)r * B.ldp; h2 += (long long)r * B.ldp;
+    npart += (long long)r * B.G;
     double s2 = 0.0;
-    for (int q = 0; q < nparts; q++) s2 += npart[q];
+    for (int q = 0; q < B.G; q++) s2 += npart[q];
     const double hn = sqrt(s2);
-    double2 *hc = H + (long long)j * ldh;
+    double2 *hc = H + (long long)j * (R + 1);
     for (int l = 0; l <= j; l++) hc[l] = make_double2(h1[l].x + h2[l].x, h1[l].y + h2[l].y);
     for (int l = 0; l < j; l++) {
         double2 x = hc[l], y = hc[l + 1], sx = sn[l];
@@ -221,32 +250,41 @@ __global__ void k_ogivens(double2 *__restrict__ H, long long ldh, double *__rest
         hc[l] = make_double2(cs[l] * x.x + a.x, cs[l] * x.y + a.y);
         hc[l + 1] = make_double2(cs[l] * y.x - bq.x, cs[l] * y.y - bq.y);
     }
-    double c; double2 s, r;
-    zgivens(hc[j], make_double2(hn, 0.0), c, s, r);
+    double c; double2 s, rr;
+    zgivens(hc[j], make_double2(hn, 0.0), c, s, rr);
     cs[j] = c; sn[j] = s;
-    hc[j] = r;
+    hc[j] = rr;
     double2 gj = g[j];
     g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
     g[j] = make_double2(c * gj.x, c * gj.y);
     const double res = hypot(g[j + 1].x, g[j + 1].y);
-    *hn_out = hn;
-    *hist = res / fnorm;                       // caller passes the slot of this iteration
-    *flag = (res > tol_abs && hn > 0.0) ? 1 : 0;
+    hn_out[r] = hn;
+    hist[(long long)r * hstride + it] = res / fnorm[r];
+    flag[r] = (res > tol * fnorm[r] && hn > 0.0) ? 1 : 0;
 }
 
-// out = w / hn (hn read from device memory)
-__global__ void k_oscale(double2 *__restrict__ out, const double2 *__restrict__ w, const double *__restrict__ hn, long long n) {
-    const double h = *hn;
+// V_{r,j+1} = w_r / hn_r
+__global__ void k_oscale(OuterBatch B, double2 *__restrict__ out, const double2 *__restrict__ w,
+                         const double *__restrict__ hn) {
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    const double h = hn[r];
     if (!(h > 0.0)) return;
+    out += r * B.n; w += r * B.n;
     const double inv = 1.0 / h;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x)
         out[i] = make_double2(w[i].x * inv, w[i].y * inv);
 }
 
-// y = H(0:k,0:k)⁻¹ g by column-oriented back substitution (one CTA).
-__global__ void k_otrisolve(const double2 *__restrict__ H, long long ldh, const double2 *__restrict__ g,
-                            int k, double2 *__restrict__ y) {
+// y_r = H_r(0:k_r,0:k_r)⁻¹ g_r by column-oriented back substitution (one CTA per RHS).
+__global__ void k_otrisolve(OuterBatch B, const double2 *__restrict__ H, const double2 *__restrict__ g,
+                            const int *__restrict__ kcols, double2 *__restrict__ y) {
     extern __shared__ double2 rhs[];
+    const int r = blockIdx.x;
+    const int k = kcols[r];
+    if (k <= 0) return;
+    const long long ldh = B.R + 1;
+    H += (long long)r * (B.R + 1) * B.R; g += (long long)r * (B.R + 1); y += (long long)r * B.ldp;
     for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = g[i];
     __syncthreads();
     for (int i = k - 1; i >= 0; i--) {
@@ -255,44 +293,51 @@ __global__ void k_otrisolve(const double2 *__restrict__ H, long long ldh, const 
         const double den = d.x * d.x + d.y * d.y;
         const double2 yi = make_double2((si.x * d.x + si.y * d.y) / den, (si.y * d.x - si.x * d.y) / den);
         __syncthreads();
-        for (int r = threadIdx.x; r < i; r += blockDim.x) caxpy_neg<double>(rhs[r], yi, H[(long long)i * ldh + r]);
+        for (int q = threadIdx.x; q < i; q += blockDim.x) caxpy_neg<double>(rhs[q], yi, H[(long long)i * ldh + q]);
         if (threadIdx.x == 0) y[i] = yi;
         __syncthreads();
     }
 }
 
-// x += Σ_{l<k} y_l Z_l
-__global__ void k_oaxpy(const double2 *__restrict__ y, int k, const double2 *__restrict__ Zb, long long ld,
-                        double2 *__restrict__ x, long long n) {
+// x_r += Σ_{l<k_r} y_{r,l} Z_{r,l}
+__global__ void k_oaxpy(OuterBatch B, const double2 *__restrict__ y, const int *__restrict__ kcols,
+                        const double2 *__restrict__ Zb, double2 *__restrict__ x) {
     extern __shared__ double2 ys[];
+    const int r = blockIdx.y;
+    const int k = kcols[r];
+    if (k <= 0) return;
+    y += (long long)r * B.ldp; Zb += r * B.n; x += r * B.n;
     for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = y[l];
     __syncthreads();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
         double2 acc = x[i];
-        for (int l = 0; l < k; l++) caxpy<double>(acc, ys[l], Zb[(long long)l * ld + i]);
+        for (int l = 0; l < k; l++) caxpy<double>(acc, ys[l], Zb[(long long)l * B.ld + i]);
         x[i] = acc;
     }
 }
 
-// Cycle start: β = sqrt(Σ partials), v0 = r/β, g = [β, 0, ..., 0] (R+1 entries).
-__global__ void k_oinit(const double2 *__restrict__ r, long long n, const double *__restrict__ npart,
-                        int nparts, double2 *__restrict__ v0, double2 *__restrict__ g, int R,
-                        double *__restrict__ beta_out) {
+// Cycle start for every active RHS: β_r = sqrt(Σ partials), v_{r,0} = r_r/β_r,
+// g_r = [β_r, 0, ..., 0] (R+1 entries).
+__global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const double *__restrict__ npart,
+                        double2 *__restrict__ V, double2 *__restrict__ g, double *__restrict__ beta_out) {
     __shared__ double beta_s;
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    rv += r * B.n; npart += (long long)r * B.G; double2 *v0 = V + r * B.n; g += (long long)r * (B.R + 1);
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int q = 0; q < nparts; q++) s += npart[q];
+        for (int q = 0; q < B.G; q++) s += npart[q];
         beta_s = sqrt(s);
-        if (blockIdx.x == 0) *beta_out = beta_s;
+        if (blockIdx.x == 0) beta_out[r] = beta_s;
     }
     __syncthreads();
     const double beta = beta_s;
     if (blockIdx.x == 0)
-        for (int l = threadIdx.x; l <= R; l += blockDim.x) g[l] = make_double2(l == 0 ? beta : 0.0, 0.0);
+        for (int l = threadIdx.x; l <= B.R; l += blockDim.x) g[l] = make_double2(l == 0 ? beta : 0.0, 0.0);
     if (!(beta > 0.0)) return;
     const double inv = 1.0 / beta;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        v0[i] = make_double2(r[i].x * inv, r[i].y * inv);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x)
+        v0[i] = make_double2(rv[i].x * inv, rv[i].y * inv);
 }
 
 static int grid_for(long long n, int threads) {
@@ -301,46 +346,50 @@ static int grid_for(long long n, int threads) {
     return g < 1 ? 1 : (int)g;
 }
 
-void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f, cudaStream_t s) {
+void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f, int nrhs,
+                     const int *active, cudaStream_t s) {
     long long n = (long long)(N - 1) * (N - 1);
-    k_gstencil<<<grid_for(n, 256), 256, 0, s>>>(st, N, x, y, f);
+    k_gstencil<<<dim3(grid_for(n, 256), nrhs), 256, 0, s>>>(st, N, x, y, f, active);
 }
 void launch_build_rhs(int N, double h, int diag, int npts, const double *pts, int nb, const double *bumps,
                       double2 *f, cudaStream_t s) {
     long long n = (long long)(N - 1) * (N - 1);
     k_build_rhs<<<grid_for(n, 256), 256, 0, s>>>(N, h, diag, npts, pts, nb, bumps, f);
 }
-void launch_odots(const double2 *V, long long ld, int nv, const double2 *w, long long n, double2 *part,
-                  int ldp, cudaStream_t s) {
-    k_odots<<<outer_grid(n), OT, 0, s>>>(V, ld, nv, w, n, part, ldp);
+void launch_odots(const OuterBatch &B, const double2 *V, int nv, const double2 *w, double2 *part, cudaStream_t s) {
+    k_odots<<<dim3(B.G, B.nrhs), OT, 0, s>>>(B, V, nv, w, part);
 }
-void launch_oupdate(const double2 *V, long long ld, int nv, const double2 *h, double2 *w, long long n,
-                    double2 *part_dots, int ldp, double *part_norm, cudaStream_t s) {
-    k_oupdate<<<outer_grid(n), OT, (size_t)nv * sizeof(double2), s>>>(V, ld, nv, h, w, n, part_dots, ldp, part_norm);
+void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2 *h, double2 *w,
+                    double2 *part_dots, double *part_norm, cudaStream_t s) {
+    k_oupdate<<<dim3(B.G, B.nrhs), OT, (size_t)nv * sizeof(double2), s>>>(B, V, nv, h, w, part_dots, part_norm);
 }
-void launch_onorm(const double2 *x, long long n, double *part, cudaStream_t s) {
-    k_onorm<<<outer_grid(n), OT, 0, s>>>(x, n, part);
+void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s) {
+    k_onorm<<<dim3(B.G, B.nrhs), OT, 0, s>>>(B, x, part);
 }
-void launch_oreduce(const double2 *part, int nparts, int ldp, int nv, double2 *out, cudaStream_t s) {
-    k_oreduce<<<(nv + 7) / 8, 256, 0, s>>>(part, nparts, ldp, nv, out);
+void launch_oreduce(const OuterBatch &B, const double2 *part, int nv, double2 *out, cudaStream_t s) {
+    k_oreduce<<<dim3((nv + 7) / 8, B.nrhs), 256, 0, s>>>(B, part, nv, out);
 }
-void launch_ogivens(double2 *H, long long ldh, double *cs, double2 *sn, double2 *g, int j, const double2 *h1,
-                    const double2 *h2, const double *npart, int nparts, double tol_abs, double *hn_out, int *flag,
-                    double *hist, double fnorm, cudaStream_t s) {
-    k_ogivens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, j, h1, h2, npart, nparts, tol_abs, hn_out, flag, hist, fnorm);
+void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, int j,
+                    const double2 *h1, const double2 *h2, const double *npart, const double *fnorm,
+                    double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
+                    cudaStream_t s) {
+    k_ogivens<<<(B.nrhs + 31) / 32, 32, 0, s>>>(B, H, cs, sn, g, j, h1, h2, npart, fnorm, tol, hn_out, flag,
+                                                hist, hstride, it);
 }
-void launch_oscale(double2 *out, const double2 *w, const double *hn, long long n, cudaStream_t s) {
-    k_oscale<<<grid_for(n, 256), 256, 0, s>>>(out, w, hn, n);
+void launch_oscale(const OuterBatch &B, double2 *out, const double2 *w, const double *hn, cudaStream_t s) {
+    k_oscale<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, out, w, hn);
 }
-void launch_otrisolve(const double2 *H, long long ldh, const double2 *g, int k, double2 *y, cudaStream_t s) {
-    k_otrisolve<<<1, 256, (size_t)k * sizeof(double2), s>>>(H, ldh, g, k, y);
+void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, const int *kcols, int kmax,
+                      double2 *y, cudaStream_t s) {
+    k_otrisolve<<<B.nrhs, 256, (size_t)kmax * sizeof(double2), s>>>(B, H, g, kcols, y);
 }
-void launch_oaxpy(const double2 *y, int k, const double2 *Zb, long long ld, double2 *x, long long n, cudaStream_t s) {
-    k_oaxpy<<<grid_for(n, 256), 256, (size_t)k * sizeof(double2), s>>>(y, k, Zb, ld, x, n);
+void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int kmax, const double2 *Zb,
+                  double2 *x, cudaStream_t s) {
+    k_oaxpy<<<dim3(grid_for(B.n, 256), B.nrhs), 256, (size_t)kmax * sizeof(double2), s>>>(B, y, kcols, Zb, x);
 }
-void launch_oinit(const double2 *r, long long n, const double *npart, double2 *v0, double2 *g, int R,
+void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, double2 *g,
                   double *beta_out, cudaStream_t s) {
-    k_oinit<<<grid_for(n, 256), 256, 0, s>>>(r, n, npart, outer_grid(n), v0, g, R, beta_out);
+    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, g, beta_out);
 }
 cudaError_t set_outer_smem_limits(size_t bytes) {
     cudaError_t e;

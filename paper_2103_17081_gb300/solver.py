@@ -30,6 +30,7 @@ class Solver:
         self.N = None
         self.k = None
         self.nsub = 0
+        self.nrhs = 1
 
     # -- plumbing ------------------------------------------------------------------------------
     def _check(self, rc: int, where: str, ctx: bool = True):
@@ -80,6 +81,13 @@ class Solver:
                      C.cast(ay, C.POINTER(C.c_int)) if ay is not None else None)
         self._check(self._L.hdd_setup_dd(self._h, C.byref(p)), "hdd_setup_dd")
         self.nsub = self._L.hdd_num_subdomains(self._h)
+        self.nrhs = 1
+        return self
+
+    def setup_batch(self, nrhs: int):
+        """Solve `nrhs` right-hand sides per call (vectors stored RHS-major)."""
+        self._check(self._L.hdd_setup_batch(self._h, int(nrhs)), "hdd_setup_batch")
+        self.nrhs = self._L.hdd_num_rhs(self._h)
         return self
 
     def setup_deflation(self, stream=None):
@@ -94,6 +102,8 @@ class Solver:
     def from_workload(cls, w, device: int = 0, deflation: bool = True, exact: bool = False):
         s = cls(device).assemble(w.k, w.N)
         s.setup_dd(w.Sx, w.Sy, w.overlap, w.ifx, w.ify)
+        if w.nrhs > 1:
+            s.setup_batch(w.nrhs)
         if deflation:
             s.setup_deflation()
         if exact:
@@ -144,11 +154,19 @@ class Solver:
         return SolveParams(outer_tol, outer_restart, outer_maxit, inner_tol, inner_restart,
                            inner_maxit, inner_prec)
 
+    def build_rhs_batch(self, specs):
+        """Load vectors of several RHSSpecs, stacked RHS-major in one tensor."""
+        f = self.empty(len(specs) * self.n)
+        for r, spec in enumerate(specs):
+            self.build_rhs(spec, out=f[r * self.n:(r + 1) * self.n])
+        return f
+
     def solve(self, f, out=None, stream=None, raise_on_error=True, **kw):
         prm = self.params(**kw)
-        x = self.empty() if out is None else out
+        nt = self.nrhs * self.n
+        x = self.empty(nt) if out is None else out
         st = SolveStats()
-        rc = self._L.hdd_solve(self._h, self._vec(f, self.n, "f"), self._vec(x, self.n, "x"),
+        rc = self._L.hdd_solve(self._h, self._vec(f, nt, "f"), self._vec(x, nt, "x"),
                                C.byref(prm), C.byref(st), self._stream(stream))
         stats = {k: getattr(st, k) for k, _ in SolveStats._fields_ if k != "res_history"}
         stats["res_history"] = [st.res_history[i] for i in range(st.n_history)]
@@ -159,19 +177,22 @@ class Solver:
 
     def ras_apply(self, v, out=None, stream=None, **kw):
         prm = self.params(**kw)
-        z = self.empty() if out is None else out
-        its = (C.c_int * max(1, self.nsub))()
-        self._check(self._L.hdd_ras_apply(self._h, self._vec(v, self.n, "v"), self._vec(z, self.n, "z"),
+        nt = self.nrhs * self.n
+        z = self.empty(nt) if out is None else out
+        its = (C.c_int * max(1, self.nsub * self.nrhs))()
+        self._check(self._L.hdd_ras_apply(self._h, self._vec(v, nt, "v"), self._vec(z, nt, "z"),
                                           C.byref(prm), its, self._stream(stream)), "hdd_ras_apply")
-        return z, list(its)[: self.nsub]
+        return z, list(its)[: self.nsub * self.nrhs]
 
-    def local_op(self, op: str, x, prec: int = 128, out_len=None, stream=None):
+    def local_op(self, op: str, x, prec: int = 128, stream=None):
+        """Apply one local operator to packed vectors of every (subdomain, RHS) task."""
         fo, co = self.offsets()
-        nout = {"A": fo[-1], "Z": fo[-1], "Zt": co[-1], "Einv": co[-1], "PA": fo[-1], "R": fo[-1],
-                "Ainv": fo[-1]}[op]
-        out = self.empty(nout if out_len is None else out_len)
-        self._check(self._L.hdd_local_op(self._h, LOCAL_OPS[op], int(prec), self._vec(x), self._vec(out),
-                                         self._stream(stream)), "hdd_local_op")
+        F, Cc = self.nrhs * fo[-1], self.nrhs * co[-1]
+        nin = {"A": F, "Z": Cc, "Zt": F, "Einv": Cc, "PA": F, "R": self.nrhs * self.n, "Ainv": F}[op]
+        nout = {"A": F, "Z": F, "Zt": Cc, "Einv": Cc, "PA": F, "R": F, "Ainv": F}[op]
+        out = self.empty(nout)
+        self._check(self._L.hdd_local_op(self._h, LOCAL_OPS[op], int(prec), self._vec(x, nin, "x"),
+                                         self._vec(out), self._stream(stream)), "hdd_local_op")
         return out
 
     # -- profiling -----------------------------------------------------------------------------

@@ -235,3 +235,58 @@ def test_k200_full_solve_against_stored_oracle(prec):
     assert np.linalg.norm(xs - xr) <= 1e-5 * np.linalg.norm(xr)
     assert abs(float(torch.linalg.vector_norm(x)) - ref["x_norm2"]) <= 1e-5 * ref["x_norm2"]
     assert float(x.imag.abs().max()) == 0.0
+
+
+def _specs(n, seed):
+    rng = W.SplitMix64(seed)
+    return [W.RHSSpec(W.point_sources(1, rng, 0.1, 0.9)) for _ in range(n)]
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_batched_rhs_match_single_rhs_runs(oracle_mod, prec):
+    """nrhs right-hand sides in one batch give the per-RHS results of separate runs."""
+    from paper_2103_17081_gb300 import Solver
+    torch = _torch()
+    w = RAGGED[1]
+    specs = _specs(3, 5)
+    s1 = Solver.from_workload(w)
+    sb = Solver.from_workload(w).setup_batch(3)
+    fb = sb.build_rhs_batch(specs)
+    n = sb.n
+    zb, itb = sb.ras_apply(fb / torch.linalg.vector_norm(fb), inner_tol=1e-2, inner_prec=prec)
+    xb, stb = sb.solve(fb, inner_prec=prec)
+    p = oracle_mod.from_workload(w)
+    for r, spec in enumerate(specs):
+        fr = fb[r * n:(r + 1) * n].clone()
+        z1, it1 = s1.ras_apply(fr / torch.linalg.vector_norm(fb), inner_tol=1e-2, inner_prec=prec)
+        assert _rel(zb[r * n:(r + 1) * n].cpu().numpy(), z1.cpu().numpy()) <= 1e-14
+        assert itb[r * s1.nsub:(r + 1) * s1.nsub] == it1
+        x1, st1 = s1.solve(fr, inner_prec=prec)
+        assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), x1.cpu().numpy()) <= 1e-12
+        xo, so = p.solve(p.rhs(spec))
+        assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), xo) < 1e-5
+        assert st1["outer_its"] <= 1.1 * so["outer_its"] + 1
+    assert stb["rel_res_true"] <= 1e-6 * 1.0001
+
+
+def test_k400x32_batched_ras_apply_full_size(oracle_mod):
+    """Jittered 16x16 decomposition of N=1280, k=400, 32 point-source right-hand sides: one RAS
+    application of all 8192 (subdomain, RHS) local solves in one batch, complex64 inner; RHS 0
+    and 21 compared with the oracle."""
+    from paper_2103_17081_gb300 import Solver
+    torch = _torch()
+    w = W.make("k400x32")
+    s = Solver.from_workload(w)
+    assert s.nrhs == 32
+    f = s.build_rhs_batch(w.rhs)
+    n = s.n
+    v = f.clone()
+    for r in range(32):
+        v[r * n:(r + 1) * n] /= torch.linalg.vector_norm(v[r * n:(r + 1) * n])
+    z, its = s.ras_apply(v, inner_tol=1e-2, inner_prec=64)
+    p = oracle_mod.from_workload(w)
+    for r in (0, 21):
+        zo, sto = p.ras_apply(v[r * n:(r + 1) * n].cpu().numpy(), 1e-2)
+        assert _rel(z[r * n:(r + 1) * n].cpu().numpy(), zo) < 1e-4
+        got = sum(its[r * s.nsub:(r + 1) * s.nsub])
+        assert abs(got - sto["inner_its_total"]) <= 0.1 * sto["inner_its_total"]
