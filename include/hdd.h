@@ -152,6 +152,8 @@ typedef struct {
     int inner_maxit;     /* total inner iterations per local solve                          */
     int inner_prec;      /* 64: complex64 inner solves with FP32 accumulation;              */
                          /* 128: complex128 inner solves.  Coarse E and outer: FP64 always  */
+    int warm_start;      /* 1: start every local solve from the learned guess (hdd_cnn_*);  */
+                         /* 0: from zero.  The tolerance stays relative to ||P f̃||          */
 } hdd_solve_params;
 
 typedef struct {
@@ -198,6 +200,36 @@ hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void
                         void *stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Learned warm start (no counterpart in the paper).  A 4-layer 3x3 convolutional network with  */
+/* 32 channels, BF16 weights and FP32 accumulation maps a restricted right-hand side f̃ of a     */
+/* subdomain (channels Re f̃/σ, Im f̃/σ, k·h with σ = RMS(f̃), zero padding at the box edge) to an */
+/* initial guess ũ₀ = σ·(a + i b) for its deflated GMRES.  Layers 4→32, 32→32, 32→32 (ReLU)    */
+/* and 32→2; parameters are one FP32 array of hdd_cnn_num_params() values, per layer the       */
+/* weights W[cout][ky·3+kx][cin] then the biases (the first layer's fourth input channel is    */
+/* zero).  Training minimises the mean over subdomains of the relative deflated residual the   */
+/* local GMRES starts from, ||P_j(f̂ - A_j(a + i b))||² / ||P_j f̂||² with f̂ = f̃/σ (Eq. 4), with */
+/* Adam (β = 0.9, 0.999, ε = 1e-8) on FP32 master weights.  Images are the packed local       */
+/* vectors of hdd_get_offsets (complex128 here); the solver applies the network in its own   */
+/* precision.  Because FGMRES is flexible, any guess keeps the outer tolerance exact.         */
+/* ---------------------------------------------------------------------------------------- */
+int hdd_cnn_num_params(void);
+/* Load parameters (host FP32 array), reset Adam's moments. */
+hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params);
+/* Read the FP32 master parameters. */
+hdd_status hdd_cnn_get_params(hdd_ctx *ctx, float *params);
+/* x0 = guess for every packed right-hand side f (complex128 packed local vectors). */
+hdd_status hdd_cnn_forward(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream);
+/* Training loss of the batch f (every packed subdomain image) and, if grad != NULL, its
+ * gradient w.r.t. every parameter (host FP32 array); synchronises the device.  Needs
+ * hdd_setup_deflation (the loss applies P_j). */
+hdd_status hdd_cnn_loss_grad(hdd_ctx *ctx, const void *f_dev, double *loss, float *grad);
+/* One Adam step with learning rate lr on the batch f; *loss receives the loss before the step. */
+hdd_status hdd_cnn_train_step(hdd_ctx *ctx, const void *f_dev, float lr, double *loss, void *stream);
+/* Copy outer Krylov vector j of the last solve (nrhs global vectors) to v_dev: the restricted
+ * Arnoldi vectors are the right-hand sides the local solves see (training inputs). */
+hdd_status hdd_get_outer_vector(hdd_ctx *ctx, int j, void *v_dev, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Profiling.  With profiling on, every kernel launch is bracketed by a pair of CUDA events on */
 /* the launching stream; durations are summed per kernel family together with the family's   */
 /* algorithmic bytes (data the step must read and write once) and floating-point operations. */
@@ -208,7 +240,7 @@ typedef struct {
     double ms;           /* sum of per-launch event durations                         */
     double bytes;        /* algorithmic bytes, summed over launches                   */
     double flops;        /* algorithmic floating-point operations, summed            */
-    int bound;           /* 0: memory-bandwidth bound, 1: FP64-arithmetic bound        */
+    int bound;           /* 0: memory bandwidth, 1: FP64 arithmetic, 2: FP32 arithmetic  */
 } hdd_kernel_stat;
 
 /* Synchronise the device, clear the counters and switch event timing on (1) or off (0). */

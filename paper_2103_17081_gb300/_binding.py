@@ -17,7 +17,8 @@ SYMBOLS = ["hdd_create", "hdd_destroy", "hdd_status_str", "hdd_last_error", "hdd
            "hdd_num_subdomains", "hdd_get_offsets", "hdd_setup_deflation", "hdd_setup_exact",
            "hdd_solve", "hdd_ras_apply", "hdd_local_op", "hdd_profile", "hdd_profile_count",
            "hdd_profile_get", "hdd_launch_count", "hdd_apply_PA_noalloc", "hdd_setup_batch",
-           "hdd_num_rhs"]
+           "hdd_num_rhs", "hdd_cnn_num_params", "hdd_cnn_set_params", "hdd_cnn_get_params",
+           "hdd_cnn_forward", "hdd_cnn_loss_grad", "hdd_cnn_train_step", "hdd_get_outer_vector"]
 
 
 def status_name(code: int) -> str:
@@ -42,7 +43,7 @@ class DDParams(C.Structure):
 class SolveParams(C.Structure):
     _fields_ = [("outer_tol", C.c_double), ("outer_restart", C.c_int), ("outer_maxit", C.c_int),
                 ("inner_tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
-                ("inner_prec", C.c_int)]
+                ("inner_prec", C.c_int), ("warm_start", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -117,6 +118,21 @@ def lib(build_if_missing: bool = True):
     L.hdd_setup_batch.restype = I
     L.hdd_num_rhs.argtypes = [P]
     L.hdd_num_rhs.restype = I
+    F = C.POINTER(C.c_float)
+    L.hdd_cnn_num_params.argtypes = []
+    L.hdd_cnn_num_params.restype = I
+    L.hdd_cnn_set_params.argtypes = [P, F]
+    L.hdd_cnn_set_params.restype = I
+    L.hdd_cnn_get_params.argtypes = [P, F]
+    L.hdd_cnn_get_params.restype = I
+    L.hdd_cnn_forward.argtypes = [P, V, V, V]
+    L.hdd_cnn_forward.restype = I
+    L.hdd_cnn_loss_grad.argtypes = [P, V, C.POINTER(D), F]
+    L.hdd_cnn_loss_grad.restype = I
+    L.hdd_cnn_train_step.argtypes = [P, V, C.c_float, C.POINTER(D), V]
+    L.hdd_cnn_train_step.restype = I
+    L.hdd_get_outer_vector.argtypes = [P, I, V, V]
+    L.hdd_get_outer_vector.restype = I
     L.hdd_apply_PA_noalloc.argtypes = [P, V, V, V]
     L.hdd_apply_PA_noalloc.restype = I
     _lib = L

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhdd.so")
-SOURCES = ["hdd_api.cu", "kernels_local.cu", "kernels_coarse.cu", "kernels_outer.cu"]
+SOURCES = ["hdd_api.cu", "kernels_local.cu", "kernels_coarse.cu", "kernels_outer.cu", "kernels_cnn.cu"]
 HEADERS = [os.path.join(CSRC, "hdd_common.cuh"), os.path.join(ROOT, "include", "hdd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -55,11 +55,11 @@ template <typename R> struct InnerWork {   // inner GMRES buffers for one precis
 
 // Kernel families timed by the profiler (CUDA events around every launch on the launching
 // stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
-enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, NFAM };
+enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, NFAM };
 const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
                               "local_cgs2_update", "local_givens_normalize", "local_misc",
-                              "outer_cgs2_fp64", "outer_misc_fp64"};
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0};
+                              "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn"};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2};
 
 struct Prof {
     bool on = false;
@@ -91,6 +91,13 @@ struct Prof {
         }
         pend.clear();
     }
+};
+
+struct CnnState {            // learned warm start: parameters, Adam moments, activations
+    bool ready = false;
+    int step = 0;
+    DevMem P, Pb, M, Vm, G, sigma, X0, A1, A2, A3, A4, dA4, Rr, dB1, dB2, part, lpart;
+    DevMem Fh, Q, T2, Yc, Sc, Pf, Pr, scale, tloss;   // deflated loss: f̂, P r, Pᵀ P r, coarse, partials
 };
 
 struct OuterWork {
@@ -126,6 +133,7 @@ struct hdd_ctx {
     InnerWork<float> w32;
     InnerWork<double> w64;
     OuterWork ow;
+    CnnState cnn;
     DevMem tmp_a, tmp_b, tmp_c;                // staging for test hooks
     int *h_counter = nullptr;                  // pinned
     DevMem d_counter;
@@ -339,6 +347,113 @@ void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *ou
                        F.maxK, s);
 }
 
+// ---- learned warm start ---------------------------------------------------------------------
+hdd_status cnn_buffers(hdd_ctx *ctx) {
+    CnnState &C = ctx->cnn;
+    const long long ld = ctx->ld;
+    const int nt = (int)ctx->h_tasks.size(), nft = (int)ctx->h_ftiles.size();
+    CK(C.P.ensure(CNN_NPARAM * sizeof(float))); CK(C.Pb.ensure(CNN_NPARAM * sizeof(__nv_bfloat16)));
+    CK(C.M.ensure(CNN_NPARAM * sizeof(float))); CK(C.Vm.ensure(CNN_NPARAM * sizeof(float)));
+    CK(C.G.ensure(CNN_NPARAM * sizeof(float)));
+    CK(C.sigma.ensure(nt * sizeof(float)));
+    CK(C.X0.ensure(ld * 4 * sizeof(float)));
+    CK(C.A1.ensure(ld * 32 * sizeof(float))); CK(C.A2.ensure(ld * 32 * sizeof(float)));
+    CK(C.A3.ensure(ld * 32 * sizeof(float))); CK(C.A4.ensure(ld * 2 * sizeof(float)));
+    CK(C.dA4.ensure(ld * 2 * sizeof(float))); CK(C.Rr.ensure(ld * 2 * sizeof(float)));
+    CK(C.dB1.ensure(ld * 32 * sizeof(float))); CK(C.dB2.ensure(ld * 32 * sizeof(float)));
+    CK(C.part.ensure((size_t)nft * (CNN_OFF[2] - CNN_OFF[1]) * sizeof(float)));
+    CK(C.lpart.ensure(nft * sizeof(float)));
+    CK(C.Fh.ensure(ld * sizeof(float2))); CK(C.Q.ensure(ld * sizeof(float2))); CK(C.T2.ensure(ld * sizeof(float2)));
+    CK(C.Yc.ensure(ctx->ldc * sizeof(double2))); CK(C.Sc.ensure(ctx->ldc * sizeof(double2)));
+    CK(C.Pf.ensure((size_t)nft * LOCAL_LDP * sizeof(float2))); CK(C.Pr.ensure((size_t)nft * LOCAL_LDP * sizeof(float2)));
+    CK(C.scale.ensure(nt * sizeof(float))); CK(C.tloss.ensure(nt * sizeof(float)));
+    return HDD_OK;
+}
+
+// forward pass: input image from the packed right-hand sides, 4 conv layers; A4 holds the output
+template <typename R>
+void cnn_forward(hdd_ctx *ctx, const c2<R> *f, cudaStream_t s) {
+    CnnState &C = ctx->cnn;
+    const Task *T = ctx->d_tasks.as<Task>();
+    const Tile *ft = ctx->d_ftiles.as<Tile>();
+    const int nt = (int)ctx->h_tasks.size(), nft = (int)ctx->h_ftiles.size();
+    const __nv_bfloat16 *Wb = C.Pb.as<__nv_bfloat16>();
+    const float *P = C.P.as<float>();
+    const int CIN[4] = {4, 32, 32, 32}, COUT[4] = {32, 32, 32, 2};
+    float *acts[5] = {C.X0.as<float>(), C.A1.as<float>(), C.A2.as<float>(), C.A3.as<float>(), C.A4.as<float>()};
+    const double px = (double)ctx->ld;
+    KL(F_CNN, px * (8 + 16), 0, launch_cnn_input<R>(T, nt, f, (float)(ctx->k * ctx->h), C.sigma.as<float>(), acts[0],
+                                                      C.Fh.as<float2>(), s));
+    for (int l = 0; l < 4; l++) {
+        const int nw = COUT[l] * 9 * CIN[l];
+        KL(F_CNN, px * 4.0 * (CIN[l] + COUT[l]), 2.0 * px * nw,
+           launch_conv_fwd(l, T, ft, nft, Wb + CNN_OFF[l], P + CNN_OFF[l] + nw, acts[l], acts[l + 1], s));
+    }
+}
+
+// mean over the batch of ||f̃/σ - A(a + i b)||²/n_t and its gradient w.r.t. every parameter
+// (into C.G, FP32); returns the loss (synchronises).
+template <typename R>
+hdd_status cnn_loss_grad(hdd_ctx *ctx, const c2<R> *f, double *loss, cudaStream_t s) {
+    CnnState &C = ctx->cnn;
+    const Task *T = ctx->d_tasks.as<Task>();
+    const Tile *ft = ctx->d_ftiles.as<Tile>();
+    const int nt = (int)ctx->h_tasks.size(), nft = (int)ctx->h_ftiles.size();
+    if (!ctx->E.ready) FAIL(HDD_ERR_STATE, "the training loss needs hdd_setup_deflation");
+    cnn_forward<R>(ctx, f, s);
+    // deflated residuals in FP32 with the solver's own kernels (coarse solves in FP64):
+    //   P f̂, r = f̂ - A y, q = P r, Pᵀ q = q - Z E⁻¹ Zᵀ A q; dL/dy_t = scale_t · A Pᵀ q
+    LocalArgs<float> a = local_args<float>(ctx);
+    const size_t lsm = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(float2));
+    if (lsm > 48 * 1024) CK(set_local_smem_limits<float>(lsm));
+    float2 *Fh = C.Fh.as<float2>(), *Q = C.Q.as<float2>(), *T2 = C.T2.as<float2>();
+    float2 *Rr = reinterpret_cast<float2 *>(C.Rr.as<float>());
+    double2 *Yc = C.Yc.as<double2>(), *Sc = C.Sc.as<double2>();
+    KL(F_CNN, 0, 0, launch_zt<float>(a, Fh, Yc, 0, nullptr, s));
+    band_solve(ctx, ctx->E, Yc, Sc, false, nullptr, s);
+    KL(F_CNN, 0, 0, launch_prolong_stencil<float>(a, 1, Fh, Sc, T2, nullptr, 0, C.Pf.as<float2>(), nullptr, s));
+    KL(F_CNN, 0, 0, launch_cnn_resid(T, ft, nft, ctx->st, C.X0.as<float>(), C.A4.as<float>(), C.Rr.as<float>(),
+                                       C.lpart.as<float>(), s));
+    KL(F_CNN, 0, 0, launch_zt<float>(a, Rr, Yc, 0, nullptr, s));
+    band_solve(ctx, ctx->E, Yc, Sc, false, nullptr, s);
+    KL(F_CNN, 0, 0, launch_prolong_stencil<float>(a, 1, Rr, Sc, Q, nullptr, 0, C.Pr.as<float2>(), nullptr, s));
+    KL(F_CNN, 0, 0, launch_zt<float>(a, Q, Yc, 1, nullptr, s));
+    band_solve(ctx, ctx->E, Yc, Sc, false, nullptr, s);
+    KL(F_CNN, 0, 0, launch_z<float>(a, Sc, Q, T2, nullptr, s, -1.0f));
+    KL(F_CNN, 0, 0, launch_cnn_task_scale(T, nt, C.Pf.as<float2>(), C.scale.as<float>(), s));
+    KL(F_CNN, 0, 0, launch_cnn_task_loss(T, nt, C.Pr.as<float2>(), C.Pf.as<float2>(), C.tloss.as<float>(), s));
+    KL(F_CNN, 0, 0, launch_cnn_out_grad(T, ft, nft, ctx->st, reinterpret_cast<float *>(T2), C.scale.as<float>(),
+                                          C.dA4.as<float>(), s));
+    const __nv_bfloat16 *Wb = C.Pb.as<__nv_bfloat16>();
+    float *G = C.G.as<float>(), *part = C.part.as<float>();
+    const int CIN[4] = {4, 32, 32, 32}, COUT[4] = {32, 32, 32, 2};
+    float *acts[5] = {C.X0.as<float>(), C.A1.as<float>(), C.A2.as<float>(), C.A3.as<float>(), C.A4.as<float>()};
+    // dY of layer 3 is dA4; walk back, alternating the two gradient buffers
+    const float *dY = C.dA4.as<float>();
+    float *bufs[2] = {C.dB1.as<float>(), C.dB2.as<float>()};
+    for (int l = 3; l >= 0; l--) {
+        const float *mask = l == 3 ? nullptr : acts[l + 1];            // ReLU of this layer's output
+        const int nw = CNN_OFF[l + 1] - CNN_OFF[l];
+        KL(F_CNN, 0, 0, launch_conv_bwd_w(l, T, ft, nft, dY, mask, acts[l], part, s));
+        KL(F_CNN, 0, 0, launch_sum_partials(part, nft, nw, 1.0f, G + CNN_OFF[l], s));
+        if (l > 0) {
+            float *dX = bufs[l & 1];
+            KL(F_CNN, 0, 0, launch_conv_bwd_data(l, T, ft, nft, Wb + CNN_OFF[l], dY, mask, dX, s));
+            dY = dX;
+        }
+        (void)CIN; (void)COUT;
+    }
+    CKL();
+    std::vector<float> lt(nt);
+    CK(cudaMemcpyAsync(lt.data(), C.tloss.p, nt * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->prof.harvest();
+    double L = 0;
+    for (int t = 0; t < nt; t++) L += lt[t];
+    if (loss) *loss = L / nt;
+    return HDD_OK;
+}
+
 template <typename R> InnerWork<R> &work(hdd_ctx *ctx);
 template <> InnerWork<float> &work<float>(hdd_ctx *ctx) { return ctx->w32; }
 template <> InnerWork<double> &work<double>(hdd_ctx *ctx) { return ctx->w64; }
@@ -385,6 +500,7 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     const int RST = prm->inner_restart;
     hdd_status st = ensure_inner<R>(ctx, RST);
     if (st != HDD_OK) return st;
+    if (prm->warm_start && ctx->cnn.ready && (st = cnn_buffers(ctx)) != HDD_OK) return st;
     InnerWork<R> &W = work<R>(ctx);
     InnerState<R> S = inner_state<R>(W);
     LocalArgs<R> a = local_args<R>(ctx);
@@ -409,13 +525,30 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     CK(cudaMemsetAsync(W.kcols.p, 0, nt * sizeof(int), s));
     CK(cudaMemsetAsync(act[0], 0, nt * sizeof(int), s));
     CK(cudaMemsetAsync(act[1], 0, nt * sizeof(int), s));
-    CK(cudaMemsetAsync(u, 0, ld * sizeof(c2<R>), s));
-    // first cycle from ũ = 0: r0 = P f̃ = f̃ - A Z E⁻¹ Zᵀ f̃, and ref = ||P f̃||
-    KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, y, 0, mask, s));
-    band_solve(ctx, ctx->E, y, sc, false, mask, s);
-    KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, V, nullptr, 0, p3, mask, s));
+    const bool warm = prm->warm_start && ctx->cnn.ready;
+    if (!warm) {
+        CK(cudaMemsetAsync(u, 0, ld * sizeof(c2<R>), s));
+        // first cycle from ũ = 0: r0 = P f̃ = f̃ - A Z E⁻¹ Zᵀ f̃, and ref = ||P f̃||
+        KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, y, 0, mask, s));
+        band_solve(ctx, ctx->E, y, sc, false, mask, s);
+        KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, V, nullptr, 0, p3, mask, s));
+    } else {
+        // learned initial guess ũ₀ = σ·CNN(f̃/σ); ref = ||P f̃|| and r0 = P(f̃ - A ũ₀)
+        cnn_forward<R>(ctx, f, s);
+        KL(F_CNN, 0, 0, launch_cnn_output<R>(ctx->d_tasks.as<Task>(), ctx->d_ftiles.as<Tile>(),
+                                               (int)ctx->h_ftiles.size(), ctx->cnn.sigma.as<float>(),
+                                               ctx->cnn.A4.as<float>(), u, mask, s));
+        KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, y, 0, mask, s));
+        band_solve(ctx, ctx->E, y, sc, false, mask, s);
+        KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, x, nullptr, 0, p3, mask, s));
+        KL(F_LMISC, 0, 0, launch_set_ref<R>(a, S, p3, mask, s));
+        KL(F_LMISC, 3 * ld * cs, 0, launch_local_A<R>(a, u, t, f, mask, s));
+        KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, t, y, 0, mask, s));
+        band_solve(ctx, ctx->E, y, sc, false, mask, s);
+        KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, t, sc, V, nullptr, 0, p3, mask, s));
+    }
     CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
-    KL(F_LMISC, 2 * ld * cs, 0, launch_init_cycle<R>(a, S, RST, V, p3, all, act[0], cnt, tol, maxit, 1, s));
+    KL(F_LMISC, 2 * ld * cs, 0, launch_init_cycle<R>(a, S, RST, V, p3, all, act[0], cnt, tol, maxit, warm ? 0 : 1, s));
     CKL();
     CK(cudaMemcpyAsync(cyc, all, nt * sizeof(int), cudaMemcpyDeviceToDevice, s));
     int cur = 0, nact = 0;
@@ -1024,6 +1157,95 @@ hdd_status hdd_profile_get(hdd_ctx *ctx, int i, hdd_kernel_stat *out) {
 }
 
 long long hdd_launch_count(const hdd_ctx *ctx) { return ctx ? ctx->prof.launches : 0; }
+
+int hdd_cnn_num_params(void) { return CNN_NPARAM; }
+
+hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (!params) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
+    for (int i = 0; i < CNN_NPARAM; i++)
+        if (!std::isfinite(params[i])) FAIL(HDD_ERR_NONFINITE, "parameter %d is not finite", i);
+    CK(cudaSetDevice(ctx->device));
+    hdd_status st = cnn_buffers(ctx);
+    if (st != HDD_OK) return st;
+    CnnState &C = ctx->cnn;
+    CK(cudaMemcpy(C.P.p, params, CNN_NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemset(C.M.p, 0, CNN_NPARAM * sizeof(float)));
+    CK(cudaMemset(C.Vm.p, 0, CNN_NPARAM * sizeof(float)));
+    launch_to_bf16(CNN_NPARAM, C.P.as<float>(), C.Pb.as<__nv_bfloat16>(), 0);
+    CKL();
+    CK(cudaDeviceSynchronize());
+    C.step = 0;
+    C.ready = true;
+    return HDD_OK;
+}
+
+hdd_status hdd_cnn_get_params(hdd_ctx *ctx, float *params) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
+    if (!params) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpy(params, ctx->cnn.P.p, CNN_NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    return HDD_OK;
+}
+
+hdd_status hdd_cnn_forward(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
+    if (!f_dev || !x0_dev || f_dev == x0_dev || !aligned16(f_dev) || !aligned16(x0_dev))
+        FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    hdd_status st = cnn_buffers(ctx);
+    if (st != HDD_OK) return st;
+    cnn_forward<double>(ctx, (const double2 *)f_dev, s);
+    KL(F_CNN, 0, 0, launch_cnn_output<double>(ctx->d_tasks.as<Task>(), ctx->d_ftiles.as<Tile>(),
+                                                (int)ctx->h_ftiles.size(), ctx->cnn.sigma.as<float>(),
+                                                ctx->cnn.A4.as<float>(), (double2 *)x0_dev, nullptr, s));
+    CKL();
+    return HDD_OK;
+}
+
+hdd_status hdd_cnn_loss_grad(hdd_ctx *ctx, const void *f_dev, double *loss, float *grad) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
+    if (!f_dev || !aligned16(f_dev)) FAIL(HDD_ERR_INVALID_ARG, "bad vector argument");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = 0;
+    hdd_status st = cnn_loss_grad<double>(ctx, (const double2 *)f_dev, loss, s);
+    if (st != HDD_OK) return st;
+    if (grad) CK(cudaMemcpy(grad, ctx->cnn.G.p, CNN_NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    return HDD_OK;
+}
+
+hdd_status hdd_cnn_train_step(hdd_ctx *ctx, const void *f_dev, float lr, double *loss, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
+    if (!f_dev || !aligned16(f_dev) || !(lr > 0)) FAIL(HDD_ERR_INVALID_ARG, "bad arguments");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    hdd_status st = cnn_loss_grad<double>(ctx, (const double2 *)f_dev, loss, s);
+    if (st != HDD_OK) return st;
+    CnnState &C = ctx->cnn;
+    C.step++;
+    KL(F_CNN, 0, 0, launch_adam(CNN_NPARAM, C.P.as<float>(), C.G.as<float>(), C.M.as<float>(), C.Vm.as<float>(),
+                                  C.Pb.as<__nv_bfloat16>(), lr, 0.9f, 0.999f, 1e-8f, C.step, s));
+    CKL();
+    return HDD_OK;
+}
+
+hdd_status hdd_get_outer_vector(hdd_ctx *ctx, int j, void *v_dev, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->ow.V.p) FAIL(HDD_ERR_STATE, "no solve has run");
+    if (j < 0 || !v_dev || !aligned16(v_dev)) FAIL(HDD_ERR_INVALID_ARG, "bad arguments");
+    const size_t bytes = (size_t)ctx->nrhs * ctx->nglob * sizeof(double2);
+    if ((size_t)(j + 1) * bytes > ctx->ow.V.bytes) FAIL(HDD_ERR_INVALID_ARG, "basis vector %d not stored", j);
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpyAsync(v_dev, ctx->ow.V.as<char>() + (size_t)j * bytes, bytes, cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    return HDD_OK;
+}
 
 hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;

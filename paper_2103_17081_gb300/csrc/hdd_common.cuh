@@ -125,8 +125,9 @@ template <typename R> void launch_local_A(const LocalArgs<R> &a, const c2<R> *in
                                           const c2<R> *f, const int *flag, cudaStream_t s);
 template <typename R> void launch_zt(const LocalArgs<R> &a, const c2<R> *in, double2 *y, int apply_A,
                                      const int *flag, cudaStream_t s);
+// out = add + sign · Z s
 template <typename R> void launch_z(const LocalArgs<R> &a, const double2 *sc, const c2<R> *add,
-                                    c2<R> *out, const int *flag, cudaStream_t s);
+                                    c2<R> *out, const int *flag, cudaStream_t s, R sign = 1);
 template <typename R> void launch_prolong_stencil(const LocalArgs<R> &a, int mode, const c2<R> *in,
                                                   const double2 *sc, c2<R> *out, const c2<R> *V,
                                                   int nv, c2<R> *part, const int *flag,
@@ -147,6 +148,8 @@ template <typename R> void launch_update_u(const LocalArgs<R> &a, const InnerSta
                                            c2<R> *u, const c2<R> *V, const int *flag, int *rs_out,
                                            int *counter, int maxit, cudaStream_t s);
 template <typename R> cudaError_t set_local_smem_limits(size_t bytes);
+template <typename R> void launch_set_ref(const LocalArgs<R> &a, const InnerState<R> &S, const c2<R> *p3,
+                                          const int *flag, cudaStream_t s);
 template <typename R> void launch_coarse_combine(const LocalArgs<R> &a, const InnerState<R> &S,
                                                  int restart, const double2 *sbuf, double2 *sc,
                                                  const int *flag, cudaStream_t s);
@@ -167,6 +170,36 @@ void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes
                         const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
                         int use_fine, const int *flag, int maxlen, int maxK, cudaStream_t s);
 cudaError_t set_block_solve_smem(int maxlen, int maxK);
+
+// learned warm start (kernels_cnn.cu)
+constexpr int CNN_NPARAM = 20258;          // 4 conv3x3 layers: 4->32, 32->32, 32->32, 32->2
+constexpr int CNN_OFF[5] = {0, 1184, 10432, 19680, 20258};   // per layer: W (COUT x 9 x CIN), b
+}  // namespace hdd
+#include <cuda_bf16.h>
+namespace hdd {
+template <typename R> void launch_cnn_input(const Task *tasks, int ntasks, const c2<R> *f, float kh,
+                                            float *sigma, float *X0, float2 *Fh, cudaStream_t s);
+void launch_cnn_task_scale(const Task *tasks, int ntasks, const float2 *p3f, float *scale, cudaStream_t s);
+void launch_cnn_task_loss(const Task *tasks, int ntasks, const float2 *p3r, const float2 *p3f, float *loss,
+                          cudaStream_t s);
+template <typename R> void launch_cnn_output(const Task *tasks, const Tile *tiles, int ntiles,
+                                             const float *sigma, const float *Y4, c2<R> *x0,
+                                             const int *flag, cudaStream_t s);
+void launch_conv_fwd(int layer, const Task *tasks, const Tile *tiles, int ntiles, const __nv_bfloat16 *W,
+                     const float *b, const float *X, float *Y, cudaStream_t s);
+void launch_conv_bwd_data(int layer, const Task *tasks, const Tile *tiles, int ntiles,
+                          const __nv_bfloat16 *W, const float *dY, const float *act_out, float *dX,
+                          cudaStream_t s);
+void launch_conv_bwd_w(int layer, const Task *tasks, const Tile *tiles, int ntiles, const float *dY,
+                       const float *act_out, const float *X, float *part, cudaStream_t s);
+void launch_sum_partials(const float *part, int ntiles, int nw, float scale, float *grad, cudaStream_t s);
+void launch_cnn_resid(const Task *tasks, const Tile *tiles, int ntiles, const Stencil &st, const float *X0,
+                      const float *Y4, float *Rr, float *lpart, cudaStream_t s);
+void launch_cnn_out_grad(const Task *tasks, const Tile *tiles, int ntiles, const Stencil &st, const float *Rr,
+                         const float *scale, float *dY4, cudaStream_t s);
+void launch_adam(int n, float *p, const float *g, float *m, float *v, __nv_bfloat16 *pb, float lr, float b1,
+                 float b2, float eps, int step, cudaStream_t s);
+void launch_to_bf16(int n, const float *p, __nv_bfloat16 *pb, cudaStream_t s);
 
 // global FP64 (outer FGMRES), batched over right-hand sides
 struct OuterBatch {

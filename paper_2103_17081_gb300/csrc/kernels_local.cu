@@ -263,7 +263,7 @@ __host__ __device__ inline int prolong_max_cy(int nrows_fine) { return nrows_fin
 template <typename R>
 __global__ void __launch_bounds__(LOCAL_THREADS)
 k_z(LocalArgs<R> a, const double2 *__restrict__ s, const c2<R> *__restrict__ add,
-    c2<R> *__restrict__ out, const int *__restrict__ flag) {
+    c2<R> *__restrict__ out, const int *__restrict__ flag, R sign) {
     extern __shared__ unsigned char smem_raw[];
     const Tile tl = a.ftiles[blockIdx.x];
     if (flag && !flag[tl.task]) return;
@@ -275,7 +275,7 @@ k_z(LocalArgs<R> a, const double2 *__restrict__ s, const c2<R> *__restrict__ add
     prolong_rows<R>(T, s, tl.r0, tl.nr, sc, px, zs);
     for (int e = threadIdx.x; e < tl.nr * T.nx; e += blockDim.x) {
         long long gi = T.foff + (long long)tl.r0 * T.nx + e;
-        c2<R> v = zs[e];
+        c2<R> v = cscale<R>(sign, zs[e]);
         if (add) v = cadd<R>(add[gi], v);
         out[gi] = v;
     }
@@ -588,6 +588,19 @@ k_update_u(LocalArgs<R> a, InnerState<R> S, int restart, c2<R> *__restrict__ u,
     }
 }
 
+// ref_t = ||P f̃_t|| from the per-tile partial norms of P f̃ (one thread per task); used when
+// the cycle starts from a non-zero initial guess.
+template <typename R>
+__global__ void k_set_ref(LocalArgs<R> a, InnerState<R> S, const c2<R> *__restrict__ p3,
+                          const int *__restrict__ flag) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.ntasks || (flag && !flag[t])) return;
+    const Task T = a.tasks[t];
+    R s = 0;
+    for (int q = 0; q < T.ntiles; q++) s += p3[(long long)(T.tile0 + q) * LDP + LDP - 1].x;
+    S.ref[t] = sqrt(s);
+}
+
 template <typename RI, typename RO>
 __global__ void k_cast(long long n, const c2<RI> *__restrict__ in, c2<RO> *__restrict__ out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -628,10 +641,10 @@ void launch_zt(const LocalArgs<R> &a, const c2<R> *in, double2 *y, int apply_A, 
 }
 template <typename R>
 void launch_z(const LocalArgs<R> &a, const double2 *sc, const c2<R> *add, c2<R> *out,
-              const int *flag, cudaStream_t s) {
+              const int *flag, cudaStream_t s, R sign) {
     int maxc = prolong_max_cy(FINE_ROWS);
     size_t sm = ((size_t)maxc * (a.max_nx / 2 + 1) + (size_t)maxc * a.max_nx + (size_t)FINE_ROWS * a.max_nx) * csz<R>();
-    k_z<R><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, sc, add, out, flag);
+    k_z<R><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, sc, add, out, flag, sign);
 }
 template <typename R>
 size_t ps_smem(const LocalArgs<R> &a) {
@@ -671,6 +684,11 @@ void launch_update_u(const LocalArgs<R> &a, const InnerState<R> &S, int restart,
                      const c2<R> *V, const int *flag, int *rs_out, int *counter, int maxit,
                      cudaStream_t s) {
     k_update_u<R><<<a.nftiles, LOCAL_THREADS, 0, s>>>(a, S, restart, u, V, flag, rs_out, counter, maxit);
+}
+template <typename R>
+void launch_set_ref(const LocalArgs<R> &a, const InnerState<R> &S, const c2<R> *p3, const int *flag,
+                    cudaStream_t s) {
+    k_set_ref<R><<<(a.ntasks + 127) / 128, 128, 0, s>>>(a, S, p3, flag);
 }
 template <typename R>
 void launch_coarse_combine(const LocalArgs<R> &a, const InnerState<R> &S, int restart,
@@ -715,14 +733,15 @@ template <typename R> cudaError_t set_local_smem_limits(size_t bytes) {
     template void launch_scatter<R>(const LocalArgs<R> &, const c2<R> *, double2 *, long long, const int *, cudaStream_t); \
     template void launch_local_A<R>(const LocalArgs<R> &, const c2<R> *, c2<R> *, const c2<R> *, const int *, cudaStream_t); \
     template void launch_zt<R>(const LocalArgs<R> &, const c2<R> *, double2 *, int, const int *, cudaStream_t); \
-    template void launch_z<R>(const LocalArgs<R> &, const double2 *, const c2<R> *, c2<R> *, const int *, cudaStream_t); \
+    template void launch_z<R>(const LocalArgs<R> &, const double2 *, const c2<R> *, c2<R> *, const int *, cudaStream_t, R); \
     template void launch_prolong_stencil<R>(const LocalArgs<R> &, int, const c2<R> *, const double2 *, c2<R> *, const c2<R> *, int, c2<R> *, const int *, cudaStream_t); \
     template void launch_cgs_update<R>(const LocalArgs<R> &, int, c2<R> *, const c2<R> *, int, const c2<R> *, c2<R> *, const int *, cudaStream_t); \
     template void launch_givens_normalize<R>(const LocalArgs<R> &, const InnerState<R> &, int, int, c2<R> *, const c2<R> *, const c2<R> *, const c2<R> *, const int *, int *, int *, R, int, cudaStream_t); \
     template void launch_init_cycle<R>(const LocalArgs<R> &, const InnerState<R> &, int, c2<R> *, const c2<R> *, const int *, int *, int *, R, int, int, cudaStream_t); \
     template void launch_update_u<R>(const LocalArgs<R> &, const InnerState<R> &, int, c2<R> *, const c2<R> *, const int *, int *, int *, int, cudaStream_t); \
     template cudaError_t set_local_smem_limits<R>(size_t); \
-    template void launch_coarse_combine<R>(const LocalArgs<R> &, const InnerState<R> &, int, const double2 *, double2 *, const int *, cudaStream_t);
+    template void launch_coarse_combine<R>(const LocalArgs<R> &, const InnerState<R> &, int, const double2 *, double2 *, const int *, cudaStream_t); \
+    template void launch_set_ref<R>(const LocalArgs<R> &, const InnerState<R> &, const c2<R> *, const int *, cudaStream_t);
 
 INST(float)
 INST(double)

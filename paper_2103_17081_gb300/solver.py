@@ -150,9 +150,9 @@ class Solver:
     # -- solves --------------------------------------------------------------------------------
     @staticmethod
     def params(outer_tol=1e-6, outer_restart=2000, outer_maxit=2000, inner_tol=1e-2,
-               inner_restart=30, inner_maxit=1000, inner_prec=64) -> SolveParams:
+               inner_restart=30, inner_maxit=1000, inner_prec=64, warm_start=0) -> SolveParams:
         return SolveParams(outer_tol, outer_restart, outer_maxit, inner_tol, inner_restart,
-                           inner_maxit, inner_prec)
+                           inner_maxit, inner_prec, int(bool(warm_start)))
 
     def build_rhs_batch(self, specs):
         """Load vectors of several RHSSpecs, stacked RHS-major in one tensor."""
@@ -206,8 +206,60 @@ class Solver:
             k = KernelStat()
             self._check(self._L.hdd_profile_get(self._h, i, C.byref(k)), "hdd_profile_get")
             out.append({"name": k.name.decode(), "launches": k.launches, "ms": k.ms,
-                        "bytes": k.bytes, "flops": k.flops, "bound": "fp64" if k.bound else "hbm"})
+                        "bytes": k.bytes, "flops": k.flops,
+                        "bound": {0: "hbm", 1: "fp64", 2: "fp32"}.get(k.bound, "hbm")})
         return out
 
     def launch_count(self) -> int:
         return int(self._L.hdd_launch_count(self._h))
+
+    # -- learned warm start ----------------------------------------------------------------------
+    def cnn_num_params(self) -> int:
+        return int(self._L.hdd_cnn_num_params())
+
+    def cnn_set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != self.cnn_num_params():
+            raise ValueError(f"expected {self.cnn_num_params()} parameters, got {a.size}")
+        self._check(self._L.hdd_cnn_set_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float))),
+                    "hdd_cnn_set_params")
+
+    def cnn_get_params(self):
+        import numpy as np
+        a = np.zeros(self.cnn_num_params(), dtype=np.float32)
+        self._check(self._L.hdd_cnn_get_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float))),
+                    "hdd_cnn_get_params")
+        return a
+
+    def packed_len(self) -> int:
+        fo, _ = self.offsets()
+        return self.nrhs * fo[-1]
+
+    def cnn_forward(self, f_packed, stream=None):
+        x0 = self.empty(self.packed_len())
+        self._check(self._L.hdd_cnn_forward(self._h, self._vec(f_packed, self.packed_len(), "f"),
+                                            self._vec(x0), self._stream(stream)), "hdd_cnn_forward")
+        return x0
+
+    def cnn_loss_grad(self, f_packed, with_grad=True):
+        import numpy as np
+        loss = C.c_double(0.0)
+        g = np.zeros(self.cnn_num_params(), dtype=np.float32) if with_grad else None
+        gp = g.ctypes.data_as(C.POINTER(C.c_float)) if with_grad else None
+        self._check(self._L.hdd_cnn_loss_grad(self._h, self._vec(f_packed, self.packed_len(), "f"),
+                                              C.byref(loss), gp), "hdd_cnn_loss_grad")
+        return loss.value, g
+
+    def cnn_train_step(self, f_packed, lr, stream=None) -> float:
+        loss = C.c_double(0.0)
+        self._check(self._L.hdd_cnn_train_step(self._h, self._vec(f_packed, self.packed_len(), "f"),
+                                               float(lr), C.byref(loss), self._stream(stream)),
+                    "hdd_cnn_train_step")
+        return loss.value
+
+    def outer_vector(self, j, stream=None):
+        v = self.empty(self.nrhs * self.n)
+        self._check(self._L.hdd_get_outer_vector(self._h, int(j), self._vec(v), self._stream(stream)),
+                    "hdd_get_outer_vector")
+        return v
