@@ -154,6 +154,10 @@ typedef struct {
                          /* 128: complex128 inner solves.  Coarse E and outer: FP64 always  */
     int warm_start;      /* 1: start every local solve from the learned guess (hdd_cnn_*);  */
                          /* 0: from zero.  The tolerance stays relative to ||P f̃||          */
+    int outer_reorth32;  /* 1: the second CGS pass of the outer Arnoldi applies its         */
+                         /* correction V h2 in FP32 from an FP32 copy of the basis whenever */
+                         /* sum |h2| <= 2^-34 ||w'|| (error below the FP64 rounding of w'), */
+                         /* FP64 otherwise; 0: FP64 always.  Dots, norms, H: FP64 always    */
 } hdd_solve_params;
 
 typedef struct {
@@ -168,6 +172,8 @@ typedef struct {
     int n_history;               /* entries in res_history                                    */
     const double *res_history;   /* |g_{j+1}|/||f|| per outer iteration; library-owned, valid */
                                  /* until the next hdd_solve or hdd_destroy                   */
+    long long outer_reorth_fp64; /* outer iterations x RHS whose second CGS pass ran in FP64  */
+                                 /* although outer_reorth32 was set (guard not met)           */
 } hdd_solve_stats;
 
 /* Solve A x = f for the batched right-hand sides (f_dev → x_dev: nrhs complex128 vectors,

@@ -43,7 +43,7 @@ class DDParams(C.Structure):
 class SolveParams(C.Structure):
     _fields_ = [("outer_tol", C.c_double), ("outer_restart", C.c_int), ("outer_maxit", C.c_int),
                 ("inner_tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
-                ("inner_prec", C.c_int), ("warm_start", C.c_int)]
+                ("inner_prec", C.c_int), ("warm_start", C.c_int), ("outer_reorth32", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -51,7 +51,7 @@ class SolveStats(C.Structure):
                 ("inner_its_total", C.c_longlong), ("inner_its_avg", C.c_double),
                 ("inner_its_max", C.c_int), ("inner_maxit_hits", C.c_longlong),
                 ("t_solve_ms", C.c_double), ("n_history", C.c_int),
-                ("res_history", C.POINTER(C.c_double))]
+                ("res_history", C.POINTER(C.c_double)), ("outer_reorth_fp64", C.c_longlong)]
 
 
 class KernelStat(C.Structure):

@@ -55,11 +55,12 @@ template <typename R> struct InnerWork {   // inner GMRES buffers for one precis
 
 // Kernel families timed by the profiler (CUDA events around every launch on the launching
 // stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
-enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, NFAM };
+enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, NFAM };
 const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
                               "local_cgs2_update", "local_givens_normalize", "local_misc",
-                              "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn"};
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2};
+                              "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn",
+                              "outer_reorth_fp32"};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0};
 
 struct Prof {
     bool on = false;
@@ -101,7 +102,8 @@ struct CnnState {            // learned warm start: parameters, Adam moments, ac
 };
 
 struct OuterWork {
-    DevMem V, Z, w, r, H, cs, sn, g, h1, h2, part, npart, hn, flag, hist, beta, y, fnorm, act, kcols;
+    DevMem V, V32, Z, w, r, H, cs, sn, g, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
+    DevMem fallbacks;
 };
 
 }  // namespace
@@ -971,6 +973,12 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     CK(O.y.ensure((size_t)nr * ldp * sizeof(double2)));
     CK(O.part.ensure((size_t)nr * G * ldp * sizeof(double2)));
     CK(O.npart.ensure((size_t)nr * G * sizeof(double)));
+    CK(O.npart1.ensure((size_t)nr * G * sizeof(double)));
+    const bool r32 = prm->outer_reorth32 != 0;
+    if (r32) CK(O.V32.ensure((size_t)(R + 1) * nr * n * sizeof(float2)));
+    float2 *V32 = r32 ? O.V32.as<float2>() : nullptr;
+    CK(O.fallbacks.ensure(sizeof(int)));
+    CK(cudaMemsetAsync(O.fallbacks.p, 0, sizeof(int), s));
     CK(O.hn.ensure(nr * sizeof(double))); CK(O.flag.ensure(nr * sizeof(int))); CK(O.beta.ensure(nr * sizeof(double)));
     CK(O.fnorm.ensure(nr * sizeof(double))); CK(O.act.ensure(nr * sizeof(int))); CK(O.kcols.ensure(nr * sizeof(int)));
     CK(O.hist.ensure((size_t)nr * (prm->outer_maxit + 1) * sizeof(double)));
@@ -1023,7 +1031,8 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
         B.active = dact;
         KL(F_OMISC, 3.0 * nr * n * 16, 0, launch_gstencil(ctx->st, ctx->N, x, rv, f, nr, dact, s));
         KL(F_OMISC, (double)nr * n * 16, 0, launch_onorm(B, rv, O.npart.as<double>(), s));
-        KL(F_OMISC, 2.0 * nr * n * 16, 0, launch_oinit(B, rv, O.npart.as<double>(), V, O.g.as<double2>(), O.beta.as<double>(), s));
+        KL(F_OMISC, 2.0 * nr * n * 16 + (r32 ? nr * n * 8.0 : 0.0), 0,
+           launch_oinit(B, rv, O.npart.as<double>(), V, V32, O.g.as<double2>(), O.beta.as<double>(), s));
         CKL();
         CK(cudaMemcpyAsync(beta.data(), O.beta.p, nr * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1055,17 +1064,23 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                              // h1 = V^H w
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
             KL(F_OCGS, fa * (nv + 2) * n * 16, fa * 16 * nv * n,
-               launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), nullptr, s));
+               launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
-            KL(F_OCGS, fa * (nv + 2) * n * 16, fa * 8 * nv * n,
-               launch_oupdate(B, V, j + 1, O.h2.as<double2>(), w, nullptr, O.npart.as<double>(), s));
+            if (r32)   // FP32 correction from the FP32 basis copy (guarded; FP64 fallback inside)
+                KL(F_OREORTH, fa * (nv * 8 + 2 * 16) * n, fa * 8 * nv * n,
+                   launch_oupdate2(B, V, V32, j + 1, O.h2.as<double2>(), w, O.npart1.as<double>(),
+                                   O.npart.as<double>(), 1, O.fallbacks.as<int>(), s));
+            else
+                KL(F_OCGS, fa * (nv + 2) * n * 16, fa * 8 * nv * n,
+                   launch_oupdate(B, V, j + 1, O.h2.as<double2>(), w, nullptr, O.npart.as<double>(), s));
             KL(F_OMISC, 0, 0,
                launch_ogivens(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(), j,
                               O.h1.as<double2>(), O.h2.as<double2>(), O.npart.as<double>(), O.fnorm.as<double>(),
                               prm->outer_tol, O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>(), hstride,
                               total, s));
-            KL(F_OMISC, 2.0 * fa * n * 16, 0,
-               launch_oscale(B, V + (long long)(j + 1) * B.ld, w, O.hn.as<double>(), s));
+            KL(F_OMISC, 2.0 * fa * n * 16 + (r32 ? fa * n * 8.0 : 0.0), 0,
+               launch_oscale(B, V + (long long)(j + 1) * B.ld, r32 ? V32 + (long long)(j + 1) * B.ld : nullptr,
+                             w, O.hn.as<double>(), s));
             CKL();
             total++;
             std::vector<int> flags(nr);
@@ -1101,6 +1116,8 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     const int n0 = its[0];
     ctx->hist.resize(n0);
     if (n0) CK(cudaMemcpy(ctx->hist.data(), O.hist.p, n0 * sizeof(double), cudaMemcpyDeviceToHost));
+    int fb = 0;
+    CK(cudaMemcpy(&fb, O.fallbacks.p, sizeof(int), cudaMemcpyDeviceToHost));
     double worst = 0;
     for (int r = 0; r < nr; r++) worst = std::max(worst, relres[r]);
     S.outer_its = total;
@@ -1115,6 +1132,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     S.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     S.n_history = n0;
     S.res_history = ctx->hist.data();
+    S.outer_reorth_fp64 = fb;
     return result;
 }
 

@@ -220,19 +220,23 @@ void launch_odots(const OuterBatch &B, const double2 *V, int nv, const double2 *
                   cudaStream_t s);
 void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2 *h, double2 *w,
                     double2 *part_dots, double *part_norm, cudaStream_t s);
+void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
+                     double2 *w, const double *npart1, double *part_norm, int allow32, int *fallbacks,
+                     cudaStream_t s);
 void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s);
 void launch_oreduce(const OuterBatch &B, const double2 *part, int nv, double2 *out, cudaStream_t s);
 void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, int j,
                     const double2 *h1, const double2 *h2, const double *npart, const double *fnorm,
                     double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
                     cudaStream_t s);
-void launch_oscale(const OuterBatch &B, double2 *out, const double2 *w, const double *hn, cudaStream_t s);
+void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, const double2 *w, const double *hn,
+                   cudaStream_t s);
 void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, const int *kcols, int kmax,
                       double2 *y, cudaStream_t s);
 void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int kmax, const double2 *Zb,
                   double2 *x, cudaStream_t s);
-void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, double2 *g,
-                  double *beta_out, cudaStream_t s);
+void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
+                  double2 *g, double *beta_out, cudaStream_t s);
 cudaError_t set_outer_smem_limits(size_t bytes);
 
 }  // namespace hdd

@@ -130,7 +130,34 @@ k_odots(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__re
     warp_dots(V, B.ld, nv, ws, b, len, part, B.ldp);
 }
 
-// w_r -= Σ_l h_{r,l} V_{r,l}; then (part_dots != null) partial dots V_r^H w_r, else ||w_r||².
+// x -= Σ_{l<nv} hs[l] V_l(i) in FP64 with two independent accumulation chains.
+__device__ __forceinline__ double2 update_fp64(double2 x0, const double2 *__restrict__ vp, long long ld,
+                                               const double2 *__restrict__ hs, int nv) {
+    double2 x1 = make_double2(0.0, 0.0);
+    int l = 0;
+    for (; l + 1 < nv; l += 2) {
+        caxpy_neg<double>(x0, hs[l], vp[(long long)l * ld]);
+        caxpy_neg<double>(x1, hs[l + 1], vp[(long long)(l + 1) * ld]);
+    }
+    if (l < nv) caxpy_neg<double>(x0, hs[l], vp[(long long)l * ld]);
+    return make_double2(x0.x + x1.x, x0.y + x1.y);
+}
+
+// Block sum of one double per thread; thread 0 writes it to *out.
+__device__ __forceinline__ void block_sum_store(double v, double *red, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < OT / 32; q++) s += red[q];
+        *out = s;
+    }
+}
+
+// w_r -= Σ_l h_{r,l} V_{r,l} in FP64; then, if part_dots != null, partial dots V_r^H w_r; if
+// part_norm != null, the partial ||w_r||² of the updated vector.
 __global__ void __launch_bounds__(OT)
 k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__restrict__ h,
           double2 *__restrict__ w, double2 *__restrict__ part_dots, double *__restrict__ part_norm) {
@@ -147,33 +174,97 @@ k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__
     __syncthreads();
     double nrm = 0.0;
     for (int i = threadIdx.x; i < len; i += OT) {
-        double2 x0 = w[b + i], x1 = make_double2(0.0, 0.0);
-        const double2 *vp = V + b + i;
-        int l = 0;
-        for (; l + 1 < nv; l += 2) {                // two independent accumulation chains
-            caxpy_neg<double>(x0, hs[l], vp[(long long)l * B.ld]);
-            caxpy_neg<double>(x1, hs[l + 1], vp[(long long)(l + 1) * B.ld]);
-        }
-        if (l < nv) caxpy_neg<double>(x0, hs[l], vp[(long long)l * B.ld]);
-        x0.x += x1.x; x0.y += x1.y;
-        w[b + i] = x0;
-        ws[i] = x0;
-        nrm = fma(x0.x, x0.x, fma(x0.y, x0.y, nrm));
+        const double2 x = update_fp64(w[b + i], V + b + i, B.ld, hs, nv);
+        w[b + i] = x;
+        ws[i] = x;
+        nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
     }
+    if (part_norm) block_sum_store(nrm, red, part_norm + (long long)r * B.G + blockIdx.x);
     if (part_dots) {
         __syncthreads();
         warp_dots(V, B.ld, nv, ws, b, len, part_dots + (long long)r * B.G * B.ldp, B.ldp);
-    } else {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int o = 16; o > 0; o >>= 1) nrm += shfl_xor(nrm, o);
-        if (lane == 0) red[warp] = nrm;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int q = 0; q < OT / 32; q++) s += red[q];
-            part_norm[(long long)r * B.G + blockIdx.x] = s;
+    }
+}
+
+// Second CGS pass, w_r -= V_r h2_r, then the partial ||w_r||².  After an FP64 first pass the
+// coefficients h2 = V^H w' are rounding-error sized, so the correction V h2 is tiny next to w'.
+// When Σ_l (|Re h2_l| + |Im h2_l|) <= 2^-34 ||w'_r|| (||w'_r||² = Σ npart1) the correction is
+// formed in FP32 from the FP32 copy V32 of the basis: products and partial sums over 32 vectors
+// in FP32, widened to FP64 between partial sums, subtracted from w' in FP64.  Its error is then
+// at most about 2^-19 Σ|h2| <= 2^-53 ||w'_r|| in the 2-norm (||V_l|| = 1), under the FP64 unit
+// roundoff of w' itself.  Otherwise (or with allow32 == 0) the FP64 update runs from V; every
+// such RHS-iteration adds one to *fallbacks.  The guard is evaluated identically in every CTA
+// (fixed-order sums), so all chunks of one RHS take the same path.
+__global__ void __launch_bounds__(OT)
+k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict__ V32, int nv,
+           const double2 *__restrict__ h, double2 *__restrict__ w, const double *__restrict__ npart1,
+           double *__restrict__ part_norm, int allow32, int *__restrict__ fallbacks) {
+    extern __shared__ double2 hs[];
+    __shared__ double red[OT / 32];
+    __shared__ int use32_s;
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    V += r * B.n; w += r * B.n; h += (long long)r * B.ldp; npart1 += (long long)r * B.G;
+    if (V32) V32 += r * B.n;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        double a = 0.0, q2 = 0.0;
+        for (int l = lane; l < nv; l += 32) a += fabs(h[l].x) + fabs(h[l].y);
+        for (int q = lane; q < B.G; q += 32) q2 += npart1[q];
+        for (int o = 16; o > 0; o >>= 1) { a += shfl_xor(a, o); q2 += shfl_xor(q2, o); }
+        if (lane == 0) {
+            const int u = allow32 && V32 && a <= ldexp(sqrt(q2), -34);
+            use32_s = u;
+            if (!u && blockIdx.x == 0 && fallbacks) atomicAdd(fallbacks, 1);
         }
     }
+    __syncthreads();
+    const bool use32 = use32_s != 0;
+    long long b, e;
+    chunk_of(B.n, b, e);
+    const int len = (int)(e > b ? e - b : 0);
+    float2 *hf = reinterpret_cast<float2 *>(hs);
+    for (int l = threadIdx.x; l < nv; l += OT) {
+        const double2 v = h[l];
+        if (use32) hf[l] = make_float2((float)v.x, (float)v.y);
+        else hs[l] = v;
+    }
+    __syncthreads();
+    double nrm = 0.0;
+    for (int i = threadIdx.x; i < len; i += OT) {
+        double2 x = w[b + i];
+        if (use32) {
+            const float2 *vp = V32 + b + i;
+            double cx = 0.0, cy = 0.0;
+            for (int l0 = 0; l0 < nv; l0 += 32) {
+                const int l1 = l0 + 32 < nv ? l0 + 32 : nv;
+                float px = 0.f, py = 0.f, qx = 0.f, qy = 0.f;
+                int l = l0;
+#pragma unroll 8
+                for (; l + 1 < l1; l += 2) {
+                    const float2 v0 = vp[(long long)l * B.ld], v1 = vp[(long long)(l + 1) * B.ld];
+                    const float2 h0 = hf[l], h1 = hf[l + 1];
+                    px = fmaf(h0.x, v0.x, px); px = fmaf(-h0.y, v0.y, px);
+                    py = fmaf(h0.x, v0.y, py); py = fmaf(h0.y, v0.x, py);
+                    qx = fmaf(h1.x, v1.x, qx); qx = fmaf(-h1.y, v1.y, qx);
+                    qy = fmaf(h1.x, v1.y, qy); qy = fmaf(h1.y, v1.x, qy);
+                }
+                if (l < l1) {
+                    const float2 v0 = vp[(long long)l * B.ld], h0 = hf[l];
+                    px = fmaf(h0.x, v0.x, px); px = fmaf(-h0.y, v0.y, px);
+                    py = fmaf(h0.x, v0.y, py); py = fmaf(h0.y, v0.x, py);
+                }
+                cx += (double)px + (double)qx;
+                cy += (double)py + (double)qy;
+            }
+            x.x -= cx; x.y -= cy;
+        } else {
+            x = update_fp64(x, V + b + i, B.ld, hs, nv);
+        }
+        w[b + i] = x;
+        nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+    }
+    block_sum_store(nrm, red, part_norm + (long long)r * B.G + blockIdx.x);
 }
 
 // Partial ||x_r||² per CTA: part[r][cta].
@@ -263,17 +354,21 @@ __global__ void k_ogivens(OuterBatch B, double2 *__restrict__ H, double *__restr
     flag[r] = (res > tol * fnorm[r] && hn > 0.0) ? 1 : 0;
 }
 
-// V_{r,j+1} = w_r / hn_r
-__global__ void k_oscale(OuterBatch B, double2 *__restrict__ out, const double2 *__restrict__ w,
-                         const double *__restrict__ hn) {
+// V_{r,j+1} = w_r / hn_r, and its FP32 copy out32 (if not null)
+__global__ void k_oscale(OuterBatch B, double2 *__restrict__ out, float2 *__restrict__ out32,
+                         const double2 *__restrict__ w, const double *__restrict__ hn) {
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     const double h = hn[r];
     if (!(h > 0.0)) return;
     out += r * B.n; w += r * B.n;
+    if (out32) out32 += r * B.n;
     const double inv = 1.0 / h;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = make_double2(w[i].x * inv, w[i].y * inv);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = make_double2(w[i].x * inv, w[i].y * inv);
+        out[i] = v;
+        if (out32) out32[i] = make_float2((float)v.x, (float)v.y);
+    }
 }
 
 // y_r = H_r(0:k_r,0:k_r)⁻¹ g_r by column-oriented back substitution (one CTA per RHS).
@@ -317,9 +412,10 @@ __global__ void k_oaxpy(OuterBatch B, const double2 *__restrict__ y, const int *
 }
 
 // Cycle start for every active RHS: β_r = sqrt(Σ partials), v_{r,0} = r_r/β_r,
-// g_r = [β_r, 0, ..., 0] (R+1 entries).
+// g_r = [β_r, 0, ..., 0] (R+1 entries); FP32 copy of v_{r,0} in V32 (if not null).
 __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const double *__restrict__ npart,
-                        double2 *__restrict__ V, double2 *__restrict__ g, double *__restrict__ beta_out) {
+                        double2 *__restrict__ V, float2 *__restrict__ V32, double2 *__restrict__ g,
+                        double *__restrict__ beta_out) {
     __shared__ double beta_s;
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
@@ -336,8 +432,12 @@ __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const doub
         for (int l = threadIdx.x; l <= B.R; l += blockDim.x) g[l] = make_double2(l == 0 ? beta : 0.0, 0.0);
     if (!(beta > 0.0)) return;
     const double inv = 1.0 / beta;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x)
-        v0[i] = make_double2(rv[i].x * inv, rv[i].y * inv);
+    float2 *v32 = V32 ? V32 + r * B.n : nullptr;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = make_double2(rv[i].x * inv, rv[i].y * inv);
+        v0[i] = v;
+        if (v32) v32[i] = make_float2((float)v.x, (float)v.y);
+    }
 }
 
 static int grid_for(long long n, int threads) {
@@ -363,6 +463,12 @@ void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2
                     double2 *part_dots, double *part_norm, cudaStream_t s) {
     k_oupdate<<<dim3(B.G, B.nrhs), OT, (size_t)nv * sizeof(double2), s>>>(B, V, nv, h, w, part_dots, part_norm);
 }
+void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
+                     double2 *w, const double *npart1, double *part_norm, int allow32, int *fallbacks,
+                     cudaStream_t s) {
+    k_oupdate2<<<dim3(B.G, B.nrhs), OT, (size_t)nv * sizeof(double2), s>>>(B, V, V32, nv, h, w, npart1, part_norm,
+                                                                           allow32, fallbacks);
+}
 void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s) {
     k_onorm<<<dim3(B.G, B.nrhs), OT, 0, s>>>(B, x, part);
 }
@@ -376,8 +482,9 @@ void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, do
     k_ogivens<<<(B.nrhs + 31) / 32, 32, 0, s>>>(B, H, cs, sn, g, j, h1, h2, npart, fnorm, tol, hn_out, flag,
                                                 hist, hstride, it);
 }
-void launch_oscale(const OuterBatch &B, double2 *out, const double2 *w, const double *hn, cudaStream_t s) {
-    k_oscale<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, out, w, hn);
+void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, const double2 *w, const double *hn,
+                   cudaStream_t s) {
+    k_oscale<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, out, out32, w, hn);
 }
 void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, const int *kcols, int kmax,
                       double2 *y, cudaStream_t s) {
@@ -387,13 +494,14 @@ void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int k
                   double2 *x, cudaStream_t s) {
     k_oaxpy<<<dim3(grid_for(B.n, 256), B.nrhs), 256, (size_t)kmax * sizeof(double2), s>>>(B, y, kcols, Zb, x);
 }
-void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, double2 *g,
-                  double *beta_out, cudaStream_t s) {
-    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, g, beta_out);
+void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
+                  double2 *g, double *beta_out, cudaStream_t s) {
+    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, V32, g, beta_out);
 }
 cudaError_t set_outer_smem_limits(size_t bytes) {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_oupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_oupdate2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_otrisolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_oaxpy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     return cudaSuccess;

@@ -150,9 +150,10 @@ class Solver:
     # -- solves --------------------------------------------------------------------------------
     @staticmethod
     def params(outer_tol=1e-6, outer_restart=2000, outer_maxit=2000, inner_tol=1e-2,
-               inner_restart=30, inner_maxit=1000, inner_prec=64, warm_start=0) -> SolveParams:
+               inner_restart=30, inner_maxit=1000, inner_prec=64, warm_start=0,
+               outer_reorth32=1) -> SolveParams:
         return SolveParams(outer_tol, outer_restart, outer_maxit, inner_tol, inner_restart,
-                           inner_maxit, inner_prec, int(bool(warm_start)))
+                           inner_maxit, inner_prec, int(bool(warm_start)), int(bool(outer_reorth32)))
 
     def build_rhs_batch(self, specs):
         """Load vectors of several RHSSpecs, stacked RHS-major in one tensor."""

@@ -172,6 +172,29 @@ def test_k100_solve_matches_oracle(oracle_mod, prec):
         assert abs(st["outer_its"] - so["outer_its"]) <= 1
 
 
+@pytest.mark.parametrize("wname", ["tiny", "k100"])
+def test_outer_fp32_reorthogonalisation_matches_fp64(wname):
+    """The outer Arnoldi's second CGS pass with its correction applied in FP32 (guarded) gives the
+    FP64 iteration: same outer count, the first residual-history entries equal to 1e-8 and the
+    rest to the 1e-2 that rounding-order differences reach late in an unrestarted FGMRES (the
+    oracle comparison of the tiny solve sees the same), solutions equal to far below the solve
+    tolerance (complex128 inner solves, so nothing else rounds at FP32)."""
+    torch = _torch()
+    from paper_2103_17081_gb300 import Solver
+    w = W.make(wname)
+    s = Solver.from_workload(w)
+    f = s.build_rhs(w.rhs[0])
+    x64, st64 = s.solve(f, inner_prec=128, outer_reorth32=0)
+    x32, st32 = s.solve(f, inner_prec=128, outer_reorth32=1)
+    assert st64["outer_reorth_fp64"] == 0
+    assert st32["outer_its"] == st64["outer_its"]
+    h64, h32 = np.array(st64["res_history"]), np.array(st32["res_history"])
+    np.testing.assert_allclose(h32[:10], h64[:10], rtol=1e-8)
+    np.testing.assert_allclose(h32, h64, rtol=1e-2)
+    assert _rel(x32.cpu().numpy(), x64.cpu().numpy()) <= 1e-7
+    assert float(torch.linalg.vector_norm(f - s.apply_A(x32)) / torch.linalg.vector_norm(f)) <= 1.0001e-6
+
+
 def test_k200_ras_apply_full_size(oracle_mod):
     """k=200, N=640, 8x8 subdomains: one full RAS application (64 local solves) vs the oracle."""
     w = W.make("k200")
