@@ -225,6 +225,12 @@ hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params);
 hdd_status hdd_cnn_get_params(hdd_ctx *ctx, float *params);
 /* x0 = guess for every packed right-hand side f (complex128 packed local vectors). */
 hdd_status hdd_cnn_forward(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream);
+/* Inference as the solver's warm start runs it: layer 1 on the CUDA cores, layers 2-4 as      */
+/* implicit GEMMs on the tensor cores (tcgen05, BF16 operands, FP32 accumulation in TMEM), with */
+/* the activations between layers rounded to BF16.  Same arguments as hdd_cnn_forward, which  */
+/* keeps FP32 activations (the training forward).  HDD_ERR_TIMEOUT if a bounded device wait    */
+/* gave up (synchronises the stream to read that flag). */
+hdd_status hdd_cnn_infer(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream);
 /* Training loss of the batch f (every packed subdomain image) and, if grad != NULL, its
  * gradient w.r.t. every parameter (host FP32 array); synchronises the device.  Needs
  * hdd_setup_deflation (the loss applies P_j). */

@@ -76,17 +76,23 @@ def input_image(f, shape, kh):
     return img, sigma
 
 
-def forward(params, img):
+def forward(params, img, act_bf16=False):
+    """Activations of every layer.  act_bf16: the inputs of layers 2-4 (the ReLU outputs) are
+    rounded to BF16, the storage format of the tensor-core inference; sums stay FP64."""
     acts = [img]
     for (W, b), (_, _, relu) in zip(unpack(params), LAYERS):
         y = conv(acts[-1], W, b)
-        acts.append(np.maximum(y, 0.0) if relu else y)
+        if relu:
+            y = np.maximum(y, 0.0)
+            if act_bf16:
+                y = bf16_round(y).reshape(y.shape)
+        acts.append(y)
     return acts
 
 
-def guess(params, f, shape, kh):
+def guess(params, f, shape, kh, act_bf16=False):
     img, sigma = input_image(f, shape, kh)
-    out = forward(params, img)[-1]
+    out = forward(params, img, act_bf16)[-1]
     return (sigma * (out[..., 0] + 1j * out[..., 1])).reshape(-1)
 
 

@@ -18,7 +18,7 @@ SYMBOLS = ["hdd_create", "hdd_destroy", "hdd_status_str", "hdd_last_error", "hdd
            "hdd_solve", "hdd_ras_apply", "hdd_local_op", "hdd_profile", "hdd_profile_count",
            "hdd_profile_get", "hdd_launch_count", "hdd_apply_PA_noalloc", "hdd_setup_batch",
            "hdd_num_rhs", "hdd_cnn_num_params", "hdd_cnn_set_params", "hdd_cnn_get_params",
-           "hdd_cnn_forward", "hdd_cnn_loss_grad", "hdd_cnn_train_step", "hdd_get_outer_vector"]
+           "hdd_cnn_forward", "hdd_cnn_infer", "hdd_cnn_loss_grad", "hdd_cnn_train_step", "hdd_get_outer_vector"]
 
 
 def status_name(code: int) -> str:
@@ -127,6 +127,8 @@ def lib(build_if_missing: bool = True):
     L.hdd_cnn_get_params.restype = I
     L.hdd_cnn_forward.argtypes = [P, V, V, V]
     L.hdd_cnn_forward.restype = I
+    L.hdd_cnn_infer.argtypes = [P, V, V, V]
+    L.hdd_cnn_infer.restype = I
     L.hdd_cnn_loss_grad.argtypes = [P, V, C.POINTER(D), F]
     L.hdd_cnn_loss_grad.restype = I
     L.hdd_cnn_train_step.argtypes = [P, V, C.c_float, C.POINTER(D), V]

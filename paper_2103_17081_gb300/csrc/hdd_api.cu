@@ -99,6 +99,10 @@ struct CnnState {            // learned warm start: parameters, Adam moments, ac
     int step = 0;
     DevMem P, Pb, M, Vm, G, sigma, X0, A1, A2, A3, A4, dA4, Rr, dB1, dB2, part, lpart;
     DevMem Fh, Q, T2, Yc, Sc, Pf, Pr, scale, tloss;   // deflated loss: f̂, P r, Pᵀ P r, coarse, partials
+    // tensor-core inference: BF16 padded planar activations (ping-pong), weight images, error flag
+    DevMem Ba, Bb, Wimg, err;
+    bool tc_dirty = true;      // weight images out of date (parameters changed)
+    bool pad_ready = false;    // frame borders of Ba, Bb zeroed for the current task layout
 };
 
 struct OuterWork {
@@ -129,6 +133,10 @@ struct hdd_ctx {
     long long ld = 0, ldc = 0;
     int max_nx = 0, max_n = 0;
     std::vector<long long> foffs, coffs;
+    std::vector<int2> h_tct;                    // tensor-core conv tiles (task, first frame position)
+    DevMem d_tct;
+    long long ptot = 0;                         // frame positions over all tasks
+    int tc_wmax = 0;                            // staged window positions per plane
     // factors
     FactorSet E, Aex;
     // work
@@ -393,6 +401,78 @@ void cnn_forward(hdd_ctx *ctx, const c2<R> *f, cudaStream_t s) {
     }
 }
 
+// Buffers of the tensor-core inference; frame borders zeroed once per task layout.
+hdd_status cnn_tc_buffers(hdd_ctx *ctx, cudaStream_t s) {
+    CnnState &C = ctx->cnn;
+    const size_t act = (size_t)4 * ctx->ptot * sizeof(uint4);
+    const bool grow = C.Ba.bytes < act || C.Bb.bytes < act;
+    CK(C.Ba.ensure(act)); CK(C.Bb.ensure(act));
+    CK(C.Wimg.ensure((size_t)(2 * 9 * 4 * 32 * 8 + 9 * 4 * 16 * 8) * sizeof(__nv_bfloat16)));
+    CK(C.err.ensure(sizeof(int)));
+    if (!C.pad_ready || grow) {
+        CK(cudaMemsetAsync(C.Ba.p, 0, act, s)); CK(cudaMemsetAsync(C.Bb.p, 0, act, s));
+        CK(cudaMemsetAsync(C.err.p, 0, sizeof(int), s));
+        CK(set_conv_tc_smem(ctx->tc_wmax));
+        C.pad_ready = true;
+    }
+    return HDD_OK;
+}
+
+// Inference on the tensor cores: input image (σ, X0), layer 1 on the CUDA cores into BF16
+// frames, layers 2-4 as tcgen05 implicit GEMMs; A4 holds the output (FP32, packed layout).
+template <typename R>
+hdd_status cnn_infer(hdd_ctx *ctx, const c2<R> *f, cudaStream_t s) {
+    CnnState &C = ctx->cnn;
+    hdd_status st = cnn_tc_buffers(ctx, s);
+    if (st != HDD_OK) return st;
+    const Task *T = ctx->d_tasks.as<Task>();
+    const Tile *ft = ctx->d_ftiles.as<Tile>();
+    const int nt = (int)ctx->h_tasks.size(), nft = (int)ctx->h_ftiles.size(), ntc = (int)ctx->h_tct.size();
+    const __nv_bfloat16 *Wb = C.Pb.as<__nv_bfloat16>();
+    const float *P = C.P.as<float>();
+    __nv_bfloat16 *img = C.Wimg.as<__nv_bfloat16>();
+    __nv_bfloat16 *img2 = img, *img3 = img + 9 * 4 * 32 * 8, *img4 = img + 2 * 9 * 4 * 32 * 8;
+    const double px = (double)ctx->ld, fr = (double)ctx->ptot;
+    if (C.tc_dirty) {
+        KL(F_CNN, 0, 0, launch_cnn_tc_weights(Wb, img2, img3, img4, s));
+        C.tc_dirty = false;
+    }
+    KL(F_CNN, px * (8 + 16), 0, launch_cnn_input<R>(T, nt, f, (float)(ctx->k * ctx->h), C.sigma.as<float>(),
+                                                      C.X0.as<float>(), nullptr, s));
+    uint4 *Ba = C.Ba.as<uint4>(), *Bb = C.Bb.as<uint4>();
+    KL(F_CNN, px * (16 + 64), 2.0 * px * 32 * 9 * 4,
+       launch_cnn_l1_bf16(T, ft, nft, Wb + CNN_OFF[0], P + CNN_OFF[0] + 32 * 9 * 4, C.X0.as<float>(), Ba, ctx->ptot, s));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int grid = std::max(1, std::min(ntc, 4 * nsm));
+    int *err = C.err.as<int>();
+    const uint4 *im2 = reinterpret_cast<const uint4 *>(img2), *im3 = reinterpret_cast<const uint4 *>(img3),
+                *im4 = reinterpret_cast<const uint4 *>(img4);
+    const double fl32 = 2.0 * px * 32 * 9 * 32;
+    KL(F_CNN, fr * 128, fl32, launch_conv_tc(32, grid, T, ctx->d_tct.as<int2>(), ntc, Ba, ctx->ptot, im2,
+                                             P + CNN_OFF[1] + 32 * 9 * 32, Bb, nullptr, ctx->tc_wmax, err, s));
+    KL(F_CNN, fr * 128, fl32, launch_conv_tc(32, grid, T, ctx->d_tct.as<int2>(), ntc, Bb, ctx->ptot, im3,
+                                             P + CNN_OFF[2] + 32 * 9 * 32, Ba, nullptr, ctx->tc_wmax, err, s));
+    KL(F_CNN, fr * 64 + px * 8, 2.0 * px * 2 * 9 * 32,
+       launch_conv_tc(16, grid, T, ctx->d_tct.as<int2>(), ntc, Ba, ctx->ptot, im4, P + CNN_OFF[3] + 2 * 9 * 32,
+                      nullptr, reinterpret_cast<float2 *>(C.A4.as<float>()), ctx->tc_wmax, err, s));
+    return HDD_OK;
+}
+
+// Reads the tensor-core kernels' timeout flag (synchronises the stream); HDD_ERR_TIMEOUT if set.
+hdd_status cnn_check_err(hdd_ctx *ctx, cudaStream_t s) {
+    CnnState &C = ctx->cnn;
+    if (!C.err.p) return HDD_OK;
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, C.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (e) {
+        CK(cudaMemsetAsync(C.err.p, 0, sizeof(int), s));
+        FAIL(HDD_ERR_TIMEOUT, "a tensor-core convolution wait timed out");
+    }
+    return HDD_OK;
+}
+
 // mean over the batch of ||f̃/σ - A(a + i b)||²/n_t and its gradient w.r.t. every parameter
 // (into C.G, FP32); returns the loss (synchronises).
 template <typename R>
@@ -535,8 +615,9 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
         band_solve(ctx, ctx->E, y, sc, false, mask, s);
         KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, V, nullptr, 0, p3, mask, s));
     } else {
-        // learned initial guess ũ₀ = σ·CNN(f̃/σ); ref = ||P f̃|| and r0 = P(f̃ - A ũ₀)
-        cnn_forward<R>(ctx, f, s);
+        // learned initial guess ũ₀ = σ·CNN(f̃/σ) (tensor-core inference); ref = ||P f̃|| and
+        // r0 = P(f̃ - A ũ₀)
+        if ((st = cnn_infer<R>(ctx, f, s)) != HDD_OK) return st;
         KL(F_CNN, 0, 0, launch_cnn_output<R>(ctx->d_tasks.as<Task>(), ctx->d_ftiles.as<Tile>(),
                                                (int)ctx->h_ftiles.size(), ctx->cnn.sigma.as<float>(),
                                                ctx->cnn.A4.as<float>(), u, mask, s));
@@ -698,9 +779,10 @@ namespace {
 // RHS r; fine tiles of FINE_ROWS box rows, coarse tiles of COARSE_ROWS coarse rows.
 hdd_status build_tasks(hdd_ctx *ctx, int nrhs) {
     const int ns = (int)ctx->subs.size();
-    ctx->h_tasks.clear(); ctx->h_ftiles.clear(); ctx->h_ctiles.clear();
+    ctx->h_tasks.clear(); ctx->h_ftiles.clear(); ctx->h_ctiles.clear(); ctx->h_tct.clear();
     ctx->foffs.assign(1, 0); ctx->coffs.assign(1, 0);
-    long long fo = 0, co = 0;
+    long long fo = 0, co = 0, po = 0;
+    int wmx = 0;
     for (int r = 0; r < nrhs; r++)
         for (int q = 0; q < ns; q++) {
             const SubBox &b = ctx->subs[q];
@@ -716,13 +798,24 @@ hdd_status build_tasks(hdd_ctx *ctx, int nrhs) {
             T.ntiles = (int)ctx->h_ftiles.size() - T.tile0;
             for (int y = 0; y < b.my; y += COARSE_ROWS)
                 ctx->h_ctiles.push_back(Tile{t, y, std::min(COARSE_ROWS, b.my - y)});
+            T.poff = po;
+            const int nxp = b.nx + 2;
+            for (long long q0 = nxp; q0 < (long long)(b.ny + 1) * nxp; q0 += 128)
+                ctx->h_tct.push_back(make_int2(t, (int)q0));
+            po += (long long)(b.ny + 2) * nxp;
+            wmx = std::max(wmx, b.nx);
             fo += (long long)b.nx * b.ny;
             co += (long long)b.mx * b.my;
             if (r == 0) { ctx->foffs.push_back(fo); ctx->coffs.push_back(co); }
             ctx->h_tasks.push_back(T);
         }
     ctx->ld = fo; ctx->ldc = co;
+    ctx->ptot = po;
+    ctx->tc_wmax = 128 + 2 * (wmx + 2) + 2;
+    ctx->cnn.pad_ready = false;
     const int nt = (int)ctx->h_tasks.size();
+    CK(ctx->d_tct.ensure(ctx->h_tct.size() * sizeof(int2)));
+    CK(cudaMemcpy(ctx->d_tct.p, ctx->h_tct.data(), ctx->h_tct.size() * sizeof(int2), cudaMemcpyHostToDevice));
     CK(ctx->d_tasks.ensure(nt * sizeof(Task)));
     CK(ctx->d_ftiles.ensure(ctx->h_ftiles.size() * sizeof(Tile)));
     CK(ctx->d_ctiles.ensure(ctx->h_ctiles.size() * sizeof(Tile)));
@@ -1118,6 +1211,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     if (n0) CK(cudaMemcpy(ctx->hist.data(), O.hist.p, n0 * sizeof(double), cudaMemcpyDeviceToHost));
     int fb = 0;
     CK(cudaMemcpy(&fb, O.fallbacks.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (prm->warm_start && ctx->cnn.ready && (st = cnn_check_err(ctx, s)) != HDD_OK) return st;
     double worst = 0;
     for (int r = 0; r < nr; r++) worst = std::max(worst, relres[r]);
     S.outer_its = total;
@@ -1192,6 +1286,7 @@ hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params) {
     CK(cudaMemset(C.M.p, 0, CNN_NPARAM * sizeof(float)));
     CK(cudaMemset(C.Vm.p, 0, CNN_NPARAM * sizeof(float)));
     launch_to_bf16(CNN_NPARAM, C.P.as<float>(), C.Pb.as<__nv_bfloat16>(), 0);
+    C.tc_dirty = true;
     CKL();
     CK(cudaDeviceSynchronize());
     C.step = 0;
@@ -1225,6 +1320,23 @@ hdd_status hdd_cnn_forward(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *
     return HDD_OK;
 }
 
+hdd_status hdd_cnn_infer(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
+    if (!f_dev || !x0_dev || f_dev == x0_dev || !aligned16(f_dev) || !aligned16(x0_dev))
+        FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    hdd_status st = cnn_buffers(ctx);
+    if (st != HDD_OK) return st;
+    if ((st = cnn_infer<double>(ctx, (const double2 *)f_dev, s)) != HDD_OK) return st;
+    KL(F_CNN, 0, 0, launch_cnn_output<double>(ctx->d_tasks.as<Task>(), ctx->d_ftiles.as<Tile>(),
+                                                (int)ctx->h_ftiles.size(), ctx->cnn.sigma.as<float>(),
+                                                ctx->cnn.A4.as<float>(), (double2 *)x0_dev, nullptr, s));
+    CKL();
+    return cnn_check_err(ctx, s);
+}
+
 hdd_status hdd_cnn_loss_grad(hdd_ctx *ctx, const void *f_dev, double *loss, float *grad) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
     if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
@@ -1247,6 +1359,7 @@ hdd_status hdd_cnn_train_step(hdd_ctx *ctx, const void *f_dev, float lr, double 
     if (st != HDD_OK) return st;
     CnnState &C = ctx->cnn;
     C.step++;
+    C.tc_dirty = true;
     KL(F_CNN, 0, 0, launch_adam(CNN_NPARAM, C.P.as<float>(), C.G.as<float>(), C.M.as<float>(), C.Vm.as<float>(),
                                   C.Pb.as<__nv_bfloat16>(), lr, 0.9f, 0.999f, 1e-8f, C.step, s));
     CKL();

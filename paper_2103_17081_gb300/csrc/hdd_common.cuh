@@ -68,6 +68,7 @@ struct Task {              // one local solve: subdomain `sub` for right-hand si
     int sub, rhs;
     int tile0, ntiles;     // fine tiles of this task
     long long foff, coff;  // packed fine / coarse offsets
+    long long poff;        // frame offset of the padded planar CNN activations, (ny+2)(nx+2) per task
 };
 
 struct Tile {              // a block of fine rows (fine tiles) or coarse rows (coarse tiles)
@@ -238,5 +239,15 @@ void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int k
 void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
                   double2 *g, double *beta_out, cudaStream_t s);
 cudaError_t set_outer_smem_limits(size_t bytes);
+
+// tensor-core inference of the warm-start network (kernels_cnn_tc.cu)
+void launch_cnn_l1_bf16(const Task *tasks, const Tile *tiles, int ntiles, const __nv_bfloat16 *W, const float *b,
+                        const float *X0, uint4 *X1, long long ptot, cudaStream_t s);
+void launch_cnn_tc_weights(const __nv_bfloat16 *Wb, __nv_bfloat16 *img2, __nv_bfloat16 *img3,
+                           __nv_bfloat16 *img4, cudaStream_t s);
+size_t conv_tc_smem(int nco, int wmax);
+cudaError_t set_conv_tc_smem(int wmax);
+void launch_conv_tc(int nco, int grid, const Task *tasks, const int2 *tct, int ntct, const uint4 *X, long long ptot,
+                    const uint4 *Wimg, const float *bias, uint4 *Y, float2 *A4, int wmax, int *err, cudaStream_t s);
 
 }  // namespace hdd

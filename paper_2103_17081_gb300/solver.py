@@ -243,6 +243,13 @@ class Solver:
                                             self._vec(x0), self._stream(stream)), "hdd_cnn_forward")
         return x0
 
+    def cnn_infer(self, f_packed, stream=None):
+        """The warm start's inference path: tensor-core layers, BF16 activations."""
+        x0 = self.empty(self.packed_len())
+        self._check(self._L.hdd_cnn_infer(self._h, self._vec(f_packed, self.packed_len(), "f"),
+                                          self._vec(x0), self._stream(stream)), "hdd_cnn_infer")
+        return x0
+
     def cnn_loss_grad(self, f_packed, with_grad=True):
         import numpy as np
         loss = C.c_double(0.0)

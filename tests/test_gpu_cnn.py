@@ -73,3 +73,58 @@ def test_training_reduces_loss():
     prm = s.cnn_get_params()
     warmstart.save(path, prm)
     assert np.array_equal(warmstart.load(path), prm)
+
+
+def test_tensor_core_inference_matches_oracle():
+    """hdd_cnn_infer (layers 2-4 on tcgen05, BF16 activations) against the oracle forward with
+    BF16-rounded activations, on boxes of six different widths (frames of 2-3 tiles of 128
+    positions, so first, interior and ragged last tiles all occur)."""
+    torch, s, p, cnn, pb, f, fo, batch, kh = _setup()
+    x0 = s.cnn_infer(torch.from_numpy(f).cuda()).cpu().numpy()
+    for t, (ft, shape, *_) in enumerate(batch):
+        ref = cnn.guess(pb, ft, shape, kh, act_bf16=True)
+        got = x0[fo[t]:fo[t + 1]]
+        assert np.linalg.norm(got - ref) <= 2e-3 * np.linalg.norm(ref), t
+
+
+def test_warm_start_gain_k100():
+    """What the trained network gains: a network trained on the restricted outer Krylov vectors of
+    four seeded k=100 solves (N=320, 4x4 subdomains) lowers the inner iteration count of a
+    held-out solve (another seed) while the outer tolerance still holds and the solution still
+    matches the zero-guess method to the solve tolerance.  Inference is the tensor-core path,
+    checked against the oracle at this box size (81 and 83 nodes wide)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import oracle
+    from oracle import cnn
+    from paper_2103_17081_gb300 import Solver, warmstart
+    w = W.make("k100")
+    s = Solver.from_workload(w)
+    s.cnn_set_params(warmstart.init_params(s.cnn_num_params(), seed=0))
+    specs = [W.make("k100", seed=100 + i).rhs[0] for i in range(4)]
+    data = warmstart.record_inputs(s, specs, outer_its=400, every=8)
+    hist = warmstart.train(s, data, epochs=4, lr=1e-3)
+    assert hist[-1] < 0.2
+    # tensor-core inference on two full-size boxes against the oracle (BF16 activations)
+    p = oracle.from_workload(w)
+    pb = cnn.bf16_round(s.cnn_get_params())
+    fo, _ = s.offsets()
+    fv = data[-1]
+    x0 = s.cnn_infer(fv).cpu().numpy()
+    fh = fv.cpu().numpy()
+    for t in (0, 5):
+        b = p.box(t)
+        ref = cnn.guess(pb, fh[fo[t]:fo[t + 1]], (b["ny"], b["nx"]), w.k / w.N, act_bf16=True)
+        assert np.linalg.norm(x0[fo[t]:fo[t + 1]] - ref) <= 2e-3 * np.linalg.norm(ref), t
+    f = s.build_rhs(W.make("k100", seed=1000).rhs[0])
+    xc, stc = s.solve(f, warm_start=0)
+    xw, stw = s.solve(f, warm_start=1)
+    assert stw["rel_res_true"] <= 1e-6 * 1.0001
+    assert stw["outer_its"] <= 1.1 * stc["outer_its"]
+    assert stw["inner_its_avg"] < stc["inner_its_avg"]
+    # same solution: two different iterates at residual 1e-6 may differ by ~cond·1e-6, so the
+    # solutions are compared at outer tolerance 1e-8
+    xc, _ = s.solve(f, warm_start=0, outer_tol=1e-8)
+    xw, _ = s.solve(f, warm_start=1, outer_tol=1e-8)
+    assert float(torch.linalg.vector_norm(xw - xc) / torch.linalg.vector_norm(xc)) < 1e-6

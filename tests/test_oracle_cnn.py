@@ -94,3 +94,22 @@ def test_zero_network_gives_zero_guess(oracle_mod):
     L, _ = cnn.loss_and_grad(np.zeros(cnn.NPARAM), batch, 0.5, False)
     # with a zero guess the loss is mean_t ||P f̂_t||²/||P f̂_t||² = 1 exactly
     assert L == pytest.approx(1.0, rel=1e-12)
+
+
+def test_bf16_activation_forward():
+    """With act_bf16 every hidden activation is a BF16 value (low 16 bits of its FP32 pattern
+    zero) and the output stays within the BF16 rounding (2^-9 relative per activation) of the
+    unrounded forward, amplified by three layers."""
+    from oracle import cnn
+    rng = np.random.default_rng(5)
+    params = rng.standard_normal(cnn.NPARAM) * 0.15
+    img = rng.standard_normal((9, 11, 4))
+    img[..., 3] = 0.0
+    a = cnn.forward(params, img, act_bf16=True)
+    b = cnn.forward(params, img)
+    for l in (1, 2, 3):
+        bits = a[l].astype(np.float32).view(np.uint32)
+        assert np.all(bits & 0xFFFF == 0)
+        assert np.array_equal(a[l].astype(np.float32).astype(np.float64), a[l])
+    rel = np.linalg.norm(a[4] - b[4]) / np.linalg.norm(b[4])
+    assert 0 < rel < 3 * 2.0 ** -9 * 8
