@@ -160,7 +160,12 @@ def run_gpu(args):
     f = s.build_rhs(w.rhs[0])
     x = s.empty()
     kw = dict(outer_tol=w.outer_tol, inner_tol=w.inner_tol, inner_prec=args.prec,
-              outer_restart=args.outer_maxit, outer_maxit=args.outer_maxit)
+              outer_restart=args.outer_maxit, outer_maxit=args.outer_maxit,
+              outer_reorth32=0 if args.fp64_reorth else 1)
+    if args.warm_start:
+        from paper_2103_17081_gb300 import warmstart
+        s.cnn_set_params(warmstart.load(args.warm_start))
+        kw["warm_start"] = 1
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
     stream = torch.cuda.current_stream(dev)
     kw["raise_on_error"] = args.outer_maxit >= 2000   # a lowered limit is a bounded profiling run
@@ -250,6 +255,7 @@ def run_gpu(args):
                        "subdomains": f"{w.Sx}x{w.Sy}", "overlap": w.overlap,
                        "inner_tol": w.inner_tol, "outer_tol": w.outer_tol, "inner_prec": args.prec,
                        "l2": "flushed between timed steps (512 MB write)",
+                       "warm_start": bool(args.warm_start), "outer_reorth": "fp64" if args.fp64_reorth else "fp32-guarded",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "solve": {"outer_its": stats["outer_its"], "inner_its_avg": round(stats["inner_its_avg"], 3),
                       "rel_res_true": rel, "status": stats["status_code"]},
@@ -284,6 +290,11 @@ def main():
     ap.add_argument("--sample-its", type=int, default=200)
     ap.add_argument("--full-outer-its", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--warm-start", default=None,
+                    help="parameter file of a trained warm-start network (written by "
+                         "python -m paper_2103_17081_gb300.warmstart train)")
+    ap.add_argument("--fp64-reorth", action="store_true",
+                    help="second outer CGS pass in FP64 (default: guarded FP32 correction)")
     args = ap.parse_args()
     if args.impl == "reference":
         if not args.full_outer_its:

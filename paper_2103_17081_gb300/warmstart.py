@@ -82,3 +82,73 @@ def load(path: str) -> np.ndarray:
     if len(payload) != 4 * n or zlib.crc32(payload) != crc:
         raise ValueError("corrupt warm-start parameter file")
     return np.frombuffer(payload, dtype=np.float32).copy()
+
+
+def _main(argv=None):
+    """Command line: train a network on a workload and save it, time the inference, or compare
+    warm- and zero-started solves of a held-out right-hand side."""
+    import argparse
+    import time
+
+    import torch
+
+    import workloads as W
+    from .solver import Solver
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2103_17081_gb300.warmstart")
+    ap.add_argument("command", choices=["train", "infer", "compare"])
+    ap.add_argument("--workload", default="k200")
+    ap.add_argument("--params", default=None, help="parameter file (read by infer/compare, written by train)")
+    ap.add_argument("--seeds", type=int, default=8, help="training right-hand sides (seeds 100, 101, ...)")
+    ap.add_argument("--outer-its", type=int, default=1270, help="outer iterations recorded per training solve")
+    ap.add_argument("--every", type=int, default=32, help="record every n-th outer Krylov vector")
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--seed", type=int, default=1000, help="held-out right-hand side of compare")
+    a = ap.parse_args(argv)
+    w = W.make(a.workload)
+    s = Solver.from_workload(w)
+    if a.command == "train":
+        s.cnn_set_params(init_params(s.cnn_num_params(), 0))
+        specs = [W.make(a.workload, seed=100 + i).rhs[0] for i in range(a.seeds)]
+        data = record_inputs(s, specs, outer_its=a.outer_its, every=a.every)
+        hist = train(s, data, epochs=a.epochs, lr=a.lr, log=print)
+        if a.params:
+            save(a.params, s.cnn_get_params())
+        print({"batches": len(data), "loss": hist})
+        return 0
+    s.cnn_set_params(load(a.params) if a.params else init_params(s.cnn_num_params(), 0))
+    f = s.build_rhs(W.make(a.workload, seed=a.seed).rhs[0])
+    if a.command == "infer":
+        v = s.local_op("R", f / torch.linalg.vector_norm(f))
+        out = {}
+        for name, fn in (("tensor_core", s.cnn_infer), ("fp32_cuda_core", s.cnn_forward)):
+            fn(v)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(a.reps):
+                fn(v)
+            e1.record()
+            torch.cuda.synchronize()
+            out[name + "_us"] = round(e0.elapsed_time(e1) * 1e3 / a.reps, 1)
+        print(out)
+        return 0
+    res = {}
+    for warm in (0, 1):
+        s.solve(f, warm_start=warm)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, st = s.solve(f, warm_start=warm)
+        torch.cuda.synchronize()
+        res["warm" if warm else "zero"] = {"s": round(time.perf_counter() - t, 3), "outer": st["outer_its"],
+                                           "inner_avg": round(st["inner_its_avg"], 3),
+                                           "rel_res": st["rel_res_true"]}
+    print(res)
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+    sys.exit(_main())
