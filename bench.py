@@ -157,8 +157,8 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     w = W.make(args.workload, seed=rank)          # independent replica per rank
     s = Solver.from_workload(w, device=dev)
-    f = s.build_rhs(w.rhs[0])
-    x = s.empty()
+    f = s.build_rhs_batch(w.rhs) if w.nrhs > 1 else s.build_rhs(w.rhs[0])
+    x = s.empty(f.numel())
     kw = dict(outer_tol=w.outer_tol, inner_tol=w.inner_tol, inner_prec=args.prec,
               outer_restart=args.outer_maxit, outer_maxit=args.outer_maxit,
               outer_reorth32=0 if args.fp64_reorth else 1)
