@@ -106,7 +106,7 @@ struct CnnState {            // learned warm start: parameters, Adam moments, ac
 };
 
 struct OuterWork {
-    DevMem V, V32, Z, w, r, H, cs, sn, g, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
+    DevMem V, V32, Z, w, r, H, cs, sn, g, Wq, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
     DevMem fallbacks;
 };
 
@@ -1062,6 +1062,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     CK(O.H.ensure((size_t)nr * (R + 1) * R * sizeof(double2)));
     CK(O.cs.ensure((size_t)nr * R * sizeof(double))); CK(O.sn.ensure((size_t)nr * R * sizeof(double2)));
     CK(O.g.ensure((size_t)nr * (R + 1) * sizeof(double2)));
+    CK(O.Wq.ensure((size_t)nr * (R + 1) * sizeof(double2)));
     CK(O.h1.ensure((size_t)nr * ldp * sizeof(double2))); CK(O.h2.ensure((size_t)nr * ldp * sizeof(double2)));
     CK(O.y.ensure((size_t)nr * ldp * sizeof(double2)));
     CK(O.part.ensure((size_t)nr * G * ldp * sizeof(double2)));
@@ -1125,7 +1126,8 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
         KL(F_OMISC, 3.0 * nr * n * 16, 0, launch_gstencil(ctx->st, ctx->N, x, rv, f, nr, dact, s));
         KL(F_OMISC, (double)nr * n * 16, 0, launch_onorm(B, rv, O.npart.as<double>(), s));
         KL(F_OMISC, 2.0 * nr * n * 16 + (r32 ? nr * n * 8.0 : 0.0), 0,
-           launch_oinit(B, rv, O.npart.as<double>(), V, V32, O.g.as<double2>(), O.beta.as<double>(), s));
+           launch_oinit(B, rv, O.npart.as<double>(), V, V32, O.g.as<double2>(), O.Wq.as<double2>(),
+                        O.beta.as<double>(), s));
         CKL();
         CK(cudaMemcpyAsync(beta.data(), O.beta.p, nr * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1167,7 +1169,8 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                 KL(F_OCGS, fa * (nv + 2) * n * 16, fa * 8 * nv * n,
                    launch_oupdate(B, V, j + 1, O.h2.as<double2>(), w, nullptr, O.npart.as<double>(), s));
             KL(F_OMISC, 0, 0,
-               launch_ogivens(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(), j,
+               launch_ogivens(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(),
+                              O.Wq.as<double2>(), j,
                               O.h1.as<double2>(), O.h2.as<double2>(), O.npart.as<double>(), O.fnorm.as<double>(),
                               prm->outer_tol, O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>(), hstride,
                               total, s));
@@ -1195,6 +1198,8 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
         for (int r = 0; r < nr; r++) kmax = std::max(kmax, kcols[r]);
         CK(cudaMemcpyAsync(O.kcols.p, kcols.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s));
         if (kmax > 0) {
+            KL(F_OMISC, 0, 0, launch_orotate(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(),
+                                             O.kcols.as<int>(), kmax, s));
             KL(F_OMISC, 0, 0, launch_otrisolve(B, O.H.as<double2>(), O.g.as<double2>(), O.kcols.as<int>(), kmax,
                                                O.y.as<double2>(), s));
             KL(F_OMISC, (kmax + 2.0) * nr * n * 16, 8.0 * kmax * nr * n,

@@ -226,7 +226,7 @@ void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, i
                      cudaStream_t s);
 void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s);
 void launch_oreduce(const OuterBatch &B, const double2 *part, int nv, double2 *out, cudaStream_t s);
-void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, int j,
+void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,
                     const double2 *h1, const double2 *h2, const double *npart, const double *fnorm,
                     double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
                     cudaStream_t s);
@@ -237,7 +237,9 @@ void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, c
 void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int kmax, const double2 *Zb,
                   double2 *x, cudaStream_t s);
 void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
-                  double2 *g, double *beta_out, cudaStream_t s);
+                  double2 *g, double2 *Wq, double *beta_out, cudaStream_t s);
+void launch_orotate(const OuterBatch &B, double2 *H, const double *cs, const double2 *sn, const int *kcols,
+                    int kmax, cudaStream_t s);
 cudaError_t set_outer_smem_limits(size_t bytes);
 
 // tensor-core inference of the warm-start network (kernels_cnn_tc.cu)

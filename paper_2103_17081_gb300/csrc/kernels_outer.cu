@@ -190,7 +190,7 @@ k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__
 // coefficients h2 = V^H w' are rounding-error sized, so the correction V h2 is tiny next to w'.
 // When Σ_l (|Re h2_l| + |Im h2_l|) <= 2^-34 ||w'_r|| (||w'_r||² = Σ npart1) the correction is
 // formed in FP32 from the FP32 copy V32 of the basis: products and partial sums over 32 vectors
-// in FP32, widened to FP64 between partial sums, subtracted from w' in FP64.  Its error is then
+// in FP32 (two chains of 16), widened to FP64 between partial sums, subtracted from w' in FP64.  Its error is then
 // at most about 2^-19 Σ|h2| <= 2^-53 ||w'_r|| in the 2-norm (||V_l|| = 1), under the FP64 unit
 // roundoff of w' itself.  Otherwise (or with allow32 == 0) the FP64 update runs from V; every
 // such RHS-iteration adds one to *fallbacks.  The guard is evaluated identically in every CTA
@@ -313,45 +313,91 @@ __device__ void zgivens(double2 a, double2 b, double &c, double2 &s, double2 &r)
     r = make_double2(ph.x * t, ph.y * t);
 }
 
-// Outer Arnoldi column j of every active RHS (one thread each): h = h1 + h2 (CGS2),
-// h_{j+1,j} = sqrt(Σ norm partials); previous rotations, rotation j, g update.
-// flag[r] = 1 while |g_{j+1}| > tol·||f_r|| and h_{j+1,j} > 0; hist[r·hstride + it] records
-// |g_{j+1}|/||f_r||.
-__global__ void k_ogivens(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs,
-                          double2 *__restrict__ sn, double2 *__restrict__ g, int j,
-                          const double2 *__restrict__ h1, const double2 *__restrict__ h2,
-                          const double *__restrict__ npart, const double *__restrict__ fnorm,
-                          double tol, double *__restrict__ hn_out, int *__restrict__ flag,
-                          double *__restrict__ hist, int hstride, int it) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= B.nrhs || (B.active && !B.active[r])) return;
-    const int R = B.R;
+// Outer Arnoldi column j of every active RHS (one CTA of OG threads each).  H keeps the
+// unrotated columns h = h1 + h2 (CGS2) with h_{j+1,j} = sqrt(Σ norm partials) below them; the
+// rotated entry that rotation j needs is formed without the sequential chain of the j earlier
+// rotations: with Q_jᵀ = G_{j-1}⋯G_0 and W_j its row j, (Q_jᵀ h)_j = W_j · h (a parallel dot
+// product), and G_j gives W_{j+1} = [-conj(s_j) W_j, c_j] (Wq, updated in place).  k_orotate
+// forms the triangular factor at the end of a cycle.  Then the g update; flag[r] = 1 while
+// |g_{j+1}| > tol·||f_r|| and h_{j+1,j} > 0; hist[r·hstride + it] records |g_{j+1}|/||f_r||.
+constexpr int OG = 128;
+__global__ void __launch_bounds__(OG)
+k_ogivens(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs, double2 *__restrict__ sn,
+          double2 *__restrict__ g, double2 *__restrict__ Wq, int j, const double2 *__restrict__ h1,
+          const double2 *__restrict__ h2, const double *__restrict__ npart, const double *__restrict__ fnorm,
+          double tol, double *__restrict__ hn_out, int *__restrict__ flag, double *__restrict__ hist,
+          int hstride, int it) {
+    __shared__ double red[OG / 32], redx[OG / 32], redy[OG / 32];
+    __shared__ double c_s;
+    __shared__ double2 s_s;
+    const int r = blockIdx.x;
+    if (B.active && !B.active[r]) return;
+    const int R = B.R, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     H += (long long)r * (R + 1) * R; cs += (long long)r * R; sn += (long long)r * R;
-    g += (long long)r * (R + 1); h1 += (long long)r * B.ldp; h2 += (long long)r * B.ldp;
-    npart += (long long)r * B.G;
-    double s2 = 0.0;
-    for (int q = 0; q < B.G; q++) s2 += npart[q];
-    const double hn = sqrt(s2);
+    g += (long long)r * (R + 1); Wq += (long long)r * (R + 1);
+    h1 += (long long)r * B.ldp; h2 += (long long)r * B.ldp; npart += (long long)r * B.G;
     double2 *hc = H + (long long)j * (R + 1);
-    for (int l = 0; l <= j; l++) hc[l] = make_double2(h1[l].x + h2[l].x, h1[l].y + h2[l].y);
-    for (int l = 0; l < j; l++) {
-        double2 x = hc[l], y = hc[l + 1], sx = sn[l];
-        double2 a = cmul<double>(sx, y);
-        double2 bq = cmul<double>(make_double2(sx.x, -sx.y), x);
-        hc[l] = make_double2(cs[l] * x.x + a.x, cs[l] * x.y + a.y);
-        hc[l + 1] = make_double2(cs[l] * y.x - bq.x, cs[l] * y.y - bq.y);
+    double s2 = 0.0;
+    for (int q = tid; q < B.G; q += OG) s2 += npart[q];
+    double dx = 0.0, dy = 0.0;
+    for (int l = tid; l <= j; l += OG) {
+        const double2 hv = make_double2(h1[l].x + h2[l].x, h1[l].y + h2[l].y);
+        hc[l] = hv;
+        const double2 wl = Wq[l];
+        dx = fma(wl.x, hv.x, fma(-wl.y, hv.y, dx));
+        dy = fma(wl.x, hv.y, fma(wl.y, hv.x, dy));
     }
-    double c; double2 s, rr;
-    zgivens(hc[j], make_double2(hn, 0.0), c, s, rr);
-    cs[j] = c; sn[j] = s;
-    hc[j] = rr;
-    double2 gj = g[j];
-    g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-    g[j] = make_double2(c * gj.x, c * gj.y);
-    const double res = hypot(g[j + 1].x, g[j + 1].y);
-    hn_out[r] = hn;
-    hist[(long long)r * hstride + it] = res / fnorm[r];
-    flag[r] = (res > tol * fnorm[r] && hn > 0.0) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += shfl_xor(s2, o); dx += shfl_xor(dx, o); dy += shfl_xor(dy, o);
+    }
+    if (lane == 0) { red[warp] = s2; redx[warp] = dx; redy[warp] = dy; }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, bx = 0.0, by = 0.0;
+        for (int q = 0; q < OG / 32; q++) { a += red[q]; bx += redx[q]; by += redy[q]; }
+        const double hn = sqrt(a);
+        hc[j + 1] = make_double2(hn, 0.0);
+        double c; double2 sr, rr;
+        zgivens(make_double2(bx, by), make_double2(hn, 0.0), c, sr, rr);
+        cs[j] = c; sn[j] = sr;
+        c_s = c; s_s = sr;
+        const double2 gj = g[j];
+        g[j + 1] = make_double2(-(sr.x * gj.x + sr.y * gj.y), -(sr.x * gj.y - sr.y * gj.x));
+        g[j] = make_double2(c * gj.x, c * gj.y);
+        const double res = hypot(g[j + 1].x, g[j + 1].y);
+        hn_out[r] = hn;
+        hist[(long long)r * hstride + it] = res / fnorm[r];
+        flag[r] = (res > tol * fnorm[r] && hn > 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    const double c = c_s;
+    const double2 sr = s_s;
+    for (int l = tid; l <= j; l += OG) {             // W_{j+1} = [-conj(s_j) W_j, c_j]
+        const double2 wl = Wq[l];
+        Wq[l] = make_double2(-(sr.x * wl.x + sr.y * wl.y), -(sr.x * wl.y - sr.y * wl.x));
+    }
+    if (tid == 0) Wq[j + 1] = make_double2(c, 0.0);
+}
+
+// End of a cycle: the triangular factor of every RHS's Hessenberg matrix, column k < kcols[r]
+// per thread: rotations 0..k-1 applied in order to the stored column, then rotation k to its
+// last two entries (x, h_{k+1,k}), leaving R(0:k, k) in place.
+__global__ void k_orotate(OuterBatch B, double2 *__restrict__ H, const double *__restrict__ cs,
+                          const double2 *__restrict__ sn, const int *__restrict__ kcols) {
+    const int r = blockIdx.y, k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kcols[r]) return;
+    const int R = B.R;
+    double2 *col = H + (long long)r * (R + 1) * R + (long long)k * (R + 1);
+    cs += (long long)r * R; sn += (long long)r * R;
+    double2 x = col[0];
+    for (int l = 0; l <= k; l++) {
+        const double2 y = col[l + 1], sv = sn[l];
+        const double c = cs[l];
+        const double2 a = cmul<double>(sv, y);
+        const double2 bq = cmul<double>(make_double2(sv.x, -sv.y), x);
+        col[l] = make_double2(c * x.x + a.x, c * x.y + a.y);
+        x = make_double2(c * y.x - bq.x, c * y.y - bq.y);
+    }
 }
 
 // V_{r,j+1} = w_r / hn_r, and its FP32 copy out32 (if not null)
@@ -412,10 +458,11 @@ __global__ void k_oaxpy(OuterBatch B, const double2 *__restrict__ y, const int *
 }
 
 // Cycle start for every active RHS: β_r = sqrt(Σ partials), v_{r,0} = r_r/β_r,
-// g_r = [β_r, 0, ..., 0] (R+1 entries); FP32 copy of v_{r,0} in V32 (if not null).
+// g_r = [β_r, 0, ..., 0] (R+1 entries); FP32 copy of v_{r,0} in V32 (if not null); row 0 of the
+// (empty) rotation product, Wq_r = [1].
 __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const double *__restrict__ npart,
                         double2 *__restrict__ V, float2 *__restrict__ V32, double2 *__restrict__ g,
-                        double *__restrict__ beta_out) {
+                        double2 *__restrict__ Wq, double *__restrict__ beta_out) {
     __shared__ double beta_s;
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
@@ -428,8 +475,10 @@ __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const doub
     }
     __syncthreads();
     const double beta = beta_s;
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int l = threadIdx.x; l <= B.R; l += blockDim.x) g[l] = make_double2(l == 0 ? beta : 0.0, 0.0);
+        if (threadIdx.x == 0) Wq[(long long)r * (B.R + 1)] = make_double2(1.0, 0.0);
+    }
     if (!(beta > 0.0)) return;
     const double inv = 1.0 / beta;
     float2 *v32 = V32 ? V32 + r * B.n : nullptr;
@@ -475,12 +524,16 @@ void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStrea
 void launch_oreduce(const OuterBatch &B, const double2 *part, int nv, double2 *out, cudaStream_t s) {
     k_oreduce<<<dim3((nv + 7) / 8, B.nrhs), 256, 0, s>>>(B, part, nv, out);
 }
-void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, int j,
+void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,
                     const double2 *h1, const double2 *h2, const double *npart, const double *fnorm,
                     double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
                     cudaStream_t s) {
-    k_ogivens<<<(B.nrhs + 31) / 32, 32, 0, s>>>(B, H, cs, sn, g, j, h1, h2, npart, fnorm, tol, hn_out, flag,
-                                                hist, hstride, it);
+    k_ogivens<<<B.nrhs, OG, 0, s>>>(B, H, cs, sn, g, Wq, j, h1, h2, npart, fnorm, tol, hn_out, flag, hist,
+                                    hstride, it);
+}
+void launch_orotate(const OuterBatch &B, double2 *H, const double *cs, const double2 *sn, const int *kcols,
+                    int kmax, cudaStream_t s) {
+    k_orotate<<<dim3((kmax + 63) / 64, B.nrhs), 64, 0, s>>>(B, H, cs, sn, kcols);
 }
 void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, const double2 *w, const double *hn,
                    cudaStream_t s) {
@@ -495,8 +548,8 @@ void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int k
     k_oaxpy<<<dim3(grid_for(B.n, 256), B.nrhs), 256, (size_t)kmax * sizeof(double2), s>>>(B, y, kcols, Zb, x);
 }
 void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
-                  double2 *g, double *beta_out, cudaStream_t s) {
-    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, V32, g, beta_out);
+                  double2 *g, double2 *Wq, double *beta_out, cudaStream_t s) {
+    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, V32, g, Wq, beta_out);
 }
 cudaError_t set_outer_smem_limits(size_t bytes) {
     cudaError_t e;
