@@ -41,9 +41,9 @@ struct FactorSet {            // banded FP64 factors of one matrix per shape, bl
     DevMem M, P, Meta, table;
     std::vector<BlockFactor> h;
     std::vector<double> fma_col;    // FP64 FMAs of one real column by banded substitution, per shape
-    int maxlen = 0, maxK = 0;       // shared-memory sizing of the blocked solve
+    BlockSolveCfg cfg;              // shared-memory plan of the blocked solve
     bool ready = false;
-    void clear() { M.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); maxlen = maxK = 0; ready = false; }
+    void clear() { M.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); cfg = BlockSolveCfg{}; ready = false; }
 };
 
 template <typename R> struct InnerWork {   // inner GMRES buffers for one precision
@@ -322,8 +322,9 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
         double fm = 0;
         for (int j = 0; j < m[q]; j++) fm += std::min(kl[q], m[q] - 1 - j) + ue[j];
         F.fma_col[q] = fm;
-        F.maxlen = std::max(F.maxlen, nbk * BNB + std::max(b.wl, b.wu));
-        F.maxK = std::max(F.maxK, BNB + std::max(b.wl, b.wu));
+        F.cfg.maxK = std::max(F.cfg.maxK, BNB + std::max(b.wl, b.wu));
+        while (F.cfg.cwy < BNB + b.wl) F.cfg.cwy = F.cfg.cwy ? 2 * F.cfg.cwy : BNB;
+        while (F.cfg.cwx < BNB + b.wu) F.cfg.cwx = F.cfg.cwx ? 2 * F.cfg.cwx : BNB;
     }
     if (mo >= (1LL << 31)) FAIL(HDD_ERR_INVALID_ARG, "blocked factors exceed 2^31 doubles");
     CK(F.M.ensure((size_t)std::max(mo, 1LL) * sizeof(double)));
@@ -337,9 +338,10 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
     CK(F.table.ensure(ns * sizeof(BlockFactor)));
     CK(cudaMemcpyAsync(F.table.p, F.h.data(), ns * sizeof(BlockFactor), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
-    if (set_block_solve_smem(F.maxlen, F.maxK) != cudaSuccess)
-        FAIL(HDD_ERR_INVALID_ARG, "factor of order %d (panel %d) exceeds the shared-memory solve",
-             F.maxlen, F.maxK);
+    if (F.cfg.cwy == 0) F.cfg.cwy = BNB;
+    if (F.cfg.cwx == 0) F.cfg.cwx = BNB;
+    if (set_block_solve_smem(F.cfg) != cudaSuccess)
+        FAIL(HDD_ERR_INVALID_ARG, "factor panels of width %d exceed the shared-memory solve", F.cfg.maxK);
     F.ready = true;
     return HDD_OK;
 }
@@ -353,8 +355,7 @@ void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *ou
     fl = 4.0 * fl * (nact < 0 ? 1.0 : (double)nact / nt);      // 2 columns x 2 flops per FMA
     Launch L(ctx, F_COARSE, fl * 2.0, fl, s);
     launch_block_solve(ctx->d_tasks.as<Task>(), nt, F.table.as<BlockFactor>(), F.M.as<double>(),
-                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, F.maxlen,
-                       F.maxK, s);
+                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, F.cfg, s);
 }
 
 // ---- learned warm start ---------------------------------------------------------------------
@@ -1407,7 +1408,7 @@ hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev,
     launch_zt<double>(a, in, y, 1, nullptr, s);                                        // y = Zᵀ A v
     launch_block_solve(ctx->d_tasks.as<Task>(), (int)ctx->h_tasks.size(), F.table.as<BlockFactor>(),
                        F.M.as<double>(), F.P.as<int>(), F.Meta.as<int4>(), y, sc, 0, nullptr,
-                       F.maxlen, F.maxK, s);                                            // s = E⁻¹ y
+                       F.cfg, s);                                                       // s = E⁻¹ y
     launch_prolong_stencil<double>(a, 0, in, sc, out, nullptr, 0, scratch, nullptr, s); // A(v - Z s)
     ctx->prof.launches += 3;
     CKL();

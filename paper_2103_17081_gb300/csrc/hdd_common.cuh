@@ -167,10 +167,15 @@ void launch_factor_prepare(int m, int kl, int ku, const double *ab, const int *p
                            double *Lp, int *lext, int *uext, int *perm, int *err, cudaStream_t s);
 void launch_block_operators(int m, int kl, int ku, const double *ab, int KLW, const double *Lp,
                             const int4 *meta, double *Mall, cudaStream_t s);
+struct BlockSolveCfg {       // shared-memory plan of the blocked solve over a set of factors
+    int maxK = 0;          // widest operator row: BNB + panel width
+    int cwy = 0, cwx = 0;  // circular y / x windows, powers of two >= BNB + widest left / right panel
+    int ring = 0;          // operator ring depth (4 or 2), chosen by set_block_solve_smem
+};
 void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
                         const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
-                        int use_fine, const int *flag, int maxlen, int maxK, cudaStream_t s);
-cudaError_t set_block_solve_smem(int maxlen, int maxK);
+                        int use_fine, const int *flag, const BlockSolveCfg &cfg, cudaStream_t s);
+cudaError_t set_block_solve_smem(BlockSolveCfg &cfg);
 
 // learned warm start (kernels_cnn.cu)
 constexpr int CNN_NPARAM = 20258;          // 4 conv3x3 layers: 4->32, 32->32, 32->32, 32->2

@@ -300,10 +300,12 @@ constexpr int BS_LPR = BS_T / BNB;        // lanes per row (8)
 
 // y = M_J [a ; window] for the BNB rows of block J: lane `part` of row r sums the columns
 // part, part + BS_LPR, ... of the row with four independent accumulators (operands loaded
-// ahead of the FMAs), then the row's lanes reduce by shuffles.
+// ahead of the FMAs), then the row's lanes reduce by shuffles.  The window is read from a
+// circular buffer: column c of the panel is win[(base + c) & mask].
 __device__ __forceinline__ double block_row_dot(const double *__restrict__ Mrow, int K,
                                                 const double *__restrict__ a,
-                                                const double *__restrict__ win, int part) {
+                                                const double *__restrict__ win, int base, int mask,
+                                                int part) {
     double s0 = Mrow[part] * a[part];
     double s1 = Mrow[part + BS_LPR] * a[part + BS_LPR];
     double s2 = 0.0, s3 = 0.0;
@@ -312,10 +314,11 @@ __device__ __forceinline__ double block_row_dot(const double *__restrict__ Mrow,
     for (; c + 3 * BS_LPR < WL; c += 4 * BS_LPR) {
         const double m0 = Mrow[BNB + c], m1 = Mrow[BNB + c + BS_LPR];
         const double m2 = Mrow[BNB + c + 2 * BS_LPR], m3 = Mrow[BNB + c + 3 * BS_LPR];
-        const double w0 = win[c], w1 = win[c + BS_LPR], w2 = win[c + 2 * BS_LPR], w3 = win[c + 3 * BS_LPR];
+        const double w0 = win[(base + c) & mask], w1 = win[(base + c + BS_LPR) & mask];
+        const double w2 = win[(base + c + 2 * BS_LPR) & mask], w3 = win[(base + c + 3 * BS_LPR) & mask];
         s0 = fma(m0, w0, s0); s1 = fma(m1, w1, s1); s2 = fma(m2, w2, s2); s3 = fma(m3, w3, s3);
     }
-    for (; c < WL; c += BS_LPR) s0 = fma(Mrow[BNB + c], win[c], s0);
+    for (; c < WL; c += BS_LPR) s0 = fma(Mrow[BNB + c], win[(base + c) & mask], s0);
     s0 = (s0 + s1) + (s2 + s3);
 #pragma unroll
     for (int o = BS_LPR / 2; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -325,95 +328,111 @@ __device__ __forceinline__ double block_row_dot(const double *__restrict__ Mrow,
 template <int N> __device__ __forceinline__ void cp_async_wait_n() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
-constexpr int BS_RING = 4;                // operator buffers; BS_RING-1 blocks in flight
+// 8-byte asynchronous copy; src_size 0 fills the destination with zeros without reading.
+__device__ __forceinline__ void cp_async8_zfill(void *smem_dst, const void *gsrc, int src_size) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_size) : "memory");
+}
 
-// x = F⁻¹ b with the blocked operators, one CTA per (task, component).  The operators stream
-// through a ring of BS_RING shared-memory buffers by cp.async, BS_RING-1 blocks ahead of the
-// block being applied (they are usually evicted from L2 between solves); one barrier per block.
-__global__ void __launch_bounds__(BS_T)
+// x = F⁻¹ b with the blocked operators, one CTA per (task, component).  Shared memory holds only
+// a ring of RING slots — the operator of one block plus that block's BNB input values, streamed
+// by cp.async RING-1 blocks ahead of the block being applied — and two circular windows (cwy,
+// cwx entries, powers of two >= BNB + panel width) of the latest y and x values; so the order of
+// the factor is not limited by shared memory.  The output vector carries the rest: it first
+// receives P b (gathered), the forward sweep overwrites block J with y_J after reading it, and the
+// backward sweep overwrites block J with x_J after reading y_J.  One barrier per block.
+template <int RING>
+__global__ void __launch_bounds__(BS_T, 2)
 k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ shapes,
               const double *__restrict__ Mall, const int *__restrict__ Pall,
               const int4 *__restrict__ Meta, const double2 *__restrict__ in,
-              double2 *__restrict__ out, int use_fine, const int *__restrict__ flag, int maxlen,
-              int maxK) {
+              double2 *__restrict__ out, int use_fine, const int *__restrict__ flag, int maxK,
+              int cwy, int cwx) {
     extern __shared__ double sm[];
     const int t = blockIdx.x >> 1, comp = blockIdx.x & 1;
     if (flag && !flag[t]) return;
     const Task T = tasks[t];
     const BlockFactor F = shapes[T.shape];
     const long long off = use_fine ? T.foff : T.coff;
-    const int m = F.m, nbk = F.nblk, WL = F.wl, WU = F.wu;
-    double *Y = sm;                         // WL zeros, then y (nbk*BNB)
-    double *X = sm + maxlen;                // Pb during the forward sweep; x (+ WU zeros) after
-    double *Mb = sm + 2 * maxlen;           // BS_RING x BNB x maxK
+    const int m = F.m, nbk = F.nblk;
+    const int slot = BNB * maxK + BNB;
+    double *CY = sm + RING * slot, *CX = CY + cwy;
     const int *perm = Pall + F.perm_off;
     const int4 *meta = Meta + F.meta_off;
     const double *inr = reinterpret_cast<const double *>(in + off) + comp;
+    double *outr = reinterpret_cast<double *>(out + off) + comp;
     const int tid = threadIdx.x, row = tid / BS_LPR, part = tid % BS_LPR;
-    auto load_block = [&](long long src_off, int K, int buf) {
-        const int nchunk = BNB * K / 2;                 // 16-byte chunks
+    // operator of block J (src_off, K = BNB + panel) and its BNB inputs from outr into slot buf
+    auto load_block = [&](long long src_off, int K, int buf, int J) {
+        double *dst = sm + buf * slot;
         const double *src = Mall + src_off;
-        double *dst = Mb + buf * BNB * maxK;
+        const int nchunk = BNB * K / 2;                 // 16-byte chunks
         for (int q = tid; q < nchunk; q += BS_T) cp_async16(dst + 2 * q, src + 2 * q);
+        if (tid < BNB) {
+            const int i = J * BNB + tid;
+            cp_async8_zfill(dst + BNB * maxK + tid, i < m ? outr + 2 * (long long)i : outr, i < m ? 8 : 0);
+        }
     };
-    // forward operators of blocks 0 .. BS_RING-2 in flight while the right-hand side is gathered
+    // (P b) into the output; zero windows (positions before 0 / after the end read zeros)
+    for (int i = tid; i < m; i += BS_T) outr[2 * (long long)i] = inr[2 * (long long)perm[i]];
+    for (int i = tid; i < cwy; i += BS_T) CY[i] = 0.0;
+    for (int i = tid; i < cwx; i += BS_T) CX[i] = 0.0;
+    __threadfence_block();
+    __syncthreads();
+    // ---- forward: y_J = M_J [(Pb)_J ; y_{J-w_J..J}] ----
 #pragma unroll
-    for (int u = 0; u < BS_RING - 1; u++) {
-        if (u < nbk) { const int4 mt = meta[u]; load_block(mt.x, BNB + mt.y, u); }
+    for (int u = 0; u < RING - 1; u++) {
+        if (u < nbk) { const int4 mt = meta[u]; load_block(mt.x, BNB + mt.y, u, u); }
         cp_async_commit();
     }
-    for (int i = tid; i < WL; i += BS_T) Y[i] = 0.0;
-    for (int i0 = 0; i0 < nbk * BNB; i0 += 4 * BS_T) {      // (P b): four gathers in flight
-        int pi[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) { const int i = i0 + u * BS_T + tid; pi[u] = i < m ? perm[i] : -1; }
-        double v[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) v[u] = pi[u] >= 0 ? inr[2 * (long long)pi[u]] : 0.0;
-#pragma unroll
-        for (int u = 0; u < 4; u++) { const int i = i0 + u * BS_T + tid; if (i < nbk * BNB) X[i] = v[u]; }
-    }
-    // ---- forward: y_J = M_J [(Pb)_J ; y_{J-w_J..J}] ----
     for (int J = 0; J < nbk; J++) {
         const int wJ = meta[J].y;
-        cp_async_wait_n<BS_RING - 2>();
+        cp_async_wait_n<RING - 2>();
         __syncthreads();
-        if (J + BS_RING - 1 < nbk) {
-            const int4 mt = meta[J + BS_RING - 1];
-            load_block(mt.x, BNB + mt.y, (J + BS_RING - 1) % BS_RING);
+        if (J + RING - 1 < nbk) {
+            const int4 mt = meta[J + RING - 1];
+            load_block(mt.x, BNB + mt.y, (J + RING - 1) % RING, J + RING - 1);
         }
         cp_async_commit();
-        const double *Mrow = Mb + (J % BS_RING) * BNB * maxK + row * (BNB + wJ);
-        const double v = block_row_dot(Mrow, BNB + wJ, X + J * BNB, Y + WL + J * BNB - wJ, part);
-        if (part == 0) Y[WL + J * BNB + row] = v;
+        const double *Mb = sm + (J % RING) * slot;
+        const double v = block_row_dot(Mb + row * (BNB + wJ), BNB + wJ, Mb + BNB * maxK, CY, J * BNB - wJ,
+                                       cwy - 1, part);
+        if (part == 0) {
+            const int i = J * BNB + row;
+            CY[i & (cwy - 1)] = v;
+            if (i < m) outr[2 * (long long)i] = v;
+        }
     }
     cp_async_wait_n<0>();
+    __threadfence_block();
     __syncthreads();
     // ---- backward: x_J = M_J [y_J ; x_{J+1..J+w_J}] ----
 #pragma unroll
-    for (int u = 0; u < BS_RING - 1; u++) {
+    for (int u = 0; u < RING - 1; u++) {
         const int J = nbk - 1 - u;
-        if (J >= 0) { const int4 mt = meta[J]; load_block(mt.z, BNB + mt.w, u); }
+        if (J >= 0) { const int4 mt = meta[J]; load_block(mt.z, BNB + mt.w, u, J); }
         cp_async_commit();
     }
-    for (int i = tid; i < nbk * BNB + WU; i += BS_T) X[i] = 0.0;
     for (int J = nbk - 1; J >= 0; J--) {
         const int k = nbk - 1 - J;                          // sweep position
         const int wJ = meta[J].w;
-        cp_async_wait_n<BS_RING - 2>();
+        cp_async_wait_n<RING - 2>();
         __syncthreads();
-        if (J - (BS_RING - 1) >= 0) {
-            const int4 mt = meta[J - (BS_RING - 1)];
-            load_block(mt.z, BNB + mt.w, (k + BS_RING - 1) % BS_RING);
+        if (J - (RING - 1) >= 0) {
+            const int4 mt = meta[J - (RING - 1)];
+            load_block(mt.z, BNB + mt.w, (k + RING - 1) % RING, J - (RING - 1));
         }
         cp_async_commit();
-        const double *Mrow = Mb + (k % BS_RING) * BNB * maxK + row * (BNB + wJ);
-        const double v = block_row_dot(Mrow, BNB + wJ, Y + WL + J * BNB, X + (J + 1) * BNB, part);
-        if (part == 0) X[J * BNB + row] = v;
+        const double *Mb = sm + (k % RING) * slot;
+        const double v = block_row_dot(Mb + row * (BNB + wJ), BNB + wJ, Mb + BNB * maxK, CX, (J + 1) * BNB,
+                                       cwx - 1, part);
+        if (part == 0) {
+            const int i = J * BNB + row;
+            CX[i & (cwx - 1)] = v;
+            if (i < m) outr[2 * (long long)i] = v;
+        }
     }
-    __syncthreads();
-    double *outr = reinterpret_cast<double *>(out + off) + comp;
-    for (int i = tid; i < m; i += BS_T) outr[2 * (long long)i] = X[i];
+    cp_async_wait_n<0>();
 }
 
 void launch_assemble_E(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s) {
@@ -440,19 +459,29 @@ void launch_block_operators(int m, int kl, int ku, const double *ab, int KLW, co
     k_block_fwd<<<nbk, 128, 0, s>>>(m, KLW, Lp, meta, Mall);
     k_block_bwd<<<nbk, 128, 0, s>>>(m, kl, ku, ab, meta, Mall);
 }
-static size_t bs_smem(int maxlen, int maxK) {
-    return (2 * (size_t)maxlen + (size_t)BS_RING * BNB * maxK) * sizeof(double);
+static size_t bs_smem(const BlockSolveCfg &c, int ring) {
+    return ((size_t)ring * ((size_t)BNB * c.maxK + BNB) + (size_t)c.cwy + (size_t)c.cwx) * sizeof(double);
 }
 void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
                         const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
-                        int use_fine, const int *flag, int maxlen, int maxK, cudaStream_t s) {
-    k_block_solve<<<2 * ntasks, BS_T, bs_smem(maxlen, maxK), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
-                                                                 use_fine, flag, maxlen, maxK);
+                        int use_fine, const int *flag, const BlockSolveCfg &c, cudaStream_t s) {
+    if (c.ring == 4)
+        k_block_solve<4><<<2 * ntasks, BS_T, bs_smem(c, 4), s>>>(tasks, shapes, Mall, Pall, Meta, in, out, use_fine,
+                                                                 flag, c.maxK, c.cwy, c.cwx);
+    else
+        k_block_solve<2><<<2 * ntasks, BS_T, bs_smem(c, 2), s>>>(tasks, shapes, Mall, Pall, Meta, in, out, use_fine,
+                                                                 flag, c.maxK, c.cwy, c.cwx);
 }
-cudaError_t set_block_solve_smem(int maxlen, int maxK) {
-    const size_t bytes = bs_smem(maxlen, maxK);
-    if (bytes > 227 * 1024) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(k_block_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// Ring depth 4 if its shared memory fits the per-CTA limit, else 2; error if not even that fits.
+// The kernels' attribute is raised to the limit itself (several factor sets with different plans
+// share the kernels; each launch requests only what its plan needs).
+cudaError_t set_block_solve_smem(BlockSolveCfg &c) {
+    const size_t lim = 227 * 1024;
+    c.ring = bs_smem(c, 4) <= lim ? 4 : 2;
+    if (bs_smem(c, c.ring) > lim) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_block_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
 }
 
 }  // namespace hdd

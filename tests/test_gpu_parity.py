@@ -118,6 +118,23 @@ def test_ras_exact_matches_oracle(oracle_mod):
     assert _rel(zg.cpu().numpy(), zo) < 1e-10
 
 
+def test_large_box_coarse_and_direct_solves(oracle_mod):
+    """Boxes of 220 x 220 nodes (N = 440, 2x2 subdomains, overlap 1): E_j of order 12,100 with
+    half-bandwidth 222 and A_j of order 48,400 — larger than a solve that keeps whole vectors in
+    shared memory could hold; the blocked solve streams them (ring depth 2 here)."""
+    w = W.custom(20.0, 440, 2, 1, name="bigbox")
+    s, p = _pair(oracle_mod, w, exact=True)
+    fo, co = s.offsets()
+    xc = W.random_complex_fast(co[-1], 21)
+    xf = W.random_complex_fast(fo[-1], 22)
+    e = s.local_op("Einv", _to_dev(xc)).cpu().numpy()
+    a = s.local_op("Ainv", _to_dev(xf)).cpu().numpy()
+    for q in (0, 3):
+        F, Cc = slice(fo[q], fo[q + 1]), slice(co[q], co[q + 1])
+        assert _rel(e[Cc], p.coarse_solve(q, xc[Cc])) < 1e-10
+        assert _rel(a[F], p.sub_solve_exact(q, xf[F])) < 1e-9
+
+
 @pytest.mark.parametrize("prec", [128, 64])
 def test_tiny_solve_matches_oracle(oracle_mod, prec):
     w = W.make("tiny")
