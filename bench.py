@@ -162,6 +162,9 @@ def run_gpu(args):
     kw = dict(outer_tol=w.outer_tol, inner_tol=w.inner_tol, inner_prec=args.prec,
               outer_restart=args.outer_maxit, outer_maxit=args.outer_maxit,
               outer_reorth32=0 if args.fp64_reorth else 1)
+    tiles = None
+    if args.autotune:
+        tiles = s.autotune(inner_tol=w.inner_tol, inner_prec=args.prec)
     if args.warm_start:
         from paper_2103_17081_gb300 import warmstart
         s.cnn_set_params(warmstart.load(args.warm_start))
@@ -260,6 +263,7 @@ def run_gpu(args):
                        "inner_tol": w.inner_tol, "outer_tol": w.outer_tol, "inner_prec": args.prec,
                        "l2": "flushed between timed steps (512 MB write)",
                        "warm_start": bool(args.warm_start), "outer_reorth": "fp64" if args.fp64_reorth else "fp32-guarded",
+                       "tiles": tiles or {"fine_rows": 8, "coarse_rows": 4},
                        "parallelism": "replicas" if ws > 1 else "single"},
             "solve": {"outer_its": stats["outer_its"], "inner_its_avg": round(stats["inner_its_avg"], 3),
                       "rel_res_true": rel, "status": stats["status_code"]},
@@ -297,6 +301,8 @@ def main():
     ap.add_argument("--warm-start", default=None,
                     help="parameter file of a trained warm-start network (written by "
                          "python -m paper_2103_17081_gb300.warmstart train)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the local tile shapes with hdd_autotune before the warm-up")
     ap.add_argument("--fp64-reorth", action="store_true",
                     help="second outer CGS pass in FP64 (default: guarded FP32 correction)")
     args = ap.parse_args()

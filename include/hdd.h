@@ -191,6 +191,19 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
 hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev,
                          const hdd_solve_params *prm, int *inner_its, void *stream);
 
+/* Tile-shape autotuner (no counterpart in the paper).  The batched local kernels work on tiles
+ * of a task's box: fine tiles of `fine_rows` box rows (fine_rows x box width <= 2048 nodes) and
+ * coarse tiles of `coarse_rows` coarse rows; defaults 8 and 4.  This times one RAS application
+ * (hdd_ras_apply with prm, on a fixed dense pseudo-random vector, best of two after a warm-up)
+ * for every admissible pair of fine_rows in {4, 6, 8, 12, 16, 24} and coarse_rows in {2, 4, 8},
+ * keeps the fastest pair for every later call on this context (until hdd_setup_dd /
+ * hdd_setup_batch rebuild the tiles with it), and returns it with its time (outputs may be
+ * NULL).  Tile shapes change the order of the per-tile partial sums, so results change at
+ * rounding level.  Needs hdd_setup_deflation (or hdd_setup_exact for inner_tol <= 0);
+ * allocates two global vectors for the duration of the call; synchronises the stream. */
+hdd_status hdd_autotune(hdd_ctx *ctx, const hdd_solve_params *prm, void *stream, int *fine_rows,
+                        int *coarse_rows, double *best_ms);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Local test hooks on packed local vectors (layout of hdd_get_offsets), complex128.         */
 /*   op 0: out = A_j in        (fine → fine, every subdomain)                                */

@@ -132,6 +132,7 @@ struct hdd_ctx {
     DevMem d_tasks, d_ftiles, d_ctiles, d_ones, d_mask;
     long long ld = 0, ldc = 0;
     int max_nx = 0, max_n = 0;
+    int frows = FINE_ROWS, crows = COARSE_ROWS;  // tile heights (hdd_autotune)
     std::vector<long long> foffs, coffs;
     std::vector<int2> h_tct;                    // tensor-core conv tiles (task, first frame position)
     DevMem d_tct;
@@ -208,6 +209,8 @@ template <typename R> LocalArgs<R> local_args(hdd_ctx *ctx) {
     a.ldc = ctx->ldc;
     a.max_nx = ctx->max_nx;
     a.gw = ctx->N - 1;
+    a.frows = ctx->frows;
+    a.crows = ctx->crows;
     return a;
 }
 
@@ -487,7 +490,7 @@ hdd_status cnn_loss_grad(hdd_ctx *ctx, const c2<R> *f, double *loss, cudaStream_
     // deflated residuals in FP32 with the solver's own kernels (coarse solves in FP64):
     //   P f̂, r = f̂ - A y, q = P r, Pᵀ q = q - Z E⁻¹ Zᵀ A q; dL/dy_t = scale_t · A Pᵀ q
     LocalArgs<float> a = local_args<float>(ctx);
-    const size_t lsm = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(float2));
+    const size_t lsm = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(float2), ctx->frows, ctx->crows);
     if (lsm > 48 * 1024) CK(set_local_smem_limits<float>(lsm));
     float2 *Fh = C.Fh.as<float2>(), *Q = C.Q.as<float2>(), *T2 = C.T2.as<float2>();
     float2 *Rr = reinterpret_cast<float2 *>(C.Rr.as<float>());
@@ -560,7 +563,7 @@ template <typename R> hdd_status ensure_inner(hdd_ctx *ctx, int R_) {
     CK(W.act0.ensure(nt * sizeof(int))); CK(W.act1.ensure(nt * sizeof(int)));
     CK(W.flagA.ensure(nt * sizeof(int))); CK(W.flagB.ensure(nt * sizeof(int)));
     W.restart = R_;
-    size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)cs);
+    size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)cs, ctx->frows, ctx->crows);
     if (smem > 48 * 1024) CK(set_local_smem_limits<R>(smem));
     return HDD_OK;
 }
@@ -777,9 +780,11 @@ cudaError_t noalloc_scratch(int device, double2 **out) {
 
 namespace {
 // Task and tile tables for nrhs right-hand sides: task t = r·nsub + s solves subdomain s for
-// RHS r; fine tiles of FINE_ROWS box rows, coarse tiles of COARSE_ROWS coarse rows.
+// RHS r; fine tiles of ctx->frows box rows, coarse tiles of ctx->crows coarse rows.
 hdd_status build_tasks(hdd_ctx *ctx, int nrhs) {
     const int ns = (int)ctx->subs.size();
+    // a fine tile holds at most LOCAL_THREADS·FINE_EPT nodes (one register slot per thread each)
+    while (ctx->frows > 1 && ctx->frows * ctx->max_nx > LOCAL_THREADS * FINE_EPT) ctx->frows--;
     ctx->h_tasks.clear(); ctx->h_ftiles.clear(); ctx->h_ctiles.clear(); ctx->h_tct.clear();
     ctx->foffs.assign(1, 0); ctx->coffs.assign(1, 0);
     long long fo = 0, co = 0, po = 0;
@@ -794,11 +799,11 @@ hdd_status build_tasks(hdd_ctx *ctx, int nrhs) {
             T.shape = ctx->sub_shape[q]; T.sub = q; T.rhs = r;
             T.foff = fo; T.coff = co;
             T.tile0 = (int)ctx->h_ftiles.size();
-            for (int y = 0; y < b.ny; y += FINE_ROWS)
-                ctx->h_ftiles.push_back(Tile{t, y, std::min(FINE_ROWS, b.ny - y)});
+            for (int y = 0; y < b.ny; y += ctx->frows)
+                ctx->h_ftiles.push_back(Tile{t, y, std::min(ctx->frows, b.ny - y)});
             T.ntiles = (int)ctx->h_ftiles.size() - T.tile0;
-            for (int y = 0; y < b.my; y += COARSE_ROWS)
-                ctx->h_ctiles.push_back(Tile{t, y, std::min(COARSE_ROWS, b.my - y)});
+            for (int y = 0; y < b.my; y += ctx->crows)
+                ctx->h_ctiles.push_back(Tile{t, y, std::min(ctx->crows, b.my - y)});
             T.poff = po;
             const int nxp = b.nx + 2;
             for (long long q0 = nxp; q0 < (long long)(b.ny + 1) * nxp; q0 += 128)
@@ -1236,6 +1241,65 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     return result;
 }
 
+hdd_status hdd_autotune(hdd_ctx *ctx, const hdd_solve_params *prm, void *stream, int *fine_rows,
+                        int *coarse_rows, double *best_ms) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    hdd_status st = check_solve_params(ctx, prm);
+    if (st != HDD_OK) return st;
+    if (prm->inner_tol > 0 && !ctx->E.ready) FAIL(HDD_ERR_STATE, "hdd_setup_deflation first");
+    if (prm->inner_tol <= 0 && !ctx->Aex.ready) FAIL(HDD_ERR_STATE, "hdd_setup_exact first");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long nv = (long long)ctx->nrhs * ctx->nglob;
+    DevMem v, z;
+    CK(v.ensure((size_t)nv * sizeof(double2)));
+    CK(z.ensure((size_t)nv * sizeof(double2)));
+    launch_fill_test(nv, 0x9e3779b97f4a7c15ULL, v.as<double2>(), s);
+    CKL();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); FAIL(HDD_ERR_CUDA, "cudaEventCreate"); }
+    const int f0 = ctx->frows, c0 = ctx->crows;
+    int bf = f0, bc = c0;
+    float best = 3.0e38f;
+    const int Fc[] = {4, 6, 8, 12, 16, 24}, Cc[] = {2, 4, 8};
+    for (int f : Fc) {
+        if (f * ctx->max_nx > LOCAL_THREADS * FINE_EPT) continue;
+        for (int c : Cc) {
+            if (local_max_dynamic_smem(ctx->max_nx, (int)sizeof(double2), f, c) > 227 * 1024) continue;
+            ctx->frows = f; ctx->crows = c;
+            if ((st = build_tasks(ctx, ctx->nrhs)) != HDD_OK) break;
+            float t = 3.0e38f;
+            for (int rep = 0; rep < 3 && st == HDD_OK; rep++) {      // rep 0: buffers, attributes
+                if (cudaMemsetAsync(z.p, 0, (size_t)nv * sizeof(double2), s) != cudaSuccess ||
+                    cudaEventRecord(e0, s) != cudaSuccess) { st = HDD_ERR_CUDA; break; }
+                st = ras_apply(ctx, v.as<double2>(), z.as<double2>(), prm, s, nullptr, nullptr, nullptr, nullptr);
+                if (st != HDD_OK) break;
+                float ms = 0.f;
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = HDD_ERR_CUDA; break; }
+                if (rep > 0) t = std::min(t, ms);
+            }
+            if (st != HDD_OK) break;
+            if (t < best) { best = t; bf = f; bc = c; }
+        }
+        if (st != HDD_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->prof.harvest();
+    if (st != HDD_OK) { bf = f0; bc = c0; }
+    ctx->frows = bf; ctx->crows = bc;
+    const hdd_status st2 = build_tasks(ctx, ctx->nrhs);
+    if (st != HDD_OK) return st;
+    if (st2 != HDD_OK) return st2;
+    if (fine_rows) *fine_rows = bf;
+    if (coarse_rows) *coarse_rows = bc;
+    if (best_ms) *best_ms = best;
+    return HDD_OK;
+}
+
 hdd_status hdd_setup_batch(hdd_ctx *ctx, int nrhs) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
@@ -1398,7 +1462,7 @@ hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev,
     CK(noalloc_scratch(ctx->device, &scratch));
     cudaStream_t s = (cudaStream_t)stream;
     LocalArgs<double> a = local_args<double>(ctx);
-    const size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(double2));
+    const size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(double2), ctx->frows, ctx->crows);
     if (smem > 48 * 1024) CK(set_local_smem_limits<double>(smem));
     double2 *y = scratch, *sc = scratch + HDD_NOALLOC_MAX_COARSE;
     const double2 *in = (const double2 *)in_dev;
@@ -1433,7 +1497,7 @@ hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void
     auto run = [&](auto tag) -> hdd_status {
         using R = decltype(tag);
         LocalArgs<R> a = local_args<R>(ctx);
-        size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(c2<R>));
+        size_t smem = local_max_dynamic_smem(ctx->max_nx, (int)sizeof(c2<R>), ctx->frows, ctx->crows);
         if (smem > 48 * 1024) CK(set_local_smem_limits<R>(smem));
         CK(ctx->tmp_a.ensure(std::max(ld, ldc) * sizeof(c2<R>)));
         CK(ctx->tmp_b.ensure(std::max(ld, ldc) * sizeof(c2<R>)));

@@ -87,8 +87,9 @@ struct BlockFactor {        // FP64 banded LU with partial pivoting in blocked s
 constexpr int BNB = 16;    // rows per block of the blocked banded solve
 
 constexpr int MAX_RESTART = 64;       // inner GMRES restart bound (Hessenberg in registers/smem)
-constexpr int FINE_ROWS = 8;          // fine rows per fine tile
-constexpr int COARSE_ROWS = 4;        // coarse rows per coarse tile
+constexpr int FINE_ROWS = 8;          // default fine rows per fine tile (hdd_autotune may change it)
+constexpr int COARSE_ROWS = 4;        // default coarse rows per coarse tile
+constexpr int FINE_EPT = 8;           // fine elements per thread: a fine tile holds <= 256·8 nodes
 constexpr int LOCAL_THREADS = 256;    // threads per tile CTA
 
 // per-task inner GMRES state (precision R)
@@ -115,6 +116,7 @@ template <typename R> struct LocalArgs {
     long long ldc;     // packed coarse length
     int max_nx;        // largest box width (shared-memory sizing), <= 256
     int gw;            // global grid width N-1
+    int frows, crows;  // largest fine / coarse tile height (shared-memory sizing)
 };
 
 // local (batched over tasks), R = float or double
@@ -154,7 +156,7 @@ template <typename R> void launch_set_ref(const LocalArgs<R> &a, const InnerStat
 template <typename R> void launch_coarse_combine(const LocalArgs<R> &a, const InnerState<R> &S,
                                                  int restart, const double2 *sbuf, double2 *sc,
                                                  const int *flag, cudaStream_t s);
-size_t local_max_dynamic_smem(int max_nx, int bytes_per_c);
+size_t local_max_dynamic_smem(int max_nx, int bytes_per_c, int frows, int crows);
 void launch_cast(long long n, const void *in, int in_double, void *out, int out_double, cudaStream_t s);
 constexpr int LOCAL_LDP = MAX_RESTART + 2;   // partial-sum slots per fine tile
 
@@ -229,6 +231,7 @@ void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2
 void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
                      double2 *w, const double *npart1, double *part_norm, int allow32, int *fallbacks,
                      cudaStream_t s);
+void launch_fill_test(long long n, unsigned long long seed, double2 *x, cudaStream_t s);
 void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s);
 void launch_oreduce(const OuterBatch &B, const double2 *part, int nv, double2 *out, cudaStream_t s);
 void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,

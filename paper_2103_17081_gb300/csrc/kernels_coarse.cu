@@ -379,21 +379,32 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
     for (int i = tid; i < cwx; i += BS_T) CX[i] = 0.0;
     __threadfence_block();
     __syncthreads();
+    // Block descriptors (operator offsets and panel widths) are global; the one a step prefetches
+    // is loaded a step ahead (mnext), and the prefetching thread stores the panel width of each
+    // slot in sw[], so no global load sits on a step's dependent path.
+    __shared__ int sw[RING];
     // ---- forward: y_J = M_J [(Pb)_J ; y_{J-w_J..J}] ----
 #pragma unroll
     for (int u = 0; u < RING - 1; u++) {
-        if (u < nbk) { const int4 mt = meta[u]; load_block(mt.x, BNB + mt.y, u, u); }
+        if (u < nbk) {
+            const int4 mt = meta[u];
+            load_block(mt.x, BNB + mt.y, u, u);
+            if (tid == 0) sw[u] = mt.y;
+        }
         cp_async_commit();
     }
+    int4 mnext = RING - 1 < nbk ? meta[RING - 1] : make_int4(0, 0, 0, 0);
     for (int J = 0; J < nbk; J++) {
-        const int wJ = meta[J].y;
         cp_async_wait_n<RING - 2>();
         __syncthreads();
         if (J + RING - 1 < nbk) {
-            const int4 mt = meta[J + RING - 1];
-            load_block(mt.x, BNB + mt.y, (J + RING - 1) % RING, J + RING - 1);
+            const int buf = (J + RING - 1) % RING;
+            load_block(mnext.x, BNB + mnext.y, buf, J + RING - 1);
+            if (tid == 0) sw[buf] = mnext.y;
         }
         cp_async_commit();
+        if (J + RING < nbk) mnext = meta[J + RING];
+        const int wJ = sw[J % RING];
         const double *Mb = sm + (J % RING) * slot;
         const double v = block_row_dot(Mb + row * (BNB + wJ), BNB + wJ, Mb + BNB * maxK, CY, J * BNB - wJ,
                                        cwy - 1, part);
@@ -410,19 +421,26 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
 #pragma unroll
     for (int u = 0; u < RING - 1; u++) {
         const int J = nbk - 1 - u;
-        if (J >= 0) { const int4 mt = meta[J]; load_block(mt.z, BNB + mt.w, u, J); }
+        if (J >= 0) {
+            const int4 mt = meta[J];
+            load_block(mt.z, BNB + mt.w, u, J);
+            if (tid == 0) sw[u] = mt.w;
+        }
         cp_async_commit();
     }
+    mnext = nbk - RING >= 0 ? meta[nbk - RING] : make_int4(0, 0, 0, 0);
     for (int J = nbk - 1; J >= 0; J--) {
         const int k = nbk - 1 - J;                          // sweep position
-        const int wJ = meta[J].w;
         cp_async_wait_n<RING - 2>();
         __syncthreads();
         if (J - (RING - 1) >= 0) {
-            const int4 mt = meta[J - (RING - 1)];
-            load_block(mt.z, BNB + mt.w, (k + RING - 1) % RING, J - (RING - 1));
+            const int buf = (k + RING - 1) % RING;
+            load_block(mnext.z, BNB + mnext.w, buf, J - (RING - 1));
+            if (tid == 0) sw[buf] = mnext.w;
         }
         cp_async_commit();
+        if (J - RING >= 0) mnext = meta[J - RING];
+        const int wJ = sw[k % RING];
         const double *Mb = sm + (k % RING) * slot;
         const double v = block_row_dot(Mb + row * (BNB + wJ), BNB + wJ, Mb + BNB * maxK, CX, (J + 1) * BNB,
                                        cwx - 1, part);
@@ -476,12 +494,17 @@ void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes
 // The kernels' attribute is raised to the limit itself (several factor sets with different plans
 // share the kernels; each launch requests only what its plan needs).
 cudaError_t set_block_solve_smem(BlockSolveCfg &c) {
-    const size_t lim = 227 * 1024;
-    c.ring = bs_smem(c, 4) <= lim ? 4 : 2;
-    if (bs_smem(c, c.ring) > lim) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    cudaFuncAttributes a4, a2;
+    cudaError_t e = cudaFuncGetAttributes(&a4, k_block_solve<4>);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_block_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    if ((e = cudaFuncGetAttributes(&a2, k_block_solve<2>)) != cudaSuccess) return e;
+    const size_t lim = 227 * 1024;                        // per-CTA limit, static + dynamic
+    const size_t lim4 = lim - a4.sharedSizeBytes, lim2 = lim - a2.sharedSizeBytes;
+    c.ring = bs_smem(c, 4) <= lim4 ? 4 : 2;
+    if (bs_smem(c, c.ring) > (c.ring == 4 ? lim4 : lim2)) return cudaErrorInvalidValue;
+    if ((e = cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim4)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_block_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim2);
 }
 
 }  // namespace hdd

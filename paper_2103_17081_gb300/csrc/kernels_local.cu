@@ -1,7 +1,9 @@
 // kernels_local.cu — batched kernels of the inner deflated GMRES (§2 Eq. 4–5, §3), one CTA per
 // tile of one task, every task of every subdomain (and right-hand side) in one launch.
 //
-// Fine tiles cover FINE_ROWS box rows of one task; coarse tiles cover COARSE_ROWS coarse rows.
+// Fine tiles cover up to LocalArgs::frows box rows of one task (frows·nx <= LOCAL_THREADS·EPT);
+// coarse tiles cover up to LocalArgs::crows coarse rows.  Kernels read each tile's height from the
+// tile table; the host sizes shared memory for the largest heights.
 // Reductions are two-stage and deterministic: each tile writes its partial sums to a slot of
 // its own, and every consumer adds the partials of a task in tile order.
 #include "hdd_common.cuh"
@@ -9,7 +11,7 @@
 namespace hdd {
 
 constexpr int LDP = MAX_RESTART + 2;     // partial-sum slots per tile
-constexpr int EPT = 8;                   // fine elements per thread (FINE_ROWS*max_nx <= 2048)
+constexpr int EPT = FINE_EPT;            // fine elements per thread (frows*max_nx <= 2048)
 constexpr int NWARP = LOCAL_THREADS / 32;
 
 // 1D Bézier deflation weight (Eq. 5 factor): fine node f, coarse node c (0-based); column c is
@@ -626,12 +628,12 @@ void launch_scatter(const LocalArgs<R> &a, const c2<R> *x, double2 *glob, long l
 template <typename R>
 void launch_local_A(const LocalArgs<R> &a, const c2<R> *in, c2<R> *out, const c2<R> *f,
                     const int *flag, cudaStream_t s) {
-    size_t sm = (size_t)(FINE_ROWS + 2) * a.max_nx * csz<R>();
+    size_t sm = (size_t)(a.frows + 2) * a.max_nx * csz<R>();
     k_local_A<R><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, in, out, f, flag);
 }
 template <typename R>
 size_t zt_smem(const LocalArgs<R> &a, int apply_A) {
-    int nF = 2 * COARSE_ROWS + 3, nV = nF + 2;
+    int nF = 2 * a.crows + 3, nV = nF + 2;
     return ((size_t)(apply_A ? nV : 0) * a.max_nx + (size_t)nF * a.max_nx + (size_t)nF * (a.max_nx / 2 + 1)) * csz<R>();
 }
 template <typename R>
@@ -642,13 +644,13 @@ void launch_zt(const LocalArgs<R> &a, const c2<R> *in, double2 *y, int apply_A, 
 template <typename R>
 void launch_z(const LocalArgs<R> &a, const double2 *sc, const c2<R> *add, c2<R> *out,
               const int *flag, cudaStream_t s, R sign) {
-    int maxc = prolong_max_cy(FINE_ROWS);
-    size_t sm = ((size_t)maxc * (a.max_nx / 2 + 1) + (size_t)maxc * a.max_nx + (size_t)FINE_ROWS * a.max_nx) * csz<R>();
+    int maxc = prolong_max_cy(a.frows);
+    size_t sm = ((size_t)maxc * (a.max_nx / 2 + 1) + (size_t)maxc * a.max_nx + (size_t)a.frows * a.max_nx) * csz<R>();
     k_z<R><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, sc, add, out, flag, sign);
 }
 template <typename R>
 size_t ps_smem(const LocalArgs<R> &a) {
-    int nF = FINE_ROWS + 2, maxc = prolong_max_cy(nF);
+    int nF = a.frows + 2, maxc = prolong_max_cy(nF);
     return ((size_t)maxc * (a.max_nx / 2 + 1) + (size_t)maxc * a.max_nx + (size_t)nF * a.max_nx +
             (size_t)NWARP * LDP) * csz<R>();
 }
@@ -710,11 +712,11 @@ void launch_cast(long long n, const void *in, int in_double, void *out, int out_
         k_cast<float, float><<<grid, 256, 0, s>>>(n, (const float2 *)in, (float2 *)out);
 }
 
-size_t local_max_dynamic_smem(int max_nx, int bytes_per_c) {
-    int nF = FINE_ROWS + 2, maxc = prolong_max_cy(nF);
+size_t local_max_dynamic_smem(int max_nx, int bytes_per_c, int frows, int crows) {
+    int nF = frows + 2, maxc = prolong_max_cy(nF);
     size_t ps = ((size_t)maxc * (max_nx / 2 + 1) + (size_t)maxc * max_nx + (size_t)nF * max_nx +
                  (size_t)NWARP * LDP) * bytes_per_c;
-    int cF = 2 * COARSE_ROWS + 3;
+    int cF = 2 * crows + 3;
     size_t zt = ((size_t)(cF + 2) * max_nx + (size_t)cF * max_nx + (size_t)cF * (max_nx / 2 + 1)) * bytes_per_c;
     return ps > zt ? ps : zt;
 }

@@ -11,6 +11,7 @@ namespace hdd {
 constexpr int OUTER_CTAS = 2 * 152;     // two CTAs per SM of a GB300 (minimum grid)
 constexpr int OT = 256;                 // threads per outer CTA
 constexpr int OCH = 2048;               // largest chunk one CTA owns (staged in shared memory)
+constexpr int OT2 = 512;                // threads of the memory-bound FP32 second pass (more loads in flight)
 // CTAs of the chunked reductions over a vector of n entries
 int outer_grid(long long n) {
     long long g = (n + OCH - 1) / OCH;
@@ -151,7 +152,7 @@ __device__ __forceinline__ void block_sum_store(double v, double *red, double *o
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int q = 0; q < OT / 32; q++) s += red[q];
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) s += red[q];
         *out = s;
     }
 }
@@ -195,12 +196,12 @@ k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__
 // roundoff of w' itself.  Otherwise (or with allow32 == 0) the FP64 update runs from V; every
 // such RHS-iteration adds one to *fallbacks.  The guard is evaluated identically in every CTA
 // (fixed-order sums), so all chunks of one RHS take the same path.
-__global__ void __launch_bounds__(OT)
+__global__ void __launch_bounds__(OT2)
 k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict__ V32, int nv,
            const double2 *__restrict__ h, double2 *__restrict__ w, const double *__restrict__ npart1,
            double *__restrict__ part_norm, int allow32, int *__restrict__ fallbacks) {
     extern __shared__ double2 hs[];
-    __shared__ double red[OT / 32];
+    __shared__ double red[OT2 / 32];
     __shared__ int use32_s;
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
@@ -224,14 +225,14 @@ k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict
     chunk_of(B.n, b, e);
     const int len = (int)(e > b ? e - b : 0);
     float2 *hf = reinterpret_cast<float2 *>(hs);
-    for (int l = threadIdx.x; l < nv; l += OT) {
+    for (int l = threadIdx.x; l < nv; l += OT2) {
         const double2 v = h[l];
         if (use32) hf[l] = make_float2((float)v.x, (float)v.y);
         else hs[l] = v;
     }
     __syncthreads();
     double nrm = 0.0;
-    for (int i = threadIdx.x; i < len; i += OT) {
+    for (int i = threadIdx.x; i < len; i += OT2) {
         double2 x = w[b + i];
         if (use32) {
             const float2 *vp = V32 + b + i;
@@ -489,12 +490,29 @@ __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const doub
     }
 }
 
+// Deterministic dense test vector x_i = (u_{2i} - 1/2) + i (u_{2i+1} - 1/2), u_j the SplitMix64
+// output mix (Steele, Lea & Flood 2014) of seed + j scaled to [0, 1); for timing runs.
+__device__ __forceinline__ double mix_unit(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+__global__ void k_fill_test(long long n, unsigned long long seed, double2 *__restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = make_double2(mix_unit(seed + 2 * (unsigned long long)i) - 0.5,
+                            mix_unit(seed + 2 * (unsigned long long)i + 1) - 0.5);
+}
+
 static int grid_for(long long n, int threads) {
     long long g = (n + threads - 1) / threads;
     if (g > 8 * 152) g = 8 * 152;
     return g < 1 ? 1 : (int)g;
 }
 
+void launch_fill_test(long long n, unsigned long long seed, double2 *x, cudaStream_t s) {
+    k_fill_test<<<grid_for(n, 256), 256, 0, s>>>(n, seed, x);
+}
 void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f, int nrhs,
                      const int *active, cudaStream_t s) {
     long long n = (long long)(N - 1) * (N - 1);
@@ -515,7 +533,7 @@ void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2
 void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
                      double2 *w, const double *npart1, double *part_norm, int allow32, int *fallbacks,
                      cudaStream_t s) {
-    k_oupdate2<<<dim3(B.G, B.nrhs), OT, (size_t)nv * sizeof(double2), s>>>(B, V, V32, nv, h, w, npart1, part_norm,
+    k_oupdate2<<<dim3(B.G, B.nrhs), OT2, (size_t)nv * sizeof(double2), s>>>(B, V, V32, nv, h, w, npart1, part_norm,
                                                                            allow32, fallbacks);
 }
 void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s) {

@@ -176,6 +176,15 @@ class Solver:
             self._check(rc, "hdd_solve")
         return x, stats
 
+    def autotune(self, stream=None, **kw):
+        """Pick the fastest tile shapes for RAS applications with these solve parameters (see
+        hdd_autotune); they apply to every later call on this solver."""
+        prm = self.params(**kw)
+        f, c, ms = C.c_int(0), C.c_int(0), C.c_double(0.0)
+        self._check(self._L.hdd_autotune(self._h, C.byref(prm), self._stream(stream), C.byref(f), C.byref(c),
+                                         C.byref(ms)), "hdd_autotune")
+        return {"fine_rows": f.value, "coarse_rows": c.value, "ras_ms": ms.value}
+
     def ras_apply(self, v, out=None, stream=None, **kw):
         prm = self.params(**kw)
         nt = self.nrhs * self.n

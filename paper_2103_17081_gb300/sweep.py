@@ -1,0 +1,99 @@
+"""The settings of the paper's iteration-count study (§3, Tables 1–4) run on the GPU.
+
+Every row: wavenumber k ∈ {20, 40, 80, 160} at about 10 or 20 points per wavelength with
+h = 1/n_glob (n_glob = 1.5k or 3k intervals per side), N = 4, 9, 16 or 25 square subdomains with
+one element layer of overlap, a unit point source at the centre, outer FGMRES to relative
+residual 1e-6, and subdomain solves by banded LU (Table 1) or by deflated GMRES to 1e-10, 1e-5 or
+1e-2 (Tables 2–4).  Each entry is "outer (average inner)" as in the paper's tables, the average
+being the inner iterations per subdomain solve.  The paper's own numbers come from FreeFem/PETSc
+with an unstated restart length and partition of unity, so they are trends to compare with, not
+values to reproduce.
+
+    python -m paper_2103_17081_gb300.sweep [--ppwl 10 20] [--k 20 40 80 160] [--json out.jsonl]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+TOLS = [("LU", 0.0), ("1e-10", 1e-10), ("1e-5", 1e-5), ("1e-2", 1e-2)]
+SUBS = [2, 3, 4, 5]                      # N = S² subdomains
+
+
+def run(ks, ppwls, tols, subs, inner_prec=128, log=print):
+    import torch
+
+    import workloads as W
+    from .solver import Solver
+
+    rows = []
+    for ppwl in ppwls:
+        for k in ks:
+            n_glob = int(round(k * (1.5 if ppwl == 10 else 3.0)))
+            for S in subs:
+                w = W.custom(float(k), n_glob, S, 1, name=f"k{k}_n{n_glob}_S{S}")
+                need_lu = any(t <= 0 for _, t in tols)
+                s = Solver.from_workload(w, exact=need_lu)
+                f = s.build_rhs(w.rhs[0])
+                for name, tol in tols:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, st = s.solve(f, outer_tol=1e-6, inner_tol=tol, inner_prec=inner_prec,
+                                    inner_restart=30, inner_maxit=1000, raise_on_error=False)
+                    torch.cuda.synchronize()
+                    r = {"ppwl": ppwl, "k": k, "n_glob": n_glob, "N": S * S, "inner": name,
+                         "outer_its": st["outer_its"], "inner_avg": round(st["inner_its_avg"], 1),
+                         "rel_res": st["rel_res_true"], "status": st["status_code"],
+                         "s": round(time.perf_counter() - t0, 3)}
+                    rows.append(r)
+                    if log:
+                        log(json.dumps(r))
+                del s
+    return rows
+
+
+def table(rows, inner):
+    """Markdown table of one inner setting, rows (ppwl, k), columns N."""
+    sel = [r for r in rows if r["inner"] == inner]
+    Ns = sorted({r["N"] for r in sel})
+    out = ["| ppwl | k | n_glob | " + " | ".join(f"N={n}" for n in Ns) + " |",
+           "|---|---|---|" + "---|" * len(Ns)]
+    for ppwl in sorted({r["ppwl"] for r in sel}):
+        for k in sorted({r["k"] for r in sel}):
+            cells, ng = [], ""
+            for n in Ns:
+                m = [r for r in sel if r["ppwl"] == ppwl and r["k"] == k and r["N"] == n]
+                if not m:
+                    cells.append("")
+                    continue
+                r = m[0]
+                ng = r["n_glob"]
+                cells.append(str(r["outer_its"]) if inner == "LU" else f"{r['outer_its']} ({r['inner_avg']:g})")
+            out.append(f"| {ppwl} | {k} | {ng} | " + " | ".join(cells) + " |")
+    return "\n".join(out)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_2103_17081_gb300.sweep")
+    ap.add_argument("--ppwl", type=int, nargs="+", default=[10, 20], choices=[10, 20])
+    ap.add_argument("--k", type=int, nargs="+", default=[20, 40, 80, 160])
+    ap.add_argument("--inner", nargs="+", default=[n for n, _ in TOLS], choices=[n for n, _ in TOLS])
+    ap.add_argument("--subdomains", type=int, nargs="+", default=SUBS, help="S for S x S subdomains")
+    ap.add_argument("--prec", type=int, default=128, choices=[64, 128], help="inner precision")
+    ap.add_argument("--json", default=None, help="also write every row as a JSON line to this file")
+    a = ap.parse_args(argv)
+    tols = [(n, t) for n, t in TOLS if n in a.inner]
+    rows = run(a.k, a.ppwl, tols, a.subdomains, a.prec)
+    if a.json:
+        with open(a.json, "w") as fh:
+            for r in rows:
+                fh.write(json.dumps(r) + "\n")
+    for name, _ in tols:
+        print(f"\ninner {name}:\n" + table(rows, name))
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+    sys.exit(main())

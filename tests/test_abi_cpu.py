@@ -65,3 +65,15 @@ def test_oracle_and_product_share_no_code():
                     txt = open(os.path.join(dp, fn), encoding="utf-8").read()
                     assert not re.search(rf"^\s*(import|from)\s+{other}\b", txt, re.M), (fn, other)
                     assert f'#include "{other}' not in txt
+
+
+def test_sweep_table_layout():
+    """The paper-table sweep prints 'outer (avg inner)' per (ppwl, k) row and N column."""
+    from paper_2103_17081_gb300.sweep import table
+    rows = [{"ppwl": 10, "k": 20, "n_glob": 30, "N": 4, "inner": "1e-2", "outer_its": 21, "inner_avg": 5.0},
+            {"ppwl": 10, "k": 20, "n_glob": 30, "N": 9, "inner": "1e-2", "outer_its": 30, "inner_avg": 6.25},
+            {"ppwl": 10, "k": 20, "n_glob": 30, "N": 4, "inner": "LU", "outer_its": 20, "inner_avg": 0.0}]
+    t = table(rows, "1e-2").splitlines()
+    assert t[0] == "| ppwl | k | n_glob | N=4 | N=9 |"
+    assert t[2] == "| 10 | 20 | 30 | 21 (5) | 30 (6.25) |"
+    assert table(rows, "LU").splitlines()[2] == "| 10 | 20 | 30 | 20 |"

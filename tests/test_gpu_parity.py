@@ -109,6 +109,27 @@ def test_ras_apply_matches_oracle(oracle_mod, prec, tol):
         assert _rel(zg, zo) < max(1e-4, 10 * tol * 1e-3)
 
 
+def test_autotuned_tiles_keep_results(oracle_mod):
+    """hdd_autotune picks admissible tile heights, and RAS applications and a whole solve with the
+    chosen tiles still match the oracle (tile shapes only reorder partial sums)."""
+    torch = _torch()
+    w = RAGGED[1]
+    s, p = _pair(oracle_mod, w)
+    best = s.autotune(inner_tol=1e-6, inner_prec=128)
+    assert best["fine_rows"] in (4, 6, 8, 12, 16, 24) and best["coarse_rows"] in (2, 4, 8)
+    assert best["ras_ms"] > 0
+    v = W.random_complex_fast(p.n, 11)
+    v /= np.linalg.norm(v)
+    zg, its = s.ras_apply(_to_dev(v), inner_tol=1e-6, inner_prec=128)
+    zo, sto = p.ras_apply(v, 1e-6)
+    assert _rel(zg.cpu().numpy(), zo) < 1e-9
+    f = s.build_rhs(w.rhs[0])
+    x, st = s.solve(f, inner_prec=128)
+    xo, so = p.solve(p.rhs(w.rhs[0]))
+    assert _rel(x.cpu().numpy(), xo) < 1e-6
+    assert abs(st["outer_its"] - so["outer_its"]) <= 1
+
+
 def test_ras_exact_matches_oracle(oracle_mod):
     w = RAGGED[0]
     s, p = _pair(oracle_mod, w, exact=True)
