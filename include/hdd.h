@@ -236,6 +236,13 @@ int hdd_cnn_num_params(void);
 hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params);
 /* Read the FP32 master parameters. */
 hdd_status hdd_cnn_get_params(hdd_ctx *ctx, float *params);
+/* Parameter file I/O (the format warmstart.save writes): "HDDCNN01", the parameter count and
+ * the CRC-32 (IEEE 802.3 / zlib) of the payload as little-endian u32, then the FP32 parameters
+ * little-endian.  load checks magic, count and CRC (HDD_ERR_INVALID_ARG naming the defect) and
+ * then acts as hdd_cnn_set_params; save writes the current master parameters (needs
+ * hdd_cnn_set_params or a load first). */
+hdd_status hdd_warmstart_load(hdd_ctx *ctx, const char *path);
+hdd_status hdd_warmstart_save(hdd_ctx *ctx, const char *path);
 /* x0 = guess for every packed right-hand side f (complex128 packed local vectors). */
 hdd_status hdd_cnn_forward(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream);
 /* Inference as the solver's warm start runs it: layer 1 on the CUDA cores, layers 2-4 as      */

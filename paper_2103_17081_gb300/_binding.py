@@ -17,6 +17,7 @@ SYMBOLS = ["hdd_create", "hdd_destroy", "hdd_status_str", "hdd_last_error", "hdd
            "hdd_num_subdomains", "hdd_get_offsets", "hdd_setup_deflation", "hdd_setup_exact",
            "hdd_solve", "hdd_ras_apply", "hdd_local_op", "hdd_profile", "hdd_profile_count",
            "hdd_profile_get", "hdd_launch_count", "hdd_apply_PA_noalloc", "hdd_setup_batch", "hdd_autotune",
+           "hdd_warmstart_load", "hdd_warmstart_save",
            "hdd_num_rhs", "hdd_cnn_num_params", "hdd_cnn_set_params", "hdd_cnn_get_params",
            "hdd_cnn_forward", "hdd_cnn_infer", "hdd_cnn_loss_grad", "hdd_cnn_train_step", "hdd_get_outer_vector"]
 
@@ -118,6 +119,10 @@ def lib(build_if_missing: bool = True):
     L.hdd_setup_batch.restype = I
     L.hdd_autotune.argtypes = [P, C.POINTER(SolveParams), V, C.POINTER(I), C.POINTER(I), C.POINTER(C.c_double)]
     L.hdd_autotune.restype = I
+    L.hdd_warmstart_load.argtypes = [P, C.c_char_p]
+    L.hdd_warmstart_load.restype = I
+    L.hdd_warmstart_save.argtypes = [P, C.c_char_p]
+    L.hdd_warmstart_save.restype = I
     L.hdd_num_rhs.argtypes = [P]
     L.hdd_num_rhs.restype = I
     F = C.POINTER(C.c_float)

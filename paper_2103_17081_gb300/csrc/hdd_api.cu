@@ -837,6 +837,28 @@ hdd_status build_tasks(hdd_ctx *ctx, int nrhs) {
 }
 }  // namespace
 
+namespace {
+// Parameter files of the warm-start network: "HDDCNN01", the count n (u32), the CRC-32 of the
+// payload (u32), then n FP32 values; integers and floats little-endian.  The CRC is the IEEE
+// 802.3 / zlib one (reflected polynomial 0xEDB88320, initial value and final XOR 0xFFFFFFFF),
+// computed bit by bit.
+const char kWsMagic[8] = {'H', 'D', 'D', 'C', 'N', 'N', '0', '1'};
+uint32_t crc32_ieee(const unsigned char *p, size_t n) {
+    uint32_t c = 0xFFFFFFFFu;
+    for (size_t i = 0; i < n; i++) {
+        c ^= p[i];
+        for (int k = 0; k < 8; k++) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+    }
+    return c ^ 0xFFFFFFFFu;
+}
+uint32_t rd_le32(const unsigned char *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+void wr_le32(unsigned char *p, uint32_t v) {
+    p[0] = (unsigned char)v; p[1] = (unsigned char)(v >> 8); p[2] = (unsigned char)(v >> 16); p[3] = (unsigned char)(v >> 24);
+}
+}  // namespace
+
 // ===========================================================================================
 // C ABI
 // ===========================================================================================
@@ -1361,6 +1383,54 @@ hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params) {
     CK(cudaDeviceSynchronize());
     C.step = 0;
     C.ready = true;
+    return HDD_OK;
+}
+
+hdd_status hdd_warmstart_load(hdd_ctx *ctx, const char *path) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!path) FAIL(HDD_ERR_INVALID_ARG, "path is NULL");
+    FILE *fh = std::fopen(path, "rb");
+    if (!fh) FAIL(HDD_ERR_INVALID_ARG, "cannot open %s", path);
+    std::vector<unsigned char> buf;
+    unsigned char tmp[65536];
+    size_t got;
+    while ((got = std::fread(tmp, 1, sizeof(tmp), fh)) > 0) buf.insert(buf.end(), tmp, tmp + got);
+    const bool rerr = std::ferror(fh) != 0;
+    std::fclose(fh);
+    if (rerr) FAIL(HDD_ERR_INVALID_ARG, "cannot read %s", path);
+    if (buf.size() < 16 || std::memcmp(buf.data(), kWsMagic, 8) != 0)
+        FAIL(HDD_ERR_INVALID_ARG, "%s is not a warm-start parameter file", path);
+    const uint32_t n = rd_le32(buf.data() + 8), crc = rd_le32(buf.data() + 12);
+    if (n != (uint32_t)CNN_NPARAM || buf.size() != 16 + 4 * (size_t)n)
+        FAIL(HDD_ERR_INVALID_ARG, "%s holds %u parameters, the network has %d", path, n, CNN_NPARAM);
+    if (crc32_ieee(buf.data() + 16, 4 * (size_t)n) != crc) FAIL(HDD_ERR_INVALID_ARG, "%s is corrupt (CRC-32)", path);
+    std::vector<float> prm(n);
+    for (uint32_t i = 0; i < n; i++) {
+        const uint32_t b = rd_le32(buf.data() + 16 + 4 * (size_t)i);
+        std::memcpy(&prm[i], &b, 4);
+    }
+    return hdd_cnn_set_params(ctx, prm.data());
+}
+
+hdd_status hdd_warmstart_save(hdd_ctx *ctx, const char *path) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (!path) FAIL(HDD_ERR_INVALID_ARG, "path is NULL");
+    std::vector<float> prm(CNN_NPARAM);
+    hdd_status st = hdd_cnn_get_params(ctx, prm.data());
+    if (st != HDD_OK) return st;
+    std::vector<unsigned char> buf(16 + 4 * (size_t)CNN_NPARAM);
+    std::memcpy(buf.data(), kWsMagic, 8);
+    for (int i = 0; i < CNN_NPARAM; i++) {
+        uint32_t b;
+        std::memcpy(&b, &prm[i], 4);
+        wr_le32(buf.data() + 16 + 4 * (size_t)i, b);
+    }
+    wr_le32(buf.data() + 8, (uint32_t)CNN_NPARAM);
+    wr_le32(buf.data() + 12, crc32_ieee(buf.data() + 16, 4 * (size_t)CNN_NPARAM));
+    FILE *fh = std::fopen(path, "wb");
+    if (!fh) FAIL(HDD_ERR_INVALID_ARG, "cannot create %s", path);
+    const bool ok = std::fwrite(buf.data(), 1, buf.size(), fh) == buf.size();
+    if (std::fclose(fh) != 0 || !ok) FAIL(HDD_ERR_INVALID_ARG, "cannot write %s", path);
     return HDD_OK;
 }
 

@@ -242,6 +242,13 @@ class Solver:
                     "hdd_cnn_get_params")
         return a
 
+    def cnn_load(self, path: str):
+        """Load warm-start parameters from a file written by warmstart.save / cnn_save (C ABI)."""
+        self._check(self._L.hdd_warmstart_load(self._h, str(path).encode()), "hdd_warmstart_load")
+
+    def cnn_save(self, path: str):
+        self._check(self._L.hdd_warmstart_save(self._h, str(path).encode()), "hdd_warmstart_save")
+
     def packed_len(self) -> int:
         fo, _ = self.offsets()
         return self.nrhs * fo[-1]

@@ -73,6 +73,19 @@ def test_training_reduces_loss():
     prm = s.cnn_get_params()
     warmstart.save(path, prm)
     assert np.array_equal(warmstart.load(path), prm)
+    # the C ABI reads and writes the same format (and rejects a corrupted file)
+    s.cnn_set_params(warmstart.init_params(s.cnn_num_params(), seed=7))
+    s.cnn_load(path)
+    assert np.array_equal(s.cnn_get_params(), prm)
+    path2 = path + ".c"
+    s.cnn_save(path2)
+    assert open(path2, "rb").read() == open(path, "rb").read()
+    raw = bytearray(open(path, "rb").read())
+    raw[40] ^= 1
+    open(path2, "wb").write(bytes(raw))
+    from paper_2103_17081_gb300 import HDDError
+    with pytest.raises(HDDError):
+        s.cnn_load(path2)
 
 
 def test_tensor_core_inference_matches_oracle():
