@@ -306,9 +306,12 @@ __device__ __forceinline__ double block_row_dot(const double *__restrict__ Mrow,
                                                 const double *__restrict__ a,
                                                 const double *__restrict__ win, int base, int mask,
                                                 int part) {
-    double s0 = Mrow[part] * a[part];
-    double s1 = Mrow[part + BS_LPR] * a[part + BS_LPR];
-    double s2 = 0.0, s3 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+    for (int c = part; c < BNB; c += 2 * BS_LPR) {
+        s0 = fma(Mrow[c], a[c], s0);
+        if (c + BS_LPR < BNB) s1 = fma(Mrow[c + BS_LPR], a[c + BS_LPR], s1);
+    }
     const int WL = K - BNB;
     int c = part;
     for (; c + 3 * BS_LPR < WL; c += 4 * BS_LPR) {
