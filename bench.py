@@ -117,6 +117,13 @@ def oracle_estimate(w, M: int, J: int):
                         f"{t2:.2f} s); t(J) = aJ + bJ^2/2 fitted and evaluated at J={J}")
 
 
+def workload_config(w) -> dict:
+    """Keys that define the workload; both arms report them identically."""
+    return {"workload": w.name, "k": w.k, "N": w.N, "ppwl": round(w.ppwl, 2),
+            "subdomains": f"{w.Sx}x{w.Sy}", "overlap": w.overlap, "nrhs": w.nrhs,
+            "inner_tol": w.inner_tol, "outer_tol": w.outer_tol}
+
+
 def run_reference(args):
     """CPU oracle arm: each step times the oracle on the first M/2 and first M outer iterations
     of the workload and extrapolates to the full outer count (oracle_estimate)."""
@@ -134,8 +141,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": w.name, "k": w.k, "N": w.N,
-                                            "subdomains": f"{w.Sx}x{w.Sy}", "overlap": w.overlap},
+            "data": "synthetic", "config": dict(workload_config(w), inner_prec=128, parallelism="single"),
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
                              "sample": "per step: " + how},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -258,9 +264,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64-inner/f64-outer" if args.prec == 64 else "c128",
             "data": "synthetic",
-            "config": {"workload": w.name, "k": w.k, "N": w.N, "ppwl": round(w.ppwl, 2),
-                       "subdomains": f"{w.Sx}x{w.Sy}", "overlap": w.overlap,
-                       "inner_tol": w.inner_tol, "outer_tol": w.outer_tol, "inner_prec": args.prec,
+            "config": {**workload_config(w), "inner_prec": args.prec,
                        "l2": "flushed between timed steps (512 MB write)",
                        "warm_start": bool(args.warm_start), "outer_reorth": "fp64" if args.fp64_reorth else "fp32-guarded",
                        "tiles": tiles or {"fine_rows": 8, "coarse_rows": 4},
