@@ -1084,6 +1084,8 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     const int G = outer_grid(n);
     const int ldp = R + 1;
     OuterBatch B{nr, n, (long long)nr * n, ldp, G, R, nullptr};
+    B.n32 = n + (n & 1);
+    B.ld32 = (long long)nr * B.n32;
     CK(O.V.ensure((size_t)(R + 1) * nr * n * sizeof(double2)));
     CK(O.Z.ensure((size_t)R * nr * n * sizeof(double2)));
     CK(O.w.ensure((size_t)nr * n * sizeof(double2))); CK(O.r.ensure((size_t)nr * n * sizeof(double2)));
@@ -1097,7 +1099,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     CK(O.npart.ensure((size_t)nr * G * sizeof(double)));
     CK(O.npart1.ensure((size_t)nr * G * sizeof(double)));
     const bool r32 = prm->outer_reorth32 != 0;
-    if (r32) CK(O.V32.ensure((size_t)(R + 1) * nr * n * sizeof(float2)));
+    if (r32) CK(O.V32.ensure((size_t)(R + 1) * B.ld32 * sizeof(float2)));
     float2 *V32 = r32 ? O.V32.as<float2>() : nullptr;
     CK(O.fallbacks.ensure(sizeof(int)));
     CK(cudaMemsetAsync(O.fallbacks.p, 0, sizeof(int), s));
@@ -1203,7 +1205,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                               prm->outer_tol, O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>(), hstride,
                               total, s));
             KL(F_OMISC, 2.0 * fa * n * 16 + (r32 ? fa * n * 8.0 : 0.0), 0,
-               launch_oscale(B, V + (long long)(j + 1) * B.ld, r32 ? V32 + (long long)(j + 1) * B.ld : nullptr,
+               launch_oscale(B, V + (long long)(j + 1) * B.ld, r32 ? V32 + (long long)(j + 1) * B.ld32 : nullptr,
                              w, O.hn.as<double>(), s));
             CKL();
             total++;

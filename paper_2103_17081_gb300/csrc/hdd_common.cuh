@@ -218,6 +218,8 @@ struct OuterBatch {
     int G;                 // CTAs per RHS of the chunked reductions
     int R;                 // Hessenberg columns (restart length)
     const int *active;     // per-RHS flag, or null for all
+    long long n32 = 0;     // FP32 basis copy: entries per RHS (n rounded up to even)
+    long long ld32 = 0;    // FP32 basis copy: stride between basis vectors (= nrhs·n32)
 };
 int outer_grid(long long n);
 void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f, int nrhs,

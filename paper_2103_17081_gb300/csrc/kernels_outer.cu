@@ -85,6 +85,14 @@ __device__ __forceinline__ void chunk_of(long long n, long long &b, long long &e
     b = blockIdx.x * per;
     e = b + per < n ? b + per : n;
 }
+// the same with an even chunk length (even chunk starts)
+__device__ __forceinline__ void chunk_even(long long n, long long &b, long long &e) {
+    long long per = (n + gridDim.x - 1) / gridDim.x;
+    per += per & 1;
+    b = blockIdx.x * per;
+    e = b + per < n ? b + per : n;
+    if (e < b) e = b;
+}
 
 // ------------------------------------------------------------------------------------------
 // Outer FGMRES kernels, batched over independent right-hand sides (blockIdx.y = r).  Layout
@@ -191,9 +199,9 @@ k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__
 // coefficients h2 = V^H w' are rounding-error sized, so the correction V h2 is tiny next to w'.
 // When Σ_l (|Re h2_l| + |Im h2_l|) <= 2^-34 ||w'_r|| (||w'_r||² = Σ npart1) the correction is
 // formed in FP32 from the FP32 copy V32 of the basis: products and partial sums over 32 vectors
-// in FP32 (two chains of 16), widened to FP64 between partial sums, subtracted from w' in FP64.  Its error is then
-// at most about 2^-19 Σ|h2| <= 2^-53 ||w'_r|| in the 2-norm (||V_l|| = 1), under the FP64 unit
-// roundoff of w' itself.  Otherwise (or with allow32 == 0) the FP64 update runs from V; every
+// in FP32 (one chain per element), widened to FP64 between partial sums, subtracted from w' in
+// FP64.  Its error is then at most about 2^-19 Σ|h2| <= 2^-53 ||w'_r|| in the 2-norm
+// (||V_l|| = 1), under the FP64 unit roundoff of w' itself.  Otherwise (or with allow32 == 0) the FP64 update runs from V; every
 // such RHS-iteration adds one to *fallbacks.  The guard is evaluated identically in every CTA
 // (fixed-order sums), so all chunks of one RHS take the same path.
 __global__ void __launch_bounds__(OT2)
@@ -206,7 +214,7 @@ k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     V += r * B.n; w += r * B.n; h += (long long)r * B.ldp; npart1 += (long long)r * B.G;
-    if (V32) V32 += r * B.n;
+    if (V32) V32 += r * B.n32;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
         double a = 0.0, q2 = 0.0;
@@ -222,8 +230,8 @@ k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict
     __syncthreads();
     const bool use32 = use32_s != 0;
     long long b, e;
-    chunk_of(B.n, b, e);
-    const int len = (int)(e > b ? e - b : 0);
+    chunk_even(B.n, b, e);
+    const int len = (int)(e - b);
     float2 *hf = reinterpret_cast<float2 *>(hs);
     for (int l = threadIdx.x; l < nv; l += OT2) {
         const double2 v = h[l];
@@ -232,38 +240,45 @@ k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict
     }
     __syncthreads();
     double nrm = 0.0;
-    for (int i = threadIdx.x; i < len; i += OT2) {
-        double2 x = w[b + i];
-        if (use32) {
-            const float2 *vp = V32 + b + i;
-            double cx = 0.0, cy = 0.0;
+    if (use32) {
+        // element pairs (b + 2p, b + 2p + 1) as one 16-byte load per basis vector: b, n32 and
+        // ld32 are even; an odd last pair reads the padding entry of its RHS and drops it
+        const float4 *vp4 = reinterpret_cast<const float4 *>(V32 + b);
+        const long long ld4 = B.ld32 / 2;
+        for (int p = threadIdx.x; 2 * p < len; p += OT2) {
+            const int i = 2 * p;
+            const bool two = i + 1 < len;
+            double2 xa = w[b + i], xb = two ? w[b + i + 1] : make_double2(0.0, 0.0);
+            double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
             for (int l0 = 0; l0 < nv; l0 += 32) {
                 const int l1 = l0 + 32 < nv ? l0 + 32 : nv;
-                float px = 0.f, py = 0.f, qx = 0.f, qy = 0.f;
-                int l = l0;
+                float pax = 0.f, pay = 0.f, pbx = 0.f, pby = 0.f;
 #pragma unroll 8
-                for (; l + 1 < l1; l += 2) {
-                    const float2 v0 = vp[(long long)l * B.ld], v1 = vp[(long long)(l + 1) * B.ld];
-                    const float2 h0 = hf[l], h1 = hf[l + 1];
-                    px = fmaf(h0.x, v0.x, px); px = fmaf(-h0.y, v0.y, px);
-                    py = fmaf(h0.x, v0.y, py); py = fmaf(h0.y, v0.x, py);
-                    qx = fmaf(h1.x, v1.x, qx); qx = fmaf(-h1.y, v1.y, qx);
-                    qy = fmaf(h1.x, v1.y, qy); qy = fmaf(h1.y, v1.x, qy);
+                for (int l = l0; l < l1; l++) {
+                    const float4 v = vp4[(long long)l * ld4 + p];
+                    const float2 hh = hf[l];
+                    pax = fmaf(hh.x, v.x, pax); pax = fmaf(-hh.y, v.y, pax);
+                    pay = fmaf(hh.x, v.y, pay); pay = fmaf(hh.y, v.x, pay);
+                    pbx = fmaf(hh.x, v.z, pbx); pbx = fmaf(-hh.y, v.w, pbx);
+                    pby = fmaf(hh.x, v.w, pby); pby = fmaf(hh.y, v.z, pby);
                 }
-                if (l < l1) {
-                    const float2 v0 = vp[(long long)l * B.ld], h0 = hf[l];
-                    px = fmaf(h0.x, v0.x, px); px = fmaf(-h0.y, v0.y, px);
-                    py = fmaf(h0.x, v0.y, py); py = fmaf(h0.y, v0.x, py);
-                }
-                cx += (double)px + (double)qx;
-                cy += (double)py + (double)qy;
+                ax += (double)pax; ay += (double)pay; bx += (double)pbx; by += (double)pby;
             }
-            x.x -= cx; x.y -= cy;
-        } else {
-            x = update_fp64(x, V + b + i, B.ld, hs, nv);
+            xa.x -= ax; xa.y -= ay;
+            w[b + i] = xa;
+            nrm = fma(xa.x, xa.x, fma(xa.y, xa.y, nrm));
+            if (two) {
+                xb.x -= bx; xb.y -= by;
+                w[b + i + 1] = xb;
+                nrm = fma(xb.x, xb.x, fma(xb.y, xb.y, nrm));
+            }
         }
-        w[b + i] = x;
-        nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+    } else {
+        for (int i = threadIdx.x; i < len; i += OT2) {
+            const double2 x = update_fp64(w[b + i], V + b + i, B.ld, hs, nv);
+            w[b + i] = x;
+            nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+        }
     }
     block_sum_store(nrm, red, part_norm + (long long)r * B.G + blockIdx.x);
 }
@@ -409,7 +424,7 @@ __global__ void k_oscale(OuterBatch B, double2 *__restrict__ out, float2 *__rest
     const double h = hn[r];
     if (!(h > 0.0)) return;
     out += r * B.n; w += r * B.n;
-    if (out32) out32 += r * B.n;
+    if (out32) out32 += r * B.n32;
     const double inv = 1.0 / h;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
         const double2 v = make_double2(w[i].x * inv, w[i].y * inv);
@@ -482,7 +497,7 @@ __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const doub
     }
     if (!(beta > 0.0)) return;
     const double inv = 1.0 / beta;
-    float2 *v32 = V32 ? V32 + r * B.n : nullptr;
+    float2 *v32 = V32 ? V32 + r * B.n32 : nullptr;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
         const double2 v = make_double2(rv[i].x * inv, rv[i].y * inv);
         v0[i] = v;
