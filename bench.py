@@ -85,6 +85,18 @@ def _dist():
     return ws, rank, int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(value: float, device: str) -> float:
+    """The largest value over the ranks of the process group (the slowest replica sets the step
+    time); the value itself without a group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
 def oracle_sample(w, outer_its: int, threads: int = 0):
     """Time the CPU oracle on the first `outer_its` outer iterations of workload w."""
     import oracle
@@ -212,11 +224,7 @@ def run_gpu(args):
     prof = s.profile_stats()
     s.profile(False)
     t_step = statistics.mean(times)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt)
+    t_step = max_over_ranks(t_step, f"cuda:{dev}")
 
     # end to end: pinned host f → device, solve, device → host x, every step
     fh = f.cpu().pin_memory()

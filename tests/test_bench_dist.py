@@ -1,0 +1,51 @@
+"""Multi-process paths of bench.py on the CPU (gloo, two ranks): the step time is the maximum over
+the replicas on every rank, and the reference arm prints only on rank 0."""
+import contextlib
+import io
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2")
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    import bench
+    out[rank] = bench.max_over_ranks(1.5 + rank, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_step_time_is_max_over_two_gloo_ranks():
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_rank_main, args=(port, out), nprocs=2, join=True)
+        assert out[0] == 2.5 and out[1] == 2.5
+
+
+def test_max_over_ranks_without_a_group():
+    import bench
+    assert bench.max_over_ranks(3.25, "cpu") == 3.25
+
+
+def test_reference_arm_prints_only_on_rank_zero(monkeypatch):
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--workload", "tiny", "--steps", "1",
+                                     "--warmup", "0"])
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        assert bench.main() == 0
+    assert buf.getvalue() == ""
