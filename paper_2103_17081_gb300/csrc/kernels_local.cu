@@ -347,6 +347,17 @@ k_prolong_stencil(LocalArgs<R> a, int mode, const c2<R> *__restrict__ in,
     }
 }
 
+// Sum over the task's tiles of the squared-norm slot (LDP-1), by one warp: lane q adds tiles
+// q, q+32, ..., then a fixed shuffle tree (deterministic); every lane returns the total.
+template <typename R>
+__device__ __forceinline__ R task_norm2_warp(const c2<R> *part, const Task &T) {
+    const int lane = threadIdx.x & 31;
+    R s = 0;
+    for (int q = lane; q < T.ntiles; q += 32) s += part[(long long)(T.tile0 + q) * LDP + LDP - 1].x;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // Sum over the task's tiles of partial slot l (fixed order → deterministic).
 template <typename R>
 __device__ __forceinline__ c2<R> task_sum(const c2<R> *part, const Task &T, int l) {
@@ -427,14 +438,18 @@ k_givens_normalize(LocalArgs<R> a, InnerState<R> S, int restart, int i, c2<R> *_
                    const c2<R> *__restrict__ p3, const int *__restrict__ act_in,
                    int *__restrict__ act_out, int *__restrict__ counter, R tol, int maxit) {
     __shared__ R hn_s;
+    __shared__ c2<R> hsum[LDP];
     const Tile tl = a.ftiles[blockIdx.x];
     if (!act_in[tl.task]) return;
     const Task T = a.tasks[tl.task];
-    if (threadIdx.x == 0) {
-        R s = 0;
-        for (int q = 0; q < T.ntiles; q++) s += p3[(long long)(T.tile0 + q) * LDP + LDP - 1].x;
-        hn_s = sqrt(s);
+    const bool first = blockIdx.x == T.tile0;          // this tile also updates the task's rotations
+    if (threadIdx.x < 32) {
+        const R s = task_norm2_warp<R>(p3, T);
+        if (threadIdx.x == 0) hn_s = sqrt(s);
     }
+    // Hessenberg column entries h_l = (pass 1 + pass 2 dots), one task sum per thread
+    if (first)
+        for (int l = threadIdx.x; l <= i; l += blockDim.x) hsum[l] = cadd<R>(task_sum<R>(p1, T, l), task_sum<R>(p2, T, l));
     __syncthreads();
     const R hn = hn_s;
     if (hn > (R)0) {
@@ -445,14 +460,14 @@ k_givens_normalize(LocalArgs<R> a, InnerState<R> S, int restart, int i, c2<R> *_
             w[base + e] = mk<R>(v.x * inv, v.y * inv);
         }
     }
-    if (blockIdx.x != T.tile0 || threadIdx.x != 0) return;
+    if (!first || threadIdx.x != 0) return;
     const int t = tl.task;
     c2<R> *H = S.H + (long long)t * (restart + 1) * restart;
     c2<R> *hc = H + (long long)i * (restart + 1);
     R *cs = S.cs + (long long)t * restart;
     c2<R> *sn = S.sn + (long long)t * restart;
     c2<R> *g = S.g + (long long)t * (restart + 1);
-    for (int l = 0; l <= i; l++) hc[l] = cadd<R>(task_sum<R>(p1, T, l), task_sum<R>(p2, T, l));
+    for (int l = 0; l <= i; l++) hc[l] = hsum[l];
     for (int l = 0; l < i; l++) {
         c2<R> x = hc[l], y = hc[l + 1];
         c2<R> sx = sn[l];
@@ -490,10 +505,9 @@ k_init_cycle(LocalArgs<R> a, InnerState<R> S, int restart, c2<R> *__restrict__ v
     const Tile tl = a.ftiles[blockIdx.x];
     if (!flag[tl.task]) return;
     const Task T = a.tasks[tl.task];
-    if (threadIdx.x == 0) {
-        R s = 0;
-        for (int q = 0; q < T.ntiles; q++) s += p3[(long long)(T.tile0 + q) * LDP + LDP - 1].x;
-        beta_s = sqrt(s);
+    if (threadIdx.x < 32) {
+        const R s = task_norm2_warp<R>(p3, T);
+        if (threadIdx.x == 0) beta_s = sqrt(s);
     }
     __syncthreads();
     const R beta = beta_s;
