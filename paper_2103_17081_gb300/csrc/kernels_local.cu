@@ -358,12 +358,24 @@ __device__ __forceinline__ R task_norm2_warp(const c2<R> *part, const Task &T) {
     return s;
 }
 
-// Sum over the task's tiles of partial slot l (fixed order → deterministic).
+// Task sums of partial slots l < nv (and, if part2, plus the same slots of part2) into out[l]:
+// warp w takes l = w, w + NWARP, ...; its lane q adds tiles q, q+32, ..., then a fixed shuffle
+// tree (deterministic).  All tile partials of a slot are loaded at once instead of one after
+// another.
 template <typename R>
-__device__ __forceinline__ c2<R> task_sum(const c2<R> *part, const Task &T, int l) {
-    c2<R> s = mk<R>(0, 0);
-    for (int q = 0; q < T.ntiles; q++) s = cadd<R>(s, part[(long long)(T.tile0 + q) * LDP + l]);
-    return s;
+__device__ __forceinline__ void task_sums_warp(const c2<R> *part, const c2<R> *part2, const Task &T, int nv,
+                                               c2<R> *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = warp; l < nv; l += NWARP) {
+        c2<R> s = mk<R>(0, 0);
+        for (int q = lane; q < T.ntiles; q += 32) {
+            s = cadd<R>(s, part[(long long)(T.tile0 + q) * LDP + l]);
+            if (part2) s = cadd<R>(s, part2[(long long)(T.tile0 + q) * LDP + l]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) { s.x += shfl_xor(s.x, o); s.y += shfl_xor(s.y, o); }
+        if (lane == 0) out[l] = s;
+    }
 }
 
 // Classical Gram-Schmidt passes 2 and 3 (CGS2): w -= V h (h = task sum of part_in);
@@ -378,7 +390,7 @@ k_cgs_update(LocalArgs<R> a, int pass, c2<R> *__restrict__ w, const c2<R> *__res
     const Tile tl = a.ftiles[blockIdx.x];
     if (flag && !flag[tl.task]) return;
     const Task T = a.tasks[tl.task];
-    for (int l = threadIdx.x; l < nv; l += blockDim.x) hv[l] = task_sum<R>(part_in, T, l);
+    task_sums_warp<R>(part_in, nullptr, T, nv, hv);
     __syncthreads();
     const int cnt = tl.nr * T.nx;
     const long long base = T.foff + (long long)tl.r0 * T.nx;
@@ -448,8 +460,7 @@ k_givens_normalize(LocalArgs<R> a, InnerState<R> S, int restart, int i, c2<R> *_
         if (threadIdx.x == 0) hn_s = sqrt(s);
     }
     // Hessenberg column entries h_l = (pass 1 + pass 2 dots), one task sum per thread
-    if (first)
-        for (int l = threadIdx.x; l <= i; l += blockDim.x) hsum[l] = cadd<R>(task_sum<R>(p1, T, l), task_sum<R>(p2, T, l));
+    if (first) task_sums_warp<R>(p1, p2, T, i + 1, hsum);
     __syncthreads();
     const R hn = hn_s;
     if (hn > (R)0) {

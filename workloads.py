@@ -128,14 +128,16 @@ def make(name: str, seed: int = 0) -> Workload:
         bump = Bump(rng.uniform(0.2, 0.8), rng.uniform(0.2, 0.8))
         return Workload(name, k, N, S, S, 2, uniform_interfaces(N, S), uniform_interfaces(N, S),
                         [RHSSpec([PointSource(0.5, 0.5)], [bump])])
-    if name == "k400x32":
+    if name in ("k400x32", "k400x4"):
+        # k400x4: the same geometry with the first 4 of the 32 right-hand sides (a batched case
+        # small enough for multi-pass profiling)
         N, S = 1280, 16
         rj = SplitMix64(seed)
         ifx = jittered_interfaces(N, S, rj)
         ify = jittered_interfaces(N, S, rj)
         rs = SplitMix64(seed + 1)
         rhs = [RHSSpec([p]) for p in point_sources(32, rs, 0.1, 0.9)]
-        return Workload(name, 400.0, N, S, S, 2, ifx, ify, rhs)
+        return Workload(name, 400.0, N, S, S, 2, ifx, ify, rhs if name == "k400x32" else rhs[:4])
     raise KeyError(name)
 
 
