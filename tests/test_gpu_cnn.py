@@ -148,3 +148,19 @@ def test_warm_start_gain_k100():
     xc, _ = s.solve(f, warm_start=0, outer_tol=1e-8)
     xw, _ = s.solve(f, warm_start=1, outer_tol=1e-8)
     assert float(torch.linalg.vector_norm(xw - xc) / torch.linalg.vector_norm(xc)) < 1e-6
+
+
+def test_batched_inference_matches_single_rhs():
+    """Tensor-core inference over the tasks of two batched right-hand sides gives, for each RHS,
+    the single-RHS result (tile tables and padded frames span all tasks)."""
+    torch, s, p, cnn, pb, f, fo, batch, kh = _setup()
+    from paper_2103_17081_gb300 import Solver
+    w = W.custom(17.0, 45, 3, 2, Sy=4, ifx=[0, 11, 29, 45], name="ragged2")
+    sb = Solver.from_workload(w).setup_batch(2)
+    sb.cnn_set_params(s.cnn_get_params())
+    n1 = fo[-1]
+    f2 = np.concatenate([f, W.random_complex_fast(n1, 10)])
+    xb = sb.cnn_infer(torch.from_numpy(f2).cuda()).cpu().numpy()
+    x0 = s.cnn_infer(torch.from_numpy(f2[:n1]).cuda()).cpu().numpy()
+    x1 = s.cnn_infer(torch.from_numpy(f2[n1:]).cuda()).cpu().numpy()
+    assert np.array_equal(xb[:n1], x0) and np.array_equal(xb[n1:], x1)

@@ -130,6 +130,25 @@ def test_autotuned_tiles_keep_results(oracle_mod):
     assert abs(st["outer_its"] - so["outer_its"]) <= 1
 
 
+def test_autotuned_batched_solve_matches_oracle(oracle_mod):
+    """After hdd_autotune on a 2-RHS batch (the tuned tiles apply to every task of the batch),
+    the batched solve matches the oracle's solve of each RHS."""
+    from paper_2103_17081_gb300 import Solver
+    _torch()
+    w = RAGGED[1]
+    specs = _specs(2, 7)
+    sb = Solver.from_workload(w).setup_batch(2)
+    sb.autotune(inner_tol=1e-2, inner_prec=128)
+    fb = sb.build_rhs_batch(specs)
+    xb, stb = sb.solve(fb, inner_prec=128)
+    p = oracle_mod.from_workload(w)
+    n = sb.n
+    for r, spec in enumerate(specs):
+        xo, _ = p.solve(p.rhs(spec))
+        assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), xo) < 1e-5
+    assert stb["rel_res_true"] <= 1e-6 * 1.0001
+
+
 def test_ras_exact_matches_oracle(oracle_mod):
     w = RAGGED[0]
     s, p = _pair(oracle_mod, w, exact=True)
