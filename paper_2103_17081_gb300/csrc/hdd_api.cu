@@ -106,7 +106,7 @@ struct CnnState {            // learned warm start: parameters, Adam moments, ac
 };
 
 struct OuterWork {
-    DevMem V, V32, Z, w, r, H, cs, sn, g, Wq, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
+    DevMem V, V32, D, Z, w, r, H, cs, sn, g, Wq, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
     DevMem fallbacks;
 };
 
@@ -1086,6 +1086,8 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     OuterBatch B{nr, n, (long long)nr * n, ldp, G, R, nullptr};
     B.n32 = n + (n & 1);
     B.ld32 = (long long)nr * B.n32;
+    CK(O.D.ensure((size_t)(R + 1) * nr * n * sizeof(double)));
+    B.D = O.D.as<double>();
     CK(O.V.ensure((size_t)(R + 1) * nr * n * sizeof(double2)));
     CK(O.Z.ensure((size_t)R * nr * n * sizeof(double2)));
     CK(O.w.ensure((size_t)nr * n * sizeof(double2))); CK(O.r.ensure((size_t)nr * n * sizeof(double2)));
@@ -1156,7 +1158,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
         KL(F_OMISC, 3.0 * nr * n * 16, 0, launch_gstencil(ctx->st, ctx->N, x, rv, f, nr, dact, s));
         KL(F_OMISC, (double)nr * n * 16, 0, launch_onorm(B, rv, O.npart.as<double>(), s));
         KL(F_OMISC, 2.0 * nr * n * 16 + (r32 ? nr * n * 8.0 : 0.0), 0,
-           launch_oinit(B, rv, O.npart.as<double>(), V, V32, O.g.as<double2>(), O.Wq.as<double2>(),
+           launch_oinit(B, rv, O.npart.as<double>(), V, V32, O.D.as<double>(), O.g.as<double2>(), O.Wq.as<double2>(),
                         O.beta.as<double>(), s));
         CKL();
         CK(cudaMemcpyAsync(beta.data(), O.beta.p, nr * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1185,10 +1187,12 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
             for (int r = 0; r < nr; r++) nact += act[r];
             const double nv = j + 1, fa = nact;
             KL(F_OMISC, 2.0 * fa * n * 16, 0, launch_gstencil(ctx->st, ctx->N, zj, w, nullptr, nr, dact, s));  // w = A z_j
-            KL(F_OCGS, fa * (nv + 1) * n * 16, fa * 8 * nv * n,
+            // CGS2 flops as executed: dots 6 per (vector, element) (three FMAs, Gauss form),
+            // update 8; bytes: V once (16 B) and d (8 B) per vector and element, w
+            KL(F_OCGS, fa * (nv * 24 + 16) * n, fa * 6 * nv * n,
                launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                              // h1 = V^H w
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
-            KL(F_OCGS, fa * (nv + 2) * n * 16, fa * 16 * nv * n,
+            KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 14 * nv * n,
                launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
             if (r32)   // FP32 correction from the FP32 basis copy (guarded; FP64 fallback inside)
@@ -1206,7 +1210,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                               total, s));
             KL(F_OMISC, 2.0 * fa * n * 16 + (r32 ? fa * n * 8.0 : 0.0), 0,
                launch_oscale(B, V + (long long)(j + 1) * B.ld, r32 ? V32 + (long long)(j + 1) * B.ld32 : nullptr,
-                             w, O.hn.as<double>(), s));
+                             O.D.as<double>() + (long long)(j + 1) * B.ld, w, O.hn.as<double>(), s));
             CKL();
             total++;
             std::vector<int> flags(nr);

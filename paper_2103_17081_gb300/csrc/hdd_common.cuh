@@ -220,6 +220,7 @@ struct OuterBatch {
     const int *active;     // per-RHS flag, or null for all
     long long n32 = 0;     // FP32 basis copy: entries per RHS (n rounded up to even)
     long long ld32 = 0;    // FP32 basis copy: stride between basis vectors (= nrhs·n32)
+    const double *D = nullptr;  // Re v - Im v of every basis vector (layout of V)
 };
 int outer_grid(long long n);
 void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f, int nrhs,
@@ -240,14 +241,14 @@ void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, do
                     const double2 *h1, const double2 *h2, const double *npart, const double *fnorm,
                     double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
                     cudaStream_t s);
-void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, const double2 *w, const double *hn,
-                   cudaStream_t s);
+void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, double *outD, const double2 *w,
+                   const double *hn, cudaStream_t s);
 void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, const int *kcols, int kmax,
                       double2 *y, cudaStream_t s);
 void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int kmax, const double2 *Zb,
                   double2 *x, cudaStream_t s);
 void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
-                  double2 *g, double2 *Wq, double *beta_out, cudaStream_t s);
+                  double *D, double2 *g, double2 *Wq, double *beta_out, cudaStream_t s);
 void launch_orotate(const OuterBatch &B, double2 *H, const double *cs, const double2 *sn, const int *kcols,
                     int kmax, cudaStream_t s);
 cudaError_t set_outer_smem_limits(size_t bytes);

@@ -10,7 +10,7 @@ namespace hdd {
 
 constexpr int OUTER_CTAS = 2 * 152;     // two CTAs per SM of a GB300 (minimum grid)
 constexpr int OT = 256;                 // threads per outer CTA
-constexpr int OCH = 2048;               // largest chunk one CTA owns (staged in shared memory)
+constexpr int OCH = 1536;               // largest chunk one CTA owns (staged in shared memory)
 constexpr int OT2 = 512;                // threads of the memory-bound FP32 second pass (more loads in flight)
 // CTAs of the chunked reductions over a vector of n entries
 int outer_grid(long long n) {
@@ -102,24 +102,44 @@ __device__ __forceinline__ void chunk_even(long long n, long long &b, long long 
 // ------------------------------------------------------------------------------------------
 
 // Each CTA owns one contiguous chunk of the vectors (at most OCH entries).  The chunk of w is
-// staged in shared memory once; then warp q of the CTA forms the partial dots of vectors
-// l = q, q + 8, ... over the chunk with shuffle reductions only (no block barrier per vector).
-__device__ __forceinline__ void warp_dots(const double2 *__restrict__ V, long long ld, int nv,
-                                          const double2 *__restrict__ ws, long long b, int len,
+// staged in shared memory once (stage_w); then warp q of the CTA forms the partial dots of
+// vectors l = q, q + 8, ... over the chunk with shuffle reductions only (no block barrier per
+// vector).  Dot products use the three-multiplication (Gauss) form of the complex product:
+// with d = Re v - Im v stored per basis vector and a = Re w, p = Re w + Im w, m = Im w - Re w
+// staged once per element of w,
+//   conj(v)·w = (P + Q) + i (P + S),  P = d·a,  Q = Im v·p,  S = Re v·m,
+// three FP64 FMAs per vector and element instead of four (the passes are bound by the FP64
+// pipe, not by the extra 8 bytes of d).  Normwise its rounding error is within a small
+// constant of the four-multiplication form's.
+struct WStage { double a[OCH], p[OCH], m[OCH]; };
+
+__device__ __forceinline__ void stage_w(WStage &ws, int i, double2 x) {
+    ws.a[i] = x.x; ws.p[i] = x.x + x.y; ws.m[i] = x.y - x.x;
+}
+
+__device__ __forceinline__ void warp_dots(const double2 *__restrict__ V, const double *__restrict__ D,
+                                          long long ld, int nv, const WStage &ws, long long b, int len,
                                           double2 *__restrict__ part, int ldp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l = warp; l < nv; l += OT / 32) {
         const double2 *vl = V + (long long)l * ld + b;
-        double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+        const double *dl = D + (long long)l * ld + b;
+        double p0 = 0.0, q0 = 0.0, s0 = 0.0, p1 = 0.0, q1 = 0.0, s1 = 0.0;
         int i = lane;
         for (; i + 32 < len; i += 64) {
-            cdotc_acc<double>(a0, vl[i], ws[i]);
-            cdotc_acc<double>(a1, vl[i + 32], ws[i + 32]);
+            const double2 v0 = vl[i], v1 = vl[i + 32];
+            const double d0 = dl[i], d1 = dl[i + 32];
+            p0 = fma(d0, ws.a[i], p0); q0 = fma(v0.y, ws.p[i], q0); s0 = fma(v0.x, ws.m[i], s0);
+            p1 = fma(d1, ws.a[i + 32], p1); q1 = fma(v1.y, ws.p[i + 32], q1); s1 = fma(v1.x, ws.m[i + 32], s1);
         }
-        if (i < len) cdotc_acc<double>(a0, vl[i], ws[i]);
-        a0.x += a1.x; a0.y += a1.y;
-        for (int o = 16; o > 0; o >>= 1) { a0.x += shfl_xor(a0.x, o); a0.y += shfl_xor(a0.y, o); }
-        if (lane == 0) part[(long long)blockIdx.x * ldp + l] = a0;
+        if (i < len) {
+            const double2 v0 = vl[i];
+            p0 = fma(dl[i], ws.a[i], p0); q0 = fma(v0.y, ws.p[i], q0); s0 = fma(v0.x, ws.m[i], s0);
+        }
+        const double P = p0 + p1;
+        double re = P + (q0 + q1), im = P + (s0 + s1);
+        for (int o = 16; o > 0; o >>= 1) { re += shfl_xor(re, o); im += shfl_xor(im, o); }
+        if (lane == 0) part[(long long)blockIdx.x * ldp + l] = make_double2(re, im);
     }
 }
 
@@ -127,16 +147,17 @@ __device__ __forceinline__ void warp_dots(const double2 *__restrict__ V, long lo
 __global__ void __launch_bounds__(OT)
 k_odots(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__restrict__ w,
         double2 *__restrict__ part) {
-    __shared__ double2 ws[OCH];
+    __shared__ WStage ws;
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     V += r * B.n; w += r * B.n; part += (long long)r * B.G * B.ldp;
+    const double *D = B.D + r * B.n;
     long long b, e;
     chunk_of(B.n, b, e);
     const int len = (int)(e > b ? e - b : 0);
-    for (int i = threadIdx.x; i < len; i += OT) ws[i] = w[b + i];
+    for (int i = threadIdx.x; i < len; i += OT) stage_w(ws, i, w[b + i]);
     __syncthreads();
-    warp_dots(V, B.ld, nv, ws, b, len, part, B.ldp);
+    warp_dots(V, D, B.ld, nv, ws, b, len, part, B.ldp);
 }
 
 // x -= Σ_{l<nv} hs[l] V_l(i) in FP64 with two independent accumulation chains.
@@ -171,11 +192,12 @@ __global__ void __launch_bounds__(OT)
 k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__restrict__ h,
           double2 *__restrict__ w, double2 *__restrict__ part_dots, double *__restrict__ part_norm) {
     extern __shared__ double2 hs[];
-    __shared__ double2 ws[OCH];
+    __shared__ WStage ws;
     __shared__ double red[OT / 32];
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     V += r * B.n; w += r * B.n; h += (long long)r * B.ldp;
+    const double *D = B.D + r * B.n;
     long long b, e;
     chunk_of(B.n, b, e);
     const int len = (int)(e > b ? e - b : 0);
@@ -185,13 +207,13 @@ k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__
     for (int i = threadIdx.x; i < len; i += OT) {
         const double2 x = update_fp64(w[b + i], V + b + i, B.ld, hs, nv);
         w[b + i] = x;
-        ws[i] = x;
+        stage_w(ws, i, x);
         nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
     }
     if (part_norm) block_sum_store(nrm, red, part_norm + (long long)r * B.G + blockIdx.x);
     if (part_dots) {
         __syncthreads();
-        warp_dots(V, B.ld, nv, ws, b, len, part_dots + (long long)r * B.G * B.ldp, B.ldp);
+        warp_dots(V, D, B.ld, nv, ws, b, len, part_dots + (long long)r * B.G * B.ldp, B.ldp);
     }
 }
 
@@ -416,20 +438,22 @@ __global__ void k_orotate(OuterBatch B, double2 *__restrict__ H, const double *_
     }
 }
 
-// V_{r,j+1} = w_r / hn_r, and its FP32 copy out32 (if not null)
+// V_{r,j+1} = w_r / hn_r, its FP32 copy out32 and Re - Im into outD (each if not null)
 __global__ void k_oscale(OuterBatch B, double2 *__restrict__ out, float2 *__restrict__ out32,
-                         const double2 *__restrict__ w, const double *__restrict__ hn) {
+                         double *__restrict__ outD, const double2 *__restrict__ w, const double *__restrict__ hn) {
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     const double h = hn[r];
     if (!(h > 0.0)) return;
     out += r * B.n; w += r * B.n;
     if (out32) out32 += r * B.n32;
+    if (outD) outD += r * B.n;
     const double inv = 1.0 / h;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
         const double2 v = make_double2(w[i].x * inv, w[i].y * inv);
         out[i] = v;
         if (out32) out32[i] = make_float2((float)v.x, (float)v.y);
+        if (outD) outD[i] = v.x - v.y;
     }
 }
 
@@ -477,8 +501,8 @@ __global__ void k_oaxpy(OuterBatch B, const double2 *__restrict__ y, const int *
 // g_r = [β_r, 0, ..., 0] (R+1 entries); FP32 copy of v_{r,0} in V32 (if not null); row 0 of the
 // (empty) rotation product, Wq_r = [1].
 __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const double *__restrict__ npart,
-                        double2 *__restrict__ V, float2 *__restrict__ V32, double2 *__restrict__ g,
-                        double2 *__restrict__ Wq, double *__restrict__ beta_out) {
+                        double2 *__restrict__ V, float2 *__restrict__ V32, double *__restrict__ D,
+                        double2 *__restrict__ g, double2 *__restrict__ Wq, double *__restrict__ beta_out) {
     __shared__ double beta_s;
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
@@ -498,10 +522,12 @@ __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const doub
     if (!(beta > 0.0)) return;
     const double inv = 1.0 / beta;
     float2 *v32 = V32 ? V32 + r * B.n32 : nullptr;
+    double *d0 = D ? D + r * B.n : nullptr;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
         const double2 v = make_double2(rv[i].x * inv, rv[i].y * inv);
         v0[i] = v;
         if (v32) v32[i] = make_float2((float)v.x, (float)v.y);
+        if (d0) d0[i] = v.x - v.y;
     }
 }
 
@@ -568,9 +594,9 @@ void launch_orotate(const OuterBatch &B, double2 *H, const double *cs, const dou
                     int kmax, cudaStream_t s) {
     k_orotate<<<dim3((kmax + 63) / 64, B.nrhs), 64, 0, s>>>(B, H, cs, sn, kcols);
 }
-void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, const double2 *w, const double *hn,
-                   cudaStream_t s) {
-    k_oscale<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, out, out32, w, hn);
+void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, double *outD, const double2 *w,
+                   const double *hn, cudaStream_t s) {
+    k_oscale<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, out, out32, outD, w, hn);
 }
 void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, const int *kcols, int kmax,
                       double2 *y, cudaStream_t s) {
@@ -581,8 +607,8 @@ void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int k
     k_oaxpy<<<dim3(grid_for(B.n, 256), B.nrhs), 256, (size_t)kmax * sizeof(double2), s>>>(B, y, kcols, Zb, x);
 }
 void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
-                  double2 *g, double2 *Wq, double *beta_out, cudaStream_t s) {
-    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, V32, g, Wq, beta_out);
+                  double *D, double2 *g, double2 *Wq, double *beta_out, cudaStream_t s) {
+    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, V32, D, g, Wq, beta_out);
 }
 cudaError_t set_outer_smem_limits(size_t bytes) {
     cudaError_t e;
