@@ -1108,7 +1108,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     CK(O.hn.ensure(nr * sizeof(double))); CK(O.flag.ensure(nr * sizeof(int))); CK(O.beta.ensure(nr * sizeof(double)));
     CK(O.fnorm.ensure(nr * sizeof(double))); CK(O.act.ensure(nr * sizeof(int))); CK(O.kcols.ensure(nr * sizeof(int)));
     CK(O.hist.ensure((size_t)nr * (prm->outer_maxit + 1) * sizeof(double)));
-    const size_t osm = (size_t)(R + 1) * sizeof(double2);   // dynamic: h (update), y (axpy, trisolve)
+    const size_t osm = (size_t)(R + 1) * 3 * sizeof(double);   // dynamic: h (update), y (axpy, trisolve)
     if (osm + 40 * 1024 > 227 * 1024) FAIL(HDD_ERR_INVALID_ARG, "outer restart %d too long", R);
     CK(set_outer_smem_limits(osm));
     double2 *V = O.V.as<double2>(), *Zb = O.Z.as<double2>(), *w = O.w.as<double2>(), *rv = O.r.as<double2>();
@@ -1187,12 +1187,12 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
             for (int r = 0; r < nr; r++) nact += act[r];
             const double nv = j + 1, fa = nact;
             KL(F_OMISC, 2.0 * fa * n * 16, 0, launch_gstencil(ctx->st, ctx->N, zj, w, nullptr, nr, dact, s));  // w = A z_j
-            // CGS2 flops as executed: dots 6 per (vector, element) (three FMAs, Gauss form),
-            // update 8; bytes: V once (16 B) and d (8 B) per vector and element, w
+            // CGS2 flops as executed: dots and update 6 per (vector, element) each (three FMAs,
+            // Gauss form); bytes: V once (16 B) and d (8 B) per vector and element, w
             KL(F_OCGS, fa * (nv * 24 + 16) * n, fa * 6 * nv * n,
                launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                              // h1 = V^H w
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
-            KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 14 * nv * n,
+            KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 12 * nv * n,
                launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
             if (r32)   // FP32 correction from the FP32 basis copy (guarded; FP64 fallback inside)
@@ -1200,7 +1200,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                    launch_oupdate2(B, V, V32, j + 1, O.h2.as<double2>(), w, O.npart1.as<double>(),
                                    O.npart.as<double>(), 1, O.fallbacks.as<int>(), s));
             else
-                KL(F_OCGS, fa * (nv + 2) * n * 16, fa * 8 * nv * n,
+                KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
                    launch_oupdate(B, V, j + 1, O.h2.as<double2>(), w, nullptr, O.npart.as<double>(), s));
             KL(F_OMISC, 0, 0,
                launch_ogivens(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(),

@@ -173,6 +173,32 @@ __device__ __forceinline__ double2 update_fp64(double2 x0, const double2 *__rest
     return make_double2(x0.x + x1.x, x0.y + x1.y);
 }
 
+// x -= Σ_{l<nv} h_l V_l(i) in the three-multiplication form: with d = Re v - Im v (stored per
+// basis vector) and c0 = Re h, c1 = Re h - Im h, c2 = Re h + Im h (staged per vector),
+//   h·v = (A + B) + i (C - A),  A = c0·d,  B = c1·Im v,  C = c2·Re v;
+// A, B and C are summed over l (two chains each) and combined once per element.
+__device__ __forceinline__ double2 update_gauss(double2 x, const double2 *__restrict__ vp,
+                                                const double *__restrict__ dp, long long ld,
+                                                const double *__restrict__ c0, const double *__restrict__ c1,
+                                                const double *__restrict__ c2, int nv) {
+    double a0 = 0.0, b0 = 0.0, k0 = 0.0, a1 = 0.0, b1 = 0.0, k1 = 0.0;
+    int l = 0;
+    for (; l + 1 < nv; l += 2) {
+        const double2 v0 = vp[(long long)l * ld], v1 = vp[(long long)(l + 1) * ld];
+        const double d0 = dp[(long long)l * ld], d1 = dp[(long long)(l + 1) * ld];
+        a0 = fma(c0[l], d0, a0); b0 = fma(c1[l], v0.y, b0); k0 = fma(c2[l], v0.x, k0);
+        a1 = fma(c0[l + 1], d1, a1); b1 = fma(c1[l + 1], v1.y, b1); k1 = fma(c2[l + 1], v1.x, k1);
+    }
+    if (l < nv) {
+        const double2 v0 = vp[(long long)l * ld];
+        a0 = fma(c0[l], dp[(long long)l * ld], a0); b0 = fma(c1[l], v0.y, b0); k0 = fma(c2[l], v0.x, k0);
+    }
+    const double A = a0 + a1;
+    x.x -= A + (b0 + b1);
+    x.y -= (k0 + k1) - A;
+    return x;
+}
+
 // Block sum of one double per thread; thread 0 writes it to *out.
 __device__ __forceinline__ void block_sum_store(double v, double *red, double *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -186,12 +212,13 @@ __device__ __forceinline__ void block_sum_store(double v, double *red, double *o
     }
 }
 
-// w_r -= Σ_l h_{r,l} V_{r,l} in FP64; then, if part_dots != null, partial dots V_r^H w_r; if
-// part_norm != null, the partial ||w_r||² of the updated vector.
+// w_r -= Σ_l h_{r,l} V_{r,l} in FP64 (three-multiplication form, update_gauss); then, if
+// part_dots != null, partial dots V_r^H w_r; if part_norm != null, the partial ||w_r||² of the
+// updated vector.  Dynamic shared memory: 3·nv doubles (c0 | c1 | c2).
 __global__ void __launch_bounds__(OT)
 k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__restrict__ h,
           double2 *__restrict__ w, double2 *__restrict__ part_dots, double *__restrict__ part_norm) {
-    extern __shared__ double2 hs[];
+    extern __shared__ double hc[];
     __shared__ WStage ws;
     __shared__ double red[OT / 32];
     const int r = blockIdx.y;
@@ -201,11 +228,15 @@ k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__
     long long b, e;
     chunk_of(B.n, b, e);
     const int len = (int)(e > b ? e - b : 0);
-    for (int l = threadIdx.x; l < nv; l += OT) hs[l] = h[l];
+    double *c0 = hc, *c1 = hc + nv, *c2 = hc + 2 * nv;
+    for (int l = threadIdx.x; l < nv; l += OT) {
+        const double2 v = h[l];
+        c0[l] = v.x; c1[l] = v.x - v.y; c2[l] = v.x + v.y;
+    }
     __syncthreads();
     double nrm = 0.0;
     for (int i = threadIdx.x; i < len; i += OT) {
-        const double2 x = update_fp64(w[b + i], V + b + i, B.ld, hs, nv);
+        const double2 x = update_gauss(w[b + i], V + b + i, D + b + i, B.ld, c0, c1, c2, nv);
         w[b + i] = x;
         stage_w(ws, i, x);
         nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
@@ -569,7 +600,7 @@ void launch_odots(const OuterBatch &B, const double2 *V, int nv, const double2 *
 }
 void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2 *h, double2 *w,
                     double2 *part_dots, double *part_norm, cudaStream_t s) {
-    k_oupdate<<<dim3(B.G, B.nrhs), OT, (size_t)nv * sizeof(double2), s>>>(B, V, nv, h, w, part_dots, part_norm);
+    k_oupdate<<<dim3(B.G, B.nrhs), OT, (size_t)nv * 3 * sizeof(double), s>>>(B, V, nv, h, w, part_dots, part_norm);
 }
 void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
                      double2 *w, const double *npart1, double *part_norm, int allow32, int *fallbacks,
