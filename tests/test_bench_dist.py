@@ -49,3 +49,27 @@ def test_reference_arm_prints_only_on_rank_zero(monkeypatch):
     with contextlib.redirect_stdout(buf):
         assert bench.main() == 0
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_json_line_keys(monkeypatch):
+    """The reference arm (CPU oracle, bounded sample) prints one JSON line with the contract's
+    keys, the same workload keys as the GPU arm, and a cpu_baseline / e2e of its own."""
+    import json
+
+    import bench
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--workload", "tiny", "--steps", "1",
+                                     "--warmup", "0"])
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        assert bench.main() == 0
+    lines = [ln for ln in buf.getvalue().splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["higher_is_better"] is False and d["value"] > 0
+    assert set(bench.workload_config(bench.W.make("tiny"))) <= set(d["config"])
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
