@@ -51,6 +51,8 @@ def lib():
         P, I, D, Z = C.c_void_p, C.c_int, C.c_double, C.c_void_p
         L.or_create.restype = P
         L.or_create.argtypes = [I, D, I]
+        L.or_create_bc.restype = P
+        L.or_create_bc.argtypes = [I, D, I, I]
         L.or_destroy.argtypes = [P]
         for name in ("or_n", "or_nsub"):
             getattr(L, name).argtypes = [P]
@@ -58,6 +60,7 @@ def lib():
         L.or_nnz.argtypes = [P, I]
         L.or_nnz.restype = I
         L.or_get_csr.argtypes = [P, I, Z, Z, Z]
+        L.or_get_csr_imag.argtypes = [P, I, Z]
         L.or_apply_global.argtypes = [P, I, Z, Z]
         L.or_rhs_point.argtypes = [P, D, D, D, Z]
         L.or_rhs_gauss.argtypes = [P, D, D, D, D, Z]
@@ -71,6 +74,7 @@ def lib():
         L.or_sub_nnz.argtypes = [P, I, I]
         L.or_sub_nnz.restype = I
         L.or_sub_get_csr.argtypes = [P, I, I, Z, Z, Z]
+        L.or_sub_get_csr_imag.argtypes = [P, I, I, Z]
         for name in ("or_sub_restrict", "or_sub_apply_A", "or_sub_apply_Z", "or_sub_apply_Zt",
                      "or_sub_apply_PA", "or_sub_apply_P"):
             getattr(L, name).argtypes = [P, I, Z, Z]
@@ -80,6 +84,7 @@ def lib():
         L.or_setup_exact.restype = I
         L.or_sub_E_band.argtypes = [P, I, Z]
         L.or_sub_E_dense.argtypes = [P, I, Z]
+        L.or_sub_E_dense_imag.argtypes = [P, I, Z]
         L.or_sub_coarse_solve.argtypes = [P, I, Z, Z]
         L.or_sub_coarse_solve.restype = I
         L.or_sub_solve.argtypes = [P, I, Z, Z, D, I, I, Z, C.POINTER(I)]
@@ -94,6 +99,9 @@ def lib():
         L.or_band_lu.argtypes = [I, I, I, Z, Z]
         L.or_band_lu.restype = I
         L.or_band_solve.argtypes = [I, I, I, Z, Z, Z]
+        L.or_band_lu_z.argtypes = [I, I, I, Z, Z]
+        L.or_band_lu_z.restype = I
+        L.or_band_solve_z.argtypes = [I, I, I, Z, Z, Z]
         L.or_set_threads.argtypes = [I]
         L.or_get_threads.restype = I
         _lib = L
@@ -137,12 +145,37 @@ def band_solve(ab, piv, m, kl, ku, b):
     return x
 
 
-class Problem:
-    """Discrete Helmholtz problem with its decomposition and local deflation (oracle side)."""
+def band_lu_z(ab: np.ndarray, m: int, kl: int, ku: int):
+    """Complex banded LU with partial pivoting (largest modulus), same storage as band_lu."""
+    ab = _c128(ab).copy()
+    piv = np.zeros(m, dtype=np.int32)
+    st = lib().or_band_lu_z(m, kl, ku, _ptr(ab), _ptr(piv))
+    _check(st, "band_lu_z")
+    return ab, piv
 
-    def __init__(self, N: int, k: float, diag: int = 0):
-        self.N, self.k, self.diag = int(N), float(k), int(diag)
-        self._h = lib().or_create(self.N, self.k, self.diag)
+
+def band_solve_z(ab, piv, m, kl, ku, b):
+    x = _c128(b).copy()
+    lib().or_band_solve_z(m, kl, ku, _ptr(_c128(ab)), _ptr(np.ascontiguousarray(piv, dtype=np.int32)),
+                          _ptr(x))
+    return x
+
+
+BC = {"dirichlet": 0, "sommerfeld": 1}
+_WHICH = {"A": 0, "K": 1, "M": 2, "B": 3}
+
+
+class Problem:
+    """Discrete Helmholtz problem with its decomposition and local deflation (oracle side).
+
+    bc 0: u = 0 on the boundary (Eq. 1), unknowns at the (N-1)² interior nodes.  bc 1: the
+    first-order absorbing condition du/dn - i k u = 0 on all four sides, unknowns at all (N+1)²
+    nodes, A = K - k²M - i k B complex symmetric (B the boundary mass matrix).
+    """
+
+    def __init__(self, N: int, k: float, diag: int = 0, bc: int = 0):
+        self.N, self.k, self.diag, self.bc = int(N), float(k), int(diag), int(bc)
+        self._h = lib().or_create_bc(self.N, self.k, self.diag, self.bc)
         if not self._h:
             raise OracleError("or_create failed")
         self.n = lib().or_n(self._h)
@@ -156,19 +189,31 @@ class Problem:
 
     # -- assembly ----------------------------------------------------------------------------
     def matrix(self, which: str = "A"):
+        """CSR of A, K, M or B (B: boundary mass, empty for Dirichlet); complex where A is."""
         import scipy.sparse as sp
-        w = {"A": 0, "K": 1, "M": 2}[which]
+        w = _WHICH[which]
         nnz = lib().or_nnz(self._h, w)
         rp = np.zeros(self.n + 1, dtype=np.int32)
         ci = np.zeros(nnz, dtype=np.int32)
         v = np.zeros(nnz, dtype=np.float64)
         lib().or_get_csr(self._h, w, _ptr(rp), _ptr(ci), _ptr(v))
+        if self.bc and which == "A":
+            vi = np.zeros(nnz, dtype=np.float64)
+            lib().or_get_csr_imag(self._h, w, _ptr(vi))
+            v = v + 1j * vi
         return sp.csr_matrix((v, ci, rp), shape=(self.n, self.n))
+
+    def node_index(self, i: int, j: int) -> int:
+        """Unknown index of mesh node (i, j) (x fastest), -1 if it is not an unknown."""
+        lo, hi = (0, self.N) if self.bc else (1, self.N - 1)
+        if not (lo <= i <= hi and lo <= j <= hi):
+            return -1
+        return (i - lo) + (j - lo) * (hi - lo + 1)
 
     def apply(self, x, which: str = "A"):
         x = _c128(x)
         y = np.empty_like(x)
-        lib().or_apply_global(self._h, {"A": 0, "K": 1, "M": 2}[which], _ptr(x), _ptr(y))
+        lib().or_apply_global(self._h, _WHICH[which], _ptr(x), _ptr(y))
         return y
 
     # -- right-hand sides ----------------------------------------------------------------------
@@ -221,6 +266,10 @@ class Problem:
         ci = np.zeros(nnz, dtype=np.int32)
         v = np.zeros(nnz, dtype=np.float64)
         lib().or_sub_get_csr(self._h, s, which, _ptr(rp), _ptr(ci), _ptr(v))
+        if self.bc and which == 0:
+            vi = np.zeros(nnz, dtype=np.float64)
+            lib().or_sub_get_csr_imag(self._h, s, which, _ptr(vi))
+            v = v + 1j * vi
         return sp.csr_matrix((v, ci, rp), shape=shape)
 
     def sub_A(self, s: int):
@@ -269,6 +318,10 @@ class Problem:
             raise OracleError("dense E is kept only for m <= 400")
         E = np.zeros((m, m), dtype=np.float64)
         lib().or_sub_E_dense(self._h, s, _ptr(E))
+        if self.bc:
+            Ei = np.zeros((m, m), dtype=np.float64)
+            lib().or_sub_E_dense_imag(self._h, s, _ptr(Ei))
+            return E + 1j * Ei
         return E
 
     def coarse_solve(self, s: int, y) -> np.ndarray:
@@ -326,7 +379,7 @@ class Problem:
 
 def from_workload(w, deflation: bool = True, exact: bool = False) -> Problem:
     """Assemble a workloads.Workload on the oracle side and set up its decomposition."""
-    p = Problem(w.N, w.k)
+    p = Problem(w.N, w.k, bc=getattr(w, "bc", 0))
     p.setup_dd(w.Sx, w.Sy, w.overlap, w.ifx, w.ify)
     if deflation:
         p.setup_deflation()

@@ -31,18 +31,22 @@ typedef struct {
     int nr, nc, nnz;
     int *rp, *ci;
     double *v;
+    double *vi;      /* imaginary parts (same pattern), NULL for a real matrix */
 } csr;
 
 static void csr_free(csr *a) {
-    free(a->rp); free(a->ci); free(a->v);
+    free(a->rp); free(a->ci); free(a->v); free(a->vi);
     memset(a, 0, sizeof(*a));
 }
 
-/* y = A x for complex x (real matrix). */
+/* y = A x for complex x (real or complex matrix). */
 static void csr_mv(const csr *a, const zc *x, zc *y) {
     for (int r = 0; r < a->nr; r++) {
         zc s = 0;
-        for (int t = a->rp[r]; t < a->rp[r + 1]; t++) s += a->v[t] * x[a->ci[t]];
+        if (a->vi)
+            for (int t = a->rp[r]; t < a->rp[r + 1]; t++) s += CMPLX(a->v[t], a->vi[t]) * x[a->ci[t]];
+        else
+            for (int t = a->rp[r]; t < a->rp[r + 1]; t++) s += a->v[t] * x[a->ci[t]];
         y[r] = s;
     }
 }
@@ -53,6 +57,7 @@ static csr csr_transpose(const csr *a) {
     t.rp = (int *)calloc((size_t)t.nr + 1, sizeof(int));
     t.ci = (int *)malloc(sizeof(int) * (size_t)(a->nnz > 0 ? a->nnz : 1));
     t.v = (double *)malloc(sizeof(double) * (size_t)(a->nnz > 0 ? a->nnz : 1));
+    t.vi = a->vi ? (double *)malloc(sizeof(double) * (size_t)(a->nnz > 0 ? a->nnz : 1)) : NULL;
     for (int k = 0; k < a->nnz; k++) t.rp[a->ci[k] + 1]++;
     for (int r = 0; r < t.nr; r++) t.rp[r + 1] += t.rp[r];
     int *pos = (int *)malloc(sizeof(int) * (size_t)(t.nr + 1));
@@ -62,32 +67,46 @@ static csr csr_transpose(const csr *a) {
             int d = pos[a->ci[k]]++;
             t.ci[d] = r;
             t.v[d] = a->v[k];
+            if (a->vi) t.vi[d] = a->vi[k];
         }
     free(pos);
     return t;
 }
 
-/* C = A B (Gustavson row-by-row product with a dense accumulator; columns sorted). */
+/* C = A B (Gustavson row-by-row product with a dense accumulator; columns sorted).  Complex
+ * if either factor is: (a + i a')(b + i b') = (ab - a'b') + i (ab' + a'b). */
 static csr csr_matmul(const csr *a, const csr *b) {
     csr c;
+    const int cplx = a->vi != NULL || b->vi != NULL;
     c.nr = a->nr; c.nc = b->nc;
     c.rp = (int *)calloc((size_t)c.nr + 1, sizeof(int));
     double *acc = (double *)calloc((size_t)b->nc, sizeof(double));
+    double *acci = cplx ? (double *)calloc((size_t)b->nc, sizeof(double)) : NULL;
     int *mark = (int *)malloc(sizeof(int) * (size_t)b->nc);
     for (int j = 0; j < b->nc; j++) mark[j] = -1;
     int cap = 16 * (a->nr + 1), nnz = 0;
     c.ci = (int *)malloc(sizeof(int) * (size_t)cap);
     c.v = (double *)malloc(sizeof(double) * (size_t)cap);
+    c.vi = cplx ? (double *)malloc(sizeof(double) * (size_t)cap) : NULL;
     int *cols = (int *)malloc(sizeof(int) * (size_t)b->nc);
     for (int r = 0; r < a->nr; r++) {
         int nc = 0;
         for (int t = a->rp[r]; t < a->rp[r + 1]; t++) {
             int k = a->ci[t];
-            double av = a->v[t];
+            double av = a->v[t], ai = a->vi ? a->vi[t] : 0.0;
             for (int u = b->rp[k]; u < b->rp[k + 1]; u++) {
                 int j = b->ci[u];
-                if (mark[j] != r) { mark[j] = r; acc[j] = 0.0; cols[nc++] = j; }
-                acc[j] += av * b->v[u];
+                if (mark[j] != r) {
+                    mark[j] = r; acc[j] = 0.0; cols[nc++] = j;
+                    if (cplx) acci[j] = 0.0;
+                }
+                if (cplx) {
+                    double bv = b->v[u], bi = b->vi ? b->vi[u] : 0.0;
+                    acc[j] += av * bv - ai * bi;
+                    acci[j] += av * bi + ai * bv;
+                } else {
+                    acc[j] += av * b->v[u];
+                }
             }
         }
         /* insertion sort of the row's column list */
@@ -100,12 +119,17 @@ static csr csr_matmul(const csr *a, const csr *b) {
             while (nnz + nc > cap) cap *= 2;
             c.ci = (int *)realloc(c.ci, sizeof(int) * (size_t)cap);
             c.v = (double *)realloc(c.v, sizeof(double) * (size_t)cap);
+            if (cplx) c.vi = (double *)realloc(c.vi, sizeof(double) * (size_t)cap);
         }
-        for (int i = 0; i < nc; i++) { c.ci[nnz] = cols[i]; c.v[nnz] = acc[cols[i]]; nnz++; }
+        for (int i = 0; i < nc; i++) {
+            c.ci[nnz] = cols[i]; c.v[nnz] = acc[cols[i]];
+            if (cplx) c.vi[nnz] = acci[cols[i]];
+            nnz++;
+        }
         c.rp[r + 1] = nnz;
     }
     c.nnz = nnz;
-    free(acc); free(mark); free(cols);
+    free(acc); free(acci); free(mark); free(cols);
     return c;
 }
 
@@ -155,10 +179,60 @@ static void band_solve_z(int m, int kl, int ku, const double *ab, const int *piv
         b[r] = s / AB(r, r);
     }
 }
-#undef AB
 
 void or_band_solve(int m, int kl, int ku, const double *ab, const int *piv, double *b_c128) {
     band_solve_z(m, kl, ku, ab, piv, (zc *)b_c128);
+}
+
+/* The same elimination for a complex band (the impedance boundary makes A_j and E_j complex
+ * symmetric): the pivot is the entry of largest modulus in the column. */
+static int band_lu_c(int m, int kl, int ku, zc *ab, int *piv) {
+    const int W = 2 * kl + ku + 1;
+    for (int j = 0; j < m; j++) {
+        int rlast = j + kl < m - 1 ? j + kl : m - 1;
+        int clast = j + kl + ku < m - 1 ? j + kl + ku : m - 1;
+        int p = j;
+        double amax = cabs(AB(j, j));
+        for (int r = j + 1; r <= rlast; r++)
+            if (cabs(AB(r, j)) > amax) { amax = cabs(AB(r, j)); p = r; }
+        piv[j] = p;
+        if (!(amax > 0.0) || !isfinite(amax)) return OR_ERR_SINGULAR;
+        if (p != j)
+            for (int c = j; c <= clast; c++) {
+                zc t = AB(j, c); AB(j, c) = AB(p, c); AB(p, c) = t;
+            }
+        for (int r = j + 1; r <= rlast; r++) {
+            zc l = AB(r, j) / AB(j, j);
+            AB(r, j) = l;
+            for (int c = j + 1; c <= clast; c++) AB(r, c) -= l * AB(j, c);
+        }
+    }
+    return OR_OK;
+}
+
+static void band_solve_c(int m, int kl, int ku, const zc *ab, const int *piv, zc *b) {
+    const int W = 2 * kl + ku + 1;
+    for (int j = 0; j < m; j++) {
+        int p = piv[j];
+        if (p != j) { zc t = b[j]; b[j] = b[p]; b[p] = t; }
+        int rlast = j + kl < m - 1 ? j + kl : m - 1;
+        for (int r = j + 1; r <= rlast; r++) b[r] -= AB(r, j) * b[j];
+    }
+    for (int r = m - 1; r >= 0; r--) {
+        int clast = r + kl + ku < m - 1 ? r + kl + ku : m - 1;
+        zc s = b[r];
+        for (int c = r + 1; c <= clast; c++) s -= AB(r, c) * b[c];
+        b[r] = s / AB(r, r);
+    }
+}
+
+#undef AB
+
+int or_band_lu_z(int m, int kl, int ku, double *ab_c128, int *piv) {
+    return band_lu_c(m, kl, ku, (zc *)ab_c128, piv);
+}
+void or_band_solve_z(int m, int kl, int ku, const double *ab_c128, const int *piv, double *b_c128) {
+    band_solve_c(m, kl, ku, (const zc *)ab_c128, piv, (zc *)b_c128);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -166,9 +240,23 @@ void or_band_solve(int m, int kl, int ku, const double *ab, const int *piv, doub
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
     int m, kl, ku;
-    double *ab;
+    double *ab;              /* real band, or NULL when the matrix is complex */
+    zc *abz;                 /* complex band, or NULL when the matrix is real */
     int *piv;
 } bandlu;
+
+static int bandlu_factor(bandlu *f) {
+    return f->abz ? band_lu_c(f->m, f->kl, f->ku, f->abz, f->piv)
+                  : or_band_lu(f->m, f->kl, f->ku, f->ab, f->piv);
+}
+static void bandlu_solve(const bandlu *f, zc *b) {
+    if (f->abz) band_solve_c(f->m, f->kl, f->ku, f->abz, f->piv, b);
+    else band_solve_z(f->m, f->kl, f->ku, f->ab, f->piv, b);
+}
+static void bandlu_free(bandlu *f) {
+    free(f->ab); free(f->abz); free(f->piv);
+    f->ab = NULL; f->abz = NULL; f->piv = NULL;
+}
 
 typedef struct {
     int ix0, ix1, iy0, iy1;  /* local interior node box (inclusive, global node indices) */
@@ -180,13 +268,16 @@ typedef struct {
     csr Z, Zt;               /* deflation matrix Z_j (n x m) and its transpose */
     bandlu E;                /* factored E_j = Z_j^T A_j Z_j */
     double *Edense;          /* E_j before factoring, kept only for small m (tests) */
+    double *Edense_i;        /* its imaginary part (complex E_j only) */
     bandlu Aex;              /* factored A_j for the direct local solve */
 } subdomain;
 
 struct or_problem {
     int N, n, diag;
+    int bc;                  /* 0: Dirichlet (Eq. 1); 1: impedance (Sommerfeld) on all four sides */
+    int lo, hi;              /* node indices 0..N that are unknowns: lo..hi in both directions */
     double k, h;
-    csr A, K, M;
+    csr A, K, M, B;          /* B: boundary mass matrix ∫_∂Ω φ_a φ_b ds (empty for bc = 0) */
     int Sx, Sy, nsub, overlap;
     subdomain *sub;
     int have_defl, have_exact;
@@ -223,6 +314,7 @@ static csr acc_to_csr(rowacc *a, int n) {
     c.nnz = c.rp[n];
     c.ci = (int *)malloc(sizeof(int) * (size_t)c.nnz);
     c.v = (double *)malloc(sizeof(double) * (size_t)c.nnz);
+    c.vi = NULL;
     for (int r = 0; r < n; r++) {
         int base = r * 8, cnt = a->cnt[r];
         int *cc = a->col + base;
@@ -238,8 +330,14 @@ static csr acc_to_csr(rowacc *a, int n) {
     return c;
 }
 
-/* Interior unknown index of node (i, j), 1 <= i, j <= N-1, x fastest; -1 on the boundary. */
-static int node_index(int N, int i, int j) {
+/* Unknown index of node (i, j), x fastest.  Dirichlet (bc 0): interior nodes 1 <= i, j <= N-1
+ * only, -1 on the boundary (eliminated, u = 0 there).  Impedance (bc 1): every node
+ * 0 <= i, j <= N is an unknown. */
+static int node_index(int N, int bc, int i, int j) {
+    if (bc) {
+        if (i < 0 || i > N || j < 0 || j > N) return -1;
+        return i + j * (N + 1);
+    }
     if (i < 1 || i > N - 1 || j < 1 || j > N - 1) return -1;
     return (i - 1) + (j - 1) * (N - 1);
 }
@@ -260,15 +358,31 @@ static void element_matrices(const double xy[3][2], double Ke[3][3], double Me[3
         }
 }
 
-or_problem *or_create(int N, double k, int diag) {
-    if (N < 2) return NULL;
+/* Element matrix of the boundary term ∫_e φ_a φ_b ds on one boundary edge e of length |e|
+ * (1D P1 mass): |e|(1+δ_ab)/6. */
+static void edge_mass(const double xy[2][2], double Be[2][2]) {
+    double len = hypot(xy[1][0] - xy[0][0], xy[1][1] - xy[0][1]);
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) Be[a][b] = len * (a == b ? 2.0 : 1.0) / 6.0;
+}
+
+or_problem *or_create(int N, double k, int diag) { return or_create_bc(N, k, diag, 0); }
+
+/* bc 1: the first-order absorbing (Sommerfeld) condition ∂u/∂n - i k u = 0 on all of ∂Ω.
+ * Integrating -Δu by parts then leaves -i k ∫_∂Ω u v ds in the bilinear form of Eq. 2 (no
+ * conjugation, so A = K - k²M - i k B is complex symmetric, not Hermitian), and every node
+ * of the mesh, boundary nodes included, is an unknown. */
+or_problem *or_create_bc(int N, double k, int diag, int bc) {
+    if (N < 2 || bc < 0 || bc > 1) return NULL;
     or_problem *p = (or_problem *)calloc(1, sizeof(or_problem));
-    p->N = N; p->k = k; p->diag = diag; p->h = 1.0 / N;
-    p->n = (N - 1) * (N - 1);
+    p->N = N; p->k = k; p->diag = diag; p->h = 1.0 / N; p->bc = bc;
+    p->lo = bc ? 0 : 1;
+    p->hi = bc ? N : N - 1;
+    p->n = (p->hi - p->lo + 1) * (p->hi - p->lo + 1);
     int n = p->n;
-    rowacc aA, aK, aM;
-    rowacc *accs[3] = {&aA, &aK, &aM};
-    for (int q = 0; q < 3; q++) {
+    rowacc aA, aK, aM, aB;
+    rowacc *accs[4] = {&aA, &aK, &aM, &aB};
+    for (int q = 0; q < 4; q++) {
         accs[q]->col = (int *)malloc(sizeof(int) * 8 * (size_t)n);
         accs[q]->val = (double *)malloc(sizeof(double) * 8 * (size_t)n);
         accs[q]->cnt = (int *)calloc((size_t)n, sizeof(int));
@@ -293,7 +407,7 @@ or_problem *or_create(int N, double k, int diag) {
                 for (int a = 0; a < 3; a++) {
                     xy[a][0] = tri[t][a][0] * h;
                     xy[a][1] = tri[t][a][1] * h;
-                    gi[a] = node_index(N, tri[t][a][0], tri[t][a][1]);
+                    gi[a] = node_index(N, bc, tri[t][a][0], tri[t][a][1]);
                 }
                 element_matrices(xy, Ke, Me);
                 for (int a = 0; a < 3; a++) {
@@ -307,23 +421,54 @@ or_problem *or_create(int N, double k, int diag) {
                 }
             }
         }
+    if (bc) {
+        /* the 4N boundary edges: bottom, top (along x), left, right (along y) */
+        for (int side = 0; side < 4; side++)
+            for (int e = 0; e < N; e++) {
+                int nd[2][2];
+                if (side < 2) { int j = side == 0 ? 0 : N; nd[0][0] = e; nd[0][1] = j; nd[1][0] = e + 1; nd[1][1] = j; }
+                else { int i = side == 2 ? 0 : N; nd[0][0] = i; nd[0][1] = e; nd[1][0] = i; nd[1][1] = e + 1; }
+                double xy[2][2], Be[2][2];
+                int gi[2];
+                for (int a = 0; a < 2; a++) {
+                    xy[a][0] = nd[a][0] * h;
+                    xy[a][1] = nd[a][1] * h;
+                    gi[a] = node_index(N, bc, nd[a][0], nd[a][1]);
+                }
+                edge_mass(xy, Be);
+                for (int a = 0; a < 2; a++)
+                    for (int b = 0; b < 2; b++) acc_add(&aB, gi[a], gi[b], Be[a][b]);
+            }
+    }
     p->A = acc_to_csr(&aA, n);
     p->K = acc_to_csr(&aK, n);
     p->M = acc_to_csr(&aM, n);
-    for (int q = 0; q < 3; q++) { free(accs[q]->col); free(accs[q]->val); free(accs[q]->cnt); }
+    p->B = acc_to_csr(&aB, n);
+    if (bc) {
+        /* Im A = -k B on A's pattern (every boundary edge is the side of a triangle, so B's
+         * pattern lies inside A's) */
+        p->A.vi = (double *)calloc((size_t)(p->A.nnz > 0 ? p->A.nnz : 1), sizeof(double));
+        for (int r = 0; r < n; r++)
+            for (int t = p->B.rp[r]; t < p->B.rp[r + 1]; t++) {
+                int q = p->A.rp[r];
+                while (q < p->A.rp[r + 1] && p->A.ci[q] != p->B.ci[t]) q++;
+                if (q < p->A.rp[r + 1]) p->A.vi[q] = -k * p->B.v[t];
+            }
+    }
+    for (int q = 0; q < 4; q++) { free(accs[q]->col); free(accs[q]->val); free(accs[q]->cnt); }
     return p;
 }
 
 static void free_sub(subdomain *s) {
     free(s->gidx);
     csr_free(&s->A); csr_free(&s->Z); csr_free(&s->Zt);
-    free(s->E.ab); free(s->E.piv); free(s->Edense);
-    free(s->Aex.ab); free(s->Aex.piv);
+    bandlu_free(&s->E); free(s->Edense); free(s->Edense_i);
+    bandlu_free(&s->Aex);
 }
 
 void or_destroy(or_problem *p) {
     if (!p) return;
-    csr_free(&p->A); csr_free(&p->K); csr_free(&p->M);
+    csr_free(&p->A); csr_free(&p->K); csr_free(&p->M); csr_free(&p->B);
     if (p->sub) { for (int s = 0; s < p->nsub; s++) free_sub(&p->sub[s]); free(p->sub); }
     free(p);
 }
@@ -331,7 +476,7 @@ void or_destroy(or_problem *p) {
 int or_n(const or_problem *p) { return p->n; }
 
 static const csr *pick(const or_problem *p, int which) {
-    return which == 0 ? &p->A : which == 1 ? &p->K : &p->M;
+    return which == 0 ? &p->A : which == 1 ? &p->K : which == 2 ? &p->M : &p->B;
 }
 int or_nnz(const or_problem *p, int which) { return pick(p, which)->nnz; }
 void or_get_csr(const or_problem *p, int which, int *rowptr, int *col, double *val) {
@@ -340,46 +485,69 @@ void or_get_csr(const or_problem *p, int which, int *rowptr, int *col, double *v
     memcpy(col, a->ci, sizeof(int) * (size_t)a->nnz);
     memcpy(val, a->v, sizeof(double) * (size_t)a->nnz);
 }
+void or_get_csr_imag(const or_problem *p, int which, double *val) {
+    const csr *a = pick(p, which);
+    if (a->vi) memcpy(val, a->vi, sizeof(double) * (size_t)a->nnz);
+    else memset(val, 0, sizeof(double) * (size_t)a->nnz);
+}
 void or_apply_global(const or_problem *p, int which, const double *x, double *y) {
     csr_mv(pick(p, which), (const zc *)x, (zc *)y);
 }
 
 /* -- right-hand sides (§3) -------------------------------------------------------------------- */
-/* Point source: F(v) = amp · v(x_c), with x_c snapped to the nearest interior node. */
+/* Point source: F(v) = amp · v(x_c), with x_c snapped to the nearest node that is an unknown
+ * (an interior node for Dirichlet, any node for the impedance condition). */
 void or_rhs_point(const or_problem *p, double x, double y, double amp, double *f) {
     int N = p->N;
     int i = (int)floor(x * N + 0.5), j = (int)floor(y * N + 0.5);
-    if (i < 1) i = 1;
-    if (i > N - 1) i = N - 1;
-    if (j < 1) j = 1;
-    if (j > N - 1) j = N - 1;
-    ((zc *)f)[node_index(N, i, j)] += amp;
+    if (i < p->lo) i = p->lo;
+    if (i > p->hi) i = p->hi;
+    if (j < p->lo) j = p->lo;
+    if (j > p->hi) j = p->hi;
+    ((zc *)f)[node_index(N, p->bc, i, j)] += amp;
 }
 
-/* F += M g_I, g_I the interpolant in V^h (zero on the boundary) of the Gaussian bump. */
+/* F += M g_I, g_I the interpolant in V^h of the Gaussian bump (its nodal values at the
+ * unknowns; zero on the boundary for Dirichlet). */
 void or_rhs_gauss(const or_problem *p, double cx, double cy, double sigma, double amp, double *f) {
     int N = p->N;
     zc *g = (zc *)calloc((size_t)p->n, sizeof(zc));
     zc *mg = (zc *)malloc(sizeof(zc) * (size_t)p->n);
-    for (int j = 1; j < N; j++)
-        for (int i = 1; i < N; i++) {
+    for (int j = p->lo; j <= p->hi; j++)
+        for (int i = p->lo; i <= p->hi; i++) {
             double dx = i * p->h - cx, dy = j * p->h - cy;
-            g[node_index(N, i, j)] = amp * exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma));
+            g[node_index(N, p->bc, i, j)] = amp * exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma));
         }
     csr_mv(&p->M, g, mg);
     for (int t = 0; t < p->n; t++) ((zc *)f)[t] += mg[t];
     free(g); free(mg);
 }
 
-/* F = M f_I with f = (2π² - k²) sin(πx) sin(πy): exact solution u = sin(πx) sin(πy). */
+/* F = M f_I with f = (2π² - k²) sin(πx) sin(πy): exact solution u = sin(πx) sin(πy).  With
+ * the impedance condition u still vanishes on ∂Ω but ∂u/∂n = -π sin(πs) on every side (s the
+ * coordinate along the side), so the boundary datum g = ∂u/∂n - i k u = -π sin(πs) is added as
+ * F += B g_I. */
 void or_rhs_manufactured(const or_problem *p, double *f) {
     int N = p->N;
     zc *g = (zc *)malloc(sizeof(zc) * (size_t)p->n);
-    for (int j = 1; j < N; j++)
-        for (int i = 1; i < N; i++)
-            g[node_index(N, i, j)] = (2.0 * M_PI * M_PI - p->k * p->k) * sin(M_PI * i * p->h) *
-                                     sin(M_PI * j * p->h);
+    for (int j = p->lo; j <= p->hi; j++)
+        for (int i = p->lo; i <= p->hi; i++)
+            g[node_index(N, p->bc, i, j)] = (2.0 * M_PI * M_PI - p->k * p->k) * sin(M_PI * i * p->h) *
+                                            sin(M_PI * j * p->h);
     csr_mv(&p->M, g, (zc *)f);
+    if (p->bc) {
+        zc *bg = (zc *)malloc(sizeof(zc) * (size_t)p->n);
+        for (int j = 0; j <= N; j++)
+            for (int i = 0; i <= N; i++) {
+                double v = 0.0;
+                if (j == 0 || j == N) v += -M_PI * sin(M_PI * i * p->h);
+                if (i == 0 || i == N) v += -M_PI * sin(M_PI * j * p->h);
+                g[node_index(N, 1, i, j)] = v;
+            }
+        csr_mv(&p->B, g, bg);
+        for (int t = 0; t < p->n; t++) ((zc *)f)[t] += bg[t];
+        free(bg);
+    }
     free(g);
 }
 
@@ -397,16 +565,19 @@ int or_setup_dd(or_problem *p, int Sx, int Sy, int overlap, const int *ifx, cons
     for (int py = 0; py < Sy; py++)
         for (int px = 0; px < Sx; px++) {
             subdomain *sd = &p->sub[px + py * Sx];
-            /* subdomain = cells [a_p - δ, a_{p+1} + δ]; its interior nodes form the local box */
-            sd->ix0 = ifx[px] - overlap + 1 < 1 ? 1 : ifx[px] - overlap + 1;
-            sd->ix1 = ifx[px + 1] + overlap - 1 > N - 1 ? N - 1 : ifx[px + 1] + overlap - 1;
-            sd->iy0 = ify[py] - overlap + 1 < 1 ? 1 : ify[py] - overlap + 1;
-            sd->iy1 = ify[py + 1] + overlap - 1 > N - 1 ? N - 1 : ify[py + 1] + overlap - 1;
-            /* owned nodes a_p <= i < a_{p+1}: each interior node owned exactly once */
-            sd->ox0 = ifx[px] < 1 ? 1 : ifx[px];
-            sd->ox1 = ifx[px + 1] - 1;
-            sd->oy0 = ify[py] < 1 ? 1 : ify[py];
-            sd->oy1 = ify[py + 1] - 1;
+            /* subdomain = cells [a_p - δ, a_{p+1} + δ]; the unknowns among its nodes, less those
+             * on its artificial boundary, form the local box (lo..hi: the global unknown range) */
+            const int lo = p->lo, hi = p->hi;
+            sd->ix0 = ifx[px] - overlap + 1 < lo ? lo : ifx[px] - overlap + 1;
+            sd->ix1 = ifx[px + 1] + overlap - 1 > hi ? hi : ifx[px + 1] + overlap - 1;
+            sd->iy0 = ify[py] - overlap + 1 < lo ? lo : ify[py] - overlap + 1;
+            sd->iy1 = ify[py + 1] + overlap - 1 > hi ? hi : ify[py + 1] + overlap - 1;
+            /* owned nodes a_p <= i < a_{p+1} (the last subdomain also owns hi): each unknown
+             * owned exactly once */
+            sd->ox0 = ifx[px] < lo ? lo : ifx[px];
+            sd->ox1 = px == Sx - 1 ? hi : ifx[px + 1] - 1;
+            sd->oy0 = ify[py] < lo ? lo : ify[py];
+            sd->oy1 = py == Sy - 1 ? hi : ify[py + 1] - 1;
             sd->nx = sd->ix1 - sd->ix0 + 1;
             sd->ny = sd->iy1 - sd->iy0 + 1;
             sd->n = sd->nx * sd->ny;
@@ -416,7 +587,7 @@ int or_setup_dd(or_problem *p, int Sx, int Sy, int overlap, const int *ifx, cons
             sd->gidx = (int *)malloc(sizeof(int) * (size_t)sd->n);
             for (int j = 0; j < sd->ny; j++)
                 for (int i = 0; i < sd->nx; i++)
-                    sd->gidx[i + j * sd->nx] = node_index(N, sd->ix0 + i, sd->iy0 + j);
+                    sd->gidx[i + j * sd->nx] = node_index(N, p->bc, sd->ix0 + i, sd->iy0 + j);
             /* A_j = R_j A R_j^T: rows and columns of the box, extracted from the assembled A */
             int *g2l = (int *)malloc(sizeof(int) * (size_t)p->n);
             for (int t = 0; t < p->n; t++) g2l[t] = -1;
@@ -425,13 +596,18 @@ int or_setup_dd(or_problem *p, int Sx, int Sy, int overlap, const int *ifx, cons
             sd->A.rp = (int *)malloc(sizeof(int) * (size_t)(sd->n + 1));
             sd->A.ci = (int *)malloc(sizeof(int) * 8 * (size_t)sd->n);
             sd->A.v = (double *)malloc(sizeof(double) * 8 * (size_t)sd->n);
+            sd->A.vi = p->A.vi ? (double *)malloc(sizeof(double) * 8 * (size_t)sd->n) : NULL;
             int nnz = 0;
             sd->A.rp[0] = 0;
             for (int t = 0; t < sd->n; t++) {
                 int g = sd->gidx[t];
                 for (int q = p->A.rp[g]; q < p->A.rp[g + 1]; q++) {
                     int lc = g2l[p->A.ci[q]];
-                    if (lc >= 0) { sd->A.ci[nnz] = lc; sd->A.v[nnz] = p->A.v[q]; nnz++; }
+                    if (lc >= 0) {
+                        sd->A.ci[nnz] = lc; sd->A.v[nnz] = p->A.v[q];
+                        if (sd->A.vi) sd->A.vi[nnz] = p->A.vi[q];
+                        nnz++;
+                    }
                 }
                 sd->A.rp[t + 1] = nnz;
             }
@@ -466,6 +642,11 @@ void or_sub_get_csr(const or_problem *p, int s, int which, int *rowptr, int *col
     memcpy(col, a->ci, sizeof(int) * (size_t)a->nnz);
     memcpy(val, a->v, sizeof(double) * (size_t)a->nnz);
 }
+void or_sub_get_csr_imag(const or_problem *p, int s, int which, double *val) {
+    const csr *a = which == 0 ? &p->sub[s].A : &p->sub[s].Z;
+    if (a->vi) memcpy(val, a->vi, sizeof(double) * (size_t)a->nnz);
+    else memset(val, 0, sizeof(double) * (size_t)a->nnz);
+}
 
 /* -- Eq. 4, Eq. 5: deflation matrix and coarse matrix ---------------------------------------- */
 /* 1D quadratic rational Bézier deflation matrix (n x n/2): column i (1-based) carries
@@ -484,6 +665,7 @@ static csr build_Z(int nx, int ny) {
     z.rp = (int *)malloc(sizeof(int) * (size_t)(n + 1));
     z.ci = (int *)malloc(sizeof(int) * 9 * (size_t)n);
     z.v = (double *)malloc(sizeof(double) * 9 * (size_t)n);
+    z.vi = NULL;
     int nnz = 0;
     z.rp[0] = 0;
     for (int fy = 0; fy < ny; fy++)
@@ -516,11 +698,16 @@ static void csr_to_band(const csr *a, bandlu *b) {
         }
     int W = 2 * kl + ku + 1;
     b->m = a->nr; b->kl = kl; b->ku = ku;
-    b->ab = (double *)calloc((size_t)a->nr * (size_t)W, sizeof(double));
+    b->ab = NULL; b->abz = NULL;
+    if (a->vi) b->abz = (zc *)calloc((size_t)a->nr * (size_t)W, sizeof(zc));
+    else b->ab = (double *)calloc((size_t)a->nr * (size_t)W, sizeof(double));
     b->piv = (int *)malloc(sizeof(int) * (size_t)(a->nr > 0 ? a->nr : 1));
     for (int r = 0; r < a->nr; r++)
-        for (int t = a->rp[r]; t < a->rp[r + 1]; t++)
-            b->ab[(size_t)r * W + (size_t)(a->ci[t] - r + kl)] = a->v[t];
+        for (int t = a->rp[r]; t < a->rp[r + 1]; t++) {
+            size_t at = (size_t)r * W + (size_t)(a->ci[t] - r + kl);
+            if (a->vi) b->abz[at] = CMPLX(a->v[t], a->vi[t]);
+            else b->ab[at] = a->v[t];
+        }
 }
 
 int or_setup_deflation(or_problem *p) {
@@ -530,8 +717,8 @@ int or_setup_deflation(or_problem *p) {
     for (int s = 0; s < p->nsub; s++) {
         subdomain *sd = &p->sub[s];
         csr_free(&sd->Z); csr_free(&sd->Zt);
-        free(sd->E.ab); free(sd->E.piv); free(sd->Edense);
-        sd->E.ab = NULL; sd->E.piv = NULL; sd->Edense = NULL;
+        bandlu_free(&sd->E); free(sd->Edense); free(sd->Edense_i);
+        sd->Edense = NULL; sd->Edense_i = NULL;
         sd->Z = build_Z(sd->nx, sd->ny);
         sd->Zt = csr_transpose(&sd->Z);
         csr AZ = csr_matmul(&sd->A, &sd->Z);
@@ -541,9 +728,15 @@ int or_setup_deflation(or_problem *p) {
             for (int r = 0; r < E.nr; r++)
                 for (int t = E.rp[r]; t < E.rp[r + 1]; t++)
                     sd->Edense[(size_t)r * sd->m + E.ci[t]] = E.v[t];
+            if (E.vi) {
+                sd->Edense_i = (double *)calloc((size_t)sd->m * (size_t)sd->m, sizeof(double));
+                for (int r = 0; r < E.nr; r++)
+                    for (int t = E.rp[r]; t < E.rp[r + 1]; t++)
+                        sd->Edense_i[(size_t)r * sd->m + E.ci[t]] = E.vi[t];
+            }
         }
         csr_to_band(&E, &sd->E);
-        int st = or_band_lu(sd->E.m, sd->E.kl, sd->E.ku, sd->E.ab, sd->E.piv);
+        int st = bandlu_factor(&sd->E);
         if (st != OR_OK) {
 #pragma omp critical
             status = st;
@@ -560,9 +753,9 @@ int or_setup_exact(or_problem *p) {
 #pragma omp parallel for schedule(dynamic) num_threads(or_get_threads())
     for (int s = 0; s < p->nsub; s++) {
         subdomain *sd = &p->sub[s];
-        free(sd->Aex.ab); free(sd->Aex.piv);
+        bandlu_free(&sd->Aex);
         csr_to_band(&sd->A, &sd->Aex);
-        int st = or_band_lu(sd->Aex.m, sd->Aex.kl, sd->Aex.ku, sd->Aex.ab, sd->Aex.piv);
+        int st = bandlu_factor(&sd->Aex);
         if (st != OR_OK) {
 #pragma omp critical
             status = st;
@@ -579,6 +772,11 @@ void or_sub_E_dense(const or_problem *p, int s, double *E) {
     const subdomain *sd = &p->sub[s];
     if (sd->Edense) memcpy(E, sd->Edense, sizeof(double) * (size_t)sd->m * (size_t)sd->m);
 }
+void or_sub_E_dense_imag(const or_problem *p, int s, double *E) {
+    const subdomain *sd = &p->sub[s];
+    if (sd->Edense_i) memcpy(E, sd->Edense_i, sizeof(double) * (size_t)sd->m * (size_t)sd->m);
+    else if (sd->Edense) memset(E, 0, sizeof(double) * (size_t)sd->m * (size_t)sd->m);
+}
 void or_sub_apply_Z(const or_problem *p, int s, const double *c, double *f) {
     csr_mv(&p->sub[s].Z, (const zc *)c, (zc *)f);
 }
@@ -588,14 +786,14 @@ void or_sub_apply_Zt(const or_problem *p, int s, const double *f, double *c) {
 int or_sub_coarse_solve(const or_problem *p, int s, const double *y, double *x) {
     const subdomain *sd = &p->sub[s];
     memcpy(x, y, sizeof(zc) * (size_t)sd->m);
-    band_solve_z(sd->E.m, sd->E.kl, sd->E.ku, sd->E.ab, sd->E.piv, (zc *)x);
+    bandlu_solve(&sd->E, (zc *)x);
     return OR_OK;
 }
 
 /* Q_j r = Z_j E_j^{-1} Z_j^T r (Eq. 4). */
 static void apply_Q(const subdomain *sd, const zc *r, zc *out, zc *cw) {
     csr_mv(&sd->Zt, r, cw);
-    band_solve_z(sd->E.m, sd->E.kl, sd->E.ku, sd->E.ab, sd->E.piv, cw);
+    bandlu_solve(&sd->E, cw);
     csr_mv(&sd->Z, cw, out);
 }
 
@@ -767,7 +965,7 @@ int or_sub_solve_exact(const or_problem *p, int s, const double *f, double *x) {
     if (!p->have_exact) return OR_ERR_STATE;
     const subdomain *sd = &p->sub[s];
     memcpy(x, f, sizeof(zc) * (size_t)sd->n);
-    band_solve_z(sd->Aex.m, sd->Aex.kl, sd->Aex.ku, sd->Aex.ab, sd->Aex.piv, (zc *)x);
+    bandlu_solve(&sd->Aex, (zc *)x);
     return OR_OK;
 }
 
@@ -793,7 +991,7 @@ int or_ras_apply(const or_problem *p, const double *v_, double *z_, double inner
             st = sub_gmres(sd, fs, NULL, inner_tol, inner_restart, inner_maxit, xs, &its);
         } else {
             memcpy(xs, fs, sizeof(zc) * (size_t)sd->n);
-            band_solve_z(sd->Aex.m, sd->Aex.kl, sd->Aex.ku, sd->Aex.ab, sd->Aex.piv, xs);
+            bandlu_solve(&sd->Aex, xs);
             st = OR_OK;
         }
         if (st != OR_OK) {

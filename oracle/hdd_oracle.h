@@ -6,7 +6,9 @@
  *
  * Everything is complex128 (C99 double complex); real matrices are real CSR.
  * Model problem: -Δu - k²u = f on (0,1)², u = 0 on the boundary (§2, Eq. 1), P1 elements on
- * a uniform mesh with N intervals per side (Eq. 2).  One-level RAS (Eq. 3) wrapped by FGMRES;
+ * a uniform mesh with N intervals per side (Eq. 2).  Variant (§3 names the solver fit for
+ * Sommerfeld problems as well): the first-order absorbing condition ∂u/∂n - i k u = 0 on all
+ * of ∂Ω instead, which makes A complex symmetric and every mesh node an unknown.  One-level RAS (Eq. 3) wrapped by FGMRES;
  * subdomain systems solved by GMRES preconditioned with two-level deflation (Eq. 4, Eq. 5).
  */
 #ifndef HDD_ORACLE_H
@@ -48,11 +50,13 @@ typedef struct {
 } or_stats;
 
 /* -- problem and assembly (Eq. 2) ------------------------------------------------------- */
-or_problem *or_create(int N, double k, int diag);
+or_problem *or_create(int N, double k, int diag);            /* Dirichlet                   */
+or_problem *or_create_bc(int N, double k, int diag, int bc); /* bc: 0 Dirichlet, 1 impedance */
 void or_destroy(or_problem *p);
 int or_n(const or_problem *p);
-int or_nnz(const or_problem *p, int which);                 /* which: 0 = A, 1 = K, 2 = M   */
+int or_nnz(const or_problem *p, int which);           /* which: 0 = A, 1 = K, 2 = M, 3 = B  */
 void or_get_csr(const or_problem *p, int which, int *rowptr, int *col, double *val);
+void or_get_csr_imag(const or_problem *p, int which, double *val);   /* zeros if real     */
 void or_apply_global(const or_problem *p, int which, const double *x_c128, double *y_c128);
 
 /* -- right-hand sides (§3) ---------------------------------------------------------------- */
@@ -71,12 +75,14 @@ void or_sub_restrict(const or_problem *p, int s, const double *v_c128, double *v
 void or_sub_apply_A(const or_problem *p, int s, const double *v_c128, double *w_c128);
 int or_sub_nnz(const or_problem *p, int s, int which);       /* 0 = A_s, 1 = Z_s            */
 void or_sub_get_csr(const or_problem *p, int s, int which, int *rowptr, int *col, double *val);
+void or_sub_get_csr_imag(const or_problem *p, int s, int which, double *val);
 
 /* -- deflation (Eq. 4, Eq. 5) ------------------------------------------------------------- */
 int or_setup_deflation(or_problem *p);
 int or_setup_exact(or_problem *p);
 void or_sub_E_band(const or_problem *p, int s, int *kl_ku);
 void or_sub_E_dense(const or_problem *p, int s, double *E);  /* m x m row-major, unfactored */
+void or_sub_E_dense_imag(const or_problem *p, int s, double *E);    /* its imaginary part  */
 void or_sub_apply_Z(const or_problem *p, int s, const double *c_c128, double *f_c128);
 void or_sub_apply_Zt(const or_problem *p, int s, const double *f_c128, double *c_c128);
 int or_sub_coarse_solve(const or_problem *p, int s, const double *y_c128, double *x_c128);
@@ -96,6 +102,8 @@ int or_solve(const or_problem *p, const double *f_c128, double *x_c128, const or
 /* -- banded LU with partial pivoting, row-band storage (exposed for pins) ----------------- */
 int or_band_lu(int m, int kl, int ku, double *ab, int *piv);
 void or_band_solve(int m, int kl, int ku, const double *ab, const int *piv, double *b_c128);
+int or_band_lu_z(int m, int kl, int ku, double *ab_c128, int *piv);      /* complex band   */
+void or_band_solve_z(int m, int kl, int ku, const double *ab_c128, const int *piv, double *b_c128);
 
 void or_set_threads(int nthreads);
 int or_get_threads(void);

@@ -5,7 +5,8 @@ numbers a workload needs (interface jitter, point-source locations, Gaussian bum
 centres) from a counter-free SplitMix64 stream and packages the problem
 parameters.  Both sides receive these numbers as plain inputs.
 
-Workloads (all on the unit square, Dirichlet boundary, P1 elements, §2–§3):
+Workloads (all on the unit square, P1 elements, §2–§3; Dirichlet boundary unless bc = 1, the
+first-order absorbing condition du/dn - i k u = 0 on all four sides):
 
   tiny      k=20,  N=32,   2x2 subdomains, overlap 2, point source at the centre
   k100      k=100, N=320,  4x4 subdomains, overlap 2, centre point source + Gaussian bump
@@ -76,6 +77,7 @@ class Workload:
     rhs: list          # one RHSSpec per right-hand side
     inner_tol: float = 1e-2
     outer_tol: float = 1e-6
+    bc: int = 0        # 0: u = 0 on the boundary; 1: impedance (Sommerfeld) on all four sides
 
     @property
     def h(self) -> float:
@@ -83,7 +85,7 @@ class Workload:
 
     @property
     def n_global(self) -> int:
-        return (self.N - 1) ** 2
+        return (self.N + 1) ** 2 if self.bc else (self.N - 1) ** 2
 
     @property
     def ppwl(self) -> float:
@@ -142,12 +144,12 @@ def make(name: str, seed: int = 0) -> Workload:
 
 
 def custom(k: float, N: int, S: int, overlap: int = 2, rhs=None, Sy: int | None = None,
-           ifx=None, ify=None, name: str = "custom") -> Workload:
+           ifx=None, ify=None, name: str = "custom", bc: int = 0) -> Workload:
     Sy = S if Sy is None else Sy
     return Workload(name, k, N, S, Sy, overlap,
                     list(ifx) if ifx is not None else uniform_interfaces(N, S),
                     list(ify) if ify is not None else uniform_interfaces(N, Sy),
-                    rhs if rhs is not None else [RHSSpec([PointSource(0.5, 0.5)])])
+                    rhs if rhs is not None else [RHSSpec([PointSource(0.5, 0.5)])], bc=bc)
 
 
 def random_complex(n: int, seed: int):
