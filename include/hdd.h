@@ -71,20 +71,31 @@ const char *hdd_last_error(const hdd_ctx *ctx);
 /*   centre 4 - k²h²/2, edge neighbours -1 - k²h²/12, the two corners joined by the cell      */
 /*   diagonals -k²h²/12 (SW/NE for diag = 0, NW/SE for diag = 1),                            */
 /* which every kernel applies matrix-free.                                                   */
+/*                                                                                          */
+/* bc = 1 selects the Sommerfeld variant (§3: the solver is meant for non-symmetric          */
+/* Sommerfeld problems too): the first-order absorbing condition du/dn - i k u = 0 on all    */
+/* four sides, so every mesh node 0 <= i, j <= N is an unknown ((N+1)² per vector, index     */
+/* i + j(N+1)) and A = K - k²M - i k B, B the P1 boundary mass matrix (h/3 centre, h/6 along */
+/* the side): complex symmetric, with the interior stencil above on interior rows.  Local    */
+/* matrices keep these rows where a box meets the boundary of the square (Dirichlet on its   */
+/* artificial sides); E and A_j are then complex and are factored as their real equivalents. */
+/* The learned warm start serves bc = 0 only.                                               */
 /* ---------------------------------------------------------------------------------------- */
 typedef struct {
     double k;   /* wave number                                            */
     int N;      /* intervals per side, h = 1/N, 4 <= N <= 65536            */
     int diag;   /* 0: cells split along SW-NE, 1: along NW-SE              */
+    int bc;     /* 0: u = 0 on the boundary (Eq. 1); 1: impedance, above  */
 } hdd_assemble_params;
 
 hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *prm);
 
-/* Load vector on the device (§3): point sources F += amp·e_c at the interior node nearest to
- * (x, y) (clamped into the interior), and Gaussian bumps F += M g with g the nodal values of
- * amp·exp(-|x - c|²/(2σ²)) at the interior nodes (the interpolant in V^h) and M the P1 mass
- * matrix.  points: npoints triples (x, y, amp); bumps: nbumps quadruples (cx, cy, σ, amp), both
- * host arrays.  f_dev: one complex128 vector of (N-1)², overwritten. */
+/* Load vector on the device (§3): point sources F += amp·e_c at the unknown node nearest to
+ * (x, y) (clamped into the interior for bc = 0), and Gaussian bumps F += M g with g the nodal
+ * values of amp·exp(-|x - c|²/(2σ²)) at the unknowns (the interpolant in V^h) and M the P1
+ * mass matrix.  points: npoints triples (x, y, amp); bumps: nbumps quadruples (cx, cy, σ, amp),
+ * both host arrays.  f_dev: one complex128 vector of (N-1)² (bc = 0) or (N+1)² (bc = 1)
+ * entries, overwritten. */
 hdd_status hdd_build_rhs(hdd_ctx *ctx, int npoints, const double *points, int nbumps,
                          const double *bumps, void *f_dev, void *stream);
 
@@ -98,7 +109,8 @@ hdd_status hdd_apply_A(hdd_ctx *ctx, const void *x_dev, void *y_dev, int nrhs, v
 /* indicator) and its local box, after appending `overlap` element layers, is               */
 /* max(1, a_p - δ + 1) <= i <= min(N-1, a_{p+1} + δ - 1) (same in y).  Subdomain index        */
 /* s = p + q·Sx.  A_j = R_j A R_jᵀ is the stencil on the box with zero Dirichlet values      */
-/* outside it.                                                                               */
+/* outside it.  With bc = 1 the unknowns run over 0..N: the box is clipped to [0, N] and the */
+/* last subdomain in each direction also owns node N.                                        */
 /* ---------------------------------------------------------------------------------------- */
 typedef struct {
     int Sx, Sy;       /* 1 <= Sx, Sy <= 4096                                 */

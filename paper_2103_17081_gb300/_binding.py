@@ -33,7 +33,7 @@ class HDDError(RuntimeError):
 
 
 class AssembleParams(C.Structure):
-    _fields_ = [("k", C.c_double), ("N", C.c_int), ("diag", C.c_int)]
+    _fields_ = [("k", C.c_double), ("N", C.c_int), ("diag", C.c_int), ("bc", C.c_int)]
 
 
 class DDParams(C.Structure):

@@ -42,8 +42,9 @@ struct FactorSet {            // banded FP64 factors of one matrix per shape, bl
     std::vector<BlockFactor> h;
     std::vector<double> fma_col;    // FP64 FMAs of one real column by banded substitution, per shape
     BlockSolveCfg cfg;              // shared-memory plan of the blocked solve
+    bool re2 = false;               // factors of real-equivalent systems (complex matrices)
     bool ready = false;
-    void clear() { M.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); cfg = BlockSolveCfg{}; ready = false; }
+    void clear() { M.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); cfg = BlockSolveCfg{}; re2 = false; ready = false; }
 };
 
 template <typename R> struct InnerWork {   // inner GMRES buffers for one precision
@@ -118,14 +119,17 @@ struct hdd_ctx {
     bool assembled = false, dd = false;
     // problem
     int N = 0, diag = 0;
+    int bc = 0;                                 // 0: Dirichlet, 1: impedance on all four sides
     double k = 0, h = 0;
     Stencil st{};
+    DevMem d_bcoef, d_bmass;                    // boundary-class rows of A and M (bc = 1)
     long long nglob = 0;
     // decomposition
     int Sx = 0, Sy = 0, overlap = 0;
     std::vector<SubBox> subs;
     std::vector<int> sub_shape;
     std::vector<std::pair<int, int>> shapes;   // (nx, ny)
+    std::vector<std::pair<int, int>> shape_org; // box origin (ix0, iy0) of one subdomain of each shape
     int nrhs = 1;                               // right-hand sides batched per solve
     std::vector<Task> h_tasks;                  // task t = r·nsub + s
     std::vector<Tile> h_ftiles, h_ctiles;
@@ -208,7 +212,8 @@ template <typename R> LocalArgs<R> local_args(hdd_ctx *ctx) {
     a.ld = ctx->ld;
     a.ldc = ctx->ldc;
     a.max_nx = ctx->max_nx;
-    a.gw = ctx->N - 1;
+    a.gw = ctx->bc ? ctx->N + 1 : ctx->N - 1;
+    a.glo = ctx->bc ? 0 : 1;
     a.frows = ctx->frows;
     a.crows = ctx->crows;
     return a;
@@ -227,11 +232,15 @@ hdd_status read_counter(hdd_ctx *ctx, cudaStream_t s, int *out) {
 hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s) {
     F.clear();
     const int ns = (int)ctx->shapes.size();
+    // under the impedance condition the matrices are complex: each is factored as its real
+    // equivalent (order 2m, half-bandwidth 2·kl+1), which the same kernels handle
+    const bool re2 = ctx->bc != 0;
     std::vector<int> m(ns), kl(ns), ku(ns);
     for (int q = 0; q < ns; q++) {
         int nx = ctx->shapes[q].first, ny = ctx->shapes[q].second;
         if (coarse) { m[q] = (nx / 2) * (ny / 2); kl[q] = ku[q] = 2 * (nx / 2) + 2; }
         else { m[q] = nx * ny; kl[q] = ku[q] = nx + 1; }
+        if (re2) { m[q] *= 2; kl[q] = ku[q] = 2 * kl[q] + 1; }
     }
     std::vector<DevMem> ab(ns), piv(ns);
     std::vector<double *> abp(ns);
@@ -244,7 +253,10 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
         abp[q] = ab[q].as<double>();
         pivp[q] = piv[q].as<int>();
         int nx = ctx->shapes[q].first, ny = ctx->shapes[q].second;
-        if (coarse) launch_assemble_E(ctx->st, nx, ny, kl[q], ku[q], abp[q], s);
+        const int gx0 = ctx->shape_org[q].first, gy0 = ctx->shape_org[q].second;
+        if (re2 && coarse) launch_assemble_E_re2(ctx->st, nx, ny, gx0, gy0, kl[q], ku[q], abp[q], s);
+        else if (re2) launch_assemble_Aloc_re2(ctx->st, nx, ny, gx0, gy0, kl[q], ku[q], abp[q], s);
+        else if (coarse) launch_assemble_E(ctx->st, nx, ny, kl[q], ku[q], abp[q], s);
         else launch_assemble_Aloc(ctx->st, nx, ny, kl[q], ku[q], abp[q], s);
         CKL();
     }
@@ -345,6 +357,7 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
     if (F.cfg.cwx == 0) F.cfg.cwx = BNB;
     if (set_block_solve_smem(F.cfg) != cudaSuccess)
         FAIL(HDD_ERR_INVALID_ARG, "factor panels of width %d exceed the shared-memory solve", F.cfg.maxK);
+    F.re2 = re2;
     F.ready = true;
     return HDD_OK;
 }
@@ -355,10 +368,11 @@ void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *ou
     const int nt = (int)ctx->h_tasks.size();
     double fl = 0;
     for (int q = 0; q < nt; q++) fl += F.fma_col[ctx->h_tasks[q].shape];
-    fl = 4.0 * fl * (nact < 0 ? 1.0 : (double)nact / nt);      // 2 columns x 2 flops per FMA
-    Launch L(ctx, F_COARSE, fl * 2.0, fl, s);
+    // 2 flops per FMA, over 2 real columns (or the one column of a real-equivalent factor)
+    fl = (F.re2 ? 2.0 : 4.0) * fl * (nact < 0 ? 1.0 : (double)nact / nt);
+    Launch L(ctx, F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
     launch_block_solve(ctx->d_tasks.as<Task>(), nt, F.table.as<BlockFactor>(), F.M.as<double>(),
-                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, F.cfg, s);
+                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, F.cfg, F.re2 ? 1 : 0, s);
 }
 
 // ---- learned warm start ---------------------------------------------------------------------
@@ -739,6 +753,71 @@ hdd_status ras_apply(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     return inner_ras<double>(ctx, v, z, prm, s, tot, mx, hits, its_out, mask);
 }
 
+// Rows of A = K - k²M - ik B and of M at a node of each class (node_class) of the impedance
+// problem, in the slots of stencil_offset.  Every triangle of the mesh is right-angled with legs
+// h, so its element matrices are: stiffness 1 at the right-angle vertex, 1/2 at the other two,
+// -1/2 along a leg, 0 along the hypotenuse; mass h²/12 on the diagonal and h²/24 off it.  A row
+// sums the triangles around the node that lie in the square; each boundary edge at the node
+// (1D P1 mass of length h) adds h/3 to the centre and h/6 to the neighbour along it.
+void boundary_rows(int N, double k, int diag, double2 *bcoef, double *bmass) {
+    const double h = 1.0 / N;
+    for (int cls = 0; cls < 9; cls++) {
+        const int cx = cls % 3, cy = cls / 3;
+        const int px = cx == 0 ? 0 : (cx == 2 ? N : 1), py = cy == 0 ? 0 : (cy == 2 ? N : 1);
+        double K[7] = {}, M[7] = {}, B[7] = {};
+        for (int cj = py - 1; cj <= py; cj++)
+            for (int ci = px - 1; ci <= px; ci++) {
+                if (ci < 0 || ci >= N || cj < 0 || cj >= N) continue;
+                // the two triangles of cell (ci, cj) and their right-angle vertices
+                int tri[2][3][2], ra[2];
+                if (diag == 0) {
+                    const int t[2][3][2] = {{{ci, cj}, {ci + 1, cj}, {ci + 1, cj + 1}},
+                                            {{ci, cj}, {ci + 1, cj + 1}, {ci, cj + 1}}};
+                    std::memcpy(tri, t, sizeof(t));
+                    ra[0] = 1; ra[1] = 2;
+                } else {
+                    const int t[2][3][2] = {{{ci, cj}, {ci + 1, cj}, {ci, cj + 1}},
+                                            {{ci + 1, cj}, {ci + 1, cj + 1}, {ci, cj + 1}}};
+                    std::memcpy(tri, t, sizeof(t));
+                    ra[0] = 0; ra[1] = 1;
+                }
+                for (int t = 0; t < 2; t++) {
+                    int me = -1;
+                    for (int v = 0; v < 3; v++)
+                        if (tri[t][v][0] == px && tri[t][v][1] == py) me = v;
+                    if (me < 0) continue;
+                    for (int v = 0; v < 3; v++) {
+                        const int dx = tri[t][v][0] - px, dy = tri[t][v][1] - py;
+                        const int q = stencil_slot(diag, dx, dy);   // a triangle's vertices are stencil neighbours
+                        if (q < 0) continue;
+                        if (v == me) {
+                            K[q] += (v == ra[t]) ? 1.0 : 0.5;
+                            M[q] += h * h / 12.0;
+                        } else {
+                            K[q] += (dx == 0 || dy == 0) ? -0.5 : 0.0;
+                            M[q] += h * h / 24.0;
+                        }
+                    }
+                }
+            }
+        for (int q = 1; q <= 4; q++) {          // E, W, N, S
+            int dx, dy;
+            stencil_offset(diag, q, dx, dy);
+            const int qx = px + dx, qy = py + dy;
+            if (qx < 0 || qx > N || qy < 0 || qy > N) continue;
+            const bool on_side = (py == 0 && qy == 0) || (py == N && qy == N) || (px == 0 && qx == 0) ||
+                                 (px == N && qx == N);
+            if (!on_side) continue;
+            B[0] += h / 3.0;
+            B[q] += h / 6.0;
+        }
+        for (int q = 0; q < 7; q++) {
+            bcoef[cls * 7 + q] = make_double2(K[q] - k * k * M[q], -k * B[q]);
+            bmass[cls * 7 + q] = M[q];
+        }
+    }
+}
+
 hdd_status check_solve_params(hdd_ctx *ctx, const hdd_solve_params *p) {
     if (!p) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
     if (!(p->outer_tol > 0) || p->outer_maxit < 1 || p->outer_restart < 1)
@@ -911,9 +990,10 @@ hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *p) {
     if (p->N < 4 || p->N > 65536) FAIL(HDD_ERR_INVALID_ARG, "N must be in 4..65536");
     if (!std::isfinite(p->k) || p->k < 0) FAIL(HDD_ERR_INVALID_ARG, "k must be finite and >= 0");
     if (p->diag != 0 && p->diag != 1) FAIL(HDD_ERR_INVALID_ARG, "diag must be 0 or 1");
+    if (p->bc != 0 && p->bc != 1) FAIL(HDD_ERR_INVALID_ARG, "bc must be 0 (Dirichlet) or 1 (impedance)");
     CK(cudaSetDevice(ctx->device));
-    ctx->N = p->N; ctx->k = p->k; ctx->diag = p->diag; ctx->h = 1.0 / p->N;
-    ctx->nglob = (long long)(p->N - 1) * (p->N - 1);
+    ctx->N = p->N; ctx->k = p->k; ctx->diag = p->diag; ctx->h = 1.0 / p->N; ctx->bc = p->bc;
+    ctx->nglob = p->bc ? (long long)(p->N + 1) * (p->N + 1) : (long long)(p->N - 1) * (p->N - 1);
     const double kh2 = p->k * p->k * ctx->h * ctx->h;
     // element-by-element P1 assembly on the uniform mesh reduces to this 7-point stencil
     // (stiffness [4; -1 x4], consistent mass h²/12 [6; 1 x6]); see the header comment.
@@ -921,6 +1001,22 @@ hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *p) {
     ctx->st.c1 = -1.0 - kh2 / 12.0;
     ctx->st.c2 = -kh2 / 12.0;
     ctx->st.diag = p->diag;
+    ctx->st.bc = p->bc;
+    ctx->st.N = p->N;
+    ctx->st.bcoef = nullptr;
+    ctx->st.bmass = nullptr;
+    if (p->bc) {
+        double2 bco[63];
+        double bma[63];
+        boundary_rows(p->N, p->k, p->diag, bco, bma);
+        CK(ctx->d_bcoef.ensure(sizeof(bco)));
+        CK(ctx->d_bmass.ensure(sizeof(bma)));
+        CK(cudaMemcpy(ctx->d_bcoef.p, bco, sizeof(bco), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_bmass.p, bma, sizeof(bma), cudaMemcpyHostToDevice));
+        ctx->st.bcoef = ctx->d_bcoef.as<double2>();
+        ctx->st.bmass = ctx->d_bmass.as<double>();
+        ctx->cnn.ready = false;               // the warm start serves the Dirichlet problem only
+    }
     ctx->assembled = true;
     ctx->dd = false;
     ctx->E.clear(); ctx->Aex.clear();
@@ -940,7 +1036,7 @@ hdd_status hdd_build_rhs(hdd_ctx *ctx, int npoints, const double *points, int nb
     for (int q = 0; q < 4 * nbumps; q++) buf[3 * npoints + q] = bumps[q];
     CK(ctx->tmp_c.ensure(buf.size() * sizeof(double)));
     CK(cudaMemcpyAsync(ctx->tmp_c.p, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_build_rhs(ctx->N, ctx->h, ctx->diag, npoints, ctx->tmp_c.as<double>(), nbumps,
+    launch_build_rhs(ctx->st, ctx->N, ctx->h, npoints, ctx->tmp_c.as<double>(), nbumps,
                      ctx->tmp_c.as<double>() + 3 * npoints, (double2 *)f_dev, s);
     CKL();
     CK(cudaStreamSynchronize(s));
@@ -978,24 +1074,35 @@ hdd_status hdd_setup_dd(hdd_ctx *ctx, const hdd_dd_params *p) {
     if (!interfaces(p->Sx, p->ifx, ax) || !interfaces(p->Sy, p->ify, ay))
         FAIL(HDD_ERR_INVALID_ARG, "interfaces must run 0 = a_0 < ... < a_S = N with gaps >= 2");
     ctx->Sx = p->Sx; ctx->Sy = p->Sy; ctx->overlap = p->overlap;
-    ctx->subs.clear(); ctx->shapes.clear(); ctx->sub_shape.clear();
-    std::map<std::pair<int, int>, int> shape_id;
+    ctx->subs.clear(); ctx->shapes.clear(); ctx->sub_shape.clear(); ctx->shape_org.clear();
+    // boxes and factors share a shape when (nx, ny) agree and, under the impedance condition,
+    // the same sides of the box lie on the boundary of the square (those rows differ)
+    std::map<std::pair<std::pair<int, int>, int>, int> shape_id;
     const int d = p->overlap;
+    const int lo = ctx->bc ? 0 : 1, hi = ctx->bc ? N : N - 1;   // mesh range of the unknowns
     for (int qy = 0; qy < p->Sy; qy++)
         for (int qx = 0; qx < p->Sx; qx++) {
             SubBox b;
-            b.ix0 = std::max(1, ax[qx] - d + 1); b.ix1 = std::min(N - 1, ax[qx + 1] + d - 1);
-            b.iy0 = std::max(1, ay[qy] - d + 1); b.iy1 = std::min(N - 1, ay[qy + 1] + d - 1);
-            b.ox0 = std::max(1, ax[qx]); b.ox1 = ax[qx + 1] - 1;
-            b.oy0 = std::max(1, ay[qy]); b.oy1 = ay[qy + 1] - 1;
+            b.ix0 = std::max(lo, ax[qx] - d + 1); b.ix1 = std::min(hi, ax[qx + 1] + d - 1);
+            b.iy0 = std::max(lo, ay[qy] - d + 1); b.iy1 = std::min(hi, ay[qy + 1] + d - 1);
+            // owned a_p <= i < a_{p+1}; the last subdomain in each direction also owns hi
+            b.ox0 = std::max(lo, ax[qx]); b.ox1 = qx == p->Sx - 1 ? hi : ax[qx + 1] - 1;
+            b.oy0 = std::max(lo, ay[qy]); b.oy1 = qy == p->Sy - 1 ? hi : ay[qy + 1] - 1;
             b.nx = b.ix1 - b.ix0 + 1; b.ny = b.iy1 - b.iy0 + 1;
             b.mx = b.nx / 2; b.my = b.ny / 2;
             if (b.nx > 256) FAIL(HDD_ERR_INVALID_ARG, "subdomain box %d nodes wide exceeds 256", b.nx);
-            auto key = std::make_pair(b.nx, b.ny);
+            const int sides = ctx->bc ? (b.ix0 == 0) | (b.ix1 == N) << 1 | (b.iy0 == 0) << 2 | (b.iy1 == N) << 3 : 0;
+            auto key = std::make_pair(std::make_pair(b.nx, b.ny), sides);
             auto it = shape_id.find(key);
             int sid;
-            if (it == shape_id.end()) { sid = (int)ctx->shapes.size(); shape_id[key] = sid; ctx->shapes.push_back(key); }
-            else sid = it->second;
+            if (it == shape_id.end()) {
+                sid = (int)ctx->shapes.size();
+                shape_id[key] = sid;
+                ctx->shapes.push_back(key.first);
+                ctx->shape_org.push_back(std::make_pair(b.ix0, b.iy0));
+            } else {
+                sid = it->second;
+            }
             ctx->subs.push_back(b);
             ctx->sub_shape.push_back(sid);
         }
@@ -1373,6 +1480,7 @@ int hdd_cnn_num_params(void) { return CNN_NPARAM; }
 hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
+    if (ctx->bc) FAIL(HDD_ERR_INVALID_ARG, "the learned warm start serves the Dirichlet problem only");
     if (!params) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
     for (int i = 0; i < CNN_NPARAM; i++)
         if (!std::isfinite(params[i])) FAIL(HDD_ERR_NONFINITE, "parameter %d is not finite", i);
@@ -1548,7 +1656,7 @@ hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev,
     launch_zt<double>(a, in, y, 1, nullptr, s);                                        // y = Zᵀ A v
     launch_block_solve(ctx->d_tasks.as<Task>(), (int)ctx->h_tasks.size(), F.table.as<BlockFactor>(),
                        F.M.as<double>(), F.P.as<int>(), F.Meta.as<int4>(), y, sc, 0, nullptr,
-                       F.cfg, s);                                                       // s = E⁻¹ y
+                       F.cfg, F.re2 ? 1 : 0, s);                                        // s = E⁻¹ y
     launch_prolong_stencil<double>(a, 0, in, sc, out, nullptr, 0, scratch, nullptr, s); // A(v - Z s)
     ctx->prof.launches += 3;
     CKL();

@@ -58,11 +58,43 @@ struct Stencil {           // P1 operator K - k²M on the uniform mesh (Eq. 2), 
     double c1;             // E, W, N, S
     double c2;             // the two corners joined by the cell diagonals
     int diag;              // 0: diagonal pair (+1,+1)/(-1,-1); 1: (+1,-1)/(-1,+1)
+    // bc = 1: impedance (first-order absorbing) condition du/dn - iku = 0 on all four sides.
+    // Every mesh node 0..N is then an unknown and A = K - k²M - ik B (B: boundary mass); the
+    // rows of nodes on the boundary differ from c0..c2 and are read, per node class
+    // (node_class), from bcoef[cls·7 + slot] (complex A) and bmass[cls·7 + slot] (real M), with
+    // the slots of stencil_slot.  Interior rows keep c0..c2.
+    int bc = 0;
+    int N = 0;                       // intervals per side
+    const double2 *bcoef = nullptr;  // device table, 9 classes x 7 slots
+    const double *bmass = nullptr;   // device table, 9 classes x 7 slots
 };
+
+// Class of mesh node (gx, gy): cx + 3·cy with cx = 0 on x = 0, 2 on x = N, 1 otherwise (cy the
+// same in y); 4 is the interior class.
+__host__ __device__ __forceinline__ int node_class(int N, int gx, int gy) {
+    return (gx == 0 ? 0 : (gx == N ? 2 : 1)) + 3 * (gy == 0 ? 0 : (gy == N ? 2 : 1));
+}
+// Stencil slots: 0 centre, 1 E (+1,0), 2 W (-1,0), 3 N (0,+1), 4 S (0,-1), 5 and 6 the corners
+// joined by the cell diagonals: (+1,+1), (-1,-1) for diag 0; (+1,-1), (-1,+1) for diag 1.
+__host__ __device__ __forceinline__ void stencil_offset(int diag, int q, int &dx, int &dy) {
+    const int ox[7] = {0, 1, -1, 0, 0, 1, -1};
+    const int oy0[7] = {0, 0, 0, 1, -1, 1, -1}, oy1[7] = {0, 0, 0, 1, -1, -1, 1};
+    dx = ox[q];
+    dy = diag == 0 ? oy0[q] : oy1[q];
+}
+// slot of offset (dx, dy), -1 if it is not a stencil neighbour
+__host__ __device__ __forceinline__ int stencil_slot(int diag, int dx, int dy) {
+    for (int q = 0; q < 7; q++) {
+        int ax, ay;
+        stencil_offset(diag, q, ax, ay);
+        if (ax == dx && ay == dy) return q;
+    }
+    return -1;
+}
 
 struct Task {              // one local solve: subdomain `sub` for right-hand side `rhs`
     int nx, ny, mx, my;    // box and coarse sizes
-    int ix0, iy0;          // global node (1-based) of the box's local (0,0)
+    int ix0, iy0;          // mesh node (i, j) of the box's local (0,0): >= 1 (Dirichlet), >= 0 (impedance)
     int ox0, ox1, oy0, oy1;// owned nodes (global, inclusive)
     int shape;             // index of the shared factor of E (and of A_j)
     int sub, rhs;
@@ -115,7 +147,8 @@ template <typename R> struct LocalArgs {
     long long ld;      // packed fine length (all tasks): stride between basis vectors
     long long ldc;     // packed coarse length
     int max_nx;        // largest box width (shared-memory sizing), <= 256
-    int gw;            // global grid width N-1
+    int gw;            // global grid width: N-1 (Dirichlet) or N+1 (impedance)
+    int glo;           // mesh index of the first global unknown in x and y: 1 or 0
     int frows, crows;  // largest fine / coarse tile height (shared-memory sizing)
 };
 
@@ -163,6 +196,13 @@ constexpr int LOCAL_LDP = MAX_RESTART + 2;   // partial-sum slots per fine tile
 // coarse / banded FP64
 void launch_assemble_E(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s);
 void launch_assemble_Aloc(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s);
+// complex E (resp. A_j) of a box with origin (gx0, gy0) under the impedance condition, written as
+// its real equivalent: unknowns (Re x_0, Im x_0, Re x_1, ...), i.e. the complex vector read as
+// doubles; order 2m, half-bandwidths kl2 = ku2 = 2·kl + 1 of the complex band kl
+void launch_assemble_E_re2(const Stencil &st, int nx, int ny, int gx0, int gy0, int kl2, int ku2, double *ab,
+                           cudaStream_t s);
+void launch_assemble_Aloc_re2(const Stencil &st, int nx, int ny, int gx0, int gy0, int kl2, int ku2, double *ab,
+                              cudaStream_t s);
 void launch_band_lu(int nmat, const int *m, const int *kl, const int *ku, double *const *ab,
                     int *const *piv, int *info, cudaStream_t s);
 void launch_factor_prepare(int m, int kl, int ku, const double *ab, const int *piv, int KLW,
@@ -174,9 +214,11 @@ struct BlockSolveCfg {       // shared-memory plan of the blocked solve over a s
     int cwy = 0, cwx = 0;  // circular y / x windows, powers of two >= BNB + widest left / right panel
     int ring = 0;          // operator ring depth (4 or 2), chosen by set_block_solve_smem
 };
+// re2 = 0: real factors, Re and Im of the complex vector solved as two columns; re2 = 1: factors
+// of real-equivalent systems (order 2m), the complex vector read as one real column
 void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
                         const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
-                        int use_fine, const int *flag, const BlockSolveCfg &cfg, cudaStream_t s);
+                        int use_fine, const int *flag, const BlockSolveCfg &cfg, int re2, cudaStream_t s);
 cudaError_t set_block_solve_smem(BlockSolveCfg &cfg);
 
 // learned warm start (kernels_cnn.cu)
@@ -225,7 +267,7 @@ struct OuterBatch {
 int outer_grid(long long n);
 void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f, int nrhs,
                      const int *active, cudaStream_t s);
-void launch_build_rhs(int N, double h, int diag, int npts, const double *pts, int nb,
+void launch_build_rhs(const Stencil &st, int N, double h, int npts, const double *pts, int nb,
                       const double *bumps, double2 *f, cudaStream_t s);
 void launch_odots(const OuterBatch &B, const double2 *V, int nv, const double2 *w, double2 *part,
                   cudaStream_t s);

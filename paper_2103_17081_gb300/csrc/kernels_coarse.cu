@@ -2,6 +2,8 @@
 // E = Zᵀ A Z on the device, banded LU with partial pivoting, and the batched banded solve
 // E⁻¹ y for every task (real factor, real and imaginary parts as two chains).
 // The same factor/solve serves the direct local solve A_j⁻¹ (§3.1 benchmark).
+#include <algorithm>
+
 #include "hdd_common.cuh"
 
 namespace hdd {
@@ -72,6 +74,80 @@ __global__ void k_assemble_Aloc(Stencil st, int nx, int ny, int kl, int ku, doub
     if (a == 0.0) return;
     const int c = gx + gy * nx;
     ab[(long long)r * W + (c - r + kl)] = a;
+}
+
+// Coefficient of A coupling mesh node (gx, gy) to (gx+dx, gy+dy): the interior stencil, or under
+// the impedance condition the complex row of a boundary node's class.
+__device__ __forceinline__ double2 acoef_z(const Stencil &st, int gx, int gy, int dx, int dy) {
+    const int cls = st.bc ? node_class(st.N, gx, gy) : 4;
+    if (cls == 4) return make_double2(acoef(st, dx, dy), 0.0);
+    const int q = stencil_slot(st.diag, dx, dy);
+    return q < 0 ? make_double2(0.0, 0.0) : st.bcoef[cls * 7 + q];
+}
+
+// Complex value v at (row r, column c) of a complex band matrix, written as its real equivalent:
+// rows/columns 2r, 2r+1 (2c, 2c+1) carry the real and imaginary parts, block [Re v, -Im v;
+// Im v, Re v], in row-band storage of half-bandwidth kl2 and row width W.
+__device__ __forceinline__ void put_re2(double *ab, int W, int kl2, long long r, long long c, double2 v) {
+    const long long r0 = 2 * r, r1 = r0 + 1, c0 = 2 * c, c1 = c0 + 1;
+    ab[r0 * W + (c0 - r0 + kl2)] = v.x;
+    ab[r0 * W + (c1 - r0 + kl2)] = -v.y;
+    ab[r1 * W + (c0 - r1 + kl2)] = v.y;
+    ab[r1 * W + (c1 - r1 + kl2)] = v.x;
+}
+
+// E = Zᵀ A Z of the box nx x ny with origin (gx0, gy0) (impedance condition: complex), as its
+// real equivalent of order 2m with kl2 = ku2 = 2·(2mx+2)+1; entries outside the 5x5 coarse
+// neighbourhood are zero and were cleared by the caller.
+__global__ void k_assemble_E_re2(Stencil st, int nx, int ny, int gx0, int gy0, int kl2, int ku2,
+                                 double *__restrict__ ab) {
+    const int mx = nx / 2, my = ny / 2, m = mx * my;
+    const int W = 2 * kl2 + ku2 + 1;
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)m * 25) return;
+    const int c = (int)(idx / 25), d = (int)(idx % 25);
+    const int cx = c % mx, cy = c / mx;
+    const int ex = cx + d % 5 - 2, ey = cy + d / 5 - 2;
+    if (ex < 0 || ex >= mx || ey < 0 || ey >= my) return;
+    double ar = 0.0, ai = 0.0;
+    for (int fy = 2 * cy - 1; fy <= 2 * cy + 3; fy++) {
+        if (fy < 0 || fy >= ny) continue;
+        const double wy = z1(fy, cy);
+        for (int fx = 2 * cx - 1; fx <= 2 * cx + 3; fx++) {
+            if (fx < 0 || fx >= nx) continue;
+            const double wf = wy * z1(fx, cx);
+            double ir = 0.0, ii = 0.0;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int gx = fx + dx, gy = fy + dy;
+                    if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
+                    const double2 a = acoef_z(st, gx0 + fx, gy0 + fy, dx, dy);
+                    if (a.x == 0.0 && a.y == 0.0) continue;
+                    const double z = z1(gx, ex) * z1(gy, ey);
+                    ir += a.x * z;
+                    ii += a.y * z;
+                }
+            ar += wf * ir;
+            ai += wf * ii;
+        }
+    }
+    put_re2(ab, W, kl2, c, ex + ey * mx, make_double2(ar, ai));
+}
+
+// A_j of the box with origin (gx0, gy0) (impedance condition) as its real equivalent of order
+// 2n, kl2 = ku2 = 2·(nx+1)+1.
+__global__ void k_assemble_Aloc_re2(Stencil st, int nx, int ny, int gx0, int gy0, int kl2, int ku2,
+                                    double *__restrict__ ab) {
+    const int n = nx * ny, W = 2 * kl2 + ku2 + 1;
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * 9) return;
+    const int r = (int)(idx / 9), d = (int)(idx % 9);
+    const int x = r % nx, y = r / nx, dx = d % 3 - 1, dy = d / 3 - 1;
+    const int gx = x + dx, gy = y + dy;
+    if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) return;
+    const double2 a = acoef_z(st, gx0 + x, gy0 + y, dx, dy);
+    if (a.x == 0.0 && a.y == 0.0) return;
+    put_re2(ab, W, kl2, r, gx + gy * nx, a);
 }
 
 // Banded LU with partial pivoting of one matrix per CTA (row-band storage, in place).  The
@@ -337,14 +413,15 @@ __device__ __forceinline__ void cp_async8_zfill(void *smem_dst, const void *gsrc
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_size) : "memory");
 }
 
-// x = F⁻¹ b with the blocked operators, one CTA per (task, component).  Shared memory holds only
+// x = F⁻¹ b with the blocked operators, one CTA per (task, component); with RE2 the factor is that
+// of a real-equivalent system and one CTA per task solves the complex vector read as doubles.  Shared memory holds only
 // a ring of RING slots — the operator of one block plus that block's BNB input values, streamed
 // by cp.async RING-1 blocks ahead of the block being applied — and two circular windows (cwy,
 // cwx entries, powers of two >= BNB + panel width) of the latest y and x values; so the order of
 // the factor is not limited by shared memory.  The output vector carries the rest: it first
 // receives P b (gathered), the forward sweep overwrites block J with y_J after reading it, and the
 // backward sweep overwrites block J with x_J after reading y_J.  One barrier per block.
-template <int RING>
+template <int RING, bool RE2>
 __global__ void __launch_bounds__(BS_T, 2)
 k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ shapes,
               const double *__restrict__ Mall, const int *__restrict__ Pall,
@@ -352,7 +429,8 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
               double2 *__restrict__ out, int use_fine, const int *__restrict__ flag, int maxK,
               int cwy, int cwx) {
     extern __shared__ double sm[];
-    const int t = blockIdx.x >> 1, comp = blockIdx.x & 1;
+    constexpr int STR = RE2 ? 1 : 2;        // stride (doubles) of the solved real column
+    const int t = RE2 ? (int)blockIdx.x : (int)(blockIdx.x >> 1), comp = RE2 ? 0 : (int)(blockIdx.x & 1);
     if (flag && !flag[t]) return;
     const Task T = tasks[t];
     const BlockFactor F = shapes[T.shape];
@@ -373,11 +451,11 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
         for (int q = tid; q < nchunk; q += BS_T) cp_async16(dst + 2 * q, src + 2 * q);
         if (tid < BNB) {
             const int i = J * BNB + tid;
-            cp_async8_zfill(dst + BNB * maxK + tid, i < m ? outr + 2 * (long long)i : outr, i < m ? 8 : 0);
+            cp_async8_zfill(dst + BNB * maxK + tid, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
         }
     };
     // (P b) into the output; zero windows (positions before 0 / after the end read zeros)
-    for (int i = tid; i < m; i += BS_T) outr[2 * (long long)i] = inr[2 * (long long)perm[i]];
+    for (int i = tid; i < m; i += BS_T) outr[STR * (long long)i] = inr[STR * (long long)perm[i]];
     for (int i = tid; i < cwy; i += BS_T) CY[i] = 0.0;
     for (int i = tid; i < cwx; i += BS_T) CX[i] = 0.0;
     __threadfence_block();
@@ -414,7 +492,7 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
         if (part == 0) {
             const int i = J * BNB + row;
             CY[i & (cwy - 1)] = v;
-            if (i < m) outr[2 * (long long)i] = v;
+            if (i < m) outr[STR * (long long)i] = v;
         }
     }
     cp_async_wait_n<0>();
@@ -450,7 +528,7 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
         if (part == 0) {
             const int i = J * BNB + row;
             CX[i & (cwx - 1)] = v;
-            if (i < m) outr[2 * (long long)i] = v;
+            if (i < m) outr[STR * (long long)i] = v;
         }
     }
     cp_async_wait_n<0>();
@@ -463,6 +541,16 @@ void launch_assemble_E(const Stencil &st, int nx, int ny, int kl, int ku, double
 void launch_assemble_Aloc(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s) {
     long long tot = (long long)nx * ny * 9;
     k_assemble_Aloc<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(st, nx, ny, kl, ku, ab);
+}
+void launch_assemble_E_re2(const Stencil &st, int nx, int ny, int gx0, int gy0, int kl2, int ku2, double *ab,
+                           cudaStream_t s) {
+    long long tot = (long long)(nx / 2) * (ny / 2) * 25;
+    k_assemble_E_re2<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(st, nx, ny, gx0, gy0, kl2, ku2, ab);
+}
+void launch_assemble_Aloc_re2(const Stencil &st, int nx, int ny, int gx0, int gy0, int kl2, int ku2, double *ab,
+                              cudaStream_t s) {
+    long long tot = (long long)nx * ny * 9;
+    k_assemble_Aloc_re2<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(st, nx, ny, gx0, gy0, kl2, ku2, ab);
 }
 void launch_band_lu(int nmat, const int *m, const int *kl, const int *ku, double *const *ab,
                     int *const *piv, int *info, cudaStream_t s) {
@@ -485,29 +573,45 @@ static size_t bs_smem(const BlockSolveCfg &c, int ring) {
 }
 void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
                         const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
-                        int use_fine, const int *flag, const BlockSolveCfg &c, cudaStream_t s) {
+                        int use_fine, const int *flag, const BlockSolveCfg &c, int re2, cudaStream_t s) {
+    if (re2) {
+        if (c.ring == 4)
+            k_block_solve<4, true><<<ntasks, BS_T, bs_smem(c, 4), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
+                                                                       use_fine, flag, c.maxK, c.cwy, c.cwx);
+        else
+            k_block_solve<2, true><<<ntasks, BS_T, bs_smem(c, 2), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
+                                                                       use_fine, flag, c.maxK, c.cwy, c.cwx);
+        return;
+    }
     if (c.ring == 4)
-        k_block_solve<4><<<2 * ntasks, BS_T, bs_smem(c, 4), s>>>(tasks, shapes, Mall, Pall, Meta, in, out, use_fine,
-                                                                 flag, c.maxK, c.cwy, c.cwx);
+        k_block_solve<4, false><<<2 * ntasks, BS_T, bs_smem(c, 4), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
+                                                                        use_fine, flag, c.maxK, c.cwy, c.cwx);
     else
-        k_block_solve<2><<<2 * ntasks, BS_T, bs_smem(c, 2), s>>>(tasks, shapes, Mall, Pall, Meta, in, out, use_fine,
-                                                                 flag, c.maxK, c.cwy, c.cwx);
+        k_block_solve<2, false><<<2 * ntasks, BS_T, bs_smem(c, 2), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
+                                                                        use_fine, flag, c.maxK, c.cwy, c.cwx);
 }
 // Ring depth 4 if its shared memory fits the per-CTA limit, else 2; error if not even that fits.
 // The kernels' attribute is raised to the limit itself (several factor sets with different plans
 // share the kernels; each launch requests only what its plan needs).
 cudaError_t set_block_solve_smem(BlockSolveCfg &c) {
-    cudaFuncAttributes a4, a2;
-    cudaError_t e = cudaFuncGetAttributes(&a4, k_block_solve<4>);
+    cudaFuncAttributes a4, a2, b4, b2;
+    cudaError_t e = cudaFuncGetAttributes(&a4, k_block_solve<4, false>);
     if (e != cudaSuccess) return e;
-    if ((e = cudaFuncGetAttributes(&a2, k_block_solve<2>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&a2, k_block_solve<2, false>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&b4, k_block_solve<4, true>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&b2, k_block_solve<2, true>)) != cudaSuccess) return e;
     const size_t lim = 227 * 1024;                        // per-CTA limit, static + dynamic
-    const size_t lim4 = lim - a4.sharedSizeBytes, lim2 = lim - a2.sharedSizeBytes;
+    const size_t lim4 = lim - std::max(a4.sharedSizeBytes, b4.sharedSizeBytes);
+    const size_t lim2 = lim - std::max(a2.sharedSizeBytes, b2.sharedSizeBytes);
     c.ring = bs_smem(c, 4) <= lim4 ? 4 : 2;
     if (bs_smem(c, c.ring) > (c.ring == 4 ? lim4 : lim2)) return cudaErrorInvalidValue;
-    if ((e = cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim4)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_block_solve<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim4)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_block_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim2);
+    if ((e = cudaFuncSetAttribute(k_block_solve<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim2)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_block_solve<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim4)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_block_solve<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim2);
 }
 
 }  // namespace hdd

@@ -23,11 +23,28 @@ template <typename R> __device__ __forceinline__ R zw(int t) { return (R)zw_f(t)
 
 template <typename R> __device__ __forceinline__ c2<R> load_c(const c2<R> *p) { return *p; }
 
+// Row of a boundary node (impedance condition): Σ_q cf[q] v_q over the 7 stencil slots.
+template <typename R>
+__device__ __forceinline__ c2<R> boundary_row(const double2 *__restrict__ cf, c2<R> v0, c2<R> v1, c2<R> v2,
+                                           c2<R> v3, c2<R> v4, c2<R> v5, c2<R> v6) {
+    const c2<R> v[7] = {v0, v1, v2, v3, v4, v5, v6};
+    c2<R> r = mk<R>(0, 0);
+#pragma unroll
+    for (int q = 0; q < 7; q++) {
+        const double2 a = cf[q];
+        r = cadd<R>(r, cmul<R>(mk<R>((R)a.x, (R)a.y), v[q]));
+    }
+    return r;
+}
+
 // w = A u at local (x, y) from a shared-memory row buffer u[rows][nx] whose row 0 is box row
 // `ybase`; rows outside [0, ny) and columns outside [0, nx) are zero (Dirichlet around the box).
-template <typename R>
+// (gx0, gy0): mesh node of the box's local (0, 0); under the impedance condition the rows of
+// nodes on the boundary of the square take their class's complex coefficients.
+// IMP: compiled for the impedance condition (the Dirichlet instantiation carries no boundary code).
+template <typename R, bool IMP>
 __device__ __forceinline__ c2<R> stencil_smem(const Stencil &st, const c2<R> *u, int ybase,
-                                              int nrows, int nx, int ny, int x, int y) {
+                                              int nrows, int nx, int ny, int x, int y, int gx0, int gy0) {
     const R c0 = (R)st.c0, c1 = (R)st.c1, c2v = (R)st.c2;
     auto U = [&](int xx, int yy) -> c2<R> {
         if (xx < 0 || xx >= nx || yy < 0 || yy >= ny) return mk<R>(0, 0);
@@ -41,6 +58,10 @@ __device__ __forceinline__ c2<R> stencil_smem(const Stencil &st, const c2<R> *u,
     if (st.diag == 0) { d1 = U(x + 1, y + 1); d2 = U(x - 1, y - 1); }
     else { d1 = U(x + 1, y - 1); d2 = U(x - 1, y + 1); }
     c2<R> r;
+    if (IMP) {
+        const int cls = node_class(st.N, gx0 + x, gy0 + y);
+        if (cls != 4) return boundary_row<R>(st.bcoef + cls * 7, cc, e, wv, n, s, d1, d2);
+    }
     r.x = c0 * cc.x + c1 * (((e.x + wv.x) + n.x) + s.x) + c2v * (d1.x + d2.x);
     r.y = c0 * cc.y + c1 * (((e.y + wv.y) + n.y) + s.y) + c2v * (d1.y + d2.y);
     return r;
@@ -90,7 +111,7 @@ k_restrict(LocalArgs<R> a, int gw, long long nglob, const double2 *__restrict__ 
     const int cnt = tl.nr * T.nx;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         int y = tl.r0 + e / T.nx, x = e % T.nx;
-        long long gi = (long long)(T.ix0 + x - 1) + (long long)(T.iy0 + y - 1) * gw +
+        long long gi = (long long)(T.ix0 + x - a.glo) + (long long)(T.iy0 + y - a.glo) * gw +
                        (long long)T.rhs * nglob;
         double2 v = glob[gi];
         out[T.foff + (long long)y * T.nx + x] = mk<R>((R)v.x, (R)v.y);
@@ -111,13 +132,13 @@ k_scatter(LocalArgs<R> a, int gw, long long nglob, const c2<R> *__restrict__ x,
         int gx = T.ix0 + xx, gy = T.iy0 + y;
         if (gx < T.ox0 || gx > T.ox1 || gy < T.oy0 || gy > T.oy1) continue;
         c2<R> v = x[T.foff + (long long)y * T.nx + xx];
-        glob[(long long)(gx - 1) + (long long)(gy - 1) * gw + (long long)T.rhs * nglob] =
+        glob[(long long)(gx - a.glo) + (long long)(gy - a.glo) * gw + (long long)T.rhs * nglob] =
             make_double2((double)v.x, (double)v.y);
     }
 }
 
 // out = A_j in   or   out = f - A_j in   (fine tiles, neighbours read through L1)
-template <typename R>
+template <typename R, bool IMP>
 __global__ void __launch_bounds__(LOCAL_THREADS)
 k_local_A(LocalArgs<R> a, const c2<R> *__restrict__ in, c2<R> *__restrict__ out,
           const c2<R> *__restrict__ f, const int *__restrict__ flag) {
@@ -134,7 +155,7 @@ k_local_A(LocalArgs<R> a, const c2<R> *__restrict__ in, c2<R> *__restrict__ out,
     __syncthreads();
     for (int e = threadIdx.x; e < tl.nr * T.nx; e += blockDim.x) {
         int y = tl.r0 + e / T.nx, x = e % T.nx;
-        c2<R> w = stencil_smem<R>(a.st, u, y0, nrows, T.nx, T.ny, x, y);
+        c2<R> w = stencil_smem<R, IMP>(a.st, u, y0, nrows, T.nx, T.ny, x, y, T.ix0, T.iy0);
         long long gi = T.foff + (long long)y * T.nx + x;
         if (f) w = csub<R>(f[gi], w);
         out[gi] = w;
@@ -142,7 +163,7 @@ k_local_A(LocalArgs<R> a, const c2<R> *__restrict__ in, c2<R> *__restrict__ out,
 }
 
 // y = Z_jᵀ t (coarse tiles), with t = A_j in (apply_A) or t = in; y in FP64.
-template <typename R>
+template <typename R, bool IMP>
 __global__ void __launch_bounds__(LOCAL_THREADS)
 k_zt(LocalArgs<R> a, const c2<R> *__restrict__ in, double2 *__restrict__ yout, int apply_A,
      const int *__restrict__ flag) {
@@ -166,7 +187,7 @@ k_zt(LocalArgs<R> a, const c2<R> *__restrict__ in, double2 *__restrict__ yout, i
         __syncthreads();
         for (int e = threadIdx.x; e < nF * nx; e += blockDim.x) {
             int yy = F0 + e / nx, xx = e % nx;
-            t[e] = (yy >= 0 && yy < ny) ? stencil_smem<R>(a.st, vin, V0, nV, nx, ny, xx, yy)
+            t[e] = (yy >= 0 && yy < ny) ? stencil_smem<R, IMP>(a.st, vin, V0, nV, nx, ny, xx, yy, T.ix0, T.iy0)
                                         : mk<R>(0, 0);
         }
     } else {
@@ -285,7 +306,7 @@ k_z(LocalArgs<R> a, const double2 *__restrict__ s, const c2<R> *__restrict__ add
 
 // Arnoldi (mode 0): out = A (in - Z s), partial dots V_l^H out (l < nv);
 // residual (mode 1): out = in - A (Z s), partial ||out||².
-template <typename R>
+template <typename R, bool IMP>
 __global__ void __launch_bounds__(LOCAL_THREADS)
 k_prolong_stencil(LocalArgs<R> a, int mode, const c2<R> *__restrict__ in,
                   const double2 *__restrict__ s, c2<R> *__restrict__ out,
@@ -319,7 +340,7 @@ k_prolong_stencil(LocalArgs<R> a, int mode, const c2<R> *__restrict__ in,
         wv[k] = mk<R>(0, 0);
         if (e < cnt) {
             int y = tl.r0 + e / nx, x = e % nx;
-            c2<R> w = stencil_smem<R>(a.st, u, F0, nF, nx, ny, x, y);
+            c2<R> w = stencil_smem<R, IMP>(a.st, u, F0, nF, nx, ny, x, y, T.ix0, T.iy0);
             long long gi = T.foff + (long long)y * nx + x;
             if (mode == 1) w = csub<R>(in[gi], w);
             out[gi] = w;
@@ -654,7 +675,8 @@ template <typename R>
 void launch_local_A(const LocalArgs<R> &a, const c2<R> *in, c2<R> *out, const c2<R> *f,
                     const int *flag, cudaStream_t s) {
     size_t sm = (size_t)(a.frows + 2) * a.max_nx * csz<R>();
-    k_local_A<R><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, in, out, f, flag);
+    if (a.st.bc) k_local_A<R, true><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, in, out, f, flag);
+    else k_local_A<R, false><<<a.nftiles, LOCAL_THREADS, sm, s>>>(a, in, out, f, flag);
 }
 template <typename R>
 size_t zt_smem(const LocalArgs<R> &a, int apply_A) {
@@ -664,7 +686,8 @@ size_t zt_smem(const LocalArgs<R> &a, int apply_A) {
 template <typename R>
 void launch_zt(const LocalArgs<R> &a, const c2<R> *in, double2 *y, int apply_A, const int *flag,
                cudaStream_t s) {
-    k_zt<R><<<a.nctiles, LOCAL_THREADS, zt_smem(a, apply_A), s>>>(a, in, y, apply_A, flag);
+    if (a.st.bc) k_zt<R, true><<<a.nctiles, LOCAL_THREADS, zt_smem(a, apply_A), s>>>(a, in, y, apply_A, flag);
+    else k_zt<R, false><<<a.nctiles, LOCAL_THREADS, zt_smem(a, apply_A), s>>>(a, in, y, apply_A, flag);
 }
 template <typename R>
 void launch_z(const LocalArgs<R> &a, const double2 *sc, const c2<R> *add, c2<R> *out,
@@ -683,8 +706,12 @@ template <typename R>
 void launch_prolong_stencil(const LocalArgs<R> &a, int mode, const c2<R> *in, const double2 *sc,
                             c2<R> *out, const c2<R> *V, int nv, c2<R> *part, const int *flag,
                             cudaStream_t s) {
-    k_prolong_stencil<R><<<a.nftiles, LOCAL_THREADS, ps_smem(a), s>>>(a, mode, in, sc, out, V, nv,
-                                                                       part, flag);
+    if (a.st.bc)
+        k_prolong_stencil<R, true><<<a.nftiles, LOCAL_THREADS, ps_smem(a), s>>>(a, mode, in, sc, out, V, nv,
+                                                                                part, flag);
+    else
+        k_prolong_stencil<R, false><<<a.nftiles, LOCAL_THREADS, ps_smem(a), s>>>(a, mode, in, sc, out, V, nv,
+                                                                                 part, flag);
 }
 template <typename R>
 void launch_cgs_update(const LocalArgs<R> &a, int pass, c2<R> *w, const c2<R> *V, int nv,
@@ -748,10 +775,13 @@ size_t local_max_dynamic_smem(int max_nx, int bytes_per_c, int frows, int crows)
 
 template <typename R> cudaError_t set_local_smem_limits(size_t bytes) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_prolong_stencil<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_zt<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_prolong_stencil<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_prolong_stencil<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_zt<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_zt<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_z<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_local_A<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_local_A<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_local_A<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 

@@ -18,12 +18,15 @@ int outer_grid(long long n) {
     return (int)(g > OUTER_CTAS ? g : OUTER_CTAS);
 }
 
-// y = A x (f == nullptr) or y = f - A x on the (N-1)² interior grid, zero Dirichlet values;
-// blockIdx.y selects the right-hand side (vectors of n entries, consecutive).
+// y = A x (f == nullptr) or y = f - A x on the (N-1)² interior grid, zero Dirichlet values, or
+// (impedance condition) on all (N+1)² nodes with the boundary rows of their node class;
+// blockIdx.y selects the right-hand side (vectors of n entries, consecutive).  IMP: compiled for
+// the impedance condition.
+template <bool IMP>
 __global__ void k_gstencil(Stencil st, int N, const double2 *__restrict__ x, double2 *__restrict__ y,
                            const double2 *__restrict__ f, const int *__restrict__ active) {
     if (active && !active[blockIdx.y]) return;
-    const int w = N - 1;
+    const int w = IMP ? N + 1 : N - 1;
     const long long n = (long long)w * w;
     x += blockIdx.y * n;
     y += blockIdx.y * n;
@@ -40,37 +43,64 @@ __global__ void k_gstencil(Stencil st, int N, const double2 *__restrict__ x, dou
         if (st.diag == 0) { d1 = X(ix + 1, iy + 1); d2 = X(ix - 1, iy - 1); }
         else { d1 = X(ix + 1, iy - 1); d2 = X(ix - 1, iy + 1); }
         double2 r;
-        r.x = st.c0 * c.x + st.c1 * (((e.x + wv.x) + nn.x) + s.x) + st.c2 * (d1.x + d2.x);
-        r.y = st.c0 * c.y + st.c1 * (((e.y + wv.y) + nn.y) + s.y) + st.c2 * (d1.y + d2.y);
+        const int cls = IMP ? node_class(N, ix, iy) : 4;    // impedance: ix, iy are mesh indices
+        if (cls != 4) {
+            const double2 *cf = st.bcoef + cls * 7;
+            const double2 v[7] = {c, e, wv, nn, s, d1, d2};
+            r = make_double2(0.0, 0.0);
+            for (int q = 0; q < 7; q++) {
+                const double2 a = cf[q];
+                r.x += a.x * v[q].x - a.y * v[q].y;
+                r.y += a.x * v[q].y + a.y * v[q].x;
+            }
+        } else {
+            r.x = st.c0 * c.x + st.c1 * (((e.x + wv.x) + nn.x) + s.x) + st.c2 * (d1.x + d2.x);
+            r.y = st.c0 * c.y + st.c1 * (((e.y + wv.y) + nn.y) + s.y) + st.c2 * (d1.y + d2.y);
+        }
         if (f) { double2 fv = f[i]; r.x = fv.x - r.x; r.y = fv.y - r.y; }
         y[i] = r;
     }
 }
 
-// Load vector F = Σ amp·e_c (point sources snapped to the nearest interior node) + Σ M g
-// (Gaussian bumps, g the nodal values at interior nodes, M the P1 mass matrix
-// h²/12 · [6 centre; 1 at E, W, N, S and the two diagonal corners]).
-__global__ void k_build_rhs(int N, double h, int diag, int npts, const double *__restrict__ pts,
+// Load vector F = Σ amp·e_c (point sources snapped to the nearest node that is an unknown) + Σ M g
+// (Gaussian bumps, g the nodal values at the unknowns, M the P1 mass matrix: at interior nodes
+// h²/12 · [6 centre; 1 at E, W, N, S and the two diagonal corners], at boundary nodes of the
+// impedance problem the row of the node's class).
+__global__ void k_build_rhs(Stencil st, int N, double h, int npts, const double *__restrict__ pts,
                             int nb, const double *__restrict__ bumps, double2 *__restrict__ f) {
-    const int w = N - 1;
+    const int diag = st.diag;
+    const int lo = st.bc ? 0 : 1, hi = st.bc ? N : N - 1;
+    const int w = hi - lo + 1;
     const long long n = (long long)w * w;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int gi = (int)(i % w) + 1, gj = (int)(i / w) + 1;
+        const int gi = (int)(i % w) + lo, gj = (int)(i / w) + lo;
         double v = 0.0;
         for (int p = 0; p < npts; p++) {
             int pi = (int)floor(pts[3 * p] * N + 0.5), pj = (int)floor(pts[3 * p + 1] * N + 0.5);
-            pi = pi < 1 ? 1 : (pi > N - 1 ? N - 1 : pi);
-            pj = pj < 1 ? 1 : (pj > N - 1 ? N - 1 : pj);
+            pi = pi < lo ? lo : (pi > hi ? hi : pi);
+            pj = pj < lo ? lo : (pj > hi ? hi : pj);
             if (pi == gi && pj == gj) v += pts[3 * p + 2];
         }
+        const int cls = st.bc ? node_class(N, gi, gj) : 4;
         for (int b = 0; b < nb; b++) {
             const double cx = bumps[4 * b], cy = bumps[4 * b + 1], sg = bumps[4 * b + 2], amp = bumps[4 * b + 3];
             auto g = [&](int a, int c) -> double {
-                if (a < 1 || a > N - 1 || c < 1 || c > N - 1) return 0.0;
+                if (a < lo || a > hi || c < lo || c > hi) return 0.0;
                 double dx = a * h - cx, dy = c * h - cy;
                 return amp * exp(-(dx * dx + dy * dy) / (2.0 * sg * sg));
             };
+            if (cls != 4) {
+                const double *mr = st.bmass + cls * 7;
+                double s = 0.0;
+                for (int q = 0; q < 7; q++) {
+                    int dx, dy;
+                    stencil_offset(diag, q, dx, dy);
+                    s += mr[q] * g(gi + dx, gj + dy);
+                }
+                v += s;
+                continue;
+            }
             double s = 6.0 * g(gi, gj) + g(gi + 1, gj) + g(gi - 1, gj) + g(gi, gj + 1) + g(gi, gj - 1);
             if (diag == 0) s += g(gi + 1, gj + 1) + g(gi - 1, gj - 1);
             else s += g(gi + 1, gj - 1) + g(gi - 1, gj + 1);
@@ -587,13 +617,14 @@ void launch_fill_test(long long n, unsigned long long seed, double2 *x, cudaStre
 }
 void launch_gstencil(const Stencil &st, int N, const double2 *x, double2 *y, const double2 *f, int nrhs,
                      const int *active, cudaStream_t s) {
-    long long n = (long long)(N - 1) * (N - 1);
-    k_gstencil<<<dim3(grid_for(n, 256), nrhs), 256, 0, s>>>(st, N, x, y, f, active);
+    const long long w = st.bc ? N + 1 : N - 1, n = w * w;
+    if (st.bc) k_gstencil<true><<<dim3(grid_for(n, 256), nrhs), 256, 0, s>>>(st, N, x, y, f, active);
+    else k_gstencil<false><<<dim3(grid_for(n, 256), nrhs), 256, 0, s>>>(st, N, x, y, f, active);
 }
-void launch_build_rhs(int N, double h, int diag, int npts, const double *pts, int nb, const double *bumps,
+void launch_build_rhs(const Stencil &st, int N, double h, int npts, const double *pts, int nb, const double *bumps,
                       double2 *f, cudaStream_t s) {
-    long long n = (long long)(N - 1) * (N - 1);
-    k_build_rhs<<<grid_for(n, 256), 256, 0, s>>>(N, h, diag, npts, pts, nb, bumps, f);
+    const long long w = st.bc ? N + 1 : N - 1, n = w * w;
+    k_build_rhs<<<grid_for(n, 256), 256, 0, s>>>(st, N, h, npts, pts, nb, bumps, f);
 }
 void launch_odots(const OuterBatch &B, const double2 *V, int nv, const double2 *w, double2 *part, cudaStream_t s) {
     k_odots<<<dim3(B.G, B.nrhs), OT, 0, s>>>(B, V, nv, w, part);

@@ -66,11 +66,13 @@ class Solver:
             pass
 
     # -- set-up --------------------------------------------------------------------------------
-    def assemble(self, k: float, N: int, diag: int = 0):
-        p = AssembleParams(float(k), int(N), int(diag))
+    def assemble(self, k: float, N: int, diag: int = 0, bc: int = 0):
+        """bc 0: u = 0 on the boundary, (N-1)² unknowns; bc 1: impedance (Sommerfeld) condition
+        du/dn - i k u = 0 on all four sides, (N+1)² unknowns."""
+        p = AssembleParams(float(k), int(N), int(diag), int(bc))
         self._check(self._L.hdd_assemble(self._h, C.byref(p)), "hdd_assemble")
-        self.N, self.k = int(N), float(k)
-        self.n = (self.N - 1) ** 2
+        self.N, self.k, self.bc = int(N), float(k), int(bc)
+        self.n = (self.N + 1) ** 2 if self.bc else (self.N - 1) ** 2
         return self
 
     def setup_dd(self, Sx: int, Sy: int, overlap: int, ifx=None, ify=None):
@@ -100,7 +102,7 @@ class Solver:
 
     @classmethod
     def from_workload(cls, w, device: int = 0, deflation: bool = True, exact: bool = False):
-        s = cls(device).assemble(w.k, w.N)
+        s = cls(device).assemble(w.k, w.N, bc=getattr(w, "bc", 0))
         s.setup_dd(w.Sx, w.Sy, w.overlap, w.ifx, w.ify)
         if w.nrhs > 1:
             s.setup_batch(w.nrhs)
