@@ -133,7 +133,8 @@ def workload_config(w) -> dict:
     """Keys that define the workload; both arms report them identically."""
     return {"workload": w.name, "k": w.k, "N": w.N, "ppwl": round(w.ppwl, 2),
             "subdomains": f"{w.Sx}x{w.Sy}", "overlap": w.overlap, "nrhs": w.nrhs,
-            "inner_tol": w.inner_tol, "outer_tol": w.outer_tol}
+            "inner_tol": w.inner_tol, "outer_tol": w.outer_tol,
+            "boundary": "impedance" if w.bc else "dirichlet"}
 
 
 def run_reference(args):
@@ -320,7 +321,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         if not args.full_outer_its:
-            args.full_outer_its = {"tiny": 18, "k100": 282, "k200": 1270}.get(args.workload, 1270)
+            args.full_outer_its = {"tiny": 18, "k100": 282, "k200": 1270, "k200s": 781}.get(args.workload, 1270)
         return run_reference(args)
     return run_gpu(args)
 

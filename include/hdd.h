@@ -90,6 +90,16 @@ typedef struct {
 
 hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *prm);
 
+/* Rows of the impedance operator (bc = 1) by node class, as every kernel applies them; host
+ * only (no context, no device).  Class c = cx + 3·cy with cx = 0 on x = 0, 2 on x = N, 1 in
+ * between (cy the same in y), so class 4 is the interior.  Slot q of a row couples the node to
+ * the neighbour at offset 0 (0,0), 1 (+1,0), 2 (-1,0), 3 (0,+1), 4 (0,-1), 5 and 6 the corners
+ * joined by the cell diagonals: (+1,+1), (-1,-1) for diag = 0, (+1,-1), (-1,+1) for diag = 1.
+ * coef_c128: 63 complex128 (interleaved re, im) entries of A = K - k²M - i k B at [c·7 + q];
+ * mass: 63 doubles of M, or NULL.  HDD_ERR_INVALID_ARG for N < 4, diag not 0/1, k < 0 or a
+ * NULL coef_c128. */
+hdd_status hdd_stencil_rows(int N, double k, int diag, double *coef_c128, double *mass);
+
 /* Load vector on the device (§3): point sources F += amp·e_c at the unknown node nearest to
  * (x, y) (clamped into the interior for bc = 0), and Gaussian bumps F += M g with g the nodal
  * values of amp·exp(-|x - c|²/(2σ²)) at the unknowns (the interpolant in V^h) and M the P1

@@ -19,7 +19,8 @@ SYMBOLS = ["hdd_create", "hdd_destroy", "hdd_status_str", "hdd_last_error", "hdd
            "hdd_profile_get", "hdd_launch_count", "hdd_apply_PA_noalloc", "hdd_setup_batch", "hdd_autotune",
            "hdd_warmstart_load", "hdd_warmstart_save",
            "hdd_num_rhs", "hdd_cnn_num_params", "hdd_cnn_set_params", "hdd_cnn_get_params",
-           "hdd_cnn_forward", "hdd_cnn_infer", "hdd_cnn_loss_grad", "hdd_cnn_train_step", "hdd_get_outer_vector"]
+           "hdd_cnn_forward", "hdd_cnn_infer", "hdd_cnn_loss_grad", "hdd_cnn_train_step", "hdd_get_outer_vector",
+           "hdd_stencil_rows"]
 
 
 def status_name(code: int) -> str:
@@ -128,6 +129,8 @@ def lib(build_if_missing: bool = True):
     F = C.POINTER(C.c_float)
     L.hdd_cnn_num_params.argtypes = []
     L.hdd_cnn_num_params.restype = I
+    L.hdd_stencil_rows.argtypes = [I, C.c_double, I, P, P]
+    L.hdd_stencil_rows.restype = I
     L.hdd_cnn_set_params.argtypes = [P, F]
     L.hdd_cnn_set_params.restype = I
     L.hdd_cnn_get_params.argtypes = [P, F]

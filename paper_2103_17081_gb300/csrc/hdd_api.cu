@@ -1023,6 +1023,17 @@ hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *p) {
     return HDD_OK;
 }
 
+hdd_status hdd_stencil_rows(int N, double k, int diag, double *coef_c128, double *mass) {
+    if (N < 4 || N > 65536 || (diag != 0 && diag != 1) || !std::isfinite(k) || k < 0 || !coef_c128)
+        return HDD_ERR_INVALID_ARG;
+    double2 bco[63];
+    double bma[63];
+    boundary_rows(N, k, diag, bco, bma);
+    for (int i = 0; i < 63; i++) { coef_c128[2 * i] = bco[i].x; coef_c128[2 * i + 1] = bco[i].y; }
+    if (mass) std::memcpy(mass, bma, sizeof(bma));
+    return HDD_OK;
+}
+
 hdd_status hdd_build_rhs(hdd_ctx *ctx, int npoints, const double *points, int nbumps,
                          const double *bumps, void *f_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;

@@ -77,3 +77,39 @@ def test_sweep_table_layout():
     assert t[0] == "| ppwl | k | n_glob | N=4 | N=9 |"
     assert t[2] == "| 10 | 20 | 30 | 21 (5) | 30 (6.25) |"
     assert table(rows, "LU").splitlines()[2] == "| 10 | 20 | 30 | 20 |"
+
+
+@pytest.mark.parametrize("diag", [0, 1])
+def test_impedance_stencil_rows_match_oracle_assembly(oracle_mod, diag):
+    """The node-class rows every kernel applies under the impedance condition (host-only
+    hdd_stencil_rows) equal the rows of the oracle's element-by-element assembly of A and M at
+    every node of the mesh; slots towards nodes outside the square are zero."""
+    import numpy as np
+    from paper_2103_17081_gb300 import lib
+    L = lib()
+    offs = [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)] + ([(1, 1), (-1, -1)] if diag == 0 else [(1, -1), (-1, 1)])
+    for (N, k) in [(6, 3.0), (9, 7.5), (16, 20.0)]:
+        coef = np.zeros(2 * 63)
+        mass = np.zeros(63)
+        assert L.hdd_stencil_rows(N, k, diag, coef.ctypes.data_as(ctypes.c_void_p),
+                                  mass.ctypes.data_as(ctypes.c_void_p)) == 0
+        coef = (coef[0::2] + 1j * coef[1::2]).reshape(9, 7)
+        mass = mass.reshape(9, 7)
+        p = oracle_mod.Problem(N, k, diag=diag, bc=1)
+        A, M = p.matrix("A").toarray(), p.matrix("M").toarray()
+        for j in range(N + 1):
+            for i in range(N + 1):
+                cls = (0 if i == 0 else (2 if i == N else 1)) + 3 * (0 if j == 0 else (2 if j == N else 1))
+                r = p.node_index(i, j)
+                cols = [p.node_index(i + dx, j + dy) for dx, dy in offs]
+                ra = np.array([A[r, c] if c >= 0 else 0.0 for c in cols])
+                rm = np.array([M[r, c] if c >= 0 else 0.0 for c in cols])
+                assert np.count_nonzero(A[r]) == np.count_nonzero(ra)     # no coupling outside the slots
+                assert np.allclose(coef[cls], ra, rtol=1e-14, atol=1e-14 * np.abs(ra).max())
+                assert np.allclose(mass[cls], rm, rtol=1e-14, atol=1e-14 * np.abs(rm).max())
+                for q, c in enumerate(cols):
+                    if c < 0:
+                        assert coef[cls, q] == 0 and mass[cls, q] == 0
+    bad = np.zeros(2 * 63)
+    assert L.hdd_stencil_rows(3, 1.0, 0, bad.ctypes.data_as(ctypes.c_void_p), None) != 0
+    assert L.hdd_stencil_rows(8, 1.0, 2, bad.ctypes.data_as(ctypes.c_void_p), None) != 0

@@ -13,6 +13,7 @@ first-order absorbing condition du/dn - i k u = 0 on all four sides):
   k200      k=200, N=640,  8x8 subdomains, overlap 2, centre point source + Gaussian bump
   k400x32   k=400, N=1280, 16x16 subdomains with jittered interfaces, 32 point sources
   k200ws    k200 geometry, used for the learned warm start
+  k200s     k200 geometry and load with the impedance (Sommerfeld) boundary on all four sides
 
 N is the number of mesh intervals per side (h = 1/N), chosen so that
 h ≈ 2π/(k·ppwl) with ppwl ≈ 10 (tiny) or ≈ 20 (the rest), §2.
@@ -124,12 +125,13 @@ def make(name: str, seed: int = 0) -> Workload:
         N, S = 32, 2
         return Workload(name, 20.0, N, S, S, 2, uniform_interfaces(N, S), uniform_interfaces(N, S),
                         [RHSSpec([PointSource(0.5, 0.5)])])
-    if name in ("k100", "k200", "k200ws"):
-        k, N, S = {"k100": (100.0, 320, 4), "k200": (200.0, 640, 8), "k200ws": (200.0, 640, 8)}[name]
+    if name in ("k100", "k200", "k200ws", "k200s"):
+        k, N, S = {"k100": (100.0, 320, 4), "k200": (200.0, 640, 8), "k200ws": (200.0, 640, 8),
+                   "k200s": (200.0, 640, 8)}[name]
         rng = SplitMix64(seed)
         bump = Bump(rng.uniform(0.2, 0.8), rng.uniform(0.2, 0.8))
         return Workload(name, k, N, S, S, 2, uniform_interfaces(N, S), uniform_interfaces(N, S),
-                        [RHSSpec([PointSource(0.5, 0.5)], [bump])])
+                        [RHSSpec([PointSource(0.5, 0.5)], [bump])], bc=1 if name == "k200s" else 0)
     if name in ("k400x32", "k400x4"):
         # k400x4: the same geometry with the first 4 of the 32 right-hand sides (a batched case
         # small enough for multi-pass profiling)
