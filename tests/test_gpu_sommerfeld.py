@@ -184,3 +184,30 @@ def test_k100_solve_matches_oracle(oracle_mod):
     assert np.linalg.norm(f - p.matrix("A") @ xg) <= 1e-6 * np.linalg.norm(f) * 1.01
     assert _rel(xg, xo) < 1e-5
     assert abs(stg["outer_its"] - sto["outer_its"]) <= 0.1 * sto["outer_its"] + 1
+
+
+def test_batched_rhs_match_single_rhs_runs(oracle_mod):
+    """Three right-hand sides (one of them on the boundary of the square) in one batch give the
+    per-RHS results of separate runs, and each matches the oracle."""
+    from paper_2103_17081_gb300 import Solver
+    torch = _torch()
+    w = CASES[1]
+    specs = [W.RHSSpec([W.PointSource(0.31, 0.62)]), W.RHSSpec([W.PointSource(1.0, 0.4)]),
+             W.RHSSpec([W.PointSource(0.7, 0.2)], [W.Bump(0.5, 0.5, 0.1)])]
+    s1 = Solver.from_workload(w)
+    sb = Solver.from_workload(w).setup_batch(3)
+    fb = sb.build_rhs_batch(specs)
+    n = sb.n
+    zb, itb = sb.ras_apply(fb / torch.linalg.vector_norm(fb), inner_tol=1e-2, inner_prec=64)
+    xb, stb = sb.solve(fb, inner_prec=64)
+    p = oracle_mod.from_workload(w)
+    for r, spec in enumerate(specs):
+        fr = fb[r * n:(r + 1) * n].clone()
+        z1, it1 = s1.ras_apply(fr / torch.linalg.vector_norm(fb), inner_tol=1e-2, inner_prec=64)
+        assert _rel(zb[r * n:(r + 1) * n].cpu().numpy(), z1.cpu().numpy()) <= 1e-14
+        assert itb[r * s1.nsub:(r + 1) * s1.nsub] == it1
+        x1, st1 = s1.solve(fr, inner_prec=64)
+        assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), x1.cpu().numpy()) <= 1e-12
+        xo, so = p.solve(p.rhs(spec))
+        assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), xo) < 1e-5
+    assert stb["rel_res_true"] <= 1e-6 * 1.0001

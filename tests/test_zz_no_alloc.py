@@ -18,13 +18,15 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_apply_PA_noalloc_matches_allocating_entry_point():
+@pytest.mark.parametrize("bc", [0, 1], ids=["dirichlet", "impedance"])
+def test_apply_PA_noalloc_matches_allocating_entry_point(bc):
+    """bc = 1: the impedance problem, whose coarse factors are real-equivalent systems."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
     from paper_2103_17081_gb300 import Solver, lib
 
-    w = W.custom(17.0, 45, 3, 2, Sy=4, ifx=[0, 11, 29, 45], name="ragged2")
+    w = W.custom(17.0, 45, 3, 2, Sy=4, ifx=[0, 11, 29, 45], name="ragged2", bc=bc)
     s = Solver.from_workload(w)
     fo, co = s.offsets()
     x = torch.from_numpy(W.random_complex_fast(fo[-1], 77)).cuda()
