@@ -1306,11 +1306,13 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
             const double nv = j + 1, fa = nact;
             KL(F_OMISC, 2.0 * fa * n * 16, 0, launch_gstencil(ctx->st, ctx->N, zj, w, nullptr, nr, dact, s));  // w = A z_j
             // CGS2 flops as executed: dots and update 6 per (vector, element) each (three FMAs,
-            // Gauss form); bytes: V once (16 B) and d (8 B) per vector and element, w
+            // Gauss form); bytes: V (16 B) and d (8 B) per vector and element for each pass over
+            // the basis (k_oupdate with dots makes two: the update, then the dots of the updated
+            // w), and w
             KL(F_OCGS, fa * (nv * 24 + 16) * n, fa * 6 * nv * n,
                launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                              // h1 = V^H w
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
-            KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 12 * nv * n,
+            KL(F_OCGS, fa * (nv * 48 + 32) * n, fa * 12 * nv * n,
                launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
             if (r32)   // FP32 correction from the FP32 basis copy (guarded; FP64 fallback inside)
