@@ -9,7 +9,11 @@ being the inner iterations per subdomain solve.  The paper's own numbers come fr
 with an unstated restart length and partition of unity, so they are trends to compare with, not
 values to reproduce.
 
-    python -m paper_2103_17081_gb300.sweep [--ppwl 10 20] [--k 20 40 80 160] [--json out.jsonl]
+With --bc 1 the same settings run with the impedance (Sommerfeld) condition du/dn - iku = 0 on
+all four sides instead of u = 0; the paper states the solver suits that problem (§3) but prints
+no iteration counts for it.
+
+    python -m paper_2103_17081_gb300.sweep [--ppwl 10 20] [--k 20 40 80 160] [--bc 0|1] [--json out.jsonl]
 """
 from __future__ import annotations
 
@@ -21,35 +25,44 @@ TOLS = [("LU", 0.0), ("1e-10", 1e-10), ("1e-5", 1e-5), ("1e-2", 1e-2)]
 SUBS = [2, 3, 4, 5]                      # N = S² subdomains
 
 
-def run(ks, ppwls, tols, subs, inner_prec=128, log=print):
-    import torch
-
+def settings(ks, ppwls, subs, bc=0):
+    """(ppwl, k, n_glob, S, workload) of every setting: h = 1/n_glob with n_glob = 1.5k (10 ppwl)
+    or 3k (20 ppwl), S x S subdomains, one element layer of overlap, centred point source."""
     import workloads as W
-    from .solver import Solver
-
-    rows = []
+    out = []
     for ppwl in ppwls:
         for k in ks:
             n_glob = int(round(k * (1.5 if ppwl == 10 else 3.0)))
             for S in subs:
-                w = W.custom(float(k), n_glob, S, 1, name=f"k{k}_n{n_glob}_S{S}")
-                need_lu = any(t <= 0 for _, t in tols)
-                s = Solver.from_workload(w, exact=need_lu)
-                f = s.build_rhs(w.rhs[0])
-                for name, tol in tols:
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    _, st = s.solve(f, outer_tol=1e-6, inner_tol=tol, inner_prec=inner_prec,
-                                    inner_restart=30, inner_maxit=1000, raise_on_error=False)
-                    torch.cuda.synchronize()
-                    r = {"ppwl": ppwl, "k": k, "n_glob": n_glob, "N": S * S, "inner": name,
-                         "outer_its": st["outer_its"], "inner_avg": round(st["inner_its_avg"], 1),
-                         "rel_res": st["rel_res_true"], "status": st["status_code"],
-                         "s": round(time.perf_counter() - t0, 3)}
-                    rows.append(r)
-                    if log:
-                        log(json.dumps(r))
-                del s
+                out.append((ppwl, k, n_glob, S,
+                            W.custom(float(k), n_glob, S, 1, name=f"k{k}_n{n_glob}_S{S}", bc=bc)))
+    return out
+
+
+def run(ks, ppwls, tols, subs, inner_prec=128, log=print, bc=0):
+    import torch
+
+    from .solver import Solver
+
+    rows = []
+    for (ppwl, k, n_glob, S, w) in settings(ks, ppwls, subs, bc):
+        need_lu = any(t <= 0 for _, t in tols)
+        s = Solver.from_workload(w, exact=need_lu)
+        f = s.build_rhs(w.rhs[0])
+        for name, tol in tols:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = s.solve(f, outer_tol=1e-6, inner_tol=tol, inner_prec=inner_prec,
+                            inner_restart=30, inner_maxit=1000, raise_on_error=False)
+            torch.cuda.synchronize()
+            r = {"ppwl": ppwl, "k": k, "n_glob": n_glob, "N": S * S, "inner": name,
+                 "outer_its": st["outer_its"], "inner_avg": round(st["inner_its_avg"], 1),
+                 "rel_res": st["rel_res_true"], "status": st["status_code"],
+                 "s": round(time.perf_counter() - t0, 3), "bc": bc}
+            rows.append(r)
+            if log:
+                log(json.dumps(r))
+        del s
     return rows
 
 
@@ -81,10 +94,12 @@ def main(argv=None):
     ap.add_argument("--inner", nargs="+", default=[n for n, _ in TOLS], choices=[n for n, _ in TOLS])
     ap.add_argument("--subdomains", type=int, nargs="+", default=SUBS, help="S for S x S subdomains")
     ap.add_argument("--prec", type=int, default=128, choices=[64, 128], help="inner precision")
+    ap.add_argument("--bc", type=int, default=0, choices=[0, 1],
+                    help="0: u = 0 on the boundary (the paper's tables); 1: impedance condition")
     ap.add_argument("--json", default=None, help="also write every row as a JSON line to this file")
     a = ap.parse_args(argv)
     tols = [(n, t) for n, t in TOLS if n in a.inner]
-    rows = run(a.k, a.ppwl, tols, a.subdomains, a.prec)
+    rows = run(a.k, a.ppwl, tols, a.subdomains, a.prec, bc=a.bc)
     if a.json:
         with open(a.json, "w") as fh:
             for r in rows:

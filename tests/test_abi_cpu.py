@@ -113,3 +113,21 @@ def test_impedance_stencil_rows_match_oracle_assembly(oracle_mod, diag):
     bad = np.zeros(2 * 63)
     assert L.hdd_stencil_rows(3, 1.0, 0, bad.ctypes.data_as(ctypes.c_void_p), None) != 0
     assert L.hdd_stencil_rows(8, 1.0, 2, bad.ctypes.data_as(ctypes.c_void_p), None) != 0
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_sweep_settings_follow_the_paper_recipe(oracle_mod, bc):
+    """Every sweep setting has n_glob = 1.5k (10 ppwl) or 3k (20 ppwl) intervals, S x S uniform
+    subdomains, one layer of overlap, a centred point source and the chosen boundary condition;
+    the oracle accepts the decomposition."""
+    from paper_2103_17081_gb300.sweep import settings
+    st = settings([20, 40], [10, 20], [2, 3], bc=bc)
+    assert len(st) == 8
+    for (ppwl, k, n_glob, S, w) in st:
+        assert n_glob == round(k * (1.5 if ppwl == 10 else 3.0)) and w.N == n_glob
+        assert (w.Sx, w.Sy, w.overlap, w.bc) == (S, S, 1, bc)
+        assert [(q.x, q.y) for q in w.rhs[0].points] == [(0.5, 0.5)]
+    ppwl, k, n_glob, S, w = st[1]
+    p = oracle_mod.Problem(w.N, w.k, bc=w.bc)
+    p.setup_dd(w.Sx, w.Sy, w.overlap, w.ifx, w.ify)
+    assert p.n == ((w.N + 1) ** 2 if bc else (w.N - 1) ** 2)
