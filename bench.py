@@ -115,23 +115,41 @@ def oracle_sample(w, outer_its: int, threads: int = 0):
     return time.perf_counter() - t0, st, oracle.get_threads()
 
 
-def oracle_estimate(w, M: int, J: int):
-    """Oracle time-to-solution for J outer iterations from two bounded samples.
+def oracle_orth_cost(n: int, nv: int = 64, reps: int = 2) -> float:
+    """Seconds per basis vector of the oracle's outer CGS2 on vectors of n entries (the best of
+    `reps` timings against nv stored vectors; the cost does not depend on the values)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(0)
+    V = np.asfortranarray(rng.standard_normal((n, nv)) + 1j * rng.standard_normal((n, nv)))
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.cgs2(V, x)
+        best = min(best, time.perf_counter() - t0)
+    return best / nv
 
-    The oracle's cost of outer iteration j is c_ras + c_orth·j (the RAS application is the same
-    every iteration, the orthogonalisation grows with j), so t(J) = a·J + b·J²/2; a and b are
-    fitted to the times of the first M/2 and the first M iterations."""
+
+def oracle_estimate(w, M: int, J: int):
+    """Oracle time-to-solution for J outer iterations from bounded samples.
+
+    Outer iteration j costs one RAS application plus a CGS2 against j+1 basis vectors.  The
+    orthogonalisation's cost per basis vector, c, is timed on its own (oracle_orth_cost); the RAS
+    cost per iteration, r, comes from the second half of an M-iteration sample (the first
+    iterations are cheaper while the Krylov vectors still vanish on most subdomains), less the
+    orthogonalisation inside that window.  Then t(J) = t(M) + (J - M) r + c (J² - M²)/2."""
     t1, st1, cores = oracle_sample(w, max(1, M // 2))
     t2, st2, _ = oracle_sample(w, M)
     j1, j2 = st1["outer_its"], st2["outer_its"]
-    if j2 <= j1 or j1 == 0:
+    if j2 >= J or j2 <= j1:
         return t2 * J / max(1, j2), cores, f"first {j2} of {J} outer iterations, scaled linearly"
-    b = 2.0 * (t2 / j2 - t1 / j1) / (j2 - j1)
-    a = t1 / j1 - b * j1 / 2.0
-    b = max(b, 0.0)
-    est = a * J + b * J * J / 2.0
+    c = oracle_orth_cost(w.n_global)
+    r = (t2 - t1) / (j2 - j1) - c * (j1 + j2) / 2.0
+    est = t2 + (J - j2) * r + c * (J * J - j2 * j2) / 2.0
     return est, cores, (f"first {j1} and first {j2} of {J} outer iterations timed ({t1:.2f} s, "
-                        f"{t2:.2f} s); t(J) = aJ + bJ^2/2 fitted and evaluated at J={J}")
+                        f"{t2:.2f} s), CGS2 cost {c * 1e3:.3f} ms per basis vector timed alone; "
+                        f"t(J) = t({j2}) + (J - {j2}) r + c (J^2 - {j2}^2)/2 at J={J}")
 
 
 def workload_config(w) -> dict:

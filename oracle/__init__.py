@@ -96,6 +96,8 @@ def lib():
         L.or_ras_apply.restype = I
         L.or_solve.argtypes = [P, Z, Z, C.POINTER(SolveParams), C.POINTER(Stats), Z, I]
         L.or_solve.restype = I
+        L.or_cgs2.argtypes = [Z, I, I, Z, Z]
+        L.or_cgs2.restype = D
         L.or_band_lu.argtypes = [I, I, I, Z, Z]
         L.or_band_lu.restype = I
         L.or_band_solve.argtypes = [I, I, I, Z, Z, Z]
@@ -127,6 +129,17 @@ def set_threads(n: int) -> None:
 
 def get_threads() -> int:
     return int(lib().or_get_threads())
+
+
+def cgs2(V: np.ndarray, w):
+    """Outer CGS2 of the oracle: (w orthogonalised against the columns of V, coefficients h, ||w||).
+    V is n x nv complex128; it is passed column-major without a copy when already Fortran-ordered."""
+    V = np.asfortranarray(V, dtype=np.complex128)
+    n, nv = V.shape
+    w = _c128(w).copy()
+    h = np.zeros(nv, dtype=np.complex128)
+    r = lib().or_cgs2(_ptr(V), n, nv, _ptr(w), _ptr(h))
+    return w, h, r
 
 
 def band_lu(ab: np.ndarray, m: int, kl: int, ku: int):

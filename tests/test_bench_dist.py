@@ -73,3 +73,32 @@ def test_reference_arm_json_line_keys(monkeypatch):
     assert d["impl"] == "reference" and d["higher_is_better"] is False and d["value"] > 0
     assert set(bench.workload_config(bench.W.make("tiny"))) <= set(d["config"])
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_oracle_estimate_recovers_a_cost_model(monkeypatch):
+    """With iteration i costing r (a third of it during a 50-iteration start-up) plus c·(i+1)
+    for its CGS2, the estimate from samples of 100 and 200 iterations and a separate timing of c
+    reproduces the exact total for J iterations; the former two-sample quadratic fit did not."""
+    import bench
+
+    r, c = 0.05, 2e-4
+
+    def cost(i):
+        return r * (0.3 if i < 50 else 1.0) + c * (i + 1)
+
+    def fake_sample(w, its, threads=0):
+        return sum(cost(i) for i in range(its)), {"outer_its": its}, 4
+
+    monkeypatch.setattr(bench, "oracle_sample", fake_sample)
+    monkeypatch.setattr(bench, "oracle_orth_cost", lambda n, nv=64, reps=2: c)
+
+    class Wl:
+        n_global = 1000
+
+    for J in (300, 781, 1270):
+        exact = sum(cost(i) for i in range(J))
+        est, cores, how = bench.oracle_estimate(Wl(), 200, J)
+        assert abs(est - exact) <= 1e-9 * exact, (J, est, exact)
+        assert cores == 4 and f"J={J}" in how
+    est, _, how = bench.oracle_estimate(Wl(), 200, 150)      # sample reaches J: no extrapolation
+    assert "scaled linearly" in how

@@ -164,3 +164,20 @@ def test_nonfinite_rhs_is_reported(oracle_mod):
     f[5] = np.nan
     with pytest.raises(oracle_mod.OracleError):
         p.solve(f)
+
+
+def test_outer_cgs2_projects_out_an_orthonormal_basis(oracle_mod):
+    """For orthonormal V: the result is orthogonal to V, w_in = w' + V h exactly in exact
+    arithmetic (here to rounding), h = Vᴴ w_in, and the returned value is ||w'||."""
+    rng = np.random.default_rng(8)
+    n, nv = 300, 12
+    V, _ = np.linalg.qr(rng.standard_normal((n, nv)) + 1j * rng.standard_normal((n, nv)))
+    w = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    wp, h, r = oracle_mod.cgs2(V, w)
+    assert np.linalg.norm(V.conj().T @ wp) <= 1e-14 * np.linalg.norm(w)
+    assert np.linalg.norm(w - (wp + V @ h)) <= 1e-14 * np.linalg.norm(w)
+    assert np.allclose(h, V.conj().T @ w, rtol=0, atol=1e-13 * np.linalg.norm(w))
+    assert r == pytest.approx(np.linalg.norm(wp), rel=1e-14)
+    # a vector already in span(V) leaves (almost) nothing
+    wp, h, r = oracle_mod.cgs2(V, V @ h)
+    assert r <= 1e-14 * np.linalg.norm(h)
