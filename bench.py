@@ -115,41 +115,30 @@ def oracle_sample(w, outer_its: int, threads: int = 0):
     return time.perf_counter() - t0, st, oracle.get_threads()
 
 
-def oracle_orth_cost(n: int, nv: int = 64, reps: int = 2) -> float:
-    """Seconds per basis vector of the oracle's outer CGS2 on vectors of n entries (the best of
-    `reps` timings against nv stored vectors; the cost does not depend on the values)."""
-    import numpy as np
-    import oracle
-    rng = np.random.default_rng(0)
-    V = np.asfortranarray(rng.standard_normal((n, nv)) + 1j * rng.standard_normal((n, nv)))
-    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
-    best = float("inf")
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        oracle.cgs2(V, x)
-        best = min(best, time.perf_counter() - t0)
-    return best / nv
-
-
 def oracle_estimate(w, M: int, J: int):
-    """Oracle time-to-solution for J outer iterations from bounded samples.
+    """Oracle time-to-solution for J outer iterations from three bounded samples.
 
-    Outer iteration j costs one RAS application plus a CGS2 against j+1 basis vectors.  The
-    orthogonalisation's cost per basis vector, c, is timed on its own (oracle_orth_cost); the RAS
-    cost per iteration, r, comes from the second half of an M-iteration sample (the first
-    iterations are cheaper while the Krylov vectors still vanish on most subdomains), less the
-    orthogonalisation inside that window.  Then t(J) = t(M) + (J - M) r + c (J² - M²)/2."""
-    t1, st1, cores = oracle_sample(w, max(1, M // 2))
+    Outer iteration j costs one RAS application plus a CGS2 against j+1 basis vectors, so past
+    the first iterations (cheaper while the Krylov vectors still vanish on most subdomains) the
+    cost per iteration grows linearly in j.  The solve is timed to M/4, M/2 and M iterations
+    (separate runs, after an untimed 10-iteration warm-up of the oracle's threads); the mean
+    costs per iteration over the windows [M/4, M/2) and [M/2, M) give that line, which is summed
+    from M to J and added to t(M)."""
+    oracle_sample(w, 10)
+    t0, st0, cores = oracle_sample(w, max(1, M // 4))
+    t1, st1, _ = oracle_sample(w, max(2, M // 2))
     t2, st2, _ = oracle_sample(w, M)
-    j1, j2 = st1["outer_its"], st2["outer_its"]
-    if j2 >= J or j2 <= j1:
+    j0, j1, j2 = st0["outer_its"], st1["outer_its"], st2["outer_its"]
+    if j2 >= J or not (j0 < j1 < j2):
         return t2 * J / max(1, j2), cores, f"first {j2} of {J} outer iterations, scaled linearly"
-    c = oracle_orth_cost(w.n_global)
-    r = (t2 - t1) / (j2 - j1) - c * (j1 + j2) / 2.0
-    est = t2 + (J - j2) * r + c * (J * J - j2 * j2) / 2.0
-    return est, cores, (f"first {j1} and first {j2} of {J} outer iterations timed ({t1:.2f} s, "
-                        f"{t2:.2f} s), CGS2 cost {c * 1e3:.3f} ms per basis vector timed alone; "
-                        f"t(J) = t({j2}) + (J - {j2}) r + c (J^2 - {j2}^2)/2 at J={J}")
+    r1 = (t1 - t0) / (j1 - j0)                  # mean cost per iteration over [j0, j1)
+    r2 = (t2 - t1) / (j2 - j1)                  # ... over [j1, j2)
+    m1, m2 = (j0 + j1 + 1) / 2.0, (j1 + j2 + 1) / 2.0
+    c = max(0.0, (r2 - r1) / (m2 - m1))         # growth per iteration (the CGS2 term)
+    est = t2 + (J - j2) * r2 + c * ((J * (J + 1) - j2 * (j2 + 1)) / 2.0 - (J - j2) * m2)
+    return est, cores, (f"first {j0}, {j1} and {j2} of {J} outer iterations timed ({t0:.2f} s, "
+                        f"{t1:.2f} s, {t2:.2f} s); the cost per iteration, linear in j through "
+                        f"the two later windows, summed to J={J}")
 
 
 def workload_config(w) -> dict:
@@ -339,7 +328,7 @@ def main():
     ap.add_argument("--prec", type=int, default=64, choices=[64, 128])
     ap.add_argument("--outer-maxit", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--sample-its", type=int, default=200)
+    ap.add_argument("--sample-its", type=int, default=400)
     ap.add_argument("--full-outer-its", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warm-start", default=None,

@@ -859,8 +859,7 @@ static double cgs2(const zc *V, int n, int j, zc *w, zc *h, zc *htmp, int par) {
 
 /* The outer orthogonalisation exactly as or_solve runs it (threads over the independent dots
  * and elements): w is made orthogonal to the nv vectors of V (n x nv, column-major) by CGS2,
- * h[0..nv) receives the coefficients, the return value is ||w||.  Exposed for pins and so that
- * the CPU baseline can time the oracle's per-vector orthogonalisation cost on its own. */
+ * h[0..nv) receives the coefficients, the return value is ||w||.  Exposed for pins. */
 double or_cgs2(const double *V_c128, int n, int nv, double *w_c128, double *h_c128) {
     if (nv < 1 || n < 1) return nrm2((const zc *)w_c128, n > 0 ? n : 0);
     zc *htmp = (zc *)malloc(sizeof(zc) * (size_t)nv);

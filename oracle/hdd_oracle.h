@@ -99,7 +99,7 @@ int or_ras_apply(const or_problem *p, const double *v_c128, double *z_c128, doub
 int or_solve(const or_problem *p, const double *f_c128, double *x_c128, const or_solve_params *prm,
              or_stats *st, double *res_history, int history_cap);
 
-/* -- outer CGS2 as or_solve applies it (pins; timing of the CPU baseline) ------------------- */
+/* -- outer CGS2 as or_solve applies it (exposed for pins) ---------------------------------- */
 double or_cgs2(const double *V_c128, int n, int nv, double *w_c128, double *h_c128);
 
 /* -- banded LU with partial pivoting, row-band storage (exposed for pins) ----------------- */

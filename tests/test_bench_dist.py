@@ -77,8 +77,9 @@ def test_reference_arm_json_line_keys(monkeypatch):
 
 def test_oracle_estimate_recovers_a_cost_model(monkeypatch):
     """With iteration i costing r (a third of it during a 50-iteration start-up) plus c·(i+1)
-    for its CGS2, the estimate from samples of 100 and 200 iterations and a separate timing of c
-    reproduces the exact total for J iterations; the former two-sample quadratic fit did not."""
+    for its CGS2, the estimate from samples of 100, 200 and 400 iterations reproduces the exact
+    total for J iterations; the former two-sample quadratic fit did not (it read the cheap
+    start-up as growth)."""
     import bench
 
     r, c = 0.05, 2e-4
@@ -90,15 +91,16 @@ def test_oracle_estimate_recovers_a_cost_model(monkeypatch):
         return sum(cost(i) for i in range(its)), {"outer_its": its}, 4
 
     monkeypatch.setattr(bench, "oracle_sample", fake_sample)
-    monkeypatch.setattr(bench, "oracle_orth_cost", lambda n, nv=64, reps=2: c)
 
-    class Wl:
-        n_global = 1000
-
-    for J in (300, 781, 1270):
+    for J in (500, 781, 1270):
         exact = sum(cost(i) for i in range(J))
-        est, cores, how = bench.oracle_estimate(Wl(), 200, J)
+        est, cores, how = bench.oracle_estimate(None, 400, J)
         assert abs(est - exact) <= 1e-9 * exact, (J, est, exact)
         assert cores == 4 and f"J={J}" in how
-    est, _, how = bench.oracle_estimate(Wl(), 200, 150)      # sample reaches J: no extrapolation
+        # the former fit on the first 100 and 200 iterations overshoots this model
+        t1, t2 = fake_sample(None, 100)[0], fake_sample(None, 200)[0]
+        b = 2.0 * (t2 / 200 - t1 / 100) / 100
+        a = t1 / 100 - b * 50
+        assert a * J + b * J * J / 2 > 1.05 * exact
+    est, _, how = bench.oracle_estimate(None, 400, 300)      # sample reaches J: no extrapolation
     assert "scaled linearly" in how
