@@ -150,18 +150,20 @@ def workload_config(w) -> dict:
 
 
 def run_reference(args):
-    """CPU oracle arm: each step times the oracle on the first M/2 and first M outer iterations
-    of the workload and extrapolates to the full outer count (oracle_estimate)."""
+    """CPU oracle arm: each timed step times the oracle on bounded samples of the workload and
+    extrapolates to the full outer count (oracle_estimate); an untimed warm-up step is a short
+    10-iteration oracle solve (each estimate warms the oracle up again on its own)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     w = W.make(args.workload)
     J = args.full_outer_its
+    for _ in range(args.warmup):
+        oracle_sample(w, 10)
     times = []
-    for k in range(args.warmup + args.steps):
+    for _ in range(args.steps):
         est, cores, how = oracle_estimate(w, args.sample_its, J)
-        if k >= args.warmup:
-            times.append(est)
+        times.append(est)
     v = statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
