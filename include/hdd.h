@@ -153,12 +153,14 @@ int hdd_num_rhs(const hdd_ctx *ctx);
 /* ---------------------------------------------------------------------------------------- */
 /* Deflation set-up (Eq. 4, Eq. 5).  For every distinct box shape: E = Zᵀ A Z (5x5 coarse   */
 /* stencil, half-bandwidth 2·mx+2) is formed and LU-factorised with partial pivoting in FP64 */
-/* on the device; subdomains with equal shape share one factor.                             */
+/* on the device; subdomains with equal shape share one factor.  With bc = 1 a shape also    */
+/* records which box sides lie on the boundary of the square, and the complex E is factored  */
+/* as its real equivalent (order 2·mx·my, unknowns Re and Im interleaved).                   */
 /* ---------------------------------------------------------------------------------------- */
 hdd_status hdd_setup_deflation(hdd_ctx *ctx, void *stream);
 
 /* Banded LU (FP64, partial pivoting) of every distinct A_j for the direct local solve
- * (inner_tol <= 0, the benchmark of §3.1). */
+ * (inner_tol <= 0, the benchmark of §3.1); for bc = 1 of its real equivalent, as for E. */
 hdd_status hdd_setup_exact(hdd_ctx *ctx, void *stream);
 
 /* ---------------------------------------------------------------------------------------- */
@@ -254,7 +256,8 @@ hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void
 /* precision.  Because FGMRES is flexible, any guess keeps the outer tolerance exact.         */
 /* ---------------------------------------------------------------------------------------- */
 int hdd_cnn_num_params(void);
-/* Load parameters (host FP32 array), reset Adam's moments. */
+/* Load parameters (host FP32 array), reset Adam's moments.  HDD_ERR_INVALID_ARG for a problem
+ * assembled with bc = 1: the network serves the Dirichlet problem only. */
 hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params);
 /* Read the FP32 master parameters. */
 hdd_status hdd_cnn_get_params(hdd_ctx *ctx, float *params);
