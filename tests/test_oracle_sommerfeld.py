@@ -311,3 +311,15 @@ def test_solve_matches_direct_energy_identity_and_symmetry(oracle_mod):
     assert np.allclose(U, U[::-1, ::-1], rtol=0, atol=1e-10 * np.abs(U).max())
     assert np.allclose(U, U.T, rtol=0, atol=1e-10 * np.abs(U).max())
     assert st["outer_its"] < 40
+
+
+def test_tight_inner_reproduces_direct_ras_history(oracle_mod):
+    """Inner GMRES to 1e-13 gives the outer residual history of exact (LU) subdomain solves."""
+    p, w = _problem(oracle_mod, N=40, k=16.0, S=2, overlap=2, exact=True)
+    f = p.rhs(w.rhs[0])
+    _, st_lu = p.solve(f, inner_tol=0.0)
+    _, st_it = p.solve(f, inner_tol=1e-13)
+    n = min(20, len(st_lu["res_history"]))
+    h1, h2 = st_lu["res_history"][:n], st_it["res_history"][:n]
+    assert np.max(np.abs(h1 - h2) / h1) < 1e-8
+    assert st_lu["outer_its"] == st_it["outer_its"]
