@@ -5,6 +5,11 @@ outer Arnoldi in FP64.
 
 One step = one full solve (every step of the path) on inputs already resident in HBM.  Prints one
 JSON line.  `--impl reference` times the CPU oracle instead (bounded sample per step).
+
+Besides the default form (the line's value) the line carries, under "forms", the plain FP64 GPU
+method (complex128 inner, all-FP64 outer) and the learned-warm-start form, each timed with fewer
+steps, and for every form its error against the oracle's stored solve of the same workload
+(tests/golden/<workload>_oracle_x.npy, written by an oracle-only script).
 """
 from __future__ import annotations
 
@@ -141,6 +146,46 @@ def oracle_estimate(w, M: int, J: int):
                         f"the two later windows, summed to J={J}")
 
 
+WARM_START_PARAMS = os.path.join(ROOT, "paper_2103_17081_gb300", "weights", "k200_warmstart.bin")
+
+
+def oracle_error(w, x):
+    """Relative error of the solution x (device tensor, one RHS) against the oracle's stored
+    solve of workload w: 2-norm and largest entry error over the largest entry; None when no
+    stored solve exists for w."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"{w.name}_oracle_x.npy")
+    if not os.path.exists(path) or w.nrhs != 1:
+        return None
+    xr = np.load(path)
+    xg = x.detach().cpu().numpy()
+    if xr.dtype.kind == "f":          # real data: the oracle stores Re x (its Im x is exactly 0)
+        xr = xr.astype(np.complex128)
+    d = xg - xr
+    return {"rel_2norm": float(np.linalg.norm(d) / np.linalg.norm(xr)),
+            "max_rel": float(np.max(np.abs(d)) / np.max(np.abs(xr))),
+            "reference": f"tests/golden/{w.name}_oracle_x.npy (oracle, complex128)"}
+
+
+def time_form(s, f, x, kw, steps, warmup, flush, stream):
+    """Mean CUDA-event time of `steps` solves after `warmup` untimed ones (L2 flushed before each
+    timed solve), with the stats of the last."""
+    import torch
+    for _ in range(warmup):
+        s.solve(f, out=x, **kw)
+    torch.cuda.synchronize()
+    ts, st = [], None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = s.solve(f, out=x, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.mean(ts), st
+
+
 def workload_config(w) -> dict:
     """Keys that define the workload; both arms report them identically."""
     return {"workload": w.name, "k": w.k, "N": w.N, "ppwl": round(w.ppwl, 2),
@@ -255,9 +300,32 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e.append(time.perf_counter() - t0)
 
-    # check the answer on the device: true relative residual
+    # check the answer on the device: true relative residual, and the error against the oracle
     r = f - s.apply_A(x)
     rel = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(f))
+    err = oracle_error(w, x) if rank == 0 else None     # the stored solves use seed 0
+
+    # the other forms of the method, fewer steps each: plain FP64 (complex128 inner, FP64
+    # second CGS pass) and the learned warm start (network trained by the library's own kernels)
+    forms = {}
+    if ws == 1 and args.form_steps > 0 and not args.warm_start and args.prec == 64 and not args.fp64_reorth:
+        cand = [("plain_fp64", dict(kw, inner_prec=128, outer_reorth32=0), None)]
+        if w.name == "k200" and os.path.exists(WARM_START_PARAMS):
+            cand.append(("warm_start", dict(kw, warm_start=1), WARM_START_PARAMS))
+        for name, fkw, params in cand:
+            if params:
+                from paper_2103_17081_gb300 import warmstart
+                s.cnn_set_params(warmstart.load(params))
+            t, fst = time_form(s, f, x, fkw, args.form_steps, 1, flush, stream)
+            forms[name] = {"value": t, "unit": "s", "steps": args.form_steps, "warmup": 1,
+                           "outer_its": fst["outer_its"], "inner_its_avg": round(fst["inner_its_avg"], 3),
+                           "rel_res_true": fst["rel_res_true"], "err_vs_oracle": oracle_error(w, x),
+                           "inner_prec": fkw["inner_prec"],
+                           "outer_reorth": "fp32-guarded" if fkw["outer_reorth32"] else "fp64",
+                           "warm_start": bool(fkw.get("warm_start", 0))}
+            if params:
+                forms[name]["params"] = os.path.relpath(params, ROOT)
+        forms["default_faster_than_plain_fp64"] = t_step < forms["plain_fp64"]["value"]
 
     # roofline of the dominant kernel family (CUDA-event time inside the timed region)
     hbm, hbm_src = _peaks()
@@ -301,7 +369,8 @@ def run_gpu(args):
                        "tiles": tiles or {"fine_rows": 8, "coarse_rows": 4},
                        "parallelism": "replicas" if ws > 1 else "single"},
             "solve": {"outer_its": stats["outer_its"], "inner_its_avg": round(stats["inner_its_avg"], 3),
-                      "rel_res_true": rel, "status": stats["status_code"]},
+                      "rel_res_true": rel, "status": stats["status_code"], "err_vs_oracle": err},
+            "forms": forms,
             "subdomain_solve_GBps": subdomain_gbs, "subdomain_solve_frac_hbm": subdomain_gbs / hbm,
             "roofline": roof, "kernels": fams,
             "e2e": {"value": statistics.mean(e2e) if e2e else None, "unit": "s",
@@ -333,6 +402,8 @@ def main():
     ap.add_argument("--sample-its", type=int, default=400)
     ap.add_argument("--full-outer-its", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form-steps", type=int, default=2,
+                    help="timed solves of each other form (plain FP64, warm start); 0 skips them")
     ap.add_argument("--warm-start", default=None,
                     help="parameter file of a trained warm-start network (written by "
                          "python -m paper_2103_17081_gb300.warmstart train)")

@@ -50,7 +50,7 @@ typedef enum {
     HDD_ERR_NO_CONVERGENCE = 7,  /* outer FGMRES reached outer_maxit above the tolerance     */
     HDD_ERR_BREAKDOWN = 8,       /* reserved                                                 */
     HDD_ERR_NONFINITE = 9,       /* NaN/Inf met in a residual                                */
-    HDD_ERR_TIMEOUT = 10         /* reserved for bounded device-side waits                   */
+    HDD_ERR_TIMEOUT = 10         /* a bounded device-side wait gave up (see hdd_cnn_infer)   */
 } hdd_status;
 
 /* Create a context on CUDA device `device`.  *out receives the handle. */
@@ -274,7 +274,10 @@ hdd_status hdd_cnn_forward(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *
 /* implicit GEMMs on the tensor cores (tcgen05, BF16 operands, FP32 accumulation in TMEM), with */
 /* the activations between layers rounded to BF16.  Same arguments as hdd_cnn_forward, which  */
 /* keeps FP32 activations (the training forward).  HDD_ERR_TIMEOUT if a bounded device wait    */
-/* gave up (synchronises the stream to read that flag). */
+/* gave up (synchronises the stream to read that flag).  If the wait's own drain of the copies  */
+/* and MMAs in flight also gave up, that work may outlive the CTA that issued it, so the error  */
+/* is fatal: the context then refuses every later call with HDD_ERR_TIMEOUT, and the caller    */
+/* should destroy it and discard its CUDA context. */
 hdd_status hdd_cnn_infer(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream);
 /* Training loss of the batch f (every packed subdomain image) and, if grad != NULL, its
  * gradient w.r.t. every parameter (host FP32 array); synchronises the device.  Needs
@@ -321,10 +324,13 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 /* (hdd_get_offsets), distinct, 16-byte aligned.  The two complex128 coarse work vectors live */
 /* in a fixed array inside the library (16 MiB, present on every GPU that loads the library  */
 /* until the process exits): the packed coarse length Σ m_x·m_y must not exceed 524288, else */
-/* HDD_ERR_INVALID_ARG.  The call allocates nothing; the first call on a device looks up that */
-/* array's device address (make the first call before any stream capture).  Every call      */
-/* shares the array, so calls that may overlap on the GPU (other streams, other contexts on  */
-/* the same device) race; serialise them.  Work is enqueued on `stream`; no synchronisation. */
+/* HDD_ERR_INVALID_ARG.  The call allocates nothing; the first call from a CUDA context     */
+/* looks up that array's device address in it (make the first call before any stream        */
+/* capture; after cudaDeviceReset the first call from the new context looks it up again).    */
+/* Each context has its own copy of the array, and every call made in one context shares     */
+/* that copy, which keeps the last call's contents: calls that may overlap on the GPU in one  */
+/* context (other streams, other host threads) race; serialise them.  Work is enqueued on     */
+/* `stream`; no synchronisation.                                                            */
 /* ---------------------------------------------------------------------------------------- */
 hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev, void *stream);
 

@@ -155,6 +155,7 @@ struct hdd_ctx {
     std::vector<double> hist;
     std::vector<int> h_its;
     Prof prof;
+    bool poisoned = false;                     // a device wait gave up with work in flight
     ~hdd_ctx() { if (h_counter) cudaFreeHost(h_counter); }
 };
 
@@ -484,6 +485,13 @@ hdd_status cnn_check_err(hdd_ctx *ctx, cudaStream_t s) {
     int e = 0;
     CK(cudaMemcpyAsync(&e, C.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (e == 2) {
+        // a bulk copy or MMA may have outlived its CTA (kernels_cnn_tc.cu): the context is lost
+        ctx->poisoned = true;
+        FAIL(HDD_ERR_TIMEOUT, "a tensor-core convolution wait and its drain timed out; work still in "
+                              "flight may have written freed memory, so this context refuses further "
+                              "work (discard it and its CUDA context)");
+    }
     if (e) {
         CK(cudaMemsetAsync(C.err.p, 0, sizeof(int), s));
         FAIL(HDD_ERR_TIMEOUT, "a tensor-core convolution wait timed out");
@@ -835,22 +843,56 @@ hdd_status check_solve_params(hdd_ctx *ctx, const hdd_solve_params *p) {
 // Fixed scratch for hdd_apply_PA_noalloc: two complex128 coarse vectors (y = Zᵀ A v and
 // s = E⁻¹ y) of at most HDD_NOALLOC_MAX_COARSE entries each, 16 MiB held by every GPU that
 // loads the library for the life of the process.  Host code cannot use the symbol itself as a
-// device address; the address is looked up once per device (noalloc_scratch below).
+// device address; the address is looked up with the device current (noalloc_scratch below) and
+// cached per device together with the ID of the context it was resolved in.  Each CUDA context
+// holds its own copy of the array, and a context created after cudaDeviceReset reloads the
+// module at a new address, so a call from a context other than the cached one looks it up again.
 // ===========================================================================================
 #define HDD_NOALLOC_MAX_COARSE (1 << 19)
 #define HDD_NOALLOC_MAX_DEVICES 64
 static __device__ __align__(256) double2 g_noalloc_scratch[2 * HDD_NOALLOC_MAX_COARSE];
 static double2 *g_noalloc_ptr[HDD_NOALLOC_MAX_DEVICES];
+static unsigned long long g_noalloc_ctx[HDD_NOALLOC_MAX_DEVICES];
 
 namespace {
-// Device address of g_noalloc_scratch on the current device (resolved on first use).
+// Unique ID (never reused within the process) of the calling thread's current CUDA context.  The
+// driver's cuCtxGetCurrent / cuCtxGetId are reached through the runtime's entry-point query, so
+// the library keeps no link-time dependency on libcuda.
+cudaError_t current_context_id(unsigned long long *id) {
+    using GetCur = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCur get_cur = nullptr;
+    static GetId get_id = nullptr;
+    if (!get_cur || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        get_cur = reinterpret_cast<GetCur>(f1);
+        get_id = reinterpret_cast<GetId>(f2);
+    }
+    void *c = nullptr;
+    if (get_cur(&c) != 0 || !c) return cudaErrorDeviceUninitialized;
+    if (get_id(c, id) != 0) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+
+// Device address of g_noalloc_scratch in the current context of `device` (looked up on the first
+// call from that context).
 cudaError_t noalloc_scratch(int device, double2 **out) {
     if (device < 0 || device >= HDD_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    if (!g_noalloc_ptr[device]) {
+    unsigned long long cid = 0;
+    cudaError_t e = current_context_id(&cid);
+    if (e != cudaSuccess) return e;
+    if (!g_noalloc_ptr[device] || g_noalloc_ctx[device] != cid) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
+        if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
         g_noalloc_ptr[device] = reinterpret_cast<double2 *>(p);
+        g_noalloc_ctx[device] = cid;
     }
     *out = g_noalloc_ptr[device];
     return cudaSuccess;
@@ -986,6 +1028,7 @@ void hdd_destroy(hdd_ctx *ctx) {
 
 hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *p) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!p) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
     if (p->N < 4 || p->N > 65536) FAIL(HDD_ERR_INVALID_ARG, "N must be in 4..65536");
     if (!std::isfinite(p->k) || p->k < 0) FAIL(HDD_ERR_INVALID_ARG, "k must be finite and >= 0");
@@ -1037,6 +1080,7 @@ hdd_status hdd_stencil_rows(int N, double k, int diag, double *coef_c128, double
 hdd_status hdd_build_rhs(hdd_ctx *ctx, int npoints, const double *points, int nbumps,
                          const double *bumps, void *f_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->assembled) FAIL(HDD_ERR_STATE, "hdd_assemble first");
     if (!f_dev || !aligned16(f_dev) || npoints < 0 || nbumps < 0 || (npoints && !points) || (nbumps && !bumps))
         FAIL(HDD_ERR_INVALID_ARG, "bad rhs arguments");
@@ -1056,6 +1100,7 @@ hdd_status hdd_build_rhs(hdd_ctx *ctx, int npoints, const double *points, int nb
 
 hdd_status hdd_apply_A(hdd_ctx *ctx, const void *x_dev, void *y_dev, int nrhs, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->assembled) FAIL(HDD_ERR_STATE, "hdd_assemble first");
     if (!x_dev || !y_dev || nrhs < 1 || x_dev == y_dev || !aligned16(x_dev) || !aligned16(y_dev))
         FAIL(HDD_ERR_INVALID_ARG, "bad apply_A arguments");
@@ -1068,6 +1113,7 @@ hdd_status hdd_apply_A(hdd_ctx *ctx, const void *x_dev, void *y_dev, int nrhs, v
 
 hdd_status hdd_setup_dd(hdd_ctx *ctx, const hdd_dd_params *p) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->assembled) FAIL(HDD_ERR_STATE, "hdd_assemble first");
     if (!p) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
     if (p->Sx < 1 || p->Sy < 1 || p->Sx > 4096 || p->Sy > 4096 || p->overlap < 1)
@@ -1134,6 +1180,7 @@ int hdd_num_subdomains(const hdd_ctx *ctx) { return ctx && ctx->dd ? (int)ctx->s
 hdd_status hdd_get_subdomain(const hdd_ctx *ctx_, int s, int *info) {
     hdd_ctx *ctx = const_cast<hdd_ctx *>(ctx_);
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     if (s < 0 || s >= (int)ctx->subs.size() || !info) FAIL(HDD_ERR_INVALID_ARG, "bad subdomain index");
     const SubBox &b = ctx->subs[s];
@@ -1145,6 +1192,7 @@ hdd_status hdd_get_subdomain(const hdd_ctx *ctx_, int s, int *info) {
 hdd_status hdd_get_offsets(const hdd_ctx *ctx_, long long *fine_off, long long *coarse_off) {
     hdd_ctx *ctx = const_cast<hdd_ctx *>(ctx_);
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     if (fine_off) std::copy(ctx->foffs.begin(), ctx->foffs.end(), fine_off);
     if (coarse_off) std::copy(ctx->coffs.begin(), ctx->coffs.end(), coarse_off);
@@ -1153,6 +1201,7 @@ hdd_status hdd_get_offsets(const hdd_ctx *ctx_, long long *fine_off, long long *
 
 hdd_status hdd_setup_deflation(hdd_ctx *ctx, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     CK(cudaSetDevice(ctx->device));
     return build_factors(ctx, ctx->E, true, (cudaStream_t)stream);
@@ -1160,6 +1209,7 @@ hdd_status hdd_setup_deflation(hdd_ctx *ctx, void *stream) {
 
 hdd_status hdd_setup_exact(hdd_ctx *ctx, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     CK(cudaSetDevice(ctx->device));
     return build_factors(ctx, ctx->Aex, false, (cudaStream_t)stream);
@@ -1168,6 +1218,7 @@ hdd_status hdd_setup_exact(hdd_ctx *ctx, void *stream) {
 hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev, const hdd_solve_params *prm,
                          int *inner_its, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     if (!v_dev || !z_dev || v_dev == z_dev || !aligned16(v_dev) || !aligned16(z_dev))
         FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
@@ -1185,6 +1236,7 @@ hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev, const hdd
 hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_solve_params *prm,
                      hdd_solve_stats *stats, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     if (!f_dev || !x_dev || f_dev == x_dev || !aligned16(f_dev) || !aligned16(x_dev))
         FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
@@ -1392,6 +1444,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
 hdd_status hdd_autotune(hdd_ctx *ctx, const hdd_solve_params *prm, void *stream, int *fine_rows,
                         int *coarse_rows, double *best_ms) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     hdd_status st = check_solve_params(ctx, prm);
     if (st != HDD_OK) return st;
@@ -1450,6 +1503,7 @@ hdd_status hdd_autotune(hdd_ctx *ctx, const hdd_solve_params *prm, void *stream,
 
 hdd_status hdd_setup_batch(hdd_ctx *ctx, int nrhs) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     if (nrhs < 1 || nrhs > 4096) FAIL(HDD_ERR_INVALID_ARG, "nrhs must be in 1..4096");
     CK(cudaSetDevice(ctx->device));
@@ -1460,6 +1514,7 @@ int hdd_num_rhs(const hdd_ctx *ctx) { return ctx && ctx->dd ? ctx->nrhs : 0; }
 
 hdd_status hdd_profile(hdd_ctx *ctx, int enable) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     CK(cudaSetDevice(ctx->device));
     CK(cudaDeviceSynchronize());
     ctx->prof.harvest();
@@ -1472,6 +1527,7 @@ int hdd_profile_count(const hdd_ctx *ctx) { return ctx ? (int)NFAM : 0; }
 
 hdd_status hdd_profile_get(hdd_ctx *ctx, int i, hdd_kernel_stat *out) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (i < 0 || i >= NFAM || !out) FAIL(HDD_ERR_INVALID_ARG, "bad profile index");
     CK(cudaSetDevice(ctx->device));
     CK(cudaDeviceSynchronize());
@@ -1492,6 +1548,7 @@ int hdd_cnn_num_params(void) { return CNN_NPARAM; }
 
 hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     if (ctx->bc) FAIL(HDD_ERR_INVALID_ARG, "the learned warm start serves the Dirichlet problem only");
     if (!params) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
@@ -1515,6 +1572,7 @@ hdd_status hdd_cnn_set_params(hdd_ctx *ctx, const float *params) {
 
 hdd_status hdd_warmstart_load(hdd_ctx *ctx, const char *path) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!path) FAIL(HDD_ERR_INVALID_ARG, "path is NULL");
     FILE *fh = std::fopen(path, "rb");
     if (!fh) FAIL(HDD_ERR_INVALID_ARG, "cannot open %s", path);
@@ -1541,6 +1599,7 @@ hdd_status hdd_warmstart_load(hdd_ctx *ctx, const char *path) {
 
 hdd_status hdd_warmstart_save(hdd_ctx *ctx, const char *path) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!path) FAIL(HDD_ERR_INVALID_ARG, "path is NULL");
     std::vector<float> prm(CNN_NPARAM);
     hdd_status st = hdd_cnn_get_params(ctx, prm.data());
@@ -1563,6 +1622,7 @@ hdd_status hdd_warmstart_save(hdd_ctx *ctx, const char *path) {
 
 hdd_status hdd_cnn_get_params(hdd_ctx *ctx, float *params) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
     if (!params) FAIL(HDD_ERR_INVALID_ARG, "params is NULL");
     CK(cudaSetDevice(ctx->device));
@@ -1572,6 +1632,7 @@ hdd_status hdd_cnn_get_params(hdd_ctx *ctx, float *params) {
 
 hdd_status hdd_cnn_forward(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
     if (!f_dev || !x0_dev || f_dev == x0_dev || !aligned16(f_dev) || !aligned16(x0_dev))
         FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
@@ -1589,6 +1650,7 @@ hdd_status hdd_cnn_forward(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *
 
 hdd_status hdd_cnn_infer(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
     if (!f_dev || !x0_dev || f_dev == x0_dev || !aligned16(f_dev) || !aligned16(x0_dev))
         FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
@@ -1606,6 +1668,7 @@ hdd_status hdd_cnn_infer(hdd_ctx *ctx, const void *f_dev, void *x0_dev, void *st
 
 hdd_status hdd_cnn_loss_grad(hdd_ctx *ctx, const void *f_dev, double *loss, float *grad) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
     if (!f_dev || !aligned16(f_dev)) FAIL(HDD_ERR_INVALID_ARG, "bad vector argument");
     CK(cudaSetDevice(ctx->device));
@@ -1618,6 +1681,7 @@ hdd_status hdd_cnn_loss_grad(hdd_ctx *ctx, const void *f_dev, double *loss, floa
 
 hdd_status hdd_cnn_train_step(hdd_ctx *ctx, const void *f_dev, float lr, double *loss, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->cnn.ready) FAIL(HDD_ERR_STATE, "hdd_cnn_set_params first");
     if (!f_dev || !aligned16(f_dev) || !(lr > 0)) FAIL(HDD_ERR_INVALID_ARG, "bad arguments");
     CK(cudaSetDevice(ctx->device));
@@ -1635,6 +1699,7 @@ hdd_status hdd_cnn_train_step(hdd_ctx *ctx, const void *f_dev, float lr, double 
 
 hdd_status hdd_get_outer_vector(hdd_ctx *ctx, int j, void *v_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->ow.V.p) FAIL(HDD_ERR_STATE, "no solve has run");
     if (j < 0 || !v_dev || !aligned16(v_dev)) FAIL(HDD_ERR_INVALID_ARG, "bad arguments");
     const size_t bytes = (size_t)ctx->nrhs * ctx->nglob * sizeof(double2);
@@ -1647,6 +1712,7 @@ hdd_status hdd_get_outer_vector(hdd_ctx *ctx, int j, void *v_dev, void *stream) 
 
 hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     if (!ctx->E.ready) FAIL(HDD_ERR_STATE, "hdd_setup_deflation first");
     if (!in_dev || !out_dev || in_dev == out_dev || !aligned16(in_dev) || !aligned16(out_dev))
@@ -1678,6 +1744,7 @@ hdd_status hdd_apply_PA_noalloc(hdd_ctx *ctx, const void *in_dev, void *out_dev,
 
 hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void *out_dev, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
     if (!ctx->dd) FAIL(HDD_ERR_STATE, "hdd_setup_dd first");
     if (op < 0 || op > 6 || (prec != 64 && prec != 128) || !in_dev || !out_dev || in_dev == out_dev ||
         !aligned16(in_dev) || !aligned16(out_dev))

@@ -200,10 +200,17 @@ k_conv_tc(const Task *__restrict__ tasks, const int2 *__restrict__ tct, int ntct
         __syncthreads();            // TMEM read and window consumed before the next tile reuses them
     }
     if (!ok) {
-        if (threadIdx.x == 0) atomicExch(err, 1);
-        // drain: copies and a committed MMA not yet seen complete, each with a bounded wait
-        if (ld_pending) umma::mbar_wait(&bar_ld, ldpar, TC_WAIT);
-        if (mma_pending) umma::mbar_wait(&bar_mma, mmapar, TC_WAIT);
+        // drain: copies and a committed MMA not yet seen complete, each with a bounded wait.
+        // Flag 1: a wait gave up and the drain then saw everything in flight complete (the
+        // context stays usable).  Flag 2: the drain gave up as well, so a bulk copy or an MMA may
+        // still be writing this CTA's shared memory or TMEM after the CTA frees them and exits;
+        // nothing bounds what that write reaches, so the host treats flag 2 as fatal for the CUDA
+        // context (the library refuses further work on it, the caller must discard the context).
+        bool drained = true;
+        if (ld_pending) drained &= umma::mbar_wait(&bar_ld, ldpar, TC_WAIT);
+        if (mma_pending) drained &= umma::mbar_wait(&bar_mma, mmapar, TC_WAIT);
+        drained = __syncthreads_and(drained);
+        if (threadIdx.x == 0) atomicMax(err, drained ? 1 : 2);
     }
     umma::fence_before_sync();
     __syncthreads();

@@ -9,11 +9,16 @@ being the inner iterations per subdomain solve.  The paper's own numbers come fr
 with an unstated restart length and partition of unity, so they are trends to compare with, not
 values to reproduce.
 
+--c2 runs the k=100 workload instead (N=320, 4x4 subdomains, overlap 2, centre point source plus
+a seeded Gaussian bump) with inner tolerances 1e-1, 1e-2, 1e-4 and exact (banded LU) subdomain
+solves in the plain FP64 form (complex128 inner, FP64 outer), timing each solve.
+
 With --bc 1 the same settings run with the impedance (Sommerfeld) condition du/dn - iku = 0 on
 all four sides instead of u = 0; the paper states the solver suits that problem (§3) but prints
 no iteration counts for it.
 
     python -m paper_2103_17081_gb300.sweep [--ppwl 10 20] [--k 20 40 80 160] [--bc 0|1] [--json out.jsonl]
+    python -m paper_2103_17081_gb300.sweep --c2
 """
 from __future__ import annotations
 
@@ -66,6 +71,36 @@ def run(ks, ppwls, tols, subs, inner_prec=128, log=print, bc=0):
     return rows
 
 
+C2_TOLS = [("1e-1", 1e-1), ("1e-2", 1e-2), ("1e-4", 1e-4), ("LU", 0.0)]
+
+
+def c2_sweep(solver, f, log=print, reps: int = 1):
+    """Inner-tolerance sweep of one solver (set up with exact local factors as well): each
+    setting of C2_TOLS solved in the plain FP64 form, after one untimed warm-up solve, timed with
+    CUDA events on the current stream (mean of `reps`).  Rows carry the last solution as "x"."""
+    import torch
+
+    rows = []
+    for name, tol in C2_TOLS:
+        kw = dict(outer_tol=1e-6, inner_tol=tol, inner_prec=128, outer_reorth32=0, raise_on_error=False)
+        x, st = solver.solve(f, **kw)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, st = solver.solve(f, out=x, **kw)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        r = {"inner": name, "outer_its": st["outer_its"], "inner_avg": round(st["inner_its_avg"], 2),
+             "rel_res": st["rel_res_true"], "status": st["status_code"], "s": round(sum(ts) / len(ts), 4),
+             "x": x}
+        rows.append(r)
+        if log:
+            log(json.dumps({k: v for k, v in r.items() if k != "x"}))
+    return rows
+
+
 def table(rows, inner):
     """Markdown table of one inner setting, rows (ppwl, k), columns N."""
     sel = [r for r in rows if r["inner"] == inner]
@@ -97,7 +132,18 @@ def main(argv=None):
     ap.add_argument("--bc", type=int, default=0, choices=[0, 1],
                     help="0: u = 0 on the boundary (the paper's tables); 1: impedance condition")
     ap.add_argument("--json", default=None, help="also write every row as a JSON line to this file")
+    ap.add_argument("--c2", action="store_true",
+                    help="the k=100 inner-tolerance sweep {1e-1, 1e-2, 1e-4, exact} instead")
+    ap.add_argument("--reps", type=int, default=3, help="timed solves per setting of --c2")
     a = ap.parse_args(argv)
+    if a.c2:
+        import workloads as W
+
+        from .solver import Solver
+        w = W.make("k100")
+        s = Solver.from_workload(w, exact=True)
+        c2_sweep(s, s.build_rhs(w.rhs[0]), reps=a.reps)
+        return 0
     tols = [(n, t) for n, t in TOLS if n in a.inner]
     rows = run(a.k, a.ppwl, tols, a.subdomains, a.prec, bc=a.bc)
     if a.json:

@@ -4,7 +4,9 @@ tighter where the arithmetic is a single stencil or gather); complex64 inner ari
 FP32 rounding amplified by the local condition number (1e-4 relative on a local solve); whole
 solves must satisfy the outer tolerance on the oracle's own assembled matrix and match the oracle
 solution to 1e-5 relative (complex64 inner) or 1e-6 (complex128 inner) with outer iteration counts
-within +10%.
+within +10%.  At the loose bars (1e-4 for complex64 operators and RAS applications, 1e-5 for whole
+solves) the check is both normwise and entrywise: every entry's error is bounded by the bar times
+the largest entry of the oracle's vector (_close).
 """
 import numpy as np
 import pytest
@@ -28,6 +30,16 @@ def _to_dev(a):
 
 def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _maxrel(a, b):
+    """Largest entrywise error relative to the largest entry of b (a bar on every node)."""
+    return float(np.max(np.abs(a - b))) / max(float(np.max(np.abs(b))), 1e-300)
+
+
+def _close(a, b, tol):
+    """Normwise and entrywise (relative to max|b|) agreement within tol."""
+    return _rel(a, b) < tol and _maxrel(a, b) < tol
 
 
 def _pair(oracle_mod, w, exact=False):
@@ -84,7 +96,10 @@ def test_local_operators(oracle_mod, w, prec):
         assert _rel(outs["Zt"][Cc], p.sub_apply_Zt(q, xf[F])) < tol
         assert _rel(outs["R"][F], p.restrict(q, xg)) == 0.0 or prec == 64
         # P A amplifies rounding by the local deflated conditioning
-        assert _rel(outs["PA"][F], p.sub_apply_PA(q, xf[F])) < (1e-11 if prec == 128 else 1e-4)
+        if prec == 128:
+            assert _rel(outs["PA"][F], p.sub_apply_PA(q, xf[F])) < 1e-11
+        else:
+            assert _close(outs["PA"][F], p.sub_apply_PA(q, xf[F]), 1e-4)
         if prec == 128:
             assert _rel(outs["Einv"][Cc], p.coarse_solve(q, xc[Cc])) < 1e-11
             assert _rel(outs["Ainv"][F], p.sub_solve_exact(q, xf[F])) < 1e-10
@@ -106,7 +121,7 @@ def test_ras_apply_matches_oracle(oracle_mod, prec, tol):
         assert _rel(zg, zo) < 1e-9
     else:
         assert abs(sum(its) - sto["inner_its_total"]) <= max(2, 0.1 * sto["inner_its_total"])
-        assert _rel(zg, zo) < max(1e-4, 10 * tol * 1e-3)
+        assert _close(zg, zo, max(1e-4, 10 * tol * 1e-3))
 
 
 def test_autotuned_tiles_keep_results(oracle_mod):
@@ -145,7 +160,7 @@ def test_autotuned_batched_solve_matches_oracle(oracle_mod):
     n = sb.n
     for r, spec in enumerate(specs):
         xo, _ = p.solve(p.rhs(spec))
-        assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), xo) < 1e-5
+        assert _close(xb[r * n:(r + 1) * n].cpu().numpy(), xo, 1e-5)
     assert stb["rel_res_true"] <= 1e-6 * 1.0001
 
 
@@ -188,7 +203,7 @@ def test_tiny_solve_matches_oracle(oracle_mod, prec):
     assert np.linalg.norm(fo - A @ xg) <= 1e-6 * np.linalg.norm(fo) * 1.0001
     # both iterates satisfy the outer tolerance; they differ by the stopping point (one
     # iteration apart at most for complex128) amplified by the conditioning of A
-    assert _rel(xg, xo) < 1e-5
+    assert _close(xg, xo, 1e-5)
     if prec == 128:
         assert abs(st["outer_its"] - so["outer_its"]) <= 1
         hg, ho = np.array(st["res_history"]), np.array(so["res_history"])
@@ -196,9 +211,7 @@ def test_tiny_solve_matches_oracle(oracle_mod, prec):
         n = min(len(hg), len(ho)) - 2
         assert np.allclose(hg[:n], ho[:n], rtol=1e-2, atol=0), np.max(np.abs(hg[:n] / ho[:n] - 1))
     else:
-        # this workload is specified in complex128; complex64 inner solves are allowed a wider
-        # margin here (at k=100 and k=200 their outer counts match the oracle within 1)
-        assert st["outer_its"] <= 1.2 * so["outer_its"] + 1
+        assert st["outer_its"] <= 1.1 * so["outer_its"] + 1
     assert np.max(np.abs(xg.imag)) == 0.0        # real data stays real (complex storage)
 
 
@@ -209,7 +222,7 @@ def test_exact_inner_solve_matches_oracle(oracle_mod):
     x, st = s.solve(f, inner_tol=0.0, inner_prec=128)
     xo, so = p.solve(p.rhs(w.rhs[0]), inner_tol=0.0)
     assert abs(st["outer_its"] - so["outer_its"]) <= 1
-    assert _rel(x.cpu().numpy(), xo) < 1e-5
+    assert _close(x.cpu().numpy(), xo, 1e-5)
 
 
 @pytest.mark.parametrize("prec", [128, 64])
@@ -224,7 +237,7 @@ def test_k100_solve_matches_oracle(oracle_mod, prec):
     xg = x.cpu().numpy()
     assert np.linalg.norm(fo - p.matrix("A") @ xg) <= 1e-6 * np.linalg.norm(fo) * 1.0001
     assert st["outer_its"] <= 1.1 * so["outer_its"]
-    assert _rel(xg, xo) < 1e-5
+    assert _close(xg, xo, 1e-5)
     if prec == 128:
         assert abs(st["outer_its"] - so["outer_its"]) <= 1
 
@@ -263,7 +276,7 @@ def test_k200_ras_apply_full_size(oracle_mod):
     for prec, bound in ((128, 1e-9), (64, 1e-4)):
         zg, its = s.ras_apply(_to_dev(v), inner_tol=1e-2, inner_prec=prec)
         zo, sto = p.ras_apply(v, 1e-2)
-        assert _rel(zg.cpu().numpy(), zo) < bound
+        assert _close(zg.cpu().numpy(), zo, bound)
         if prec == 128:
             assert sum(its) == sto["inner_its_total"]
 
@@ -297,26 +310,30 @@ def test_errors_are_status_codes(oracle_mod):
 @pytest.mark.parametrize("prec", [64, 128])
 def test_k200_full_solve_against_stored_oracle(prec):
     """k=200, N=640, 8x8 subdomains (the bench workload), whole solve at outer tolerance 1e-6,
-    compared with the oracle's solve stored by tests/golden/make_k200_reference.py: outer
-    iterations within +10 %, solution at 256 seeded nodes within 1e-5 relative, same ||x||."""
+    compared at all 408,321 nodes with the oracle's solution stored by
+    tests/golden/make_k200_reference.py (Re x as float64; Im x is exactly zero): outer iterations
+    within +10 %, every node within 1e-5 of max|x|, and the whole vector within 1e-5 relative in
+    the 2-norm."""
     import json
     import os
     torch = _torch()
     from paper_2103_17081_gb300 import Solver
-    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "k200_oracle.json")))
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    ref = json.load(open(os.path.join(gold, "k200_oracle.json")))
+    xr = np.load(os.path.join(gold, "k200_oracle_x.npy"))
     w = W.make("k200")
+    assert xr.shape == ((w.N - 1) ** 2,)
     s = Solver.from_workload(w)
     f = s.build_rhs(w.rhs[0])
     x, st = s.solve(f, outer_tol=w.outer_tol, inner_tol=w.inner_tol, inner_prec=prec)
     r = f - s.apply_A(x)
     assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(f)) <= 1.0001e-6
     assert st["outer_its"] <= 1.1 * ref["outer_its"]
-    idx = torch.tensor(ref["sample_index"], device=x.device)
-    xs = x[idx].cpu().numpy()
-    xr = np.array(ref["sample_re"])
-    assert np.linalg.norm(xs - xr) <= 1e-5 * np.linalg.norm(xr)
-    assert abs(float(torch.linalg.vector_norm(x)) - ref["x_norm2"]) <= 1e-5 * ref["x_norm2"]
-    assert float(x.imag.abs().max()) == 0.0
+    xg = x.cpu().numpy()
+    assert float(np.max(np.abs(xg.imag))) == 0.0
+    assert _close(xg.real, xr, 1e-5), (_rel(xg.real, xr), _maxrel(xg.real, xr))
+    idx = np.array(ref["sample_index"])
+    assert np.array_equal(xr[idx], np.array(ref["sample_re"]))
 
 
 def _specs(n, seed):
@@ -346,7 +363,7 @@ def test_batched_rhs_match_single_rhs_runs(oracle_mod, prec):
         x1, st1 = s1.solve(fr, inner_prec=prec)
         assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), x1.cpu().numpy()) <= 1e-12
         xo, so = p.solve(p.rhs(spec))
-        assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), xo) < 1e-5
+        assert _close(xb[r * n:(r + 1) * n].cpu().numpy(), xo, 1e-5)
         assert st1["outer_its"] <= 1.1 * so["outer_its"] + 1
     assert stb["rel_res_true"] <= 1e-6 * 1.0001
 
@@ -369,6 +386,6 @@ def test_k400x32_batched_ras_apply_full_size(oracle_mod):
     p = oracle_mod.from_workload(w)
     for r in (0, 21):
         zo, sto = p.ras_apply(v[r * n:(r + 1) * n].cpu().numpy(), 1e-2)
-        assert _rel(z[r * n:(r + 1) * n].cpu().numpy(), zo) < 1e-4
+        assert _close(z[r * n:(r + 1) * n].cpu().numpy(), zo, 1e-4)
         got = sum(its[r * s.nsub:(r + 1) * s.nsub])
         assert abs(got - sto["inner_its_total"]) <= 0.1 * sto["inner_its_total"]

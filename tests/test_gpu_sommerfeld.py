@@ -34,6 +34,16 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def _maxrel(a, b):
+    """Largest entrywise error relative to the largest entry of b (a bar on every node)."""
+    return float(np.max(np.abs(a - b))) / max(float(np.max(np.abs(b))), 1e-300)
+
+
+def _close(a, b, tol):
+    """Normwise and entrywise (relative to max|b|) agreement within tol."""
+    return _rel(a, b) < tol and _maxrel(a, b) < tol
+
+
 def _pair(oracle_mod, w, exact=False):
     from paper_2103_17081_gb300 import Solver
     _torch()
@@ -100,7 +110,10 @@ def test_local_operators(oracle_mod, w, prec):
         assert _rel(outs["Z"][F], p.sub_apply_Z(q, xc[Cc])) < tol
         assert _rel(outs["Zt"][Cc], p.sub_apply_Zt(q, xf[F])) < tol
         assert _rel(outs["R"][F], p.restrict(q, xg)) == 0.0 or prec == 64
-        assert _rel(outs["PA"][F], p.sub_apply_PA(q, xf[F])) < (1e-11 if prec == 128 else 1e-4)
+        if prec == 128:
+            assert _rel(outs["PA"][F], p.sub_apply_PA(q, xf[F])) < 1e-11
+        else:
+            assert _close(outs["PA"][F], p.sub_apply_PA(q, xf[F]), 1e-4)
         if prec == 128:
             assert _rel(outs["Einv"][Cc], p.coarse_solve(q, xc[Cc])) < 1e-11
             assert _rel(outs["Ainv"][F], p.sub_solve_exact(q, xf[F])) < 1e-10
@@ -120,7 +133,7 @@ def test_ras_apply_matches_oracle(oracle_mod, prec, tol):
         assert _rel(zg, zo) < 1e-9
     else:
         assert abs(sum(its) - sto["inner_its_total"]) <= max(2, 0.1 * sto["inner_its_total"])
-        assert _rel(zg, zo) < 1e-4
+        assert _close(zg, zo, 1e-4)
 
 
 @pytest.mark.parametrize("prec", [128, 64])
@@ -133,8 +146,8 @@ def test_solve_matches_oracle(oracle_mod, prec):
     xg, stg = s.solve(s.build_rhs(w.rhs[0]), outer_tol=1e-6, inner_tol=1e-2, inner_prec=prec)
     xg = xg.cpu().numpy()
     A = p.matrix("A")
-    assert np.linalg.norm(f - A @ xg) <= 1e-6 * np.linalg.norm(f) * 1.01
-    assert _rel(xg, xo) < (1e-6 if prec == 128 else 1e-5)
+    assert np.linalg.norm(f - A @ xg) <= 1e-6 * np.linalg.norm(f) * 1.0001
+    assert _close(xg, xo, 1e-6 if prec == 128 else 1e-5)
     assert abs(stg["outer_its"] - sto["outer_its"]) <= 0.1 * sto["outer_its"] + 1
     assert np.linalg.norm(xg.imag) > 0.1 * np.linalg.norm(xg)        # a radiating solution
 
@@ -158,8 +171,8 @@ def test_k60_solve_matches_oracle(oracle_mod):
     xo, sto = p.solve(f, outer_tol=1e-6, inner_tol=1e-2)
     xg, stg = s.solve(s.build_rhs(w.rhs[0]), outer_tol=1e-6, inner_tol=1e-2, inner_prec=64)
     xg = xg.cpu().numpy()
-    assert np.linalg.norm(f - p.matrix("A") @ xg) <= 1e-6 * np.linalg.norm(f) * 1.01
-    assert _rel(xg, xo) < 1e-5
+    assert np.linalg.norm(f - p.matrix("A") @ xg) <= 1e-6 * np.linalg.norm(f) * 1.0001
+    assert _close(xg, xo, 1e-5)
     assert abs(stg["outer_its"] - sto["outer_its"]) <= 0.1 * sto["outer_its"] + 1
 
 
@@ -181,8 +194,8 @@ def test_k100_solve_matches_oracle(oracle_mod):
     xo, sto = p.solve(f, outer_tol=1e-6, inner_tol=1e-2)
     xg, stg = s.solve(s.build_rhs(w.rhs[0]), outer_tol=1e-6, inner_tol=1e-2, inner_prec=64)
     xg = xg.cpu().numpy()
-    assert np.linalg.norm(f - p.matrix("A") @ xg) <= 1e-6 * np.linalg.norm(f) * 1.01
-    assert _rel(xg, xo) < 1e-5
+    assert np.linalg.norm(f - p.matrix("A") @ xg) <= 1e-6 * np.linalg.norm(f) * 1.0001
+    assert _close(xg, xo, 1e-5)
     assert abs(stg["outer_its"] - sto["outer_its"]) <= 0.1 * sto["outer_its"] + 1
 
 
@@ -209,5 +222,29 @@ def test_batched_rhs_match_single_rhs_runs(oracle_mod):
         x1, st1 = s1.solve(fr, inner_prec=64)
         assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), x1.cpu().numpy()) <= 1e-12
         xo, so = p.solve(p.rhs(spec))
-        assert _rel(xb[r * n:(r + 1) * n].cpu().numpy(), xo) < 1e-5
+        assert _close(xb[r * n:(r + 1) * n].cpu().numpy(), xo, 1e-5)
     assert stb["rel_res_true"] <= 1e-6 * 1.0001
+
+
+def test_k200s_full_solve_against_stored_oracle():
+    """The k=200 impedance workload (N=640, (N+1)² = 410,881 unknowns, 8x8 subdomains, the k200
+    load), complex64 inner solves to 1e-2, outer FGMRES to 1e-6, against the oracle's solution
+    stored by tests/golden/make_k200_reference.py (complex128): every node within 1e-5 of max|x|,
+    the whole vector within 1e-5 relative in the 2-norm, outer iterations within +10 %."""
+    import json
+    import os
+    torch = _torch()
+    from paper_2103_17081_gb300 import Solver
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    ref = json.load(open(os.path.join(gold, "k200s_oracle.json")))
+    xr = np.load(os.path.join(gold, "k200s_oracle_x.npy"))
+    w = W.make("k200s")
+    assert xr.shape == ((w.N + 1) ** 2,)
+    s = Solver.from_workload(w)
+    f = s.build_rhs(w.rhs[0])
+    x, st = s.solve(f, outer_tol=w.outer_tol, inner_tol=w.inner_tol, inner_prec=64)
+    r = f - s.apply_A(x)
+    assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(f)) <= 1.0001e-6
+    assert st["outer_its"] <= 1.1 * ref["outer_its"]
+    xg = x.cpu().numpy()
+    assert _close(xg, xr, 1e-5), (_rel(xg, xr), _maxrel(xg, xr))
