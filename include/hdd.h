@@ -312,6 +312,18 @@ hdd_status hdd_profile_get(hdd_ctx *ctx, int i, hdd_kernel_stat *out);
 /* Kernel launches made by this context since creation (counted whether or not profiling is on). */
 long long hdd_launch_count(const hdd_ctx *ctx);
 
+/* Implementation choices of one context (no counterpart in the paper; every choice computes   */
+/* the same method).  HDD_OPT_COARSE_LOOKAHEAD (1): the FP64 block solves of E_j (Eq. 4) and    */
+/* A_j use the look-ahead kernel (value 1, the default) or the plain blocked kernel (0); both   */
+/* apply the same precomputed block operators, summed in a different fixed order.              */
+/* HDD_OPT_FUSED_INNER (2): each inner Arnoldi step runs as one cluster-resident kernel per     */
+/* step between the coarse solves (1, the default, where every box fits its plan) or as the    */
+/* separate stencil / CGS / Givens kernels (0).  HDD_ERR_INVALID_ARG for an unknown key or a   */
+/* value other than 0 or 1.  Takes effect from the next call that solves.                      */
+#define HDD_OPT_COARSE_LOOKAHEAD 1
+#define HDD_OPT_FUSED_INNER 2
+hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Deflated operator without device allocation.                                             */
 /*                                                                                          */

@@ -20,7 +20,7 @@ SYMBOLS = ["hdd_create", "hdd_destroy", "hdd_status_str", "hdd_last_error", "hdd
            "hdd_warmstart_load", "hdd_warmstart_save",
            "hdd_num_rhs", "hdd_cnn_num_params", "hdd_cnn_set_params", "hdd_cnn_get_params",
            "hdd_cnn_forward", "hdd_cnn_infer", "hdd_cnn_loss_grad", "hdd_cnn_train_step", "hdd_get_outer_vector",
-           "hdd_stencil_rows"]
+           "hdd_stencil_rows", "hdd_set_option"]
 
 
 def status_name(code: int) -> str:
@@ -147,5 +147,7 @@ def lib(build_if_missing: bool = True):
     L.hdd_get_outer_vector.restype = I
     L.hdd_apply_PA_noalloc.argtypes = [P, V, V, V]
     L.hdd_apply_PA_noalloc.restype = I
+    L.hdd_set_option.argtypes = [P, I, I]
+    L.hdd_set_option.restype = I
     _lib = L
     return L

@@ -56,12 +56,12 @@ template <typename R> struct InnerWork {   // inner GMRES buffers for one precis
 
 // Kernel families timed by the profiler (CUDA events around every launch on the launching
 // stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
-enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, NFAM };
+enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, F_STEP, NFAM };
 const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
                               "local_cgs2_update", "local_givens_normalize", "local_misc",
                               "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn",
-                              "outer_reorth_fp32"};
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0};
+                              "outer_reorth_fp32", "local_arnoldi_step"};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0};
 
 struct Prof {
     bool on = false;
@@ -155,6 +155,10 @@ struct hdd_ctx {
     std::vector<double> hist;
     std::vector<int> h_its;
     Prof prof;
+    int coarse_la = 1;                         // HDD_OPT_COARSE_LOOKAHEAD
+    int fused_inner = 1;                       // HDD_OPT_FUSED_INNER
+    int step_C[2] = {-1, -1};                  // fused-step cluster size per inner precision (0: off, -1: unplanned)
+    size_t step_smem[2] = {0, 0};
     bool poisoned = false;                     // a device wait gave up with work in flight
     ~hdd_ctx() { if (h_counter) cudaFreeHost(h_counter); }
 };
@@ -372,8 +376,10 @@ void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *ou
     // 2 flops per FMA, over 2 real columns (or the one column of a real-equivalent factor)
     fl = (F.re2 ? 2.0 : 4.0) * fl * (nact < 0 ? 1.0 : (double)nact / nt);
     Launch L(ctx, F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
+    BlockSolveCfg cfg = F.cfg;
+    cfg.lookahead = ctx->coarse_la;
     launch_block_solve(ctx->d_tasks.as<Task>(), nt, F.table.as<BlockFactor>(), F.M.as<double>(),
-                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, F.cfg, F.re2 ? 1 : 0, s);
+                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, cfg, F.re2 ? 1 : 0, s);
 }
 
 // ---- learned warm start ---------------------------------------------------------------------
@@ -598,6 +604,35 @@ template <typename R> InnerState<R> inner_state(InnerWork<R> &W) {
     return S;
 }
 
+// Cluster size of the one-launch Arnoldi step for the current task layout: the smallest power of
+// two C <= 8 with ceil(ny/C)·nx <= STEP_ROWS_MAX nodes per CTA for every box, raised (up to 8)
+// until the tasks fill about two CTAs per SM; 0 (the separate kernels serve) if no C fits or the
+// device cannot co-schedule such a cluster.
+template <typename R> int step_plan(hdd_ctx *ctx) {
+    const int pi = sizeof(R) == 4 ? 0 : 1;
+    if (ctx->step_C[pi] >= 0) return ctx->step_C[pi];
+    int max_ny = 0;
+    for (const SubBox &b : ctx->subs) max_ny = std::max(max_ny, b.ny);
+    int C = 0;
+    for (int c = 1; c <= 8; c *= 2) {
+        bool ok = true;
+        for (const SubBox &b : ctx->subs)
+            if ((long long)((b.ny + c - 1) / c) * b.nx > STEP_ROWS_MAX) { ok = false; break; }
+        if (ok) { C = c; break; }
+    }
+    if (C > 0) {
+        int dev = 0, nsm = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long long nt = (long long)ctx->h_tasks.size();
+        while (C < 8 && nt * C < 2LL * nsm) C *= 2;
+        const size_t sm = step_smem_bytes(ctx->max_nx, max_ny, C, (int)sizeof(c2<R>));
+        if (sm > 160 * 1024 || arnoldi_step_max_cluster<R>(sm, C) < 1) C = 0;
+        ctx->step_smem[pi] = sm;
+    }
+    ctx->step_C[pi] = C;
+    return C;
+}
+
 // All local solves of one RAS application (Eq. 3): z = Σ_j R_jᵀ D_j ũ_j, ũ_j from deflated
 // GMRES on P_j A_j ũ = P_j R_j v (Eq. 4), then completed by ũ += Q_j (f̃ - A_j ũ).
 // mask (may be null = every task): tasks whose RHS takes part; the others are left untouched.
@@ -663,25 +698,41 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     int cur = 0, nact = 0;
     st = read_counter(ctx, s, &nact);
     if (st != HDD_OK) return st;
+    // one launch per Arnoldi step between the coarse solves (cluster per task), or the separate
+    // stencil, CGS and Givens kernels
+    const int stepC = ctx->fused_inner ? step_plan<R>(ctx) : 0;
+    const size_t step_sm = ctx->step_smem[sizeof(R) == 4 ? 0 : 1];
     for (;;) {
+        if (stepC > 0 && nact > 0)                        // y = Zᵀ A v_0 of this cycle's tasks
+            KL(F_ZT, (double)nact / nt * (ld * cs + ldc * 16), 0, launch_zt<R>(a, V, y, 1, act[cur], s));
         for (int i = 0; i < RST && nact > 0; i++) {
             const int *ain = act[cur];
             int *aout = act[cur ^ 1];
             c2<R> *vi = V + (long long)i * ld, *vn = V + (long long)(i + 1) * ld;
             const double fa = (double)nact / nt;            // fraction of tasks still iterating
-            KL(F_ZT, fa * (ld * cs + ldc * 16), 0, launch_zt<R>(a, vi, y, 1, ain, s));
             double2 *si = sc + (long long)(i + 1) * ldc;  // E⁻¹ Zᵀ A v_i, kept for the completion
-            band_solve(ctx, ctx->E, y, si, false, ain, s, nact);
-            KL(F_PS, fa * ((i + 3) * ld * cs + ldc * 16), fa * 8.0 * (i + 1) * ld,
-               launch_prolong_stencil<R>(a, 0, vi, si, vn, V, i + 1, p1, ain, s));
-            KL(F_CGS, fa * (i + 3) * ld * cs, fa * 16.0 * (i + 1) * ld,
-               launch_cgs_update<R>(a, 2, vn, V, i + 1, p1, p2, ain, s));
-            KL(F_CGS, fa * (i + 3) * ld * cs, fa * 8.0 * (i + 1) * ld,
-               launch_cgs_update<R>(a, 3, vn, V, i + 1, p2, p3, ain, s));
-            CK(cudaMemsetAsync(aout, 0, nt * sizeof(int), s));
-            CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
-            KL(F_GIVENS, fa * 2 * ld * cs, 0,
-               launch_givens_normalize<R>(a, S, RST, i, vn, p1, p2, p3, ain, aout, cnt, tol, maxit, s));
+            if (stepC > 0) {
+                band_solve(ctx, ctx->E, y, si, false, ain, s, nact);
+                CK(cudaMemsetAsync(aout, 0, nt * sizeof(int), s));
+                CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+                // algorithmic bytes of the fused schedule: 3 passes over V_0..V_i, v_i, v_{i+1}
+                // written and read back for the next Zᵀ A, s read and y written
+                KL(F_STEP, fa * ((3.0 * i + 7) * ld * cs + 2.0 * ldc * 16), fa * 40.0 * (i + 1) * ld,
+                   CK(launch_arnoldi_step<R>(a, stepC, i, RST, V, si, y, S, ain, aout, cnt, tol, maxit, step_sm, s)));
+            } else {
+                KL(F_ZT, fa * (ld * cs + ldc * 16), 0, launch_zt<R>(a, vi, y, 1, ain, s));
+                band_solve(ctx, ctx->E, y, si, false, ain, s, nact);
+                KL(F_PS, fa * ((i + 3) * ld * cs + ldc * 16), fa * 8.0 * (i + 1) * ld,
+                   launch_prolong_stencil<R>(a, 0, vi, si, vn, V, i + 1, p1, ain, s));
+                KL(F_CGS, fa * (i + 3) * ld * cs, fa * 16.0 * (i + 1) * ld,
+                   launch_cgs_update<R>(a, 2, vn, V, i + 1, p1, p2, ain, s));
+                KL(F_CGS, fa * (i + 3) * ld * cs, fa * 8.0 * (i + 1) * ld,
+                   launch_cgs_update<R>(a, 3, vn, V, i + 1, p2, p3, ain, s));
+                CK(cudaMemsetAsync(aout, 0, nt * sizeof(int), s));
+                CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+                KL(F_GIVENS, fa * 2 * ld * cs, 0,
+                   launch_givens_normalize<R>(a, S, RST, i, vn, p1, p2, p3, ain, aout, cnt, tol, maxit, s));
+            }
             CKL();
             cur ^= 1;
             st = read_counter(ctx, s, &nact);
@@ -907,6 +958,7 @@ hdd_status build_tasks(hdd_ctx *ctx, int nrhs) {
     // a fine tile holds at most LOCAL_THREADS·FINE_EPT nodes (one register slot per thread each)
     while (ctx->frows > 1 && ctx->frows * ctx->max_nx > LOCAL_THREADS * FINE_EPT) ctx->frows--;
     ctx->h_tasks.clear(); ctx->h_ftiles.clear(); ctx->h_ctiles.clear(); ctx->h_tct.clear();
+    ctx->step_C[0] = ctx->step_C[1] = -1;
     ctx->foffs.assign(1, 0); ctx->coffs.assign(1, 0);
     long long fo = 0, co = 0, po = 0;
     int wmx = 0;
@@ -1707,6 +1759,15 @@ hdd_status hdd_get_outer_vector(hdd_ctx *ctx, int j, void *v_dev, void *stream) 
     CK(cudaSetDevice(ctx->device));
     CK(cudaMemcpyAsync(v_dev, ctx->ow.V.as<char>() + (size_t)j * bytes, bytes, cudaMemcpyDeviceToDevice,
                        (cudaStream_t)stream));
+    return HDD_OK;
+}
+
+hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (value != 0 && value != 1) FAIL(HDD_ERR_INVALID_ARG, "option values are 0 or 1");
+    if (key == HDD_OPT_COARSE_LOOKAHEAD) ctx->coarse_la = value;
+    else if (key == HDD_OPT_FUSED_INNER) ctx->fused_inner = value;
+    else FAIL(HDD_ERR_INVALID_ARG, "unknown option %d", key);
     return HDD_OK;
 }
 

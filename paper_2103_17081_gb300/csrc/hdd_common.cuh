@@ -190,6 +190,14 @@ template <typename R> void launch_coarse_combine(const LocalArgs<R> &a, const In
                                                  int restart, const double2 *sbuf, double2 *sc,
                                                  const int *flag, cudaStream_t s);
 size_t local_max_dynamic_smem(int max_nx, int bytes_per_c, int frows, int crows);
+// one inner Arnoldi step per launch, one cluster of C CTAs per task (kernels_local.cu)
+constexpr int STEP_ROWS_MAX = LOCAL_THREADS * FINE_EPT;   // box nodes a CTA of the fused step holds
+size_t step_smem_bytes(int max_nx, int max_ny, int C, int bytes_per_c);
+template <typename R>
+cudaError_t launch_arnoldi_step(const LocalArgs<R> &la, int C, int i, int restart, c2<R> *V, const double2 *sc,
+                                double2 *y, const InnerState<R> &S, const int *act_in, int *act_out,
+                                int *counter, R tol, int maxit, size_t smem, cudaStream_t s);
+template <typename R> int arnoldi_step_max_cluster(size_t smem, int C);
 void launch_cast(long long n, const void *in, int in_double, void *out, int out_double, cudaStream_t s);
 constexpr int LOCAL_LDP = MAX_RESTART + 2;   // partial-sum slots per fine tile
 
@@ -213,6 +221,8 @@ struct BlockSolveCfg {       // shared-memory plan of the blocked solve over a s
     int maxK = 0;          // widest operator row: BNB + panel width
     int cwy = 0, cwx = 0;  // circular y / x windows, powers of two >= BNB + widest left / right panel
     int ring = 0;          // operator ring depth (4 or 2), chosen by set_block_solve_smem
+    int la_ring = 0;       // ring of the look-ahead kernel (6, 4 or 3; 0 if it does not fit)
+    int lookahead = 1;     // use the look-ahead kernel when la_ring > 0
 };
 // re2 = 0: real factors, Re and Im of the complex vector solved as two columns; re2 = 1: factors
 // of real-equivalent systems (order 2m), the complex vector read as one real column

@@ -534,6 +534,204 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
     cp_async_wait_n<0>();
 }
 
+// ------------------------------------------------------------------------------------------
+// Look-ahead form of the blocked solve.  In block J's product y_J = M_J [(Pb)_J ; panel] only the
+// panel columns of the previous block (y_{J-1}; backward: x_{J+1}) depend on the step just
+// finished; the diagonal part and the older panel columns are known one block earlier.  So while
+// warp 0 finishes block J (its recent columns plus the partial sums below: at most 16 columns
+// per row), the other LA_BW warps already sum the diagonal and older columns of block J+1 into
+// per-warp partials.  The dependent chain per block shrinks to one 16-column product and a
+// barrier, and the bulk of the FP64 work of consecutive blocks overlaps.  Same operators, ring
+// and windows as k_block_solve; the sums are taken in a fixed order (deterministic).
+// ------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int la_stride(int K) { return K + ((K & 3) ? 0 : 2); }
+__host__ __device__ __forceinline__ int la_slot(int maxK) { return BNB * (maxK + 2) + BNB; }
+constexpr int LA_T = 256;                 // threads: warp 0 (chain) + LA_BW bulk warps
+constexpr int LA_BW = LA_T / 32 - 1;      // bulk warps (7)
+constexpr int LA_BL = 2 * LA_BW;          // bulk lanes per row (14): (warp, half)
+
+template <int RING, bool RE2>
+__global__ void __launch_bounds__(LA_T, 2)
+k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__ shapes,
+                 const double *__restrict__ Mall, const int *__restrict__ Pall,
+                 const int4 *__restrict__ Meta, const double2 *__restrict__ in,
+                 double2 *__restrict__ out, int use_fine, const int *__restrict__ flag, int maxK,
+                 int cwy, int cwx) {
+    static_assert(RING >= 3, "the look-ahead needs blocks J and J+1 resident while J+2 loads");
+    extern __shared__ double sm[];
+    __shared__ double part[2][LA_BW][BNB];   // bulk partial sums of the next block, by parity
+    __shared__ int sw[RING];                  // panel width of the block in each ring slot
+    constexpr int STR = RE2 ? 1 : 2;
+    const int t = RE2 ? (int)blockIdx.x : (int)(blockIdx.x >> 1), comp = RE2 ? 0 : (int)(blockIdx.x & 1);
+    if (flag && !flag[t]) return;
+    const Task T = tasks[t];
+    const BlockFactor F = shapes[T.shape];
+    const long long off = use_fine ? T.foff : T.coff;
+    const int m = F.m, nbk = F.nblk;
+    const int slot = la_slot(maxK);
+    double *CY = sm + RING * slot, *CX = CY + cwy;
+    const int *perm = Pall + F.perm_off;
+    const int4 *meta = Meta + F.meta_off;
+    const double *inr = reinterpret_cast<const double *>(in + off) + comp;
+    double *outr = reinterpret_cast<double *>(out + off) + comp;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = lane >> 1, half = lane & 1;          // 16 rows x 2 lanes per warp
+    const int q = (warp - 1) * 2 + half;                 // bulk lane of the row (warp >= 1)
+    // operator rows land at stride la_stride(K) (≡ 2 mod 4 doubles: the 16 rows x 2 lanes of a
+    // warp then hit distinct 8-byte banks pairwise); inputs after the widest operator
+    auto load_block = [&](long long src_off, int K, int buf, int J) {
+        double *dst = sm + buf * slot;
+        const double *src = Mall + src_off;
+        const int S = la_stride(K), cpr = K / 2;          // 16-byte chunks per row (K is even)
+        for (int c = tid; c < BNB * cpr; c += LA_T) {
+            const int r = c / cpr;
+            cp_async16(dst + r * S + 2 * (c - r * cpr), src + 2 * c);
+        }
+        if (tid < BNB) {
+            const int i = J * BNB + tid;
+            cp_async8_zfill(dst + BNB * (maxK + 2) + tid, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
+        }
+    };
+    for (int i = tid; i < m; i += LA_T) outr[STR * (long long)i] = inr[STR * (long long)perm[i]];
+    for (int i = tid; i < cwy; i += LA_T) CY[i] = 0.0;
+    for (int i = tid; i < cwx; i += LA_T) CX[i] = 0.0;
+    __threadfence_block();
+    __syncthreads();
+
+    // Sum over the columns [k0, k1) of block J's operator (slot Mb, row stride K) for this bulk
+    // lane's row: diagonal columns k < BNB take the block's inputs, panel column p = k - BNB takes
+    // win[(pbase + p) & mask].  Columns q, q + LA_BL, ... of the range; four accumulators.
+    auto bulk_row = [&](const double *Mb, int K, int k0, int k1, const double *win, int pbase, int mask) {
+        const double *Mr = Mb + row * la_stride(K);
+        const double *a = Mb + BNB * (maxK + 2);
+        double s0 = 0.0, s1 = 0.0;
+        int k = q;
+        for (; k < BNB; k += LA_BL) s0 = fma(Mr[k], a[k], s0);
+        if (k < k0) k += ((k0 - k + LA_BL - 1) / LA_BL) * LA_BL;
+        for (; k + LA_BL < k1; k += 2 * LA_BL) {
+            const double m0 = Mr[k], m1 = Mr[k + LA_BL];
+            const double w0 = win[(pbase + k - BNB) & mask], w1 = win[(pbase + k + LA_BL - BNB) & mask];
+            s0 = fma(m0, w0, s0); s1 = fma(m1, w1, s1);
+        }
+        if (k < k1) s0 = fma(Mr[k], win[(pbase + k - BNB) & mask], s0);
+        double v = s0 + s1;
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        return v;
+    };
+    // Warp 0: block J from the bulk partials (parity par) and the recent panel columns [p0, p1).
+    auto chain_row = [&](const double *Mb, int K, int p0, int p1, const double *win, int pbase, int mask,
+                         int par) {
+        const double *Mr = Mb + row * la_stride(K) + BNB;
+        double s0 = 0.0, s1 = 0.0;
+        for (int w = half; w < LA_BW; w += 2) s0 += part[par][w][row];
+        int p = p0 + half;
+        for (; p + 2 < p1; p += 4) {
+            s0 = fma(Mr[p], win[(pbase + p) & mask], s0);
+            s1 = fma(Mr[p + 2], win[(pbase + p + 2) & mask], s1);
+        }
+        for (; p < p1; p += 2) s0 = fma(Mr[p], win[(pbase + p) & mask], s0);
+        double v = s0 + s1;
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        return v;
+    };
+
+    // ---- forward: y_J = M_J [(Pb)_J ; y_{J-w_J..J}] ----
+    int4 mnext = make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < RING - 1; u++) {
+        if (u < nbk) {
+            const int4 mt = meta[u];
+            load_block(mt.x, BNB + mt.y, u, u);
+            if (tid == 0) sw[u] = mt.y;
+        }
+        cp_async_commit();
+    }
+    if (RING - 1 < nbk) mnext = meta[RING - 1];
+    cp_async_wait_n<RING - 2>();                           // block 0 resident
+    __syncthreads();
+    if (warp > 0) {                                        // bulk part of block 0
+        const int w0 = sw[0], nold = w0 > BNB ? w0 - BNB : 0;
+        const double v = bulk_row(sm, BNB + w0, BNB, BNB + nold, CY, -w0, cwy - 1);
+        if (half == 0) part[0][warp - 1][row] = v;
+    }
+    for (int J = 0; J < nbk; J++) {
+        cp_async_wait_n<RING - 3>();                       // blocks J and J+1 resident
+        __syncthreads();
+        if (J + RING - 1 < nbk) {                          // into the slot block J-1 used
+            const int buf = (J + RING - 1) % RING;
+            load_block(mnext.x, BNB + mnext.y, buf, J + RING - 1);
+            if (tid == 0) sw[buf] = mnext.y;
+        }
+        cp_async_commit();
+        if (J + RING < nbk) mnext = meta[J + RING];
+        if (warp == 0) {
+            const int wJ = sw[J % RING];
+            const int p0 = wJ > BNB ? wJ - BNB : 0;
+            const double v = chain_row(sm + (J % RING) * slot, BNB + wJ, p0, wJ, CY, J * BNB - wJ, cwy - 1, J & 1);
+            if (half == 0) {
+                const int i = J * BNB + row;
+                CY[i & (cwy - 1)] = v;
+                if (i < m) outr[STR * (long long)i] = v;
+            }
+        } else if (J + 1 < nbk) {
+            const int Jn = J + 1, w1 = sw[Jn % RING], nold = w1 > BNB ? w1 - BNB : 0;
+            const double v = bulk_row(sm + (Jn % RING) * slot, BNB + w1, BNB, BNB + nold, CY, Jn * BNB - w1, cwy - 1);
+            if (half == 0) part[Jn & 1][warp - 1][row] = v;
+        }
+    }
+    cp_async_wait_n<0>();
+    __threadfence_block();
+    __syncthreads();
+
+    // ---- backward: x_J = M_J [y_J ; x_{J+1..J+w_J}] ----
+#pragma unroll
+    for (int u = 0; u < RING - 1; u++) {
+        const int J = nbk - 1 - u;
+        if (J >= 0) {
+            const int4 mt = meta[J];
+            load_block(mt.z, BNB + mt.w, u, J);
+            if (tid == 0) sw[u] = mt.w;
+        }
+        cp_async_commit();
+    }
+    mnext = nbk - RING >= 0 ? meta[nbk - RING] : make_int4(0, 0, 0, 0);
+    cp_async_wait_n<RING - 2>();
+    __syncthreads();
+    if (warp > 0) {                                        // bulk part of block nbk-1
+        const int J = nbk - 1, w0 = sw[0];
+        const double v = bulk_row(sm, BNB + w0, 2 * BNB, BNB + w0, CX, (J + 1) * BNB, cwx - 1);
+        if (half == 0) part[0][warp - 1][row] = v;
+    }
+    for (int k = 0; k < nbk; k++) {                        // sweep position k: block J = nbk-1-k
+        const int J = nbk - 1 - k;
+        cp_async_wait_n<RING - 3>();
+        __syncthreads();
+        if (J - (RING - 1) >= 0) {
+            const int buf = (k + RING - 1) % RING;
+            load_block(mnext.z, BNB + mnext.w, buf, J - (RING - 1));
+            if (tid == 0) sw[buf] = mnext.w;
+        }
+        cp_async_commit();
+        if (J - RING >= 0) mnext = meta[J - RING];
+        if (warp == 0) {
+            const int wJ = sw[k % RING];
+            const double v = chain_row(sm + (k % RING) * slot, BNB + wJ, 0, wJ < BNB ? wJ : BNB, CX, (J + 1) * BNB,
+                                       cwx - 1, k & 1);
+            if (half == 0) {
+                const int i = J * BNB + row;
+                CX[i & (cwx - 1)] = v;
+                if (i < m) outr[STR * (long long)i] = v;
+            }
+        } else if (J - 1 >= 0) {
+            const int kn = k + 1, Jn = J - 1, w1 = sw[kn % RING];
+            const double v = bulk_row(sm + (kn % RING) * slot, BNB + w1, 2 * BNB, BNB + w1, CX, (Jn + 1) * BNB,
+                                      cwx - 1);
+            if (half == 0) part[kn & 1][warp - 1][row] = v;
+        }
+    }
+    cp_async_wait_n<0>();
+}
+
 void launch_assemble_E(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s) {
     long long tot = (long long)(nx / 2) * (ny / 2) * 25;
     k_assemble_E<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(st, nx, ny, kl, ku, ab);
@@ -571,9 +769,48 @@ void launch_block_operators(int m, int kl, int ku, const double *ab, int KLW, co
 static size_t bs_smem(const BlockSolveCfg &c, int ring) {
     return ((size_t)ring * ((size_t)BNB * c.maxK + BNB) + (size_t)c.cwy + (size_t)c.cwx) * sizeof(double);
 }
+static size_t la_smem(const BlockSolveCfg &c, int ring) {
+    return ((size_t)ring * la_slot(c.maxK) + (size_t)c.cwy + (size_t)c.cwx) * sizeof(double);
+}
+
+template <int RING, bool RE2>
+static void la_launch(int grid, const BlockSolveCfg &c, const Task *tasks, const BlockFactor *shapes,
+                      const double *Mall, const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
+                      int use_fine, const int *flag, cudaStream_t s) {
+    k_block_solve_la<RING, RE2><<<grid, LA_T, la_smem(c, RING), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
+                                                                      use_fine, flag, c.maxK, c.cwy, c.cwx);
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+    }
+    return n;
+}
+
 void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
                         const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
                         int use_fine, const int *flag, const BlockSolveCfg &c, int re2, cudaStream_t s) {
+    const int chains = re2 ? ntasks : 2 * ntasks;
+    if (c.lookahead && c.la_ring >= 3) {
+        // the deepest ring that fits, unless there are more chains than SMs and a ring of 4 lets
+        // two CTAs share an SM (many chains: throughput over latency)
+        int ring = c.la_ring;
+        if (ring > 4 && chains > sm_count() && 2 * (la_smem(c, 4) + 4096) <= 228 * 1024) ring = 4;
+        if (re2) {
+            if (ring == 6) la_launch<6, true>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
+            else if (ring == 4) la_launch<4, true>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
+            else la_launch<3, true>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
+        } else {
+            if (ring == 6) la_launch<6, false>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
+            else if (ring == 4) la_launch<4, false>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
+            else la_launch<3, false>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
+        }
+        return;
+    }
     if (re2) {
         if (c.ring == 4)
             k_block_solve<4, true><<<ntasks, BS_T, bs_smem(c, 4), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
@@ -590,9 +827,20 @@ void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes
         k_block_solve<2, false><<<2 * ntasks, BS_T, bs_smem(c, 2), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
                                                                         use_fine, flag, c.maxK, c.cwy, c.cwx);
 }
+
+template <int RING, bool RE2> static cudaError_t la_attr(size_t lim, size_t &static_bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_block_solve_la<RING, RE2>);
+    if (e != cudaSuccess) return e;
+    static_bytes = std::max(static_bytes, a.sharedSizeBytes);
+    return cudaFuncSetAttribute(k_block_solve_la<RING, RE2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(lim - a.sharedSizeBytes));
+}
+
 // Ring depth 4 if its shared memory fits the per-CTA limit, else 2; error if not even that fits.
 // The kernels' attribute is raised to the limit itself (several factor sets with different plans
-// share the kernels; each launch requests only what its plan needs).
+// share the kernels; each launch requests only what its plan needs).  The look-ahead kernel takes
+// the deepest of rings 6, 4, 3 that fits (la_ring, 0 if none: the plain kernel then serves).
 cudaError_t set_block_solve_smem(BlockSolveCfg &c) {
     cudaFuncAttributes a4, a2, b4, b2;
     cudaError_t e = cudaFuncGetAttributes(&a4, k_block_solve<4, false>);
@@ -611,7 +859,19 @@ cudaError_t set_block_solve_smem(BlockSolveCfg &c) {
         return e;
     if ((e = cudaFuncSetAttribute(k_block_solve<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim4)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_block_solve<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim2);
+    if ((e = cudaFuncSetAttribute(k_block_solve<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim2)) != cudaSuccess)
+        return e;
+    size_t st = 0;
+    if ((e = la_attr<6, false>(lim, st)) != cudaSuccess) return e;
+    if ((e = la_attr<4, false>(lim, st)) != cudaSuccess) return e;
+    if ((e = la_attr<3, false>(lim, st)) != cudaSuccess) return e;
+    if ((e = la_attr<6, true>(lim, st)) != cudaSuccess) return e;
+    if ((e = la_attr<4, true>(lim, st)) != cudaSuccess) return e;
+    if ((e = la_attr<3, true>(lim, st)) != cudaSuccess) return e;
+    c.la_ring = 0;
+    for (int r : {6, 4, 3})
+        if (la_smem(c, r) + st <= lim) { c.la_ring = r; break; }
+    return cudaSuccess;
 }
 
 }  // namespace hdd

@@ -657,6 +657,283 @@ __global__ void k_cast(long long n, const c2<RI> *__restrict__ in, c2<RO> *__res
 }
 
 // ------------------------------------------------------------------------------------------
+// One inner Arnoldi step in one launch (every phase between two coarse solves), one cluster of
+// C CTAs per task: CTA `rank` holds box rows [rank·ny/C, (rank+1)·ny/C) and coarse rows
+// [rank·my/C, (rank+1)·my/C).  The new vector w stays in registers from the stencil to the
+// normalisation; the three task-wide sums (first CGS dots, second CGS dots, ||w||²) are
+// all-gathered through distributed shared memory, one cluster barrier each, and every CTA adds
+// the C partials in rank order (deterministic, bitwise the same in every CTA).  Steps:
+//   A  w = A_j(v_i - Z_j s_{i+1}) (s_{i+1} = E_j⁻¹ Z_jᵀ A_j v_i from the coarse solve), h1 = V^H w
+//   B  w -= V h1, h2 = V^H w          (CGS2, both passes against V_0..V_i)
+//   C  w -= V h2, ||w||
+//   D  v_{i+1} = w/||w||; Hessenberg column h1 + h2, Givens rotation, stop test (every CTA
+//      computes the same decision; rank 0 writes the state)
+//   E  if the task goes on: y = Z_jᵀ A_j v_{i+1} for the next step's coarse solve (after a
+//      cluster barrier that publishes v_{i+1})
+// ------------------------------------------------------------------------------------------
+constexpr int STEP_CMAX = 8;                       // largest cluster (portable size)
+
+template <typename R> struct StepArgs {
+    const Task *tasks;
+    Stencil st;
+    long long ld;
+    int C;                  // CTAs per task (cluster size)
+    int i;                  // Arnoldi index
+    int restart;
+    c2<R> *V;               // basis, vector l at V + l·ld
+    const double2 *s;       // s_{i+1} (coarse, FP64)
+    double2 *y;             // out: Zᵀ A v_{i+1}
+    InnerState<R> S;
+    const int *act_in;
+    int *act_out;
+    int *counter;
+    R tol;
+    int maxit;
+};
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// generic address of the same shared-memory object in CTA `rank` of the cluster
+template <typename T> __device__ __forceinline__ T *cluster_map(T *p, unsigned rank) {
+    uint64_t out;
+    asm volatile("mapa.u64 %0, %1, %2;\n" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+    return reinterpret_cast<T *>(out);
+}
+
+size_t step_smem_bytes(int max_nx, int max_ny, int C, int bytes_per_c) {
+    const int nr = (max_ny + C - 1) / C, nF = nr + 2, maxc = nF / 2 + 4;
+    const int mx = max_nx / 2 + 1, my = max_ny / 2;
+    const int ncy = (my + C - 1) / C, nFz = 2 * ncy + 3, nVz = nFz + 2;
+    const size_t a = (size_t)maxc * mx + (size_t)maxc * max_nx + (size_t)nF * max_nx;
+    const size_t e = (size_t)nVz * max_nx + (size_t)nFz * max_nx + (size_t)nFz * mx;
+    return (a > e ? a : e) * bytes_per_c;
+}
+
+template <typename R, bool IMP>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_arnoldi_step(StepArgs<R> a) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ c2<R> red[NWARP * LDP];            // per-warp partials
+    __shared__ c2<R> gat[2][STEP_CMAX][LDP];      // cluster all-gather slots (written remotely)
+    __shared__ c2<R> h1s[LDP], h2s[LDP], nrm_s[1];   // task sums: the two CGS passes, ||w||²
+    __shared__ R cs_s[MAX_RESTART];
+    __shared__ c2<R> sn_s[MAX_RESTART];
+    __shared__ c2<R> g_s;
+    __shared__ R ref_s, hn_s;
+    __shared__ int its_s, stop_s;
+    const int C = a.C;
+    const int t = (int)blockIdx.x / C;
+    const unsigned rank = cluster_rank();
+    if (!a.act_in[t]) return;                     // the same flag for every CTA of the cluster
+    const Task T = a.tasks[t];
+    const int nx = T.nx, ny = T.ny, mx = T.mx, my = T.my;
+    const int i = a.i, nv = i + 1;
+    const int r0 = (int)(rank * ny) / C, r1 = (int)((rank + 1) * ny) / C, nr = r1 - r0;
+    const int cnt = nr * nx;
+    const long long base = T.foff + (long long)r0 * nx;
+    const int tid = threadIdx.x;
+    // Givens state of earlier steps (written by earlier launches; rank 0 rewrites it below, after
+    // every CTA has passed the first cluster barrier)
+    if (tid < i) {
+        cs_s[tid] = a.S.cs[(long long)t * a.restart + tid];
+        sn_s[tid] = a.S.sn[(long long)t * a.restart + tid];
+    }
+    if (tid == 0) {
+        g_s = a.S.g[(long long)t * (a.restart + 1) + i];
+        ref_s = a.S.ref[t];
+        its_s = a.S.its[t];
+    }
+    // ---- A: u = v_i - Z s on rows [r0-1, r1], w = A u on own rows, partial h1 ----
+    c2<R> *sc = reinterpret_cast<c2<R> *>(smem_raw);
+    const int F0 = r0 - 1, nF = nr + 2, maxc = prolong_max_cy(nF);
+    c2<R> *px = sc + maxc * mx;
+    c2<R> *u = px + maxc * nx;
+    const c2<R> *vi = a.V + (long long)i * a.ld;
+    c2<R> wv[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; k++) wv[k] = mk<R>(0, 0);
+    if (nr > 0) {
+        prolong_rows<R>(T, a.s, F0, nF, sc, px, u);
+        for (int e = tid; e < nF * nx; e += blockDim.x) {
+            const int yy = F0 + e / nx;
+            if (yy >= 0 && yy < ny) u[e] = csub<R>(vi[T.foff + (long long)yy * nx + e % nx], u[e]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < EPT; k++) {
+            const int e = tid + k * LOCAL_THREADS;
+            if (e < cnt) {
+                const int yy = r0 + e / nx, xx = e % nx;
+                wv[k] = stencil_smem<R, IMP>(a.st, u, F0, nF, nx, ny, xx, yy, T.ix0, T.iy0);
+            }
+        }
+    }
+    // task-wide sums of nv values: per-CTA sums go to slot gat[b][rank][l] of every CTA, then one
+    // cluster barrier, then each CTA adds the C slots in rank order into out[l]
+    auto allreduce = [&](int b, int n, auto get, c2<R> *out) {
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int l = 0; l < n; l++) {
+            c2<R> v = get(l);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) { v.x += shfl_xor(v.x, o); v.y += shfl_xor(v.y, o); }
+            if (lane == 0) red[warp * LDP + l] = v;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < n * C; idx += blockDim.x) {
+            const int l = idx % n, dst = idx / n;
+            c2<R> sum = mk<R>(0, 0);
+            for (int q = 0; q < NWARP; q++) sum = cadd<R>(sum, red[q * LDP + l]);
+            *cluster_map(&gat[b][rank][l], (unsigned)dst) = sum;
+        }
+        cluster_barrier();
+        for (int l = tid; l < n; l += blockDim.x) {
+            c2<R> sum = mk<R>(0, 0);
+            for (int q = 0; q < C; q++) sum = cadd<R>(sum, gat[b][q][l]);
+            out[l] = sum;
+        }
+        __syncthreads();
+    };
+    auto dots = [&](int l) {
+        c2<R> acc = mk<R>(0, 0);
+        const c2<R> *vl = a.V + (long long)l * a.ld + base;
+#pragma unroll
+        for (int k = 0; k < EPT; k++) {
+            const int e = tid + k * LOCAL_THREADS;
+            if (e < cnt) cdotc_acc<R>(acc, vl[e], wv[k]);
+        }
+        return acc;
+    };
+    auto update = [&](const c2<R> *h) {
+        for (int l = 0; l < nv; l++) {
+            const c2<R> hl = h[l];
+            const c2<R> *vl = a.V + (long long)l * a.ld + base;
+#pragma unroll
+            for (int k = 0; k < EPT; k++) {
+                const int e = tid + k * LOCAL_THREADS;
+                if (e < cnt) caxpy_neg<R>(wv[k], hl, vl[e]);
+            }
+        }
+    };
+    allreduce(0, nv, dots, h1s);
+    // ---- B: w -= V h1, partial h2 ----
+    update(h1s);
+    allreduce(1, nv, dots, h2s);
+    // ---- C: w -= V h2, ||w||² ----
+    update(h2s);
+    allreduce(0, 1, [&](int) {
+        R nrm = 0;
+#pragma unroll
+        for (int k = 0; k < EPT; k++) nrm = fma(wv[k].x, wv[k].x, fma(wv[k].y, wv[k].y, nrm));
+        return mk<R>(nrm, 0);
+    }, nrm_s);
+    if (tid == 0) hn_s = sqrt(nrm_s[0].x);
+    __syncthreads();
+    const R hn = hn_s;
+    // ---- D: v_{i+1} = w/||w||; Givens rotation and stop test ----
+    c2<R> *vn = a.V + (long long)(i + 1) * a.ld + base;
+    if (hn > (R)0) {
+        const R inv = (R)1 / hn;
+#pragma unroll
+        for (int k = 0; k < EPT; k++) {
+            const int e = tid + k * LOCAL_THREADS;
+            if (e < cnt) vn[e] = mk<R>(wv[k].x * inv, wv[k].y * inv);
+        }
+    }
+    if (tid == 0) {
+        c2<R> hc[MAX_RESTART + 1];
+        for (int l = 0; l <= i; l++) hc[l] = cadd<R>(h1s[l], h2s[l]);
+        for (int l = 0; l < i; l++) {
+            const c2<R> x = hc[l], yv = hc[l + 1], sx = sn_s[l];
+            hc[l] = cadd<R>(cscale<R>(cs_s[l], x), cmul<R>(sx, yv));
+            hc[l + 1] = csub<R>(cscale<R>(cs_s[l], yv), cmul<R>(mk<R>(sx.x, -sx.y), x));
+        }
+        R c; c2<R> sv, rr;
+        givens<R>(hc[i], mk<R>(hn, 0), c, sv, rr);
+        hc[i] = rr;
+        hc[i + 1] = mk<R>(0, 0);
+        const c2<R> gi = g_s;
+        const c2<R> gn = mk<R>(-(sv.x * gi.x + sv.y * gi.y), -(sv.x * gi.y - sv.y * gi.x));   // -conj(s) g_i
+        const int its = its_s + 1;
+        const R res = hypot(gn.x, gn.y);
+        const bool conv = res <= a.tol * ref_s || !(hn > (R)0);
+        const bool stop = conv || its >= a.maxit || i + 1 >= a.restart;
+        stop_s = stop ? 1 : 0;
+        if (rank == 0) {
+            c2<R> *Hc = a.S.H + (long long)t * (a.restart + 1) * a.restart + (long long)i * (a.restart + 1);
+            for (int l = 0; l <= i + 1; l++) Hc[l] = hc[l];
+            a.S.cs[(long long)t * a.restart + i] = c;
+            a.S.sn[(long long)t * a.restart + i] = sv;
+            c2<R> *g = a.S.g + (long long)t * (a.restart + 1);
+            g[i] = cscale<R>(c, gi);
+            g[i + 1] = gn;
+            a.S.its[t] = its;
+            a.S.kcols[t] = i + 1;
+            if (conv || its >= a.maxit) a.S.conv[t] = 1;
+            a.act_out[t] = stop ? 0 : 1;
+            if (!stop) atomicAdd(a.counter, 1);
+        }
+    }
+    __syncthreads();
+    if (stop_s) return;                           // the same decision in every CTA
+    // ---- E: y = Zᵀ A v_{i+1} on coarse rows [c0, c1) ----
+    cluster_barrier();                            // v_{i+1} of every CTA written and visible
+    const int c0 = (int)(rank * my) / C, c1 = (int)((rank + 1) * my) / C;
+    if (c1 <= c0) return;
+    const int G0 = 2 * c0 - 1, G1 = 2 * (c1 - 1) + 3, nG = G1 - G0 + 1;
+    const int W0 = G0 - 1, nW = nG + 2;
+    c2<R> *vin = reinterpret_cast<c2<R> *>(smem_raw);
+    c2<R> *tt = vin + nW * nx;
+    c2<R> *sx = tt + nG * nx;
+    const c2<R> *vnf = a.V + (long long)(i + 1) * a.ld + T.foff;
+    for (int e = tid; e < nW * nx; e += blockDim.x) {
+        const int yy = W0 + e / nx;
+        vin[e] = (yy >= 0 && yy < ny) ? vnf[(long long)yy * nx + e % nx] : mk<R>(0, 0);
+    }
+    __syncthreads();
+    for (int e = tid; e < nG * nx; e += blockDim.x) {
+        const int yy = G0 + e / nx, xx = e % nx;
+        tt[e] = (yy >= 0 && yy < ny) ? stencil_smem<R, IMP>(a.st, vin, W0, nW, nx, ny, xx, yy, T.ix0, T.iy0)
+                                     : mk<R>(0, 0);
+    }
+    __syncthreads();
+    for (int e = tid; e < nG * mx; e += blockDim.x) {
+        const int fr = e / mx, cx = e % mx;
+        c2<R> acc = mk<R>(0, 0);
+#pragma unroll
+        for (int qq = 0; qq < 5; qq++) {
+            const int fx = 2 * cx - 1 + qq;
+            if (fx >= 0 && fx < nx) {
+                const c2<R> v = tt[fr * nx + fx];
+                acc.x = fma(zw<R>(qq), v.x, acc.x);
+                acc.y = fma(zw<R>(qq), v.y, acc.y);
+            }
+        }
+        sx[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < (c1 - c0) * mx; e += blockDim.x) {
+        const int cy = c0 + e / mx, cx = e % mx;
+        c2<R> acc = mk<R>(0, 0);
+#pragma unroll
+        for (int qq = 0; qq < 5; qq++) {
+            const int fy = 2 * cy - 1 + qq;
+            if (fy >= 0 && fy < ny) {
+                const c2<R> v = sx[(fy - G0) * mx + cx];
+                acc.x = fma(zw<R>(qq), v.x, acc.x);
+                acc.y = fma(zw<R>(qq), v.y, acc.y);
+            }
+        }
+        a.y[T.coff + (long long)cy * mx + cx] = make_double2((double)acc.x, (double)acc.y);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
 template <typename R> static size_t csz() { return sizeof(c2<R>); }
@@ -749,6 +1026,54 @@ void launch_coarse_combine(const LocalArgs<R> &a, const InnerState<R> &S, int re
                            const double2 *sbuf, double2 *sc, const int *flag, cudaStream_t s) {
     k_coarse_combine<R><<<a.nctiles, LOCAL_THREADS, 0, s>>>(a, S, restart, sbuf, sc, flag);
 }
+template <typename R>
+cudaError_t launch_arnoldi_step(const LocalArgs<R> &la, int C, int i, int restart, c2<R> *V, const double2 *sc,
+                                double2 *y, const InnerState<R> &S, const int *act_in, int *act_out,
+                                int *counter, R tol, int maxit, size_t smem, cudaStream_t s) {
+    StepArgs<R> a;
+    a.tasks = la.tasks; a.st = la.st; a.ld = la.ld; a.C = C; a.i = i; a.restart = restart;
+    a.V = V; a.s = sc; a.y = y; a.S = S; a.act_in = act_in; a.act_out = act_out; a.counter = counter;
+    a.tol = tol; a.maxit = maxit;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(la.ntasks * C));
+    cfg.blockDim = dim3(LOCAL_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (la.st.bc) return cudaLaunchKernelEx(&cfg, k_arnoldi_step<R, true>, a);
+    return cudaLaunchKernelEx(&cfg, k_arnoldi_step<R, false>, a);
+}
+
+// Largest cluster of CTAs holding `smem` bytes of dynamic shared memory each that the device can
+// co-schedule (0 on error); sets the kernels' dynamic shared-memory limit to `smem` first.
+template <typename R> int arnoldi_step_max_cluster(size_t smem, int C) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_arnoldi_step<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return 0;
+    if ((e = cudaFuncSetAttribute(k_arnoldi_step<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(LOCAL_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_arnoldi_step<R, false>, &cfg) != cudaSuccess) return 0;
+    return n;
+}
+
 void launch_cast(long long n, const void *in, int in_double, void *out, int out_double,
                  cudaStream_t s) {
     int grid = (int)((n + 255) / 256);
@@ -798,7 +1123,9 @@ template <typename R> cudaError_t set_local_smem_limits(size_t bytes) {
     template void launch_update_u<R>(const LocalArgs<R> &, const InnerState<R> &, int, c2<R> *, const c2<R> *, const int *, int *, int *, int, cudaStream_t); \
     template cudaError_t set_local_smem_limits<R>(size_t); \
     template void launch_coarse_combine<R>(const LocalArgs<R> &, const InnerState<R> &, int, const double2 *, double2 *, const int *, cudaStream_t); \
-    template void launch_set_ref<R>(const LocalArgs<R> &, const InnerState<R> &, const c2<R> *, const int *, cudaStream_t);
+    template void launch_set_ref<R>(const LocalArgs<R> &, const InnerState<R> &, const c2<R> *, const int *, cudaStream_t); \
+    template cudaError_t launch_arnoldi_step<R>(const LocalArgs<R> &, int, int, int, c2<R> *, const double2 *, double2 *, const InnerState<R> &, const int *, int *, int *, R, int, size_t, cudaStream_t); \
+    template int arnoldi_step_max_cluster<R>(size_t, int);
 
 INST(float)
 INST(double)

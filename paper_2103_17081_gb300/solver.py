@@ -225,6 +225,15 @@ class Solver:
     def launch_count(self) -> int:
         return int(self._L.hdd_launch_count(self._h))
 
+    OPTIONS = {"coarse_lookahead": 1, "fused_inner": 2}
+
+    def set_option(self, name: str, value: int):
+        """Implementation choice of this context (hdd_set_option): "coarse_lookahead" selects
+        the look-ahead block solve (1) or the plain one (0); "fused_inner" the one-kernel inner
+        Arnoldi step (1) or the separate kernels (0)."""
+        self._check(self._L.hdd_set_option(self._h, self.OPTIONS[name], int(value)), "hdd_set_option")
+        return self
+
     # -- learned warm start ----------------------------------------------------------------------
     def cnn_num_params(self) -> int:
         return int(self._L.hdd_cnn_num_params())
