@@ -56,12 +56,12 @@ template <typename R> struct InnerWork {   // inner GMRES buffers for one precis
 
 // Kernel families timed by the profiler (CUDA events around every launch on the launching
 // stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
-enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, F_STEP, NFAM };
+enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, F_STEP, F_ODF, NFAM };
 const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
                               "local_cgs2_update", "local_givens_normalize", "local_misc",
                               "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn",
-                              "outer_reorth_fp32", "local_arnoldi_step"};
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0};
+                              "outer_reorth_fp32", "local_arnoldi_step", "outer_dots_df32"};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 0};
 
 struct Prof {
     bool on = false;
@@ -107,7 +107,7 @@ struct CnnState {            // learned warm start: parameters, Adam moments, ac
 };
 
 struct OuterWork {
-    DevMem V, V32, D, Z, w, r, H, cs, sn, g, Wq, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
+    DevMem V, V32, V32L, D, Z, w, r, H, cs, sn, g, Wq, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
     DevMem fallbacks;
 };
 
@@ -157,6 +157,7 @@ struct hdd_ctx {
     Prof prof;
     int coarse_la = 1;                         // HDD_OPT_COARSE_LOOKAHEAD
     int fused_inner = 1;                       // HDD_OPT_FUSED_INNER
+    int outer_df = 1;                          // HDD_OPT_OUTER_DOTS_DF
     int step_C[2] = {-1, -1};                  // fused-step cluster size per inner precision (0: off, -1: unplanned)
     size_t step_smem[2] = {0, 0};
     bool poisoned = false;                     // a device wait gave up with work in flight
@@ -606,8 +607,8 @@ template <typename R> InnerState<R> inner_state(InnerWork<R> &W) {
 
 // Cluster size of the one-launch Arnoldi step for the current task layout: the smallest power of
 // two C <= 8 with ceil(ny/C)·nx <= STEP_ROWS_MAX nodes per CTA for every box, raised (up to 8)
-// until the tasks fill about two CTAs per SM; 0 (the separate kernels serve) if no C fits or the
-// device cannot co-schedule such a cluster.
+// while the device can still hold the clusters of every task at once (more SMs per task, one
+// wave); 0 (the separate kernels serve) if no C fits or the device cannot co-schedule a cluster.
 template <typename R> int step_plan(hdd_ctx *ctx) {
     const int pi = sizeof(R) == 4 ? 0 : 1;
     if (ctx->step_C[pi] >= 0) return ctx->step_C[pi];
@@ -620,15 +621,22 @@ template <typename R> int step_plan(hdd_ctx *ctx) {
             if ((long long)((b.ny + c - 1) / c) * b.nx > STEP_ROWS_MAX) { ok = false; break; }
         if (ok) { C = c; break; }
     }
+    size_t sm = 0;
     if (C > 0) {
-        int dev = 0, nsm = 152;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long nt = (long long)ctx->h_tasks.size();
-        while (C < 8 && nt * C < 2LL * nsm) C *= 2;
-        const size_t sm = step_smem_bytes(ctx->max_nx, max_ny, C, (int)sizeof(c2<R>));
+        sm = step_smem_bytes(ctx->max_nx, max_ny, C, (int)sizeof(c2<R>));
         if (sm > 160 * 1024 || arnoldi_step_max_cluster<R>(sm, C) < 1) C = 0;
-        ctx->step_smem[pi] = sm;
     }
+    if (C > 0) {
+        const long long nt = (long long)ctx->h_tasks.size();
+        while (C < 8) {
+            const size_t sm2 = step_smem_bytes(ctx->max_nx, max_ny, 2 * C, (int)sizeof(c2<R>));
+            if (sm2 > 160 * 1024 || arnoldi_step_max_cluster<R>(sm2, 2 * C) < nt) break;
+            C *= 2;
+            sm = sm2;
+        }
+        arnoldi_step_max_cluster<R>(sm, C);          // leaves the kernels' smem limit at the plan's
+    }
+    ctx->step_smem[pi] = sm;
     ctx->step_C[pi] = C;
     return C;
 }
@@ -1323,8 +1331,13 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     CK(O.npart.ensure((size_t)nr * G * sizeof(double)));
     CK(O.npart1.ensure((size_t)nr * G * sizeof(double)));
     const bool r32 = prm->outer_reorth32 != 0;
+    // the double-FP32 first pass pairs with the guarded FP32 second pass (its coefficients are
+    // what that guard tests); with the FP64 second pass both passes stay FP64
+    const bool df = r32 && ctx->outer_df;
     if (r32) CK(O.V32.ensure((size_t)(R + 1) * B.ld32 * sizeof(float2)));
+    if (df) CK(O.V32L.ensure((size_t)(R + 1) * B.ld32 * sizeof(float2)));
     float2 *V32 = r32 ? O.V32.as<float2>() : nullptr;
+    float2 *V32L = df ? O.V32L.as<float2>() : nullptr;
     CK(O.fallbacks.ensure(sizeof(int)));
     CK(cudaMemsetAsync(O.fallbacks.p, 0, sizeof(int), s));
     CK(O.hn.ensure(nr * sizeof(double))); CK(O.flag.ensure(nr * sizeof(int))); CK(O.beta.ensure(nr * sizeof(double)));
@@ -1379,9 +1392,9 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
         B.active = dact;
         KL(F_OMISC, 3.0 * nr * n * 16, 0, launch_gstencil(ctx->st, ctx->N, x, rv, f, nr, dact, s));
         KL(F_OMISC, (double)nr * n * 16, 0, launch_onorm(B, rv, O.npart.as<double>(), s));
-        KL(F_OMISC, 2.0 * nr * n * 16 + (r32 ? nr * n * 8.0 : 0.0), 0,
-           launch_oinit(B, rv, O.npart.as<double>(), V, V32, O.D.as<double>(), O.g.as<double2>(), O.Wq.as<double2>(),
-                        O.beta.as<double>(), s));
+        KL(F_OMISC, 2.0 * nr * n * 16 + (r32 ? nr * n * 8.0 : 0.0) + (df ? nr * n * 8.0 : 0.0), 0,
+           launch_oinit(B, rv, O.npart.as<double>(), V, V32, V32L, O.D.as<double>(), O.g.as<double2>(),
+                        O.Wq.as<double2>(), O.beta.as<double>(), s));
         CKL();
         CK(cudaMemcpyAsync(beta.data(), O.beta.p, nr * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1413,8 +1426,12 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
             // Gauss form); bytes: V (16 B) and d (8 B) per vector and element for each pass over
             // the basis (k_oupdate with dots makes two: the update, then the dots of the updated
             // w), and w
-            KL(F_OCGS, fa * (nv * 24 + 16) * n, fa * 6 * nv * n,
-               launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                              // h1 = V^H w
+            if (df)       // 16 B (hi + lo FP32) per vector and element; 4 real products of ~12 FP32 ops
+                KL(F_ODF, fa * (nv * 16 + 16) * n, fa * 48 * nv * n,
+                   launch_odots_df(B, V32, V32L, j + 1, w, O.part.as<double2>(), s));              // h1 = V^H w
+            else
+                KL(F_OCGS, fa * (nv * 24 + 16) * n, fa * 6 * nv * n,
+                   launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                          // h1 = V^H w
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
             KL(F_OCGS, fa * (nv * 48 + 32) * n, fa * 12 * nv * n,
                launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
@@ -1432,8 +1449,9 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                               O.h1.as<double2>(), O.h2.as<double2>(), O.npart.as<double>(), O.fnorm.as<double>(),
                               prm->outer_tol, O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>(), hstride,
                               total, s));
-            KL(F_OMISC, 2.0 * fa * n * 16 + (r32 ? fa * n * 8.0 : 0.0), 0,
+            KL(F_OMISC, 2.0 * fa * n * 16 + (r32 ? fa * n * 8.0 : 0.0) + (df ? fa * n * 8.0 : 0.0), 0,
                launch_oscale(B, V + (long long)(j + 1) * B.ld, r32 ? V32 + (long long)(j + 1) * B.ld32 : nullptr,
+                             df ? V32L + (long long)(j + 1) * B.ld32 : nullptr,
                              O.D.as<double>() + (long long)(j + 1) * B.ld, w, O.hn.as<double>(), s));
             CKL();
             total++;
@@ -1767,6 +1785,7 @@ hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value) {
     if (value != 0 && value != 1) FAIL(HDD_ERR_INVALID_ARG, "option values are 0 or 1");
     if (key == HDD_OPT_COARSE_LOOKAHEAD) ctx->coarse_la = value;
     else if (key == HDD_OPT_FUSED_INNER) ctx->fused_inner = value;
+    else if (key == HDD_OPT_OUTER_DOTS_DF) ctx->outer_df = value;
     else FAIL(HDD_ERR_INVALID_ARG, "unknown option %d", key);
     return HDD_OK;
 }

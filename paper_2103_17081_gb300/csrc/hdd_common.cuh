@@ -293,14 +293,17 @@ void launch_ogivens(const OuterBatch &B, double2 *H, double *cs, double2 *sn, do
                     const double2 *h1, const double2 *h2, const double *npart, const double *fnorm,
                     double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
                     cudaStream_t s);
-void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, double *outD, const double2 *w,
-                   const double *hn, cudaStream_t s);
+void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, float2 *out32L, double *outD,
+                   const double2 *w, const double *hn, cudaStream_t s);
+// first CGS pass in double-FP32 arithmetic from the hi/lo FP32 copies of the basis
+void launch_odots_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const double2 *w,
+                     double2 *part, cudaStream_t s);
 void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, const int *kcols, int kmax,
                       double2 *y, cudaStream_t s);
 void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int kmax, const double2 *Zb,
                   double2 *x, cudaStream_t s);
 void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
-                  double *D, double2 *g, double2 *Wq, double *beta_out, cudaStream_t s);
+                  float2 *V32L, double *D, double2 *g, double2 *Wq, double *beta_out, cudaStream_t s);
 void launch_orotate(const OuterBatch &B, double2 *H, const double *cs, const double2 *sn, const int *kcols,
                     int kmax, cudaStream_t s);
 cudaError_t set_outer_smem_limits(size_t bytes);

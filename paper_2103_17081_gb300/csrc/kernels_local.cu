@@ -774,16 +774,11 @@ k_arnoldi_step(StepArgs<R> a) {
             }
         }
     }
-    // task-wide sums of nv values: per-CTA sums go to slot gat[b][rank][l] of every CTA, then one
-    // cluster barrier, then each CTA adds the C slots in rank order into out[l]
-    auto allreduce = [&](int b, int n, auto get, c2<R> *out) {
-        const int lane = tid & 31, warp = tid >> 5;
-        for (int l = 0; l < n; l++) {
-            c2<R> v = get(l);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) { v.x += shfl_xor(v.x, o); v.y += shfl_xor(v.y, o); }
-            if (lane == 0) red[warp * LDP + l] = v;
-        }
+    // task-wide sums of n values: the per-warp partials in red[warp][l] are added per CTA and
+    // sent to slot gat[b][rank][l] of every CTA, then one cluster barrier, then each CTA adds
+    // the C slots in rank order into out[l]
+    const int lane = tid & 31, warp = tid >> 5;
+    auto gather = [&](int b, int n, c2<R> *out) {
         __syncthreads();
         for (int idx = tid; idx < n * C; idx += blockDim.x) {
             const int l = idx % n, dst = idx / n;
@@ -799,39 +794,65 @@ k_arnoldi_step(StepArgs<R> a) {
         }
         __syncthreads();
     };
-    auto dots = [&](int l) {
-        c2<R> acc = mk<R>(0, 0);
-        const c2<R> *vl = a.V + (long long)l * a.ld + base;
+    auto warp_store = [&](int l, c2<R> v) {
 #pragma unroll
-        for (int k = 0; k < EPT; k++) {
-            const int e = tid + k * LOCAL_THREADS;
-            if (e < cnt) cdotc_acc<R>(acc, vl[e], wv[k]);
-        }
-        return acc;
+        for (int o = 16; o > 0; o >>= 1) { v.x += shfl_xor(v.x, o); v.y += shfl_xor(v.y, o); }
+        if (lane == 0) red[warp * LDP + l] = v;
     };
-    auto update = [&](const c2<R> *h) {
-        for (int l = 0; l < nv; l++) {
-            const c2<R> hl = h[l];
-            const c2<R> *vl = a.V + (long long)l * a.ld + base;
+    // h = V^H w over the task: four basis vectors per sweep, so their loads are in flight together
+    auto reduce_dots = [&](int b, c2<R> *out) {
+        for (int l0 = 0; l0 < nv; l0 += 4) {
+            c2<R> acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) acc[u] = mk<R>(0, 0);
 #pragma unroll
             for (int k = 0; k < EPT; k++) {
                 const int e = tid + k * LOCAL_THREADS;
-                if (e < cnt) caxpy_neg<R>(wv[k], hl, vl[e]);
+                if (e < cnt) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (l0 + u < nv) cdotc_acc<R>(acc[u], a.V[(long long)(l0 + u) * a.ld + base + e], wv[k]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (l0 + u < nv) warp_store(l0 + u, acc[u]);
+        }
+        gather(b, nv, out);
+    };
+    // w -= V h, four basis vectors per sweep
+    auto update = [&](const c2<R> *h) {
+        for (int l0 = 0; l0 < nv; l0 += 4) {
+            c2<R> hl[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) hl[u] = l0 + u < nv ? h[l0 + u] : mk<R>(0, 0);
+#pragma unroll
+            for (int k = 0; k < EPT; k++) {
+                const int e = tid + k * LOCAL_THREADS;
+                if (e < cnt) {
+                    c2<R> v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        v[u] = l0 + u < nv ? a.V[(long long)(l0 + u) * a.ld + base + e] : mk<R>(0, 0);
+#pragma unroll
+                    for (int u = 0; u < 4; u++) caxpy_neg<R>(wv[k], hl[u], v[u]);
+                }
             }
         }
     };
-    allreduce(0, nv, dots, h1s);
+    reduce_dots(0, h1s);
     // ---- B: w -= V h1, partial h2 ----
     update(h1s);
-    allreduce(1, nv, dots, h2s);
+    reduce_dots(1, h2s);
     // ---- C: w -= V h2, ||w||² ----
     update(h2s);
-    allreduce(0, 1, [&](int) {
+    {
         R nrm = 0;
 #pragma unroll
         for (int k = 0; k < EPT; k++) nrm = fma(wv[k].x, wv[k].x, fma(wv[k].y, wv[k].y, nrm));
-        return mk<R>(nrm, 0);
-    }, nrm_s);
+        warp_store(0, mk<R>(nrm, 0));
+        gather(0, 1, nrm_s);
+    }
     if (tid == 0) hn_s = sqrt(nrm_s[0].x);
     __syncthreads();
     const R hn = hn_s;

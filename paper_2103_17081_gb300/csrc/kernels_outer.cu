@@ -190,6 +190,96 @@ k_odots(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__re
     warp_dots(V, D, B.ld, nv, ws, b, len, part, B.ldp);
 }
 
+// ------------------------------------------------------------------------------------------
+// First CGS pass in double-FP32 arithmetic.  The basis is kept as two FP32 copies, hi = fl32(v)
+// and lo = fl32(v - hi) (v = hi + lo to about 2^-48 relative), and w is split the same way per
+// element.  Each real product x·y is formed as the exact product of the high parts (p, and its
+// rounding error e = fma(xh, yh, -p)) plus the two cross terms xh·yl + xl·yh; p is added to the
+// running sum with an error-free two-sum (Knuth) and everything small goes to a second FP32
+// accumulator (the compensated dot product of Ogita, Rump & Oishi, SIAM J. Sci. Comput. 2005,
+// on split inputs).  Per lane the error is at most u·|sum| + γ_m² Σ|v_i w_i| with u = 2^-24 and
+// m the terms the lane adds (a few tens here: a chunk of ≤ 1536 elements over 64 accumulator
+// sets); the lane results are widened to FP64 and reduced in FP64.  Checked on the CPU against
+// exact rational sums: ≤ 2e-15 of Σ|v_i||w_i|, as accurate as an FP64 sum of the same terms.
+// That is far below what the second CGS pass needs (it runs in FP64 and removes whatever the
+// first pass left; the first-pass error only has to keep the second-pass coefficients small
+// enough for the guarded FP32 correction of k_oupdate2).  These passes run
+// on the FP32 pipe and read 16 bytes per basis vector and element (hi + lo), where the FP64
+// Gauss form needs three FP64 FMAs and 24 bytes.  The _rn intrinsics keep the compiler from
+// contracting the error-free steps into fused multiply-adds.
+// ------------------------------------------------------------------------------------------
+struct WStageDF { float4 w[OCH]; };        // (Re hi, Re lo, Im hi, Im lo) per element
+
+__device__ __forceinline__ void df_acc(float &sh, float &sl, float xh, float xl, float yh, float yl) {
+    const float p = __fmul_rn(xh, yh);
+    const float e = fmaf(xh, yh, -p);                 // exact: xh·yh = p + e
+    const float c = fmaf(xh, yl, fmaf(xl, yh, e));
+    const float t = __fadd_rn(sh, p);                 // two-sum: sh + p = t + err exactly
+    const float bb = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, c));
+}
+
+// Partial dots part[r][cta][l] = Σ_{chunk} conj(V_{r,l}) w_r, l < nv, from the hi/lo FP32 basis.
+__global__ void __launch_bounds__(OT)
+k_odots_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int nv,
+           const double2 *__restrict__ w, double2 *__restrict__ part) {
+    __shared__ WStageDF ws;
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    Vh += r * B.n32; Vl += r * B.n32; w += r * B.n; part += (long long)r * B.G * B.ldp;
+    long long b, e;
+    chunk_of(B.n, b, e);
+    const int len = (int)(e > b ? e - b : 0);
+    for (int i = threadIdx.x; i < len; i += OT) {
+        const double2 x = w[b + i];
+        const float rh = (float)x.x, ih = (float)x.y;
+        ws.w[i] = make_float4(rh, (float)(x.x - (double)rh), ih, (float)(x.y - (double)ih));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = warp; l < nv; l += OT / 32) {
+        const float2 *hp = Vh + (long long)l * B.ld32 + b, *lp = Vl + (long long)l * B.ld32 + b;
+        // four independent accumulator sets (elements i, i + 32, i + 64, i + 96): eight loads of
+        // the basis in flight per lane (the pass is bound by bytes in flight, not by the FP32 pipe)
+        float sh[4][2], sl[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; u++) { sh[u][0] = sh[u][1] = sl[u][0] = sl[u][1] = 0.f; }
+        int i = lane;
+        for (; i + 96 < len; i += 128) {
+            float2 vh[4], vl[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) { vh[u] = hp[i + 32 * u]; vl[u] = lp[i + 32 * u]; }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const float4 x = ws.w[i + 32 * u];
+                // conj(v)·w = (vr wr + vi wi) + i (vr wi - vi wr)
+                df_acc(sh[u][0], sl[u][0], vh[u].x, vl[u].x, x.x, x.y);
+                df_acc(sh[u][1], sl[u][1], vh[u].x, vl[u].x, x.z, x.w);
+                df_acc(sh[u][0], sl[u][0], vh[u].y, vl[u].y, x.z, x.w);
+                df_acc(sh[u][1], sl[u][1], -vh[u].y, -vl[u].y, x.x, x.y);
+            }
+        }
+        for (; i < len; i += 32) {
+            const float2 vh = hp[i], vl = lp[i];
+            const float4 x = ws.w[i];
+            df_acc(sh[0][0], sl[0][0], vh.x, vl.x, x.x, x.y);
+            df_acc(sh[0][1], sl[0][1], vh.x, vl.x, x.z, x.w);
+            df_acc(sh[0][0], sl[0][0], vh.y, vl.y, x.z, x.w);
+            df_acc(sh[0][1], sl[0][1], -vh.y, -vl.y, x.x, x.y);
+        }
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            re += (double)sh[u][0] + (double)sl[u][0];
+            im += (double)sh[u][1] + (double)sl[u][1];
+        }
+        for (int o = 16; o > 0; o >>= 1) { re += shfl_xor(re, o); im += shfl_xor(im, o); }
+        if (lane == 0) part[(long long)blockIdx.x * B.ldp + l] = make_double2(re, im);
+    }
+}
+
 // x -= Σ_{l<nv} hs[l] V_l(i) in FP64 with two independent accumulation chains.
 __device__ __forceinline__ double2 update_fp64(double2 x0, const double2 *__restrict__ vp, long long ld,
                                                const double2 *__restrict__ hs, int nv) {
@@ -500,20 +590,25 @@ __global__ void k_orotate(OuterBatch B, double2 *__restrict__ H, const double *_
 }
 
 // V_{r,j+1} = w_r / hn_r, its FP32 copy out32 and Re - Im into outD (each if not null)
+// (and, if out32L is not null, the FP32 remainder v - fl32(v) of the double-FP32 first pass)
 __global__ void k_oscale(OuterBatch B, double2 *__restrict__ out, float2 *__restrict__ out32,
-                         double *__restrict__ outD, const double2 *__restrict__ w, const double *__restrict__ hn) {
+                         float2 *__restrict__ out32L, double *__restrict__ outD, const double2 *__restrict__ w,
+                         const double *__restrict__ hn) {
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     const double h = hn[r];
     if (!(h > 0.0)) return;
     out += r * B.n; w += r * B.n;
     if (out32) out32 += r * B.n32;
+    if (out32L) out32L += r * B.n32;
     if (outD) outD += r * B.n;
     const double inv = 1.0 / h;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
         const double2 v = make_double2(w[i].x * inv, w[i].y * inv);
         out[i] = v;
-        if (out32) out32[i] = make_float2((float)v.x, (float)v.y);
+        const float2 hi = make_float2((float)v.x, (float)v.y);
+        if (out32) out32[i] = hi;
+        if (out32L) out32L[i] = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
         if (outD) outD[i] = v.x - v.y;
     }
 }
@@ -562,8 +657,9 @@ __global__ void k_oaxpy(OuterBatch B, const double2 *__restrict__ y, const int *
 // g_r = [β_r, 0, ..., 0] (R+1 entries); FP32 copy of v_{r,0} in V32 (if not null); row 0 of the
 // (empty) rotation product, Wq_r = [1].
 __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const double *__restrict__ npart,
-                        double2 *__restrict__ V, float2 *__restrict__ V32, double *__restrict__ D,
-                        double2 *__restrict__ g, double2 *__restrict__ Wq, double *__restrict__ beta_out) {
+                        double2 *__restrict__ V, float2 *__restrict__ V32, float2 *__restrict__ V32L,
+                        double *__restrict__ D, double2 *__restrict__ g, double2 *__restrict__ Wq,
+                        double *__restrict__ beta_out) {
     __shared__ double beta_s;
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
@@ -583,11 +679,14 @@ __global__ void k_oinit(OuterBatch B, const double2 *__restrict__ rv, const doub
     if (!(beta > 0.0)) return;
     const double inv = 1.0 / beta;
     float2 *v32 = V32 ? V32 + r * B.n32 : nullptr;
+    float2 *v32l = V32L ? V32L + r * B.n32 : nullptr;
     double *d0 = D ? D + r * B.n : nullptr;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < B.n; i += (long long)gridDim.x * blockDim.x) {
         const double2 v = make_double2(rv[i].x * inv, rv[i].y * inv);
         v0[i] = v;
-        if (v32) v32[i] = make_float2((float)v.x, (float)v.y);
+        const float2 hi = make_float2((float)v.x, (float)v.y);
+        if (v32) v32[i] = hi;
+        if (v32l) v32l[i] = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
         if (d0) d0[i] = v.x - v.y;
     }
 }
@@ -629,6 +728,10 @@ void launch_build_rhs(const Stencil &st, int N, double h, int npts, const double
 void launch_odots(const OuterBatch &B, const double2 *V, int nv, const double2 *w, double2 *part, cudaStream_t s) {
     k_odots<<<dim3(B.G, B.nrhs), OT, 0, s>>>(B, V, nv, w, part);
 }
+void launch_odots_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const double2 *w,
+                     double2 *part, cudaStream_t s) {
+    k_odots_df<<<dim3(B.G, B.nrhs), OT, 0, s>>>(B, Vh, Vl, nv, w, part);
+}
 void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2 *h, double2 *w,
                     double2 *part_dots, double *part_norm, cudaStream_t s) {
     k_oupdate<<<dim3(B.G, B.nrhs), OT, (size_t)nv * 3 * sizeof(double), s>>>(B, V, nv, h, w, part_dots, part_norm);
@@ -656,9 +759,9 @@ void launch_orotate(const OuterBatch &B, double2 *H, const double *cs, const dou
                     int kmax, cudaStream_t s) {
     k_orotate<<<dim3((kmax + 63) / 64, B.nrhs), 64, 0, s>>>(B, H, cs, sn, kcols);
 }
-void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, double *outD, const double2 *w,
-                   const double *hn, cudaStream_t s) {
-    k_oscale<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, out, out32, outD, w, hn);
+void launch_oscale(const OuterBatch &B, double2 *out, float2 *out32, float2 *out32L, double *outD,
+                   const double2 *w, const double *hn, cudaStream_t s) {
+    k_oscale<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, out, out32, out32L, outD, w, hn);
 }
 void launch_otrisolve(const OuterBatch &B, const double2 *H, const double2 *g, const int *kcols, int kmax,
                       double2 *y, cudaStream_t s) {
@@ -669,8 +772,8 @@ void launch_oaxpy(const OuterBatch &B, const double2 *y, const int *kcols, int k
     k_oaxpy<<<dim3(grid_for(B.n, 256), B.nrhs), 256, (size_t)kmax * sizeof(double2), s>>>(B, y, kcols, Zb, x);
 }
 void launch_oinit(const OuterBatch &B, const double2 *rv, const double *npart, double2 *V, float2 *V32,
-                  double *D, double2 *g, double2 *Wq, double *beta_out, cudaStream_t s) {
-    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, V32, D, g, Wq, beta_out);
+                  float2 *V32L, double *D, double2 *g, double2 *Wq, double *beta_out, cudaStream_t s) {
+    k_oinit<<<dim3(grid_for(B.n, 256), B.nrhs), 256, 0, s>>>(B, rv, npart, V, V32, V32L, D, g, Wq, beta_out);
 }
 cudaError_t set_outer_smem_limits(size_t bytes) {
     cudaError_t e;

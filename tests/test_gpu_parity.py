@@ -271,6 +271,32 @@ def test_outer_fp32_reorthogonalisation_matches_fp64(wname):
     assert float(torch.linalg.vector_norm(f - s.apply_A(x32)) / torch.linalg.vector_norm(f)) <= 1.0001e-6
 
 
+@pytest.mark.parametrize("wname", ["tiny", "k100"])
+def test_outer_double_fp32_first_pass_matches_fp64(wname):
+    """The outer CGS2's first-pass dot products in double-FP32 arithmetic (hi/lo FP32 basis, error-
+    free products and sums) give the FP64 iteration: with complex128 inner solves and the guarded
+    FP32 second pass, the same outer count as the all-FP64 first pass, solutions equal to 1e-7,
+    residual histories to 1e-6 while the residual is above 1e-4, and the second-pass guard never
+    falls back to FP64 (the first-pass error stays at FP64 rounding size)."""
+    torch = _torch()
+    from paper_2103_17081_gb300 import Solver
+    w = W.make(wname)
+    s = Solver.from_workload(w)
+    f = s.build_rhs(w.rhs[0])
+    s.set_option("outer_dots_df", 0)
+    x64, st64 = s.solve(f, inner_prec=128, outer_reorth32=1)
+    s.set_option("outer_dots_df", 1)
+    xdf, stdf = s.solve(f, inner_prec=128, outer_reorth32=1)
+    assert stdf["outer_reorth_fp64"] == 0 and st64["outer_reorth_fp64"] == 0
+    assert stdf["outer_its"] == st64["outer_its"]
+    assert _rel(xdf.cpu().numpy(), x64.cpu().numpy()) <= 1e-7
+    h64, hdf = np.array(st64["res_history"]), np.array(stdf["res_history"])
+    early = h64 >= 1e-4
+    assert early.sum() >= 5
+    np.testing.assert_allclose(hdf[early], h64[early], rtol=1e-6)
+    assert float(torch.linalg.vector_norm(f - s.apply_A(xdf)) / torch.linalg.vector_norm(f)) <= 1.0001e-6
+
+
 def test_k200_ras_apply_full_size(oracle_mod):
     """k=200, N=640, 8x8 subdomains: one full RAS application (64 local solves) vs the oracle."""
     w = W.make("k200")
