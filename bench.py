@@ -35,10 +35,10 @@ L2_FLUSH_BYTES = 512 << 20                      # > 129 MB L2
 # capture of k_odots and k_oupdate at outer iteration 200 of the k=200 solve (201 basis vectors:
 # 1.9827 + 4.0434 GB against 1.9763 + 3.9525 GB algorithmic).  Their traffic grows with the
 # basis vectors read, so the ratio scales that capture to the average launch of a k=200 run.
-# With the double-FP32 first pass (the default) the FP64 family holds k_oupdate alone, whose
-# own ratio from the same capture applies (the kernel is unchanged since).
+# With the double-FP32 dots (the default) the FP64 family is k_oupdate_df alone; its ratio comes
+# from its own capture (None until one exists: the traffic field is then null).
 OCGS_DRAM_PER_ALG = (1.982693 + 4.043380) / (1.976274 + 3.952547)
-OUPDATE_DRAM_PER_ALG = 4.043380 / 3.952547
+OUPDATE_DF_DRAM_PER_ALG = None
 
 
 def _peaks():
@@ -334,15 +334,19 @@ def run_gpu(args):
     hbm, hbm_src = _peaks()
     dom = max(prof, key=lambda d: d["ms"])
     per_launch_ms = dom["ms"] / max(1, dom["launches"])
-    if dom["bound"] == "fp64":
+    fp64_frac = dom["flops"] / (dom["ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
+    hbm_frac = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9 / hbm
+    if dom["bound"] == "fp64" and fp64_frac >= hbm_frac:      # the roof it sits closer to binds
         ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom["name"],
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (measured 1.19)"}
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (measured 1.19)",
+                "hbm_frac": hbm_frac}
     else:
         ach = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": dom["name"], "peak_source": hbm_src}
+                "traffic": None, "kernel": dom["name"], "peak_source": hbm_src,
+                "fp64_frac": fp64_frac if dom["bound"] == "fp64" else None}
     roof["launches"] = dom["launches"]
     roof["ms_per_launch"] = per_launch_ms
     if (dom["name"] == "outer_cgs2_fp64" and w.name == "k200" and w.nrhs == 1 and args.prec == 64
@@ -350,10 +354,15 @@ def run_gpu(args):
         # the configuration of the ncu capture; elsewhere (bases that fit in L2, other kernels)
         # no measured traffic exists and the field stays null
         df = any(d["name"] == "outer_dots_df32" and d["launches"] for d in prof)
-        roof["traffic"] = dom["bytes"] / max(1, dom["launches"]) * (OUPDATE_DRAM_PER_ALG if df else OCGS_DRAM_PER_ALG)
-        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of " +
-                                  ("k_oupdate" if df else "k_odots and k_oupdate") +
-                                  " at outer iteration 200, scaled by basis vectors to this run's average launch")
+        if df and OUPDATE_DF_DRAM_PER_ALG is not None:
+            roof["traffic"] = dom["bytes"] / max(1, dom["launches"]) * OUPDATE_DF_DRAM_PER_ALG
+            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_oupdate_df, "
+                                      "scaled by basis vectors to this run's average launch")
+        elif not df:
+            roof["traffic"] = dom["bytes"] / max(1, dom["launches"]) * OCGS_DRAM_PER_ALG
+            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_odots and "
+                                      "k_oupdate at outer iteration 200, scaled by basis vectors to this "
+                                      "run's average launch")
     fams = {d["name"]: {"ms": round(d["ms"], 3), "launches": d["launches"],
                         "GB/s": round(d["bytes"] / max(d["ms"], 1e-9) / 1e6, 1),
                         "TFLOP/s": round(d["flops"] / max(d["ms"], 1e-9) / 1e9, 4)}
@@ -393,6 +402,57 @@ def run_gpu(args):
     return 0
 
 
+def run_ras_dense(args):
+    """Subdomain-solve throughput: `args.ras_dense` timed RAS applications (after one untimed) of a
+    seeded dense vector, so every (subdomain, RHS) task is active, complex64 inner solves to the
+    workload's tolerance; per kernel family the CUDA-event time, launches and algorithmic GB/s,
+    and the subdomain-solve families (local_* and the coarse solve) against the HBM peak.  Prints
+    one JSON line (not the time-to-solution line)."""
+    import torch
+
+    from paper_2103_17081_gb300 import Solver
+
+    w = W.make(args.workload)
+    s = Solver.from_workload(w)
+    if args.autotune:
+        s.autotune(inner_tol=w.inner_tol, inner_prec=args.prec)
+    n = s.n
+    g = torch.Generator(device="cuda").manual_seed(5)
+    v = torch.complex(torch.rand(s.nrhs * n, generator=g, device="cuda", dtype=torch.float64) - 0.5,
+                      torch.rand(s.nrhs * n, generator=g, device="cuda", dtype=torch.float64) - 0.5)
+    for r in range(s.nrhs):
+        v[r * n:(r + 1) * n] /= torch.linalg.vector_norm(v[r * n:(r + 1) * n])
+    z = s.empty(v.numel())
+    kw = dict(inner_tol=w.inner_tol, inner_prec=args.prec)
+    s.ras_apply(v, out=z, **kw)
+    torch.cuda.synchronize()
+    s.profile(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its = []
+    for _ in range(args.ras_dense):
+        _, its = s.ras_apply(v, out=z, **kw)
+    e1.record(stream)
+    e1.synchronize()
+    prof = s.profile_stats()
+    s.profile(False)
+    hbm, hbm_src = _peaks()
+    fams = {d["name"]: {"ms": round(d["ms"], 3), "launches": d["launches"],
+                        "GB/s": round(d["bytes"] / max(d["ms"], 1e-9) / 1e6, 1)}
+            for d in prof if d["launches"]}
+    loc = [d for d in prof if d["name"].startswith("local_")]
+    sub = loc + [d for d in prof if d["name"] == "coarse_solve_fp64"]
+    lgbs = sum(d["bytes"] for d in loc) / max(sum(d["ms"] for d in loc), 1e-9) / 1e6
+    print(json.dumps({"mode": "ras_dense", "config": workload_config(w), "inner_prec": args.prec,
+                      "applications": args.ras_dense, "ms_per_application": e0.elapsed_time(e1) / args.ras_dense,
+                      "inner_its_avg": sum(its) / max(1, len(its)), "inner_its_max": max(its) if its else 0,
+                      "local_GBps": lgbs, "local_frac_hbm": lgbs / hbm,
+                      "local_ms": sum(d["ms"] for d in loc), "subdomain_ms": sum(d["ms"] for d in sub),
+                      "hbm_peak": hbm, "peak_source": hbm_src, "kernels": fams}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,7 +475,12 @@ def main():
                     help="pick the local tile shapes with hdd_autotune before the warm-up")
     ap.add_argument("--fp64-reorth", action="store_true",
                     help="second outer CGS pass in FP64 (default: guarded FP32 correction)")
+    ap.add_argument("--ras-dense", type=int, default=0,
+                    help="instead of solves: time this many RAS applications of a dense seeded vector "
+                         "(every local solve active) and report the subdomain-solve kernels' bandwidth")
     args = ap.parse_args()
+    if args.ras_dense > 0:
+        return run_ras_dense(args)
     if args.impl == "reference":
         if not args.full_outer_its:
             args.full_outer_its = {"tiny": 18, "k100": 282, "k200": 1270, "k200s": 781}.get(args.workload, 1270)

@@ -1327,7 +1327,11 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     CK(O.Wq.ensure((size_t)nr * (R + 1) * sizeof(double2)));
     CK(O.h1.ensure((size_t)nr * ldp * sizeof(double2))); CK(O.h2.ensure((size_t)nr * ldp * sizeof(double2)));
     CK(O.y.ensure((size_t)nr * ldp * sizeof(double2)));
-    CK(O.part.ensure((size_t)nr * G * ldp * sizeof(double2)));
+    // the double-FP32 first pass runs on a grid of its own (smaller chunks: more of the basis in
+    // flight per SM); its partials share the buffer
+    OuterBatch Bd = B;
+    Bd.G = 2 * G;
+    CK(O.part.ensure((size_t)nr * Bd.G * ldp * sizeof(double2)));
     CK(O.npart.ensure((size_t)nr * G * sizeof(double)));
     CK(O.npart1.ensure((size_t)nr * G * sizeof(double)));
     const bool r32 = prm->outer_reorth32 != 0;
@@ -1390,6 +1394,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
         for (int r = 0; r < nr; r++) act[r] = !done[r];
         if ((st = push_active()) != HDD_OK) return st;
         B.active = dact;
+        Bd.active = dact;
         KL(F_OMISC, 3.0 * nr * n * 16, 0, launch_gstencil(ctx->st, ctx->N, x, rv, f, nr, dact, s));
         KL(F_OMISC, (double)nr * n * 16, 0, launch_onorm(B, rv, O.npart.as<double>(), s));
         KL(F_OMISC, 2.0 * nr * n * 16 + (r32 ? nr * n * 8.0 : 0.0) + (df ? nr * n * 8.0 : 0.0), 0,
@@ -1426,13 +1431,15 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
             // Gauss form); bytes: V (16 B) and d (8 B) per vector and element for each pass over
             // the basis (k_oupdate with dots makes two: the update, then the dots of the updated
             // w), and w
-            if (df)       // 16 B (hi + lo FP32) per vector and element; 4 real products of ~12 FP32 ops
+            if (df) {     // 16 B (hi + lo FP32) per vector and element; 4 real products of ~12 FP32 ops
                 KL(F_ODF, fa * (nv * 16 + 16) * n, fa * 48 * nv * n,
-                   launch_odots_df(B, V32, V32L, j + 1, w, O.part.as<double2>(), s));              // h1 = V^H w
-            else
+                   launch_odots_df(Bd, V32, V32L, j + 1, w, O.part.as<double2>(), s));             // h1 = V^H w
+                KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
+            } else {
                 KL(F_OCGS, fa * (nv * 24 + 16) * n, fa * 6 * nv * n,
                    launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                          // h1 = V^H w
-            KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
+                KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
+            }
             KL(F_OCGS, fa * (nv * 48 + 32) * n, fa * 12 * nv * n,
                launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
             KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));

@@ -544,8 +544,7 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
 // barrier, and the bulk of the FP64 work of consecutive blocks overlaps.  Same operators, ring
 // and windows as k_block_solve; the sums are taken in a fixed order (deterministic).
 // ------------------------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int la_stride(int K) { return K + ((K & 3) ? 0 : 2); }
-__host__ __device__ __forceinline__ int la_slot(int maxK) { return BNB * (maxK + 2) + BNB; }
+__host__ __device__ __forceinline__ int la_slot(int maxK) { return BNB * maxK + BNB; }
 constexpr int LA_T = 256;                 // threads: warp 0 (chain) + LA_BW bulk warps
 constexpr int LA_BW = LA_T / 32 - 1;      // bulk warps (7)
 constexpr int LA_BL = 2 * LA_BW;          // bulk lanes per row (14): (warp, half)
@@ -577,19 +576,14 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = lane >> 1, half = lane & 1;          // 16 rows x 2 lanes per warp
     const int q = (warp - 1) * 2 + half;                 // bulk lane of the row (warp >= 1)
-    // operator rows land at stride la_stride(K) (≡ 2 mod 4 doubles: the 16 rows x 2 lanes of a
-    // warp then hit distinct 8-byte banks pairwise); inputs after the widest operator
     auto load_block = [&](long long src_off, int K, int buf, int J) {
         double *dst = sm + buf * slot;
         const double *src = Mall + src_off;
-        const int S = la_stride(K), cpr = K / 2;          // 16-byte chunks per row (K is even)
-        for (int c = tid; c < BNB * cpr; c += LA_T) {
-            const int r = c / cpr;
-            cp_async16(dst + r * S + 2 * (c - r * cpr), src + 2 * c);
-        }
+        const int nchunk = BNB * K / 2;                  // 16-byte chunks
+        for (int c = tid; c < nchunk; c += LA_T) cp_async16(dst + 2 * c, src + 2 * c);
         if (tid < BNB) {
             const int i = J * BNB + tid;
-            cp_async8_zfill(dst + BNB * (maxK + 2) + tid, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
+            cp_async8_zfill(dst + BNB * maxK + tid, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
         }
     };
     for (int i = tid; i < m; i += LA_T) outr[STR * (long long)i] = inr[STR * (long long)perm[i]];
@@ -602,8 +596,8 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
     // lane's row: diagonal columns k < BNB take the block's inputs, panel column p = k - BNB takes
     // win[(pbase + p) & mask].  Columns q, q + LA_BL, ... of the range; four accumulators.
     auto bulk_row = [&](const double *Mb, int K, int k0, int k1, const double *win, int pbase, int mask) {
-        const double *Mr = Mb + row * la_stride(K);
-        const double *a = Mb + BNB * (maxK + 2);
+        const double *Mr = Mb + row * K;
+        const double *a = Mb + BNB * maxK;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int k = q;
         for (; k < BNB; k += LA_BL) s0 = fma(Mr[k], a[k], s0);
@@ -623,7 +617,7 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
     // Warp 0: block J from the bulk partials (parity par) and the recent panel columns [p0, p1).
     auto chain_row = [&](const double *Mb, int K, int p0, int p1, const double *win, int pbase, int mask,
                          int par) {
-        const double *Mr = Mb + row * la_stride(K) + BNB;
+        const double *Mr = Mb + row * K + BNB;
         double s0 = 0.0, s1 = 0.0;
         for (int w = half; w < LA_BW; w += 2) s0 += part[par][w][row];
         int p = p0 + half;

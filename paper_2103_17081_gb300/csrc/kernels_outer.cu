@@ -221,26 +221,20 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, float xh, float xl,
     sl = __fadd_rn(sl, __fadd_rn(err, c));
 }
 
-// Partial dots part[r][cta][l] = Σ_{chunk} conj(V_{r,l}) w_r, l < nv, from the hi/lo FP32 basis.
-__global__ void __launch_bounds__(OT)
-k_odots_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int nv,
-           const double2 *__restrict__ w, double2 *__restrict__ part) {
-    __shared__ WStageDF ws;
-    const int r = blockIdx.y;
-    if (B.active && !B.active[r]) return;
-    Vh += r * B.n32; Vl += r * B.n32; w += r * B.n; part += (long long)r * B.G * B.ldp;
-    long long b, e;
-    chunk_of(B.n, b, e);
-    const int len = (int)(e > b ? e - b : 0);
-    for (int i = threadIdx.x; i < len; i += OT) {
-        const double2 x = w[b + i];
-        const float rh = (float)x.x, ih = (float)x.y;
-        ws.w[i] = make_float4(rh, (float)(x.x - (double)rh), ih, (float)(x.y - (double)ih));
-    }
-    __syncthreads();
+// w (FP64) split per element into (Re hi, Re lo, Im hi, Im lo) for the double-FP32 dots
+__device__ __forceinline__ void stage_w_df(WStageDF &ws, int i, double2 x) {
+    const float rh = (float)x.x, ih = (float)x.y;
+    ws.w[i] = make_float4(rh, (float)(x.x - (double)rh), ih, (float)(x.y - (double)ih));
+}
+
+// Warp q of the CTA forms the partial dots of vectors l = q, q + 8, ... over the chunk
+// [b, b + len) from the hi/lo FP32 basis (element stride of the copies: B.ld32 between vectors).
+__device__ __forceinline__ void warp_dots_df(const float2 *__restrict__ Vh, const float2 *__restrict__ Vl,
+                                             long long ld32, int nv, const WStageDF &ws, long long b, int len,
+                                             double2 *__restrict__ part, int ldp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l = warp; l < nv; l += OT / 32) {
-        const float2 *hp = Vh + (long long)l * B.ld32 + b, *lp = Vl + (long long)l * B.ld32 + b;
+        const float2 *hp = Vh + (long long)l * ld32 + b, *lp = Vl + (long long)l * ld32 + b;
         // four independent accumulator sets (elements i, i + 32, i + 64, i + 96): eight loads of
         // the basis in flight per lane (the pass is bound by bytes in flight, not by the FP32 pipe)
         float sh[4][2], sl[4][2];
@@ -276,8 +270,24 @@ k_odots_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict
             im += (double)sh[u][1] + (double)sl[u][1];
         }
         for (int o = 16; o > 0; o >>= 1) { re += shfl_xor(re, o); im += shfl_xor(im, o); }
-        if (lane == 0) part[(long long)blockIdx.x * B.ldp + l] = make_double2(re, im);
+        if (lane == 0) part[(long long)blockIdx.x * ldp + l] = make_double2(re, im);
     }
+}
+
+// Partial dots part[r][cta][l] = Σ_{chunk} conj(V_{r,l}) w_r, l < nv, from the hi/lo FP32 basis.
+__global__ void __launch_bounds__(OT)
+k_odots_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int nv,
+           const double2 *__restrict__ w, double2 *__restrict__ part) {
+    __shared__ WStageDF ws;
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    Vh += r * B.n32; Vl += r * B.n32; w += r * B.n; part += (long long)r * B.G * B.ldp;
+    long long b, e;
+    chunk_of(B.n, b, e);
+    const int len = (int)(e > b ? e - b : 0);
+    for (int i = threadIdx.x; i < len; i += OT) stage_w_df(ws, i, w[b + i]);
+    __syncthreads();
+    warp_dots_df(Vh, Vl, B.ld32, nv, ws, b, len, part, B.ldp);
 }
 
 // x -= Σ_{l<nv} hs[l] V_l(i) in FP64 with two independent accumulation chains.
