@@ -799,44 +799,29 @@ k_arnoldi_step(StepArgs<R> a) {
         for (int o = 16; o > 0; o >>= 1) { v.x += shfl_xor(v.x, o); v.y += shfl_xor(v.y, o); }
         if (lane == 0) red[warp * LDP + l] = v;
     };
-    // h = V^H w over the task: four basis vectors per sweep, so their loads are in flight together
+    // h = V^H w over the task (per-warp partials, then the cluster gather)
     auto reduce_dots = [&](int b, c2<R> *out) {
-        for (int l0 = 0; l0 < nv; l0 += 4) {
-            c2<R> acc[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) acc[u] = mk<R>(0, 0);
+        for (int l = 0; l < nv; l++) {
+            c2<R> acc = mk<R>(0, 0);
+            const c2<R> *vl = a.V + (long long)l * a.ld + base;
 #pragma unroll
             for (int k = 0; k < EPT; k++) {
                 const int e = tid + k * LOCAL_THREADS;
-                if (e < cnt) {
-#pragma unroll
-                    for (int u = 0; u < 4; u++)
-                        if (l0 + u < nv) cdotc_acc<R>(acc[u], a.V[(long long)(l0 + u) * a.ld + base + e], wv[k]);
-                }
+                if (e < cnt) cdotc_acc<R>(acc, vl[e], wv[k]);
             }
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-                if (l0 + u < nv) warp_store(l0 + u, acc[u]);
+            warp_store(l, acc);
         }
         gather(b, nv, out);
     };
-    // w -= V h, four basis vectors per sweep
+    // w -= V h
     auto update = [&](const c2<R> *h) {
-        for (int l0 = 0; l0 < nv; l0 += 4) {
-            c2<R> hl[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) hl[u] = l0 + u < nv ? h[l0 + u] : mk<R>(0, 0);
+        for (int l = 0; l < nv; l++) {
+            const c2<R> hl = h[l];
+            const c2<R> *vl = a.V + (long long)l * a.ld + base;
 #pragma unroll
             for (int k = 0; k < EPT; k++) {
                 const int e = tid + k * LOCAL_THREADS;
-                if (e < cnt) {
-                    c2<R> v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; u++)
-                        v[u] = l0 + u < nv ? a.V[(long long)(l0 + u) * a.ld + base + e] : mk<R>(0, 0);
-#pragma unroll
-                    for (int u = 0; u < 4; u++) caxpy_neg<R>(wv[k], hl[u], v[u]);
-                }
+                if (e < cnt) caxpy_neg<R>(wv[k], hl, vl[e]);
             }
         }
     };
