@@ -35,10 +35,10 @@ L2_FLUSH_BYTES = 512 << 20                      # > 129 MB L2
 # capture of k_odots and k_oupdate at outer iteration 200 of the k=200 solve (201 basis vectors:
 # 1.9827 + 4.0434 GB against 1.9763 + 3.9525 GB algorithmic).  Their traffic grows with the
 # basis vectors read, so the ratio scales that capture to the average launch of a k=200 run.
-# With the double-FP32 dots (the default) the FP64 family is k_oupdate_df alone; its ratio comes
-# from its own capture (None until one exists: the traffic field is then null).
+# With the double-FP32 first pass (the default) the FP64 family is k_oupdate alone, whose own
+# ratio from the same capture applies (4.0434 GB against 3.9525 GB; the kernel is unchanged).
 OCGS_DRAM_PER_ALG = (1.982693 + 4.043380) / (1.976274 + 3.952547)
-OUPDATE_DF_DRAM_PER_ALG = None
+OUPDATE_DRAM_PER_ALG = 4.043380 / 3.952547
 
 
 def _peaks():
@@ -354,15 +354,11 @@ def run_gpu(args):
         # the configuration of the ncu capture; elsewhere (bases that fit in L2, other kernels)
         # no measured traffic exists and the field stays null
         df = any(d["name"] == "outer_dots_df32" and d["launches"] for d in prof)
-        if df and OUPDATE_DF_DRAM_PER_ALG is not None:
-            roof["traffic"] = dom["bytes"] / max(1, dom["launches"]) * OUPDATE_DF_DRAM_PER_ALG
-            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_oupdate_df, "
-                                      "scaled by basis vectors to this run's average launch")
-        elif not df:
-            roof["traffic"] = dom["bytes"] / max(1, dom["launches"]) * OCGS_DRAM_PER_ALG
-            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_odots and "
-                                      "k_oupdate at outer iteration 200, scaled by basis vectors to this "
-                                      "run's average launch")
+        roof["traffic"] = dom["bytes"] / max(1, dom["launches"]) * (OUPDATE_DRAM_PER_ALG if df else OCGS_DRAM_PER_ALG)
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of " +
+                                  ("k_oupdate" if df else "k_odots and k_oupdate") +
+                                  " at outer iteration 200 (profiles/outer_cgs2_gauss_k200.md), scaled by "
+                                  "basis vectors to this run's average launch")
     fams = {d["name"]: {"ms": round(d["ms"], 3), "launches": d["launches"],
                         "GB/s": round(d["bytes"] / max(d["ms"], 1e-9) / 1e6, 1),
                         "TFLOP/s": round(d["flops"] / max(d["ms"], 1e-9) / 1e9, 4)}

@@ -50,6 +50,7 @@ struct FactorSet {            // banded FP64 factors of one matrix per shape, bl
 template <typename R> struct InnerWork {   // inner GMRES buffers for one precision
     int restart = 0;
     DevMem f, u, x, t, V, y, s, p1, p2, p3;
+    DevMem y2, s2;                              // two coarse vectors per task (warm start)
     DevMem H, cs, sn, g, ref, its, kcols, conv, rsf;
     DevMem act0, act1, flagA, flagB;
 };
@@ -134,6 +135,8 @@ struct hdd_ctx {
     std::vector<Task> h_tasks;                  // task t = r·nsub + s
     std::vector<Tile> h_ftiles, h_ctiles;
     DevMem d_tasks, d_ftiles, d_ctiles, d_ones, d_mask;
+    DevMem d_tasks2, d_mask2;                   // every task twice, the copy's coarse offsets + ldc (two
+                                                // coarse solves per task in one launch)
     long long ld = 0, ldc = 0;
     int max_nx = 0, max_n = 0;
     int frows = FINE_ROWS, crows = COARSE_ROWS;  // tile heights (hdd_autotune)
@@ -155,6 +158,7 @@ struct hdd_ctx {
     std::vector<double> hist;
     std::vector<int> h_its;
     Prof prof;
+    int nsm = 152;                             // SMs of the device
     int coarse_la = 1;                         // HDD_OPT_COARSE_LOOKAHEAD
     int fused_inner = 1;                       // HDD_OPT_FUSED_INNER
     int outer_df = 1;                          // HDD_OPT_OUTER_DOTS_DF
@@ -383,6 +387,21 @@ void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *ou
                        F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, cfg, F.re2 ? 1 : 0, s);
 }
 
+// Two coarse solves per flagged task in one launch: in[0, ldc) and in[ldc, 2·ldc) into the same
+// halves of out (the doubled task table); `flag` (if not null) must cover 2·ntasks entries.
+void band_solve2(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *out, const int *flag,
+                 cudaStream_t s) {
+    const int nt = (int)ctx->h_tasks.size();
+    double fl = 0;
+    for (int q = 0; q < nt; q++) fl += F.fma_col[ctx->h_tasks[q].shape];
+    fl = 2.0 * (F.re2 ? 2.0 : 4.0) * fl;
+    Launch L(ctx, F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
+    BlockSolveCfg cfg = F.cfg;
+    cfg.lookahead = ctx->coarse_la;
+    launch_block_solve(ctx->d_tasks2.as<Task>(), 2 * nt, F.table.as<BlockFactor>(), F.M.as<double>(),
+                       F.P.as<int>(), F.Meta.as<int4>(), in, out, 0, flag, cfg, F.re2 ? 1 : 0, s);
+}
+
 // ---- learned warm start ---------------------------------------------------------------------
 hdd_status cnn_buffers(hdd_ctx *ctx) {
     CnnState &C = ctx->cnn;
@@ -581,6 +600,7 @@ template <typename R> hdd_status ensure_inner(hdd_ctx *ctx, int R_) {
     CK(W.f.ensure(ld * cs)); CK(W.u.ensure(ld * cs)); CK(W.x.ensure(ld * cs)); CK(W.t.ensure(ld * cs));
     CK(W.V.ensure((size_t)(R_ + 1) * ld * cs));
     CK(W.y.ensure(ldc * sizeof(double2))); CK(W.s.ensure((size_t)(R_ + 2) * ldc * sizeof(double2)));
+    CK(W.y2.ensure(2 * ldc * sizeof(double2))); CK(W.s2.ensure(2 * ldc * sizeof(double2)));
     CK(W.p1.ensure(nft * LOCAL_LDP * cs)); CK(W.p2.ensure(nft * LOCAL_LDP * cs)); CK(W.p3.ensure(nft * LOCAL_LDP * cs));
     CK(W.H.ensure((size_t)nt * (R_ + 1) * R_ * cs));
     CK(W.cs.ensure((size_t)nt * R_ * sizeof(R)));
@@ -690,13 +710,23 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
         KL(F_CNN, 0, 0, launch_cnn_output<R>(ctx->d_tasks.as<Task>(), ctx->d_ftiles.as<Tile>(),
                                                (int)ctx->h_ftiles.size(), ctx->cnn.sigma.as<float>(),
                                                ctx->cnn.A4.as<float>(), u, mask, s));
-        KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, y, 0, mask, s));
-        band_solve(ctx, ctx->E, y, sc, false, mask, s);
-        KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, x, nullptr, 0, p3, mask, s));
-        KL(F_LMISC, 0, 0, launch_set_ref<R>(a, S, p3, mask, s));
+        // E⁻¹ Zᵀ f̃ (for ||P f̃||) and E⁻¹ Zᵀ (f̃ - A ũ₀) (for r0) are independent: one launch solves
+        // both, the second into slot 0 of sc (kept for the completion)
+        double2 *yy = W.y2.template as<double2>(), *ss = W.s2.template as<double2>();
+        const int *m2 = nullptr;
+        if (mask) {
+            int *dm2 = ctx->d_mask2.as<int>();
+            CK(cudaMemcpyAsync(dm2, mask, nt * sizeof(int), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(dm2 + nt, mask, nt * sizeof(int), cudaMemcpyDeviceToDevice, s));
+            m2 = dm2;
+        }
         KL(F_LMISC, 3 * ld * cs, 0, launch_local_A<R>(a, u, t, f, mask, s));
-        KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, t, y, 0, mask, s));
-        band_solve(ctx, ctx->E, y, sc, false, mask, s);
+        KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, yy, 0, mask, s));
+        KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, t, yy + ldc, 0, mask, s));
+        band_solve2(ctx, ctx->E, yy, ss, m2, s);
+        CK(cudaMemcpyAsync(sc, ss + ldc, ldc * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, ss, x, nullptr, 0, p3, mask, s));
+        KL(F_LMISC, 0, 0, launch_set_ref<R>(a, S, p3, mask, s));
         KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, t, sc, V, nullptr, 0, p3, mask, s));
     }
     CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
@@ -1013,6 +1043,12 @@ hdd_status build_tasks(hdd_ctx *ctx, int nrhs) {
     CK(cudaMemcpy(ctx->d_ftiles.p, ctx->h_ftiles.data(), ctx->h_ftiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_ctiles.p, ctx->h_ctiles.data(), ctx->h_ctiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_ones.p, ones.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<Task> t2(ctx->h_tasks);
+    t2.insert(t2.end(), ctx->h_tasks.begin(), ctx->h_tasks.end());
+    for (int q = nt; q < 2 * nt; q++) t2[q].coff += ctx->ldc;
+    CK(ctx->d_tasks2.ensure(2 * (size_t)nt * sizeof(Task)));
+    CK(ctx->d_mask2.ensure(2 * (size_t)nt * sizeof(int)));
+    CK(cudaMemcpy(ctx->d_tasks2.p, t2.data(), 2 * (size_t)nt * sizeof(Task), cudaMemcpyHostToDevice));
     ctx->nrhs = nrhs;
     return HDD_OK;
 }
@@ -1072,6 +1108,8 @@ hdd_status hdd_create(hdd_ctx **out, int device) {
     if (cudaSetDevice(device) != cudaSuccess) return HDD_ERR_CUDA;
     hdd_ctx *ctx = new hdd_ctx();
     ctx->device = device;
+    if (cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || ctx->nsm < 1)
+        ctx->nsm = 152;
     if (cudaMallocHost(&ctx->h_counter, sizeof(int)) != cudaSuccess || ctx->d_counter.ensure(sizeof(int)) != cudaSuccess) {
         delete ctx;
         return HDD_ERR_OOM;
@@ -1327,10 +1365,11 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     CK(O.Wq.ensure((size_t)nr * (R + 1) * sizeof(double2)));
     CK(O.h1.ensure((size_t)nr * ldp * sizeof(double2))); CK(O.h2.ensure((size_t)nr * ldp * sizeof(double2)));
     CK(O.y.ensure((size_t)nr * ldp * sizeof(double2)));
-    // the double-FP32 first pass runs on a grid of its own (smaller chunks: more of the basis in
-    // flight per SM); its partials share the buffer
+    // the double-FP32 first pass runs on a grid of its own, three CTAs per SM (its register
+    // budget), at least as many CTAs as the other kernels: more of the basis in flight per SM;
+    // its partials share the buffer
     OuterBatch Bd = B;
-    Bd.G = 2 * G;
+    Bd.G = std::max(G, 3 * ctx->nsm);
     CK(O.part.ensure((size_t)nr * Bd.G * ldp * sizeof(double2)));
     CK(O.npart.ensure((size_t)nr * G * sizeof(double)));
     CK(O.npart1.ensure((size_t)nr * G * sizeof(double)));

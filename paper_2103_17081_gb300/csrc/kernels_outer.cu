@@ -235,16 +235,27 @@ __device__ __forceinline__ void warp_dots_df(const float2 *__restrict__ Vh, cons
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l = warp; l < nv; l += OT / 32) {
         const float2 *hp = Vh + (long long)l * ld32 + b, *lp = Vl + (long long)l * ld32 + b;
-        // four independent accumulator sets (elements i, i + 32, i + 64, i + 96): eight loads of
-        // the basis in flight per lane (the pass is bound by bytes in flight, not by the FP32 pipe)
+        // four independent accumulator sets (elements i, i + 32, i + 64, i + 96), software-
+        // pipelined: the eight basis loads of the next group are issued before the current
+        // group's arithmetic (the pass is bound by bytes in flight, not by the FP32 pipe)
         float sh[4][2], sl[4][2];
 #pragma unroll
         for (int u = 0; u < 4; u++) { sh[u][0] = sh[u][1] = sl[u][0] = sl[u][1] = 0.f; }
+        const int full = len & ~127;                     // elements in whole groups of 128
+        float2 vh[4], vl[4];
         int i = lane;
-        for (; i + 96 < len; i += 128) {
-            float2 vh[4], vl[4];
+        if (i < full) {
 #pragma unroll
             for (int u = 0; u < 4; u++) { vh[u] = hp[i + 32 * u]; vl[u] = lp[i + 32 * u]; }
+        }
+        for (; i < full; i += 128) {
+            float2 nh[4], nl[4];
+            const bool more = i + 128 < full;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                nh[u] = more ? hp[i + 128 + 32 * u] : make_float2(0.f, 0.f);
+                nl[u] = more ? lp[i + 128 + 32 * u] : make_float2(0.f, 0.f);
+            }
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const float4 x = ws.w[i + 32 * u];
@@ -254,14 +265,16 @@ __device__ __forceinline__ void warp_dots_df(const float2 *__restrict__ Vh, cons
                 df_acc(sh[u][0], sl[u][0], vh[u].y, vl[u].y, x.z, x.w);
                 df_acc(sh[u][1], sl[u][1], -vh[u].y, -vl[u].y, x.x, x.y);
             }
+#pragma unroll
+            for (int u = 0; u < 4; u++) { vh[u] = nh[u]; vl[u] = nl[u]; }
         }
-        for (; i < len; i += 32) {
-            const float2 vh = hp[i], vl = lp[i];
+        for (i = full + lane; i < len; i += 32) {
+            const float2 h1 = hp[i], l1 = lp[i];
             const float4 x = ws.w[i];
-            df_acc(sh[0][0], sl[0][0], vh.x, vl.x, x.x, x.y);
-            df_acc(sh[0][1], sl[0][1], vh.x, vl.x, x.z, x.w);
-            df_acc(sh[0][0], sl[0][0], vh.y, vl.y, x.z, x.w);
-            df_acc(sh[0][1], sl[0][1], -vh.y, -vl.y, x.x, x.y);
+            df_acc(sh[0][0], sl[0][0], h1.x, l1.x, x.x, x.y);
+            df_acc(sh[0][1], sl[0][1], h1.x, l1.x, x.z, x.w);
+            df_acc(sh[0][0], sl[0][0], h1.y, l1.y, x.z, x.w);
+            df_acc(sh[0][1], sl[0][1], -h1.y, -l1.y, x.x, x.y);
         }
         double re = 0.0, im = 0.0;
 #pragma unroll
@@ -275,7 +288,7 @@ __device__ __forceinline__ void warp_dots_df(const float2 *__restrict__ Vh, cons
 }
 
 // Partial dots part[r][cta][l] = Σ_{chunk} conj(V_{r,l}) w_r, l < nv, from the hi/lo FP32 basis.
-__global__ void __launch_bounds__(OT)
+__global__ void __launch_bounds__(OT, 3)
 k_odots_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int nv,
            const double2 *__restrict__ w, double2 *__restrict__ part) {
     __shared__ WStageDF ws;
