@@ -31,14 +31,15 @@ import workloads as W  # noqa: E402
 METRIC = "time-to-solution at rel-res 1e-6 (k=200, 20 ppwl); subdomain-solve GB/s vs peak"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 L2_FLUSH_BYTES = 512 << 20                      # > 129 MB L2
-# DRAM bytes (read + written) per algorithmic byte of the outer CGS2 kernels, from one ncu
-# capture of k_odots and k_oupdate at outer iteration 200 of the k=200 solve (201 basis vectors:
-# 1.9827 + 4.0434 GB against 1.9763 + 3.9525 GB algorithmic).  Their traffic grows with the
+# DRAM bytes (read + written) per algorithmic byte of a kernel family, from one ncu capture of its
+# kernels at outer iteration 200 of the k=200 solve (profiles/); their traffic grows with the
 # basis vectors read, so the ratio scales that capture to the average launch of a k=200 run.
-# With the double-FP32 first pass (the default) the FP64 family is k_oupdate alone, whose own
-# ratio from the same capture applies (4.0434 GB against 3.9525 GB; the kernel is unchanged).
-OCGS_DRAM_PER_ALG = (1.982693 + 4.043380) / (1.976274 + 3.952547)
-OUPDATE_DRAM_PER_ALG = 4.043380 / 3.952547
+# Keyed by (family, double-FP32 dots on); a family whose kernels changed since their capture has
+# no entry, and the roofline's traffic field is then null.
+TRAFFIC_PER_ALG = {
+    # k_odots + k_oupdate (FP64 dots): 1.9827 + 4.0434 GB against 1.9763 + 3.9525 GB
+    ("outer_cgs2_fp64", False): (1.982693 + 4.043380) / (1.976274 + 3.952547),
+}
 
 
 def _peaks():
@@ -349,16 +350,15 @@ def run_gpu(args):
                 "fp64_frac": fp64_frac if dom["bound"] == "fp64" else None}
     roof["launches"] = dom["launches"]
     roof["ms_per_launch"] = per_launch_ms
-    if (dom["name"] == "outer_cgs2_fp64" and w.name == "k200" and w.nrhs == 1 and args.prec == 64
-            and not args.fp64_reorth):
+    df = any(d["name"] == "outer_dots_df32" and d["launches"] for d in prof)
+    ratio = TRAFFIC_PER_ALG.get((dom["name"], df))
+    if ratio is not None and w.name == "k200" and w.nrhs == 1 and args.prec == 64 and not args.fp64_reorth:
         # the configuration of the ncu capture; elsewhere (bases that fit in L2, other kernels)
         # no measured traffic exists and the field stays null
-        df = any(d["name"] == "outer_dots_df32" and d["launches"] for d in prof)
-        roof["traffic"] = dom["bytes"] / max(1, dom["launches"]) * (OUPDATE_DRAM_PER_ALG if df else OCGS_DRAM_PER_ALG)
-        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of " +
-                                  ("k_oupdate" if df else "k_odots and k_oupdate") +
-                                  " at outer iteration 200 (profiles/outer_cgs2_gauss_k200.md), scaled by "
-                                  "basis vectors to this run's average launch")
+        roof["traffic"] = dom["bytes"] / max(1, dom["launches"]) * ratio
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the family's kernels at "
+                                  "outer iteration 200 (profiles/), scaled by basis vectors to this run's "
+                                  "average launch")
     fams = {d["name"]: {"ms": round(d["ms"], 3), "launches": d["launches"],
                         "GB/s": round(d["bytes"] / max(d["ms"], 1e-9) / 1e6, 1),
                         "TFLOP/s": round(d["flops"] / max(d["ms"], 1e-9) / 1e9, 4)}

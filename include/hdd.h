@@ -319,11 +319,10 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 /* HDD_OPT_FUSED_INNER (2): each inner Arnoldi step runs as one cluster-resident kernel per     */
 /* step between the coarse solves (1, the default, where every box fits its plan) or as the    */
 /* separate stencil / CGS / Givens kernels (0).  HDD_OPT_OUTER_DOTS_DF (3): with the guarded    */
-/* FP32 second outer CGS pass (outer_reorth32 = 1), the first pass's dot products run in       */
-/* double-FP32 arithmetic (error-free products and sums, as accurate as FP64 sums) from hi/lo  */
-/* FP32 copies of the basis (1, the default; another 8 bytes per basis entry) or in FP64 (0);  */
-/* the second pass's dots and every update of the Krylov vector (the Arnoldi relation) stay    */
-/* FP64.                                                                                        */
+/* FP32 second outer CGS pass (outer_reorth32 = 1), the dot products of both outer CGS passes  */
+/* run in double-FP32 arithmetic (error-free products and sums, as accurate as FP64 sums) from  */
+/* hi/lo FP32 copies of the basis (1, the default; another 8 bytes per basis entry) or in FP64  */
+/* (0); every update of the Krylov vector (the Arnoldi relation) stays FP64.                    */
 /* HDD_ERR_INVALID_ARG for an unknown key or a value other than 0 or 1.  Takes effect from the  */
 /* next call that solves.                                                                       */
 #define HDD_OPT_COARSE_LOOKAHEAD 1

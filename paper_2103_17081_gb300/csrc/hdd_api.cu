@@ -1479,9 +1479,17 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                    launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                          // h1 = V^H w
                 KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
             }
-            KL(F_OCGS, fa * (nv * 48 + 32) * n, fa * 12 * nv * n,
-               launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
-            KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
+            if (df) {     // FP64 update w' = w - V h1 (24 B, 3 FMAs), then h2 = V^H w' in double-FP32 (16 B)
+                KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
+                   launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, nullptr, O.npart1.as<double>(), s));
+                KL(F_ODF, fa * (nv * 16 + 16) * n, fa * 48 * nv * n,
+                   launch_odots_df(Bd, V32, V32L, j + 1, w, O.part.as<double2>(), s));
+                KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
+            } else {
+                KL(F_OCGS, fa * (nv * 48 + 32) * n, fa * 12 * nv * n,
+                   launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
+                KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
+            }
             if (r32)   // FP32 correction from the FP32 basis copy (guarded; FP64 fallback inside)
                 KL(F_OREORTH, fa * (nv * 8 + 2 * 16) * n, fa * 8 * nv * n,
                    launch_oupdate2(B, V, V32, j + 1, O.h2.as<double2>(), w, O.npart1.as<double>(),

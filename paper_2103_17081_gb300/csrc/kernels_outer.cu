@@ -221,6 +221,15 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, float xh, float xl,
     sl = __fadd_rn(sl, __fadd_rn(err, c));
 }
 
+// (sh, sl) += (bh, bl): two-sum of the high parts, the low parts added
+__device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl) {
+    const float t = __fadd_rn(sh, bh);
+    const float bb = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(bh, bb));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, bl));
+}
+
 // w (FP64) split per element into (Re hi, Re lo, Im hi, Im lo) for the double-FP32 dots
 __device__ __forceinline__ void stage_w_df(WStageDF &ws, int i, double2 x) {
     const float rh = (float)x.x, ih = (float)x.y;
@@ -276,14 +285,23 @@ __device__ __forceinline__ void warp_dots_df(const float2 *__restrict__ Vh, cons
             df_acc(sh[0][0], sl[0][0], h1.y, l1.y, x.z, x.w);
             df_acc(sh[0][1], sl[0][1], -h1.y, -l1.y, x.x, x.y);
         }
-        double re = 0.0, im = 0.0;
+        // the four sets and then the 32 lanes are added as (hi, lo) pairs in FP32 (two-sum for
+        // the high parts, low parts added): the epilogue stays off the FP64 pipe; lane 0 widens
+        // the result to FP64
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            re += (double)sh[u][0] + (double)sl[u][0];
-            im += (double)sh[u][1] + (double)sl[u][1];
+        for (int u = 1; u < 4; u++) {
+            df_add(sh[0][0], sl[0][0], sh[u][0], sl[u][0]);
+            df_add(sh[0][1], sl[0][1], sh[u][1], sl[u][1]);
         }
-        for (int o = 16; o > 0; o >>= 1) { re += shfl_xor(re, o); im += shfl_xor(im, o); }
-        if (lane == 0) part[(long long)blockIdx.x * ldp + l] = make_double2(re, im);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float rh = __shfl_xor_sync(0xffffffffu, sh[0][0], o), rl = __shfl_xor_sync(0xffffffffu, sl[0][0], o);
+            const float ih = __shfl_xor_sync(0xffffffffu, sh[0][1], o), il = __shfl_xor_sync(0xffffffffu, sl[0][1], o);
+            df_add(sh[0][0], sl[0][0], rh, rl);
+            df_add(sh[0][1], sl[0][1], ih, il);
+        }
+        if (lane == 0)
+            part[(long long)blockIdx.x * ldp + l] = make_double2((double)sh[0][0] + (double)sl[0][0],
+                                                                 (double)sh[0][1] + (double)sl[0][1]);
     }
 }
 

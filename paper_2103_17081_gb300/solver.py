@@ -230,8 +230,8 @@ class Solver:
     def set_option(self, name: str, value: int):
         """Implementation choice of this context (hdd_set_option): "coarse_lookahead" selects
         the look-ahead block solve (1) or the plain one (0); "fused_inner" the one-kernel inner
-        Arnoldi step (1) or the separate kernels (0); "outer_dots_df" the double-FP32 first outer
-        CGS pass (1) or the FP64 one (0)."""
+        Arnoldi step (1) or the separate kernels (0); "outer_dots_df" the outer CGS dot products
+        in double-FP32 arithmetic (1) or in FP64 (0)."""
         self._check(self._L.hdd_set_option(self._h, self.OPTIONS[name], int(value)), "hdd_set_option")
         return self
 

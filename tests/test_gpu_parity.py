@@ -276,10 +276,9 @@ def test_outer_fp32_reorthogonalisation_matches_fp64(wname):
 
 @pytest.mark.parametrize("wname", ["tiny", "k100"])
 def test_outer_double_fp32_first_pass_matches_fp64(wname):
-    """The outer CGS2's first-pass dot products in double-FP32 arithmetic (hi/lo FP32 basis,
-    error-free products and sums; the second pass and the updates stay FP64) give the FP64
-    iteration: with complex128 inner solves and the guarded FP32 second-pass correction, residual
-    histories equal to 1e-6
+    """The outer CGS2's dot products (both passes) in double-FP32 arithmetic (hi/lo FP32 basis,
+    error-free products and sums; the updates stay FP64) give the FP64 iteration: with complex128
+    inner solves and the guarded FP32 second-pass correction, residual histories equal to 1e-6
     while the residual is above 1e-4, the same outer count within one (a different rounding order
     can move the stop across the tolerance: 19 against 20 on the tiny workload), solutions within
     1e-5 of each other (the complex128 whole-solve bar), and the second-pass guard never falls
