@@ -39,6 +39,10 @@ L2_FLUSH_BYTES = 512 << 20                      # > 129 MB L2
 TRAFFIC_PER_ALG = {
     # k_odots + k_oupdate (FP64 dots): 1.9827 + 4.0434 GB against 1.9763 + 3.9525 GB
     ("outer_cgs2_fp64", False): (1.982693 + 4.043380) / (1.976274 + 3.952547),
+    # k_oupdate without dots (double-FP32 dots on): 2.0608 + 0.0061 GB against 1.9828 GB
+    ("outer_cgs2_fp64", True): (2.060811 + 0.006137) / ((201 * 24 + 32) * 408321 / 1e9),
+    # k_odots_df (both passes): 1.3205 + 0.0046 GB against 1.3197 GB
+    ("outer_dots_df32", True): (1.320545 + 0.004604) / ((201 * 16 + 16) * 408321 / 1e9),
 }
 
 

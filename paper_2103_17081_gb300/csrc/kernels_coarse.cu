@@ -557,6 +557,7 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
                  double2 *__restrict__ out, int use_fine, const int *__restrict__ flag, int maxK,
                  int cwy, int cwx) {
     static_assert(RING >= 3, "the look-ahead needs blocks J and J+1 resident while J+2 loads");
+    static_assert(LA_BW == 7, "chain_row adds the seven bulk partials in four accumulators");
     extern __shared__ double sm[];
     __shared__ double part[2][LA_BW][BNB];   // bulk partial sums of the next block, by parity
     __shared__ int sw[RING];                  // panel width of the block in each ring slot
@@ -576,14 +577,18 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = lane >> 1, half = lane & 1;          // 16 rows x 2 lanes per warp
     const int q = (warp - 1) * 2 + half;                 // bulk lane of the row (warp >= 1)
+    // copies are issued by the bulk warps only (warp 0 goes straight to the dependent chain);
+    // the thread of index LA_T - LA_BW·32 = 32 records each slot's panel width
+    const int bt = tid - 32;                             // bulk thread index (< 0 in warp 0)
     auto load_block = [&](long long src_off, int K, int buf, int J) {
+        if (bt < 0) return;
         double *dst = sm + buf * slot;
         const double *src = Mall + src_off;
         const int nchunk = BNB * K / 2;                  // 16-byte chunks
-        for (int c = tid; c < nchunk; c += LA_T) cp_async16(dst + 2 * c, src + 2 * c);
-        if (tid < BNB) {
-            const int i = J * BNB + tid;
-            cp_async8_zfill(dst + BNB * maxK + tid, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
+        for (int c = bt; c < nchunk; c += LA_T - 32) cp_async16(dst + 2 * c, src + 2 * c);
+        if (bt < BNB) {
+            const int i = J * BNB + bt;
+            cp_async8_zfill(dst + BNB * maxK + bt, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
         }
     };
     for (int i = tid; i < m; i += LA_T) outr[STR * (long long)i] = inr[STR * (long long)perm[i]];
@@ -615,18 +620,25 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
         return v;
     };
     // Warp 0: block J from the bulk partials (parity par) and the recent panel columns [p0, p1).
+    // This is the dependent chain of the solve, so its FP64 latency is kept short: the lane's
+    // partials (three or four) and its products (at most eight) go round-robin into four
+    // independent accumulators, combined by a two-level tree and one shuffle.
     auto chain_row = [&](const double *Mb, int K, int p0, int p1, const double *win, int pbase, int mask,
                          int par) {
         const double *Mr = Mb + row * K + BNB;
-        double s0 = 0.0, s1 = 0.0;
-        for (int w = half; w < LA_BW; w += 2) s0 += part[par][w][row];
+        double a0 = part[par][half][row], a1 = part[par][half + 2][row], a2 = part[par][half + 4][row];
+        double a3 = half == 0 ? part[par][6][row] : 0.0;
         int p = p0 + half;
-        for (; p + 2 < p1; p += 4) {
-            s0 = fma(Mr[p], win[(pbase + p) & mask], s0);
-            s1 = fma(Mr[p + 2], win[(pbase + p + 2) & mask], s1);
+        for (; p + 6 < p1; p += 8) {
+            a0 = fma(Mr[p], win[(pbase + p) & mask], a0);
+            a1 = fma(Mr[p + 2], win[(pbase + p + 2) & mask], a1);
+            a2 = fma(Mr[p + 4], win[(pbase + p + 4) & mask], a2);
+            a3 = fma(Mr[p + 6], win[(pbase + p + 6) & mask], a3);
         }
-        for (; p < p1; p += 2) s0 = fma(Mr[p], win[(pbase + p) & mask], s0);
-        double v = s0 + s1;
+        if (p < p1) a0 = fma(Mr[p], win[(pbase + p) & mask], a0);
+        if (p + 2 < p1) a1 = fma(Mr[p + 2], win[(pbase + p + 2) & mask], a1);
+        if (p + 4 < p1) a2 = fma(Mr[p + 4], win[(pbase + p + 4) & mask], a2);
+        double v = (a0 + a1) + (a2 + a3);
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         return v;
     };
@@ -638,7 +650,7 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
         if (u < nbk) {
             const int4 mt = meta[u];
             load_block(mt.x, BNB + mt.y, u, u);
-            if (tid == 0) sw[u] = mt.y;
+            if (tid == 32) sw[u] = mt.y;
         }
         cp_async_commit();
     }
@@ -656,7 +668,7 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
         if (J + RING - 1 < nbk) {                          // into the slot block J-1 used
             const int buf = (J + RING - 1) % RING;
             load_block(mnext.x, BNB + mnext.y, buf, J + RING - 1);
-            if (tid == 0) sw[buf] = mnext.y;
+            if (tid == 32) sw[buf] = mnext.y;
         }
         cp_async_commit();
         if (J + RING < nbk) mnext = meta[J + RING];
@@ -686,7 +698,7 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
         if (J >= 0) {
             const int4 mt = meta[J];
             load_block(mt.z, BNB + mt.w, u, J);
-            if (tid == 0) sw[u] = mt.w;
+            if (tid == 32) sw[u] = mt.w;
         }
         cp_async_commit();
     }
@@ -705,7 +717,7 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
         if (J - (RING - 1) >= 0) {
             const int buf = (k + RING - 1) % RING;
             load_block(mnext.z, BNB + mnext.w, buf, J - (RING - 1));
-            if (tid == 0) sw[buf] = mnext.w;
+            if (tid == 32) sw[buf] = mnext.w;
         }
         cp_async_commit();
         if (J - RING >= 0) mnext = meta[J - RING];
