@@ -50,6 +50,17 @@ template <typename R> __device__ __forceinline__ void caxpy(c2<R> &acc, c2<R> h,
 
 template <typename R> __device__ __forceinline__ R shfl_xor(R v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 
+// Division by a box dimension d (1 <= d <= 256) of an index 0 <= e < 2^24, as the high word of
+// e·M with M = ceil(2^32/d): with M·d = 2^32 + r (0 <= r < d) the excess over e/d is
+// e·r/(2^32·d) < e/2^32 < 1/d, too small to reach the next integer (checked on the CPU for every
+// d <= 256).  Replaces the integer division in the row/column splits of the tile loops.
+struct BoxDiv {
+    unsigned m;
+    __device__ __forceinline__ explicit BoxDiv(int d)
+        : m(d > 1 ? (unsigned)((0x100000000ull + (unsigned)d - 1) / (unsigned)d) : 0u) {}
+    __device__ __forceinline__ int q(int e) const { return m ? (int)__umulhi((unsigned)e, m) : e; }
+};
+
 // ------------------------------------------------------------------------------------------
 // problem description shared with the kernels
 // ------------------------------------------------------------------------------------------

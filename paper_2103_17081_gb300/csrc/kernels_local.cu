@@ -241,13 +241,15 @@ __device__ void prolong_rows(const Task &T, const double2 *__restrict__ s, int F
     if (C0 < 0) C0 = 0;
     if (C1 > my - 1) C1 = my - 1;
     const int ncy = C1 - C0 + 1;
+    const BoxDiv dmx(mx), dnx(nx);
     for (int e = threadIdx.x; e < ncy * mx; e += blockDim.x) {
-        double2 v = s[T.coff + (long long)(C0 + e / mx) * mx + (e % mx)];
+        const int rr = dmx.q(e);
+        double2 v = s[T.coff + (long long)(C0 + rr) * mx + (e - rr * mx)];
         sc[e] = mk<R>((R)v.x, (R)v.y);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < ncy * nx; e += blockDim.x) {
-        int r = e / nx, fx = e % nx;
+        const int r = dnx.q(e), fx = e - r * nx;
         c2<R> acc = mk<R>(0, 0);
         int cx0 = (fx - 3) >= 0 ? (fx - 3 + 1) / 2 : 0;
         int cx1 = (fx + 1) / 2;
@@ -262,7 +264,8 @@ __device__ void prolong_rows(const Task &T, const double2 *__restrict__ s, int F
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nF * nx; e += blockDim.x) {
-        int fy = F0 + e / nx, fx = e % nx;
+        const int qy = dnx.q(e);
+        int fy = F0 + qy, fx = e - qy * nx;
         c2<R> acc = mk<R>(0, 0);
         if (fy >= 0 && fy < ny) {
             int cy0 = (fy - 3) >= 0 ? (fy - 3 + 1) / 2 : 0;
@@ -733,6 +736,7 @@ k_arnoldi_step(StepArgs<R> a) {
     if (!a.act_in[t]) return;                     // the same flag for every CTA of the cluster
     const Task T = a.tasks[t];
     const int nx = T.nx, ny = T.ny, mx = T.mx, my = T.my;
+    const BoxDiv dnx(nx), dmx(mx);
     const int i = a.i, nv = i + 1;
     const int r0 = (int)(rank * ny) / C, r1 = (int)((rank + 1) * ny) / C, nr = r1 - r0;
     const int cnt = nr * nx;
@@ -761,15 +765,15 @@ k_arnoldi_step(StepArgs<R> a) {
     if (nr > 0) {
         prolong_rows<R>(T, a.s, F0, nF, sc, px, u);
         for (int e = tid; e < nF * nx; e += blockDim.x) {
-            const int yy = F0 + e / nx;
-            if (yy >= 0 && yy < ny) u[e] = csub<R>(vi[T.foff + (long long)yy * nx + e % nx], u[e]);
+            const int qy = dnx.q(e), yy = F0 + qy;
+            if (yy >= 0 && yy < ny) u[e] = csub<R>(vi[T.foff + (long long)yy * nx + (e - qy * nx)], u[e]);
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < EPT; k++) {
             const int e = tid + k * LOCAL_THREADS;
             if (e < cnt) {
-                const int yy = r0 + e / nx, xx = e % nx;
+                const int qy = dnx.q(e), yy = r0 + qy, xx = e - qy * nx;
                 wv[k] = stencil_smem<R, IMP>(a.st, u, F0, nF, nx, ny, xx, yy, T.ix0, T.iy0);
             }
         }
@@ -898,18 +902,18 @@ k_arnoldi_step(StepArgs<R> a) {
     c2<R> *sx = tt + nG * nx;
     const c2<R> *vnf = a.V + (long long)(i + 1) * a.ld + T.foff;
     for (int e = tid; e < nW * nx; e += blockDim.x) {
-        const int yy = W0 + e / nx;
-        vin[e] = (yy >= 0 && yy < ny) ? vnf[(long long)yy * nx + e % nx] : mk<R>(0, 0);
+        const int qy = dnx.q(e), yy = W0 + qy;
+        vin[e] = (yy >= 0 && yy < ny) ? vnf[(long long)yy * nx + (e - qy * nx)] : mk<R>(0, 0);
     }
     __syncthreads();
     for (int e = tid; e < nG * nx; e += blockDim.x) {
-        const int yy = G0 + e / nx, xx = e % nx;
+        const int qy = dnx.q(e), yy = G0 + qy, xx = e - qy * nx;
         tt[e] = (yy >= 0 && yy < ny) ? stencil_smem<R, IMP>(a.st, vin, W0, nW, nx, ny, xx, yy, T.ix0, T.iy0)
                                      : mk<R>(0, 0);
     }
     __syncthreads();
     for (int e = tid; e < nG * mx; e += blockDim.x) {
-        const int fr = e / mx, cx = e % mx;
+        const int fr = dmx.q(e), cx = e - fr * mx;
         c2<R> acc = mk<R>(0, 0);
 #pragma unroll
         for (int qq = 0; qq < 5; qq++) {
@@ -924,7 +928,7 @@ k_arnoldi_step(StepArgs<R> a) {
     }
     __syncthreads();
     for (int e = tid; e < (c1 - c0) * mx; e += blockDim.x) {
-        const int cy = c0 + e / mx, cx = e % mx;
+        const int qc = dmx.q(e), cy = c0 + qc, cx = e - qc * mx;
         c2<R> acc = mk<R>(0, 0);
 #pragma unroll
         for (int qq = 0; qq < 5; qq++) {
