@@ -33,7 +33,8 @@ _ERR = {1: "bad argument", 2: "bad call order", 3: "singular pivot", 4: "no conv
 
 class SolveParams(C.Structure):
     _fields_ = [("outer_tol", C.c_double), ("outer_restart", C.c_int), ("outer_maxit", C.c_int),
-                ("inner_tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int)]
+                ("inner_tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
+                ("two_level", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -106,6 +107,13 @@ def lib():
         L.or_band_solve_z.argtypes = [I, I, I, Z, Z, Z]
         L.or_set_threads.argtypes = [I]
         L.or_get_threads.restype = I
+        L.or_setup_coarse_grid.argtypes = [P, I]
+        L.or_setup_coarse_grid.restype = I
+        L.or_cg_n.argtypes = [P]
+        L.or_cg_n.restype = I
+        for name in ("or_cg_apply_P", "or_cg_apply_Pt", "or_cg_solve"):
+            getattr(L, name).argtypes = [P, Z, Z]
+            getattr(L, name).restype = None
         _lib = L
     return _lib
 
@@ -372,12 +380,38 @@ class Problem:
         return z, {"inner_its_total": tot.value, "inner_its_max": mx.value,
                    "inner_maxit_hits": hits.value}
 
+    # -- two-level variant: grid coarse space ------------------------------------------------
+    def setup_coarse_grid(self, c: int = 2):
+        """P1 on the mesh of N/c intervals: interpolation P, lumped coarse operator A_H, factored."""
+        _check(lib().or_setup_coarse_grid(self._h, int(c)), "setup_coarse_grid")
+
+    def cg_n(self) -> int:
+        return lib().or_cg_n(self._h)
+
+    def cg_P(self, uH):
+        uH = _c128(uH)
+        u = np.empty(self.n, dtype=np.complex128)
+        lib().or_cg_apply_P(self._h, _ptr(uH), _ptr(u))
+        return u
+
+    def cg_Pt(self, v):
+        v = _c128(v)
+        vH = np.empty(self.cg_n(), dtype=np.complex128)
+        lib().or_cg_apply_Pt(self._h, _ptr(v), _ptr(vH))
+        return vH
+
+    def cg_solve(self, yH):
+        yH = _c128(yH)
+        xH = np.empty_like(yH)
+        lib().or_cg_solve(self._h, _ptr(yH), _ptr(xH))
+        return xH
+
     def solve(self, f, outer_tol=1e-6, outer_restart=2000, outer_maxit=2000, inner_tol=1e-2,
-              inner_restart=30, inner_maxit=1000, raise_on_error=True):
+              inner_restart=30, inner_maxit=1000, raise_on_error=True, two_level=0):
         f = _c128(f)
         x = np.zeros_like(f)
         prm = SolveParams(outer_tol, outer_restart, outer_maxit, inner_tol, inner_restart,
-                          inner_maxit)
+                          inner_maxit, int(bool(two_level)))
         st = Stats()
         hist = np.zeros(outer_maxit + 1, dtype=np.float64)
         rc = lib().or_solve(self._h, _ptr(f), _ptr(x), C.byref(prm), C.byref(st), _ptr(hist),

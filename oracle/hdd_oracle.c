@@ -272,7 +272,18 @@ typedef struct {
     bandlu Aex;              /* factored A_j for the direct local solve */
 } subdomain;
 
+/* Grid coarse space of the two-level variant: P1 on the mesh of N/c intervals, interpolation P
+ * (fine interior nodes x coarse interior nodes), and the coarse operator A_H = K_H - k² M_H^lumped
+ * in band form, factored. */
+typedef struct {
+    int have, c, Nc, mc, nH, kl;
+    csr P, Pt;
+    double *ab;
+    int *piv;
+} cgrid;
+
 struct or_problem {
+    cgrid cg;
     int N, n, diag;
     int bc;                  /* 0: Dirichlet (Eq. 1); 1: impedance (Sommerfeld) on all four sides */
     int lo, hi;              /* node indices 0..N that are unknowns: lo..hi in both directions */
@@ -468,6 +479,7 @@ static void free_sub(subdomain *s) {
 
 void or_destroy(or_problem *p) {
     if (!p) return;
+    csr_free(&p->cg.P); csr_free(&p->cg.Pt); free(p->cg.ab); free(p->cg.piv);
     csr_free(&p->A); csr_free(&p->K); csr_free(&p->M); csr_free(&p->B);
     if (p->sub) { for (int s = 0; s < p->nsub; s++) free_sub(&p->sub[s]); free(p->sub); }
     free(p);
@@ -1028,6 +1040,91 @@ int or_ras_apply(const or_problem *p, const double *v_, double *z_, double inner
 /* -- outer solve: restarted flexible GMRES, right-preconditioned by RAS (§3; Saad, SIAM J.
  *    Sci. Comput. 14 (1993)).  Stops on ||f - A x|| <= tol ||f||, checked on the true
  *    residual at every restart and at exit. --------------------------------------------------- */
+/* ------------------------------------------------------------------------------------------ */
+/* Two-level variant (the paper's §4 names a coarse space as the next step): the grid coarse    */
+/* space — P1 on a coarser mesh of the same triangulation, H = c h — with P1 interpolation P, */
+/* restriction Pᵀ and the coarse operator rediscretised on that mesh with its mass lumped      */
+/* (A_H = K_H - k² diag(row sums of M_H)), solved exactly by banded LU.                        */
+/* ------------------------------------------------------------------------------------------ */
+int or_setup_coarse_grid(or_problem *p, int c) {
+    if (!p || p->bc != 0 || c < 2 || p->N % c != 0 || p->N / c < 2) return OR_ERR_ARG;
+    cgrid *g = &p->cg;
+    csr_free(&g->P); csr_free(&g->Pt); free(g->ab); free(g->piv);
+    memset(g, 0, sizeof(*g));
+    const int N = p->N, Nc = N / c, mc = Nc - 1, nH = mc * mc;
+    g->c = c; g->Nc = Nc; g->mc = mc; g->nH = nH;
+    /* P: value at each fine interior node of the coarse piecewise-linear function, by barycentric
+     * coordinates in the coarse triangle that contains the node */
+    rowacc acc;
+    acc.col = (int *)malloc(sizeof(int) * 8 * (size_t)p->n);
+    acc.val = (double *)malloc(sizeof(double) * 8 * (size_t)p->n);
+    acc.cnt = (int *)calloc((size_t)p->n, sizeof(int));
+    for (int j = 1; j < N; j++)
+        for (int i = 1; i < N; i++) {
+            const int cx0 = i / c, cy0 = j / c;
+            const double a = (double)(i - cx0 * c) / c, b = (double)(j - cy0 * c) / c;
+            int vx[3], vy[3];
+            double wt[3];
+            if (p->diag == 0) {          /* triangles (cx0,cy0),(cx0+1,cy0),(cx0+1,cy0+1) and (cx0,cy0),(cx0+1,cy0+1),(cx0,cy0+1) */
+                if (a >= b) { vx[0] = cx0; vy[0] = cy0; wt[0] = 1 - a; vx[1] = cx0 + 1; vy[1] = cy0; wt[1] = a - b;
+                              vx[2] = cx0 + 1; vy[2] = cy0 + 1; wt[2] = b; }
+                else { vx[0] = cx0; vy[0] = cy0; wt[0] = 1 - b; vx[1] = cx0 + 1; vy[1] = cy0 + 1; wt[1] = a;
+                       vx[2] = cx0; vy[2] = cy0 + 1; wt[2] = b - a; }
+            } else {                     /* triangles (cx0,cy0),(cx0+1,cy0),(cx0,cy0+1) and (cx0+1,cy0),(cx0+1,cy0+1),(cx0,cy0+1) */
+                if (a + b <= 1) { vx[0] = cx0; vy[0] = cy0; wt[0] = 1 - a - b; vx[1] = cx0 + 1; vy[1] = cy0; wt[1] = a;
+                                  vx[2] = cx0; vy[2] = cy0 + 1; wt[2] = b; }
+                else { vx[0] = cx0 + 1; vy[0] = cy0; wt[0] = 1 - b; vx[1] = cx0 + 1; vy[1] = cy0 + 1; wt[1] = a + b - 1;
+                       vx[2] = cx0; vy[2] = cy0 + 1; wt[2] = 1 - a; }
+            }
+            const int r = (i - 1) + (j - 1) * (N - 1);
+            for (int t = 0; t < 3; t++) {
+                if (wt[t] == 0.0 || vx[t] < 1 || vy[t] < 1 || vx[t] > mc || vy[t] > mc) continue;
+                acc_add(&acc, r, (vx[t] - 1) + (vy[t] - 1) * mc, wt[t]);
+            }
+        }
+    g->P = acc_to_csr(&acc, p->n);
+    g->P.nc = nH;
+    g->Pt = csr_transpose(&g->P);
+    free(acc.col); free(acc.val); free(acc.cnt);
+    /* A_H from the coarse mesh's own element assembly, mass lumped, in band storage */
+    or_problem *q = or_create(Nc, p->k, p->diag);
+    if (!q) return OR_ERR_ARG;
+    const int kl = mc + 1, W = 3 * kl + 1;
+    g->kl = kl;
+    g->ab = (double *)calloc((size_t)nH * W, sizeof(double));
+    g->piv = (int *)malloc(sizeof(int) * (size_t)nH);
+    double *ab = g->ab;
+    const double k2 = p->k * p->k;
+#define AB(r, col) ab[(size_t)(r) * W + (size_t)((col) - (r) + kl)]
+    /* lumped mass: the integral of the coarse hat function, i.e. the row sum of the full mass
+     * matrix with the boundary columns included = area of its support / 3 = 6 (H^2/2) / 3 = H^2 at
+     * every interior node (summing only the interior columns would lose mass next to the boundary) */
+    const double H = 1.0 / Nc, mlump = H * H;
+    for (int r = 0; r < nH; r++) {
+        for (int t = q->K.rp[r]; t < q->K.rp[r + 1]; t++) AB(r, q->K.ci[t]) += q->K.v[t];
+        AB(r, r) -= k2 * mlump;
+    }
+#undef AB
+    or_destroy(q);
+    int st = or_band_lu(nH, kl, kl, ab, g->piv);
+    if (st != OR_OK) return st;
+    g->have = 1;
+    return OR_OK;
+}
+
+int or_cg_n(const or_problem *p) { return p->cg.have ? p->cg.nH : 0; }
+void or_cg_apply_P(const or_problem *p, const double *uH, double *u) {
+    csr_mv(&p->cg.P, (const zc *)uH, (zc *)u);
+}
+void or_cg_apply_Pt(const or_problem *p, const double *v, double *vH) {
+    csr_mv(&p->cg.Pt, (const zc *)v, (zc *)vH);
+}
+/* xH = A_H⁻¹ yH */
+void or_cg_solve(const or_problem *p, const double *yH, double *xH) {
+    memcpy(xH, yH, sizeof(zc) * (size_t)p->cg.nH);
+    band_solve_z(p->cg.nH, p->cg.kl, p->cg.kl, p->cg.ab, p->cg.piv, (zc *)xH);
+}
+
 int or_solve(const or_problem *p, const double *f_, double *x_, const or_solve_params *prm,
              or_stats *st, double *hist, int hcap) {
     const zc *f = (const zc *)f_;
@@ -1048,6 +1145,15 @@ int or_solve(const or_problem *p, const double *f_, double *x_, const or_solve_p
     zc *htmp = (zc *)malloc(sizeof(zc) * (size_t)(R + 1));
     zc *r = (zc *)malloc(sizeof(zc) * (size_t)n);
     zc *w = (zc *)malloc(sizeof(zc) * (size_t)n);
+    const int two = prm->two_level != 0;
+    if (two && !p->cg.have) {
+        free(V); free(Zb); free(H); free(g); free(sn); free(cs); free(y); free(htmp); free(r); free(w);
+        st->status = OR_ERR_STATE;
+        return OR_ERR_STATE;
+    }
+    const int nH = two ? p->cg.nH : 1;
+    zc *vH = (zc *)malloc(sizeof(zc) * (size_t)nH), *xH = (zc *)malloc(sizeof(zc) * (size_t)nH);
+    zc *tv = (zc *)malloc(sizeof(zc) * (size_t)(two ? n : 1)), *z2 = (zc *)malloc(sizeof(zc) * (size_t)(two ? n : 1));
     int status = OR_OK, total = 0, nh = 0;
     long long inner_tot = 0, hits = 0;
     int inner_max = 0;
@@ -1070,9 +1176,23 @@ int or_solve(const or_problem *p, const double *f_, double *x_, const or_solve_p
             zc *zj = Zb + (size_t)j * n;
             long long it_tot = 0, it_hits = 0;
             int it_max = 0;
-            int s2 = or_ras_apply(p, (const double *)(V + (size_t)j * n), (double *)zj,
-                                  prm->inner_tol, prm->inner_restart, prm->inner_maxit, &it_tot,
-                                  &it_max, &it_hits);
+            const zc *vj = V + (size_t)j * n;
+            int s2;
+            if (two) {
+                /* coarse correction z0 = P A_H⁻¹ Pᵀ v, then RAS on the residual v - A z0 */
+                csr_mv(&p->cg.Pt, vj, vH);
+                memcpy(xH, vH, sizeof(zc) * (size_t)nH);
+                band_solve_z(nH, p->cg.kl, p->cg.kl, p->cg.ab, p->cg.piv, xH);
+                csr_mv(&p->cg.P, xH, zj);
+                csr_mv(&p->A, zj, w);
+                for (int t = 0; t < n; t++) tv[t] = vj[t] - w[t];
+                s2 = or_ras_apply(p, (const double *)tv, (double *)z2, prm->inner_tol, prm->inner_restart,
+                                  prm->inner_maxit, &it_tot, &it_max, &it_hits);
+                for (int t = 0; t < n; t++) zj[t] += z2[t];
+            } else {
+                s2 = or_ras_apply(p, (const double *)vj, (double *)zj, prm->inner_tol, prm->inner_restart,
+                                  prm->inner_maxit, &it_tot, &it_max, &it_hits);
+            }
             if (s2 != OR_OK) { status = s2; break; }
             inner_tot += it_tot; hits += it_hits;
             if (it_max > inner_max) inner_max = it_max;
@@ -1114,5 +1234,6 @@ int or_solve(const or_problem *p, const double *f_, double *x_, const or_solve_p
     st->inner_maxit_hits = hits;
     st->n_history = nh;
     free(V); free(Zb); free(H); free(g); free(sn); free(cs); free(y); free(htmp); free(r); free(w);
+    free(vH); free(xH); free(tv); free(z2);
     return status;
 }

@@ -36,6 +36,7 @@ typedef struct {
     double inner_tol;     /* relative deflated residual; <= 0 selects the direct (LU) local solve */
     int inner_restart;
     int inner_maxit;
+    int two_level;        /* 1: hybrid two-level preconditioner with the grid coarse space       */
 } or_solve_params;
 
 typedef struct {
@@ -98,6 +99,14 @@ int or_ras_apply(const or_problem *p, const double *v_c128, double *z_c128, doub
                  int *inner_its_max, long long *maxit_hits);
 int or_solve(const or_problem *p, const double *f_c128, double *x_c128, const or_solve_params *prm,
              or_stats *st, double *res_history, int history_cap);
+
+/* -- two-level variant: grid coarse space (P1 on the mesh of N/c intervals, lumped mass) ----- */
+/* z = Q v + M_RAS⁻¹ (v - A Q v), Q = P A_H⁻¹ Pᵀ (coarse correction first, then one-level RAS)   */
+int or_setup_coarse_grid(or_problem *p, int c);             /* Dirichlet only; c | N        */
+int or_cg_n(const or_problem *p);                           /* coarse unknowns (N/c - 1)²  */
+void or_cg_apply_P(const or_problem *p, const double *uH_c128, double *u_c128);
+void or_cg_apply_Pt(const or_problem *p, const double *v_c128, double *vH_c128);
+void or_cg_solve(const or_problem *p, const double *yH_c128, double *xH_c128);
 
 /* -- outer CGS2 as or_solve applies it (exposed for pins) ---------------------------------- */
 double or_cgs2(const double *V_c128, int n, int nv, double *w_c128, double *h_c128);
