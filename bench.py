@@ -157,12 +157,13 @@ def oracle_estimate(w, M: int, J: int):
 WARM_START_PARAMS = os.path.join(ROOT, "paper_2103_17081_gb300", "weights", "k200_warmstart.bin")
 
 
-def oracle_error(w, x):
+def oracle_error(w, x, name=None):
     """Relative error of the solution x (device tensor, one RHS) against the oracle's stored
-    solve of workload w: 2-norm and largest entry error over the largest entry; None when no
-    stored solve exists for w."""
+    solve `name` (default: workload w's own): 2-norm and largest entry error over the largest
+    entry; None when no stored solve exists."""
     import numpy as np
-    path = os.path.join(ROOT, "tests", "golden", f"{w.name}_oracle_x.npy")
+    name = name or w.name
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle_x.npy")
     if not os.path.exists(path) or w.nrhs != 1:
         return None
     xr = np.load(path)
@@ -172,7 +173,7 @@ def oracle_error(w, x):
     d = xg - xr
     return {"rel_2norm": float(np.linalg.norm(d) / np.linalg.norm(xr)),
             "max_rel": float(np.max(np.abs(d)) / np.max(np.abs(xr))),
-            "reference": f"tests/golden/{w.name}_oracle_x.npy (oracle, complex128)"}
+            "reference": f"tests/golden/{name}_oracle_x.npy (oracle, complex128)"}
 
 
 def time_form(s, f, x, kw, steps, warmup, flush, stream):
@@ -314,16 +315,21 @@ def run_gpu(args):
     err = oracle_error(w, x) if rank == 0 else None     # the stored solves use seed 0
 
     # the other forms of the method, fewer steps each: plain FP64 (complex128 inner, FP64
-    # second CGS pass) and the learned warm start (network trained by the library's own kernels)
+    # second CGS pass), the learned warm start (network trained by the library's own kernels) and
+    # the two-level hybrid RAS with the grid coarse space H = 2h (Dirichlet problem only)
     forms = {}
     if ws == 1 and args.form_steps > 0 and not args.warm_start and args.prec == 64 and not args.fp64_reorth:
         cand = [("plain_fp64", dict(kw, inner_prec=128, outer_reorth32=0), None)]
         if w.name == "k200" and os.path.exists(WARM_START_PARAMS):
             cand.append(("warm_start", dict(kw, warm_start=1), WARM_START_PARAMS))
+        if w.bc == 0 and w.N % 2 == 0:
+            cand.append(("two_level", dict(kw, two_level=1), None))
         for name, fkw, params in cand:
             if params:
                 from paper_2103_17081_gb300 import warmstart
                 s.cnn_set_params(warmstart.load(params))
+            if fkw.get("two_level"):
+                s.setup_coarse_grid(2)
             t, fst = time_form(s, f, x, fkw, args.form_steps, 1, flush, stream)
             forms[name] = {"value": t, "unit": "s", "steps": args.form_steps, "warmup": 1,
                            "outer_its": fst["outer_its"], "inner_its_avg": round(fst["inner_its_avg"], 3),
@@ -333,7 +339,24 @@ def run_gpu(args):
                            "warm_start": bool(fkw.get("warm_start", 0))}
             if params:
                 forms[name]["params"] = os.path.relpath(params, ROOT)
+            if fkw.get("two_level"):
+                # against the oracle's own two-level solve, and the coarse-grid kernels' share of
+                # one more (profiled) solve
+                forms[name]["err_vs_oracle_two_level"] = oracle_error(w, x, w.name + "tl")
+                forms[name]["coarse_grid"] = "P1, H = 2h, lumped mass, DST solve in FP32"
+                s.profile(True)
+                s.solve(f, out=x, **fkw)
+                torch.cuda.synchronize()
+                fam = {d["name"]: d for d in s.profile_stats()}
+                s.profile(False)
+                tot = sum(d["ms"] for d in fam.values())
+                cg = fam.get("two_level_grid_coarse", {"ms": 0.0, "launches": 0})
+                forms[name]["grid_coarse_ms"] = round(cg["ms"], 3)
+                forms[name]["grid_coarse_launches"] = cg["launches"]
+                forms[name]["grid_coarse_share"] = round(cg["ms"] / tot, 4) if tot > 0 else None
         forms["default_faster_than_plain_fp64"] = t_step < forms["plain_fp64"]["value"]
+        if "two_level" in forms:
+            forms["two_level_faster_than_default"] = forms["two_level"]["value"] < t_step
 
     # roofline of the dominant kernel family (CUDA-event time inside the timed region)
     hbm, hbm_src = _peaks()

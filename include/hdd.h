@@ -159,6 +159,41 @@ int hdd_num_rhs(const hdd_ctx *ctx);
 /* ---------------------------------------------------------------------------------------- */
 hdd_status hdd_setup_deflation(hdd_ctx *ctx, void *stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Two-level RAS (the coarse space the conclusions, §4, name as the next step).  The coarse   */
+/* space is P1 on the mesh of N/c intervals with the same diagonal direction (H = c h): P     */
+/* interpolates a coarse nodal vector to the fine interior nodes (the coarse hat functions    */
+/* are φ = max(0, 1 - max(|ξ|, |η|, |ξ - η|)) for diag 0, |ξ + η| in place of |ξ - η| for diag */
+/* 1, in units of H), Pᵀ restricts.  The coarse operator is rediscretised on that mesh with a */
+/* lumped mass, A_H = K_H - k² H² I (every coarse hat integrates to H²), whose eigenvectors   */
+/* are the discrete sine modes: A_H⁻¹ = S D⁻¹ S with S the orthonormal DST-I of order m =     */
+/* N/c - 1 along each axis and D_pq = 4 sin²(pπ/2Nc) + 4 sin²(qπ/2Nc) - k²H².  The two-level   */
+/* preconditioner is the hybrid z = Q v + M_RAS⁻¹(v - A Q v), Q = P A_H⁻¹ Pᵀ, applied by       */
+/* hdd_solve and hdd_ras_apply when hdd_solve_params.two_level is 1.  Coarse vectors hold     */
+/* m² complex entries, x fastest (node (I, J), 1 <= I, J <= m, at (I-1) + (J-1) m).           */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Build P's tables and S, D⁻¹ (FP64 on the host, an FP32 copy beside them) for coarsening   */
+/* factor c.  HDD_ERR_INVALID_ARG unless c >= 2 divides N with N/c >= 2, or for bc = 1;       */
+/* HDD_ERR_SINGULAR_COARSE if some |D_pq| <= 1e-13 max |D| (k H on a coarse resonance).       */
+/* Needs hdd_assemble; kept across hdd_setup_dd and hdd_setup_batch; synchronises the stream. */
+hdd_status hdd_setup_coarse_grid(hdd_ctx *ctx, int c, void *stream);
+
+/* Test hook: apply the stages set in `stages` to nrhs complex128 vectors, in this order:     */
+/*   HDD_CG_RESTRICT  v (fine, nglob) → Pᵀ v (coarse, m²)                                       */
+/*   HDD_CG_SOLVE     y (coarse) → A_H⁻¹ y (coarse; four DST passes and the diagonal scaling,  */
+/*                    in FP32 for prec 64, FP64 for prec 128)                                  */
+/*   HDD_CG_PROLONG   u (coarse) → P u (fine)                                                  */
+/* in_dev and out_dev hold nrhs consecutive vectors of the stage's input and output lengths   */
+/* (distinct device buffers, 16-byte aligned).  All three: out = Q in.                        */
+#define HDD_CG_RESTRICT 1
+#define HDD_CG_SOLVE 2
+#define HDD_CG_PROLONG 4
+hdd_status hdd_coarse_grid_op(hdd_ctx *ctx, int stages, int prec, const void *in_dev, void *out_dev,
+                              void *stream);
+/* m² of the coarse grid set up, 0 if none */
+long long hdd_coarse_grid_size(const hdd_ctx *ctx);
+
 /* Banded LU (FP64, partial pivoting) of every distinct A_j for the direct local solve
  * (inner_tol <= 0, the benchmark of §3.1); for bc = 1 of its real equivalent, as for E. */
 hdd_status hdd_setup_exact(hdd_ctx *ctx, void *stream);
@@ -182,6 +217,9 @@ typedef struct {
                          /* correction V h2 in FP32 from an FP32 copy of the basis whenever */
                          /* sum |h2| <= 2^-34 ||w'|| (error below the FP64 rounding of w'), */
                          /* FP64 otherwise; 0: FP64 always.  Dots, norms, H: FP64 always    */
+    int two_level;       /* 1: hybrid two-level RAS with the grid coarse space of            */
+                         /* hdd_setup_coarse_grid, z = Q v + M_RAS⁻¹(v - A Q v); 0: one-level */
+                         /* RAS as in the paper (§3).  Ignored by hdd_autotune              */
 } hdd_solve_params;
 
 typedef struct {
@@ -211,7 +249,9 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
 /* One application of the RAS preconditioner z = Σ_j R_jᵀ D_j ũ_j with ũ_j the inexact (or,
  * for inner_tol <= 0, direct) solution of A_j ũ_j = R_j v (Eq. 3): the inner-solve hot path on
  * its own.  v_dev, z_dev: nrhs global complex128 vectors.  inner_its (may be NULL): host array
- * of nsub x nrhs receiving each local solve's Arnoldi step count (task r·nsub + s). */
+ * of nsub x nrhs receiving each local solve's Arnoldi step count (task r·nsub + s).  With
+ * prm->two_level = 1 it applies the hybrid two-level preconditioner z = Q v + M_RAS⁻¹(v - A Q v)
+ * (needs hdd_setup_coarse_grid; inner_its then counts the local solves of M_RAS⁻¹). */
 hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev,
                          const hdd_solve_params *prm, int *inner_its, void *stream);
 

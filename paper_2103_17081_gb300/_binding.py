@@ -20,7 +20,8 @@ SYMBOLS = ["hdd_create", "hdd_destroy", "hdd_status_str", "hdd_last_error", "hdd
            "hdd_warmstart_load", "hdd_warmstart_save",
            "hdd_num_rhs", "hdd_cnn_num_params", "hdd_cnn_set_params", "hdd_cnn_get_params",
            "hdd_cnn_forward", "hdd_cnn_infer", "hdd_cnn_loss_grad", "hdd_cnn_train_step", "hdd_get_outer_vector",
-           "hdd_stencil_rows", "hdd_set_option"]
+           "hdd_stencil_rows", "hdd_set_option", "hdd_setup_coarse_grid", "hdd_coarse_grid_op",
+           "hdd_coarse_grid_size"]
 
 
 def status_name(code: int) -> str:
@@ -45,7 +46,8 @@ class DDParams(C.Structure):
 class SolveParams(C.Structure):
     _fields_ = [("outer_tol", C.c_double), ("outer_restart", C.c_int), ("outer_maxit", C.c_int),
                 ("inner_tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
-                ("inner_prec", C.c_int), ("warm_start", C.c_int), ("outer_reorth32", C.c_int)]
+                ("inner_prec", C.c_int), ("warm_start", C.c_int), ("outer_reorth32", C.c_int),
+                ("two_level", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -147,6 +149,12 @@ def lib(build_if_missing: bool = True):
     L.hdd_get_outer_vector.restype = I
     L.hdd_apply_PA_noalloc.argtypes = [P, V, V, V]
     L.hdd_apply_PA_noalloc.restype = I
+    L.hdd_setup_coarse_grid.argtypes = [P, I, V]
+    L.hdd_setup_coarse_grid.restype = I
+    L.hdd_coarse_grid_op.argtypes = [P, I, I, V, V, V]
+    L.hdd_coarse_grid_op.restype = I
+    L.hdd_coarse_grid_size.argtypes = [P]
+    L.hdd_coarse_grid_size.restype = C.c_longlong
     L.hdd_set_option.argtypes = [P, I, I]
     L.hdd_set_option.restype = I
     _lib = L

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhdd.so")
 SOURCES = ["hdd_api.cu", "kernels_local.cu", "kernels_coarse.cu", "kernels_outer.cu", "kernels_cnn.cu",
-           "kernels_cnn_tc.cu"]
+           "kernels_cnn_tc.cu", "kernels_cgrid.cu"]
 HEADERS = [os.path.join(CSRC, "hdd_common.cuh"), os.path.join(ROOT, "include", "hdd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -57,12 +57,14 @@ template <typename R> struct InnerWork {   // inner GMRES buffers for one precis
 
 // Kernel families timed by the profiler (CUDA events around every launch on the launching
 // stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
-enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, F_STEP, F_ODF, NFAM };
+enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, F_STEP, F_ODF,
+           F_CGRID, NFAM };
 const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
                               "local_cgs2_update", "local_givens_normalize", "local_misc",
                               "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn",
-                              "outer_reorth_fp32", "local_arnoldi_step", "outer_dots_df32"};
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 0};
+                              "outer_reorth_fp32", "local_arnoldi_step", "outer_dots_df32",
+                              "two_level_grid_coarse"};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 0, 0};
 
 struct Prof {
     bool on = false;
@@ -165,6 +167,13 @@ struct hdd_ctx {
     int step_C[2] = {-1, -1};                  // fused-step cluster size per inner precision (0: off, -1: unplanned)
     size_t step_smem[2] = {0, 0};
     bool poisoned = false;                     // a device wait gave up with work in flight
+    // grid coarse space of the two-level variant: sine transform S and D⁻¹ (FP64 and FP32 copies),
+    // two coarse work vectors, and the fine vectors Q v and v - A Q v of the hybrid step
+    struct CoarseGrid {
+        bool ready = false;
+        int c = 0, Nc = 0, m = 0;
+        DevMem S64, S32, D64, D32, bufA, bufB, z0, t;
+    } cg;
     ~hdd_ctx() { if (h_counter) cudaFreeHost(h_counter); }
 };
 
@@ -923,6 +932,99 @@ hdd_status check_solve_params(hdd_ctx *ctx, const hdd_solve_params *p) {
         FAIL(HDD_ERR_INVALID_ARG, "inner_restart must be in 1..%d and inner_maxit >= 1", MAX_RESTART);
     if (p->inner_prec != 64 && p->inner_prec != 128)
         FAIL(HDD_ERR_INVALID_ARG, "inner_prec must be 64 or 128");
+    if (p->two_level != 0 && p->two_level != 1) FAIL(HDD_ERR_INVALID_ARG, "two_level must be 0 or 1");
+    if (p->two_level && !ctx->cg.ready) FAIL(HDD_ERR_STATE, "two_level needs hdd_setup_coarse_grid");
+    return HDD_OK;
+}
+
+// Stages of Q = P A_H⁻¹ Pᵀ (HDD_CG_* bits, applied in the order restrict, solve, prolong) on the
+// nrhs vectors of `in`; `active` (per RHS, may be null) skips vectors.  Fine vectors complex128;
+// coarse ones in the work precision T inside, complex128 at the boundary.  The last coarse
+// result stays in bufA (the hybrid step prolongs it a second time).
+template <typename T>
+hdd_status cg_stages(hdd_ctx *ctx, int stages, const void *in, void *out, const int *active, cudaStream_t s) {
+    auto &G = ctx->cg;
+    const long long n = ctx->nglob, mm = (long long)G.m * G.m;
+    const int nr = ctx->nrhs;
+    CK(G.bufA.ensure((size_t)nr * mm * sizeof(double2)));
+    CK(G.bufB.ensure((size_t)nr * mm * sizeof(double2)));
+    c2<T> *a = G.bufA.as<c2<T>>(), *b = G.bufB.as<c2<T>>();
+    const CGrid g{ctx->N, G.c, G.Nc, G.m, ctx->diag};
+    const bool f32 = sizeof(T) == 4;
+    const T *S = f32 ? reinterpret_cast<const T *>(G.S32.p) : reinterpret_cast<const T *>(G.S64.p);
+    const T *Dinv = f32 ? reinterpret_cast<const T *>(G.D32.p) : reinterpret_cast<const T *>(G.D64.p);
+    const double cs = (double)sizeof(c2<T>);
+    const c2<T> *cur = nullptr;
+    auto coarse_input = [&]() -> hdd_status {      // complex128 coarse input in the work precision
+        if (f32) {
+            KL(F_CGRID, nr * mm * (16 + cs), 0,
+               launch_cg_narrow(nr * mm, (const double2 *)in, reinterpret_cast<float2 *>(a), s));
+            cur = a;
+        } else {
+            cur = reinterpret_cast<const c2<T> *>(in);
+        }
+        return HDD_OK;
+    };
+    if (stages & HDD_CG_RESTRICT) {
+        KL(F_CGRID, nr * (n * 16.0 + mm * cs), 2.0 * nr * mm * (2 * G.c - 1) * (2 * G.c - 1),
+           launch_cg_restrict<T>(g, (const double2 *)in, a, nr, n, mm, active, s));
+        cur = a;
+    }
+    if (stages & HDD_CG_SOLVE) {
+        if (!cur) coarse_input();
+        // four passes of m³ complex-by-real products each: S Y S, scaled by D⁻¹, then S · S
+        const double fl = 4.0 * nr * mm * (double)G.m;
+        KL(F_CGRID, 2.0 * nr * mm * cs, fl, launch_dst_pass<T>(G.m, S, nullptr, cur, b, nr, mm, active, s));
+        KL(F_CGRID, 2.0 * nr * mm * cs, fl, launch_dst_pass<T>(G.m, S, Dinv, b, a, nr, mm, active, s));
+        KL(F_CGRID, 2.0 * nr * mm * cs, fl, launch_dst_pass<T>(G.m, S, nullptr, a, b, nr, mm, active, s));
+        KL(F_CGRID, 2.0 * nr * mm * cs, fl, launch_dst_pass<T>(G.m, S, nullptr, b, a, nr, mm, active, s));
+        cur = a;
+    }
+    if (stages & HDD_CG_PROLONG) {
+        if (!cur) coarse_input();
+        KL(F_CGRID, nr * (n * 16.0 + mm * cs), 0,
+           launch_cg_prolong<T>(g, cur, (double2 *)out, 0, nr, n, mm, active, s));
+    } else if (f32) {
+        KL(F_CGRID, nr * mm * (16 + cs), 0,
+           launch_cg_widen(nr * mm, reinterpret_cast<const float2 *>(cur), (double2 *)out, s));
+    } else {
+        CK(cudaMemcpyAsync(out, cur, (size_t)nr * mm * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    }
+    CKL();
+    return HDD_OK;
+}
+
+// The preconditioner of the outer FGMRES: one-level RAS (Eq. 3), or with two_level the hybrid
+// two-level form z = Q v + M_RAS⁻¹(v - A Q v) with Q = P A_H⁻¹ Pᵀ.  The coarse solve runs in
+// FP32 with the complex64 inner solves, in FP64 otherwise.  mask: per task, ract: per RHS
+// (either may be null = all).
+hdd_status precond_apply(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve_params *prm,
+                         cudaStream_t s, long long *tot, int *mx, long long *hits, int *its_out,
+                         const int *mask, const int *ract) {
+    if (!prm->two_level) return ras_apply(ctx, v, z, prm, s, tot, mx, hits, its_out, mask);
+    auto &G = ctx->cg;
+    if (!G.ready) FAIL(HDD_ERR_STATE, "two_level needs hdd_setup_coarse_grid");
+    const long long n = ctx->nglob, mm = (long long)G.m * G.m;
+    const int nr = ctx->nrhs;
+    CK(G.z0.ensure((size_t)nr * n * sizeof(double2)));
+    CK(G.t.ensure((size_t)nr * n * sizeof(double2)));
+    double2 *z0 = G.z0.as<double2>(), *t = G.t.as<double2>();
+    const bool f32 = prm->inner_tol > 0 && prm->inner_prec == 64;
+    const int all = HDD_CG_RESTRICT | HDD_CG_SOLVE | HDD_CG_PROLONG;
+    hdd_status st = f32 ? cg_stages<float>(ctx, all, v, z0, ract, s) : cg_stages<double>(ctx, all, v, z0, ract, s);
+    if (st != HDD_OK) return st;
+    KL(F_CGRID, 3.0 * nr * n * 16, 0, launch_gstencil(ctx->st, ctx->N, z0, t, v, nr, ract, s));  // t = v - A Q v
+    CKL();
+    if ((st = ras_apply(ctx, t, z, prm, s, tot, mx, hits, its_out, mask)) != HDD_OK) return st;
+    // z += Q v, interpolated again from the coarse solution kept in bufA
+    const CGrid g{ctx->N, G.c, G.Nc, G.m, ctx->diag};
+    if (f32)
+        KL(F_CGRID, nr * (2.0 * n * 16 + mm * 8), 0,
+           launch_cg_prolong<float>(g, G.bufA.as<float2>(), z, 1, nr, n, mm, ract, s));
+    else
+        KL(F_CGRID, nr * (2.0 * n * 16 + mm * 16), 0,
+           launch_cg_prolong<double>(g, G.bufA.as<double2>(), z, 1, nr, n, mm, ract, s));
+    CKL();
     return HDD_OK;
 }
 
@@ -1161,6 +1263,7 @@ hdd_status hdd_assemble(hdd_ctx *ctx, const hdd_assemble_params *p) {
     ctx->assembled = true;
     ctx->dd = false;
     ctx->E.clear(); ctx->Aex.clear();
+    ctx->cg.ready = false;
     return HDD_OK;
 }
 
@@ -1313,6 +1416,80 @@ hdd_status hdd_setup_exact(hdd_ctx *ctx, void *stream) {
     return build_factors(ctx, ctx->Aex, false, (cudaStream_t)stream);
 }
 
+hdd_status hdd_setup_coarse_grid(hdd_ctx *ctx, int c, void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
+    if (!ctx->assembled) FAIL(HDD_ERR_STATE, "hdd_assemble first");
+    if (ctx->bc != 0) FAIL(HDD_ERR_INVALID_ARG, "the grid coarse space serves the Dirichlet problem only");
+    if (c < 2 || ctx->N % c != 0 || ctx->N / c < 2)
+        FAIL(HDD_ERR_INVALID_ARG, "coarsening factor %d must be >= 2 and divide N = %d with N/c >= 2", c, ctx->N);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    auto &G = ctx->cg;
+    G.ready = false;
+    const int Nc = ctx->N / c, m = Nc - 1;
+    const double H = 1.0 / Nc, kH2 = ctx->k * ctx->k * H * H, sc = std::sqrt(2.0 / Nc), pi = 3.141592653589793;
+    const size_t mm = (size_t)m * m;
+    // orthonormal DST-I: S_ij = sqrt(2/Nc) sin(π (i+1)(j+1) / Nc), the argument reduced modulo 2π
+    // exactly in integers; eigenvalues of tridiag(-1, 2, -1): λ_p = 4 sin²(pπ / 2Nc)
+    std::vector<double> S(mm), D(mm), lam(m);
+    std::vector<float> S32(mm), D32(mm);
+    for (int p = 1; p <= m; p++) {
+        const double sn = std::sin(pi * p / (2.0 * Nc));
+        lam[p - 1] = 4.0 * sn * sn;
+    }
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < m; j++) {
+            const long long t = ((long long)(i + 1) * (j + 1)) % (2LL * Nc);
+            S[(size_t)i * m + j] = sc * std::sin(pi * (double)t / Nc);
+        }
+    double dmin = 1e300, dmax = 0.0;
+    for (int q = 0; q < m; q++)
+        for (int p = 0; p < m; p++) {
+            const double d = lam[p] + lam[q] - kH2;
+            dmin = std::min(dmin, std::fabs(d));
+            dmax = std::max(dmax, std::fabs(d));
+            D[(size_t)q * m + p] = 1.0 / d;
+        }
+    if (!(dmin > 1e-13 * dmax))
+        FAIL(HDD_ERR_SINGULAR_COARSE, "coarse operator singular: min |D| = %.3e (k H on a coarse resonance)", dmin);
+    for (size_t e = 0; e < mm; e++) { S32[e] = (float)S[e]; D32[e] = (float)D[e]; }
+    CK(G.S64.ensure(mm * sizeof(double))); CK(G.D64.ensure(mm * sizeof(double)));
+    CK(G.S32.ensure(mm * sizeof(float))); CK(G.D32.ensure(mm * sizeof(float)));
+    CK(cudaMemcpyAsync(G.S64.p, S.data(), mm * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(G.D64.p, D.data(), mm * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(G.S32.p, S32.data(), mm * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(G.D32.p, D32.data(), mm * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    G.c = c; G.Nc = Nc; G.m = m;
+    G.ready = true;
+    return HDD_OK;
+}
+
+long long hdd_coarse_grid_size(const hdd_ctx *ctx) {
+    if (!ctx || !ctx->cg.ready) return 0;
+    return (long long)ctx->cg.m * ctx->cg.m;
+}
+
+hdd_status hdd_coarse_grid_op(hdd_ctx *ctx, int stages, int prec, const void *in_dev, void *out_dev,
+                              void *stream) {
+    if (!ctx) return HDD_ERR_INVALID_ARG;
+    if (ctx->poisoned) FAIL(HDD_ERR_TIMEOUT, "context lost: a device wait and its drain timed out earlier");
+    if (!ctx->cg.ready) FAIL(HDD_ERR_STATE, "hdd_setup_coarse_grid first");
+    if (stages < 1 || stages > 7)
+        FAIL(HDD_ERR_INVALID_ARG, "stages must be a non-empty set of HDD_CG_* bits");
+    if (prec != 64 && prec != 128) FAIL(HDD_ERR_INVALID_ARG, "prec must be 64 or 128");
+    if (!in_dev || !out_dev || in_dev == out_dev || !aligned16(in_dev) || !aligned16(out_dev))
+        FAIL(HDD_ERR_INVALID_ARG, "bad vector arguments");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    hdd_status st = prec == 64 ? cg_stages<float>(ctx, stages, in_dev, out_dev, nullptr, s)
+                               : cg_stages<double>(ctx, stages, in_dev, out_dev, nullptr, s);
+    if (st != HDD_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    return HDD_OK;
+}
+
 hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev, const hdd_solve_params *prm,
                          int *inner_its, void *stream) {
     if (!ctx) return HDD_ERR_INVALID_ARG;
@@ -1325,7 +1502,8 @@ hdd_status hdd_ras_apply(hdd_ctx *ctx, const void *v_dev, void *z_dev, const hdd
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemsetAsync(z_dev, 0, (size_t)ctx->nrhs * ctx->nglob * sizeof(double2), s));
-    st = ras_apply(ctx, (const double2 *)v_dev, (double2 *)z_dev, prm, s, nullptr, nullptr, nullptr, inner_its);
+    st = precond_apply(ctx, (const double2 *)v_dev, (double2 *)z_dev, prm, s, nullptr, nullptr, nullptr, inner_its,
+                       nullptr, nullptr);
     if (st != HDD_OK) return st;
     CK(cudaStreamSynchronize(s));
     return HDD_OK;
@@ -1459,7 +1637,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
             double2 *vj = V + (long long)j * B.ld, *zj = Zb + (long long)j * B.ld;
             long long it_tot = 0, it_hits = 0;
             int it_mx = 0;
-            st = ras_apply(ctx, vj, zj, prm, s, &it_tot, &it_mx, &it_hits, nullptr, ctx->d_mask.as<int>());
+            st = precond_apply(ctx, vj, zj, prm, s, &it_tot, &it_mx, &it_hits, nullptr, ctx->d_mask.as<int>(), dact);
             if (st != HDD_OK) return st;
             inner_tot += it_tot; hits += it_hits; inner_mx = std::max(inner_mx, it_mx);
             int nact = 0;

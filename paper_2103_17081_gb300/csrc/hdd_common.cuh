@@ -329,4 +329,19 @@ cudaError_t set_conv_tc_smem(int wmax);
 void launch_conv_tc(int nco, int grid, const Task *tasks, const int2 *tct, int ntct, const uint4 *X, long long ptot,
                     const uint4 *Wimg, const float *bias, uint4 *Y, float2 *A4, int wmax, int *err, cudaStream_t s);
 
+// grid coarse space of the two-level variant (kernels_cgrid.cu): the fine mesh of N intervals,
+// coarsening factor c, Nc = N / c coarse intervals, m = Nc - 1 coarse unknowns per axis
+struct CGrid { int N, c, Nc, m, diag; };
+template <typename T>
+void launch_cg_restrict(const CGrid &g, const double2 *v, c2<T> *vH, int nrhs, long long ldv, long long ldh,
+                        const int *active, cudaStream_t s);
+template <typename T>
+void launch_cg_prolong(const CGrid &g, const c2<T> *xH, double2 *z, int accumulate, int nrhs, long long ldv,
+                       long long ldh, const int *active, cudaStream_t s);
+template <typename T>
+void launch_dst_pass(int m, const T *S, const T *Dinv, const c2<T> *in, c2<T> *out, int nrhs, long long ldh,
+                     const int *active, cudaStream_t s);
+void launch_cg_widen(long long n, const float2 *in, double2 *out, cudaStream_t s);
+void launch_cg_narrow(long long n, const double2 *in, float2 *out, cudaStream_t s);
+
 }  // namespace hdd

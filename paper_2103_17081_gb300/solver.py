@@ -100,6 +100,32 @@ class Solver:
         self._check(self._L.hdd_setup_exact(self._h, self._stream(stream)), "hdd_setup_exact")
         return self
 
+    def setup_coarse_grid(self, c: int = 2, stream=None):
+        """Grid coarse space of the two-level variant: P1 on the mesh of N/c intervals."""
+        self._check(self._L.hdd_setup_coarse_grid(self._h, int(c), self._stream(stream)),
+                    "hdd_setup_coarse_grid")
+        return self
+
+    @property
+    def coarse_grid_size(self) -> int:
+        return int(self._L.hdd_coarse_grid_size(self._h))
+
+    def coarse_grid_op(self, stages: str, x, prec: int = 128, stream=None):
+        """Apply the stages of Q = P A_H⁻¹ Pᵀ named in `stages` ("R" restrict, "S" solve,
+        "P" prolong, in that order; "RSP" is Q) to nrhs complex128 vectors."""
+        bits = {"R": 1, "S": 2, "P": 4}
+        st = 0
+        for ch in stages:
+            st |= bits[ch]
+        mm = self.coarse_grid_size
+        nin = self.nrhs * (self.n if st & 1 else mm)
+        nout = self.nrhs * (self.n if st & 4 else mm)
+        out = self.empty(nout)
+        self._check(self._L.hdd_coarse_grid_op(self._h, st, int(prec), self._vec(x, nin, "x"),
+                                               self._vec(out), self._stream(stream)),
+                    "hdd_coarse_grid_op")
+        return out
+
     @classmethod
     def from_workload(cls, w, device: int = 0, deflation: bool = True, exact: bool = False):
         s = cls(device).assemble(w.k, w.N, bc=getattr(w, "bc", 0))
@@ -153,9 +179,10 @@ class Solver:
     @staticmethod
     def params(outer_tol=1e-6, outer_restart=2000, outer_maxit=2000, inner_tol=1e-2,
                inner_restart=30, inner_maxit=1000, inner_prec=64, warm_start=0,
-               outer_reorth32=1) -> SolveParams:
+               outer_reorth32=1, two_level=0) -> SolveParams:
         return SolveParams(outer_tol, outer_restart, outer_maxit, inner_tol, inner_restart,
-                           inner_maxit, inner_prec, int(bool(warm_start)), int(bool(outer_reorth32)))
+                           inner_maxit, inner_prec, int(bool(warm_start)), int(bool(outer_reorth32)),
+                           int(bool(two_level)))
 
     def build_rhs_batch(self, specs):
         """Load vectors of several RHSSpecs, stacked RHS-major in one tensor."""

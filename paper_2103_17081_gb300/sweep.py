@@ -44,7 +44,11 @@ def settings(ks, ppwls, subs, bc=0):
     return out
 
 
-def run(ks, ppwls, tols, subs, inner_prec=128, log=print, bc=0):
+def run(ks, ppwls, tols, subs, inner_prec=128, log=print, bc=0, two_level=0):
+    """One solve per (setting, inner tolerance).  With complex128 inner solves the outer Arnoldi
+    runs in plain FP64 as well (the form whose counts follow the oracle's stopping decisions);
+    with complex64 ones it uses the default double-FP32 dots and guarded FP32 second pass.
+    two_level: the hybrid two-level RAS with the grid coarse space H = 2h."""
     import torch
 
     from .solver import Solver
@@ -53,17 +57,20 @@ def run(ks, ppwls, tols, subs, inner_prec=128, log=print, bc=0):
     for (ppwl, k, n_glob, S, w) in settings(ks, ppwls, subs, bc):
         need_lu = any(t <= 0 for _, t in tols)
         s = Solver.from_workload(w, exact=need_lu)
+        if two_level:
+            s.setup_coarse_grid(2)
         f = s.build_rhs(w.rhs[0])
         for name, tol in tols:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, st = s.solve(f, outer_tol=1e-6, inner_tol=tol, inner_prec=inner_prec,
-                            inner_restart=30, inner_maxit=1000, raise_on_error=False)
+                            inner_restart=30, inner_maxit=1000, raise_on_error=False,
+                            outer_reorth32=int(inner_prec == 64), two_level=two_level)
             torch.cuda.synchronize()
             r = {"ppwl": ppwl, "k": k, "n_glob": n_glob, "N": S * S, "inner": name,
                  "outer_its": st["outer_its"], "inner_avg": round(st["inner_its_avg"], 1),
                  "rel_res": st["rel_res_true"], "status": st["status_code"],
-                 "s": round(time.perf_counter() - t0, 3), "bc": bc}
+                 "s": round(time.perf_counter() - t0, 3), "bc": bc, "two_level": int(bool(two_level))}
             rows.append(r)
             if log:
                 log(json.dumps(r))
@@ -131,6 +138,8 @@ def main(argv=None):
     ap.add_argument("--prec", type=int, default=128, choices=[64, 128], help="inner precision")
     ap.add_argument("--bc", type=int, default=0, choices=[0, 1],
                     help="0: u = 0 on the boundary (the paper's tables); 1: impedance condition")
+    ap.add_argument("--two-level", action="store_true",
+                    help="hybrid two-level RAS with the grid coarse space H = 2h (bc 0 only)")
     ap.add_argument("--json", default=None, help="also write every row as a JSON line to this file")
     ap.add_argument("--c2", action="store_true",
                     help="the k=100 inner-tolerance sweep {1e-1, 1e-2, 1e-4, exact} instead")
@@ -145,7 +154,7 @@ def main(argv=None):
         c2_sweep(s, s.build_rhs(w.rhs[0]), reps=a.reps)
         return 0
     tols = [(n, t) for n, t in TOLS if n in a.inner]
-    rows = run(a.k, a.ppwl, tols, a.subdomains, a.prec, bc=a.bc)
+    rows = run(a.k, a.ppwl, tols, a.subdomains, a.prec, bc=a.bc, two_level=int(a.two_level))
     if a.json:
         with open(a.json, "w") as fh:
             for r in rows:

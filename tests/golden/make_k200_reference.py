@@ -1,7 +1,8 @@
 """Write the CPU oracle's solve of a k=200 workload under tests/golden/.
 
 Runs only oracle/ (no CUDA code).  For workload W (k200: Dirichlet, the default; k200s: the
-impedance boundary) it writes
+impedance boundary; k200tl: k200 with the two-level hybrid RAS preconditioner, grid coarse
+space H = 2h) it writes
 
   W_oracle.json   outer/inner iteration counts, the residual history every 50 iterations,
                   ||x||_2, ||x||_inf and x at 256 seeded nodes;
@@ -11,7 +12,7 @@ impedance boundary) it writes
 The GPU tests compare their full-size solves against these at every node.  Each solve takes
 10-25 minutes on 8 cores.
 
-    python tests/golden/make_k200_reference.py [k200|k200s]
+    python tests/golden/make_k200_reference.py [k200|k200s|k200tl]
 """
 import json
 import os
@@ -28,16 +29,19 @@ import workloads as W  # noqa: E402
 
 
 def main(name: str = "k200"):
-    w = W.make(name)
+    two_level = name.endswith("tl")
+    w = W.make(name[:-2] if two_level else name)
     p = oracle.from_workload(w)
+    if two_level:
+        p.setup_coarse_grid(2)
     f = p.rhs(w.rhs[0])
     t0 = time.time()
-    x, st = p.solve(f, outer_tol=w.outer_tol, inner_tol=w.inner_tol)
+    x, st = p.solve(f, outer_tol=w.outer_tol, inner_tol=w.inner_tol, two_level=int(two_level))
     secs = time.time() - t0
     rng = W.SplitMix64(2024)
     idx = sorted({int(rng.uniform(0, p.n)) for _ in range(256)})
     out = {
-        "workload": w.name, "N": w.N, "k": w.k, "bc": w.bc, "outer_tol": w.outer_tol,
+        "workload": w.name, "two_level": int(two_level), "coarse_factor": 2 if two_level else 0, "N": w.N, "k": w.k, "bc": w.bc, "outer_tol": w.outer_tol,
         "inner_tol": w.inner_tol, "outer_restart": 2000, "inner_restart": 30,
         "outer_its": st["outer_its"], "inner_its_total": st["inner_its_total"],
         "inner_its_avg": st["inner_its_avg"], "rel_res_true": st["rel_res_true"],
