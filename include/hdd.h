@@ -362,12 +362,18 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 /* FP32 second outer CGS pass (outer_reorth32 = 1), the dot products of both outer CGS passes  */
 /* run in double-FP32 arithmetic (error-free products and sums, as accurate as FP64 sums) from  */
 /* hi/lo FP32 copies of the basis (1, the default; another 8 bytes per basis entry) or in FP64  */
-/* (0); every update of the Krylov vector (the Arnoldi relation) stays FP64.                    */
+/* (0).  HDD_OPT_OUTER_UPDATE_DF (4): with HDD_OPT_OUTER_DOTS_DF, the first-pass update         */
+/* w' = w - V h1 also runs in double-FP32 arithmetic from those copies, widened to FP64 every   */
+/* 32 basis vectors (1, the default: 16 bytes per basis entry on the FP32 pipe; worst-case      */
+/* error 3.6e-12 Σ|v h| against 1.4e-13 for the FP64 sum at 1270 vectors, removed from the      */
+/* basis directions by the second pass) or in FP64 (0).  Hessenberg entries, norms, w and the   */
+/* solution stay FP64.  outer_reorth32 = 0 runs every outer step in FP64 whatever these say.    */
 /* HDD_ERR_INVALID_ARG for an unknown key or a value other than 0 or 1.  Takes effect from the  */
 /* next call that solves.                                                                       */
 #define HDD_OPT_COARSE_LOOKAHEAD 1
 #define HDD_OPT_FUSED_INNER 2
 #define HDD_OPT_OUTER_DOTS_DF 3
+#define HDD_OPT_OUTER_UPDATE_DF 4
 hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value);
 
 /* ---------------------------------------------------------------------------------------- */

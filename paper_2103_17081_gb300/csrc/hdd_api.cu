@@ -58,13 +58,13 @@ template <typename R> struct InnerWork {   // inner GMRES buffers for one precis
 // Kernel families timed by the profiler (CUDA events around every launch on the launching
 // stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
 enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, F_STEP, F_ODF,
-           F_CGRID, NFAM };
+           F_CGRID, F_OUDF, NFAM };
 const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
                               "local_cgs2_update", "local_givens_normalize", "local_misc",
                               "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn",
                               "outer_reorth_fp32", "local_arnoldi_step", "outer_dots_df32",
-                              "two_level_grid_coarse"};
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 0, 0};
+                              "two_level_grid_coarse", "outer_update_df32"};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 0, 0, 0};
 
 struct Prof {
     bool on = false;
@@ -164,6 +164,7 @@ struct hdd_ctx {
     int coarse_la = 1;                         // HDD_OPT_COARSE_LOOKAHEAD
     int fused_inner = 1;                       // HDD_OPT_FUSED_INNER
     int outer_df = 1;                          // HDD_OPT_OUTER_DOTS_DF
+    int outer_udf = 1;                         // HDD_OPT_OUTER_UPDATE_DF
     int step_C[2] = {-1, -1};                  // fused-step cluster size per inner precision (0: off, -1: unplanned)
     size_t step_smem[2] = {0, 0};
     bool poisoned = false;                     // a device wait gave up with work in flight
@@ -1550,7 +1551,8 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     Bd.G = std::max(G, 3 * ctx->nsm);
     CK(O.part.ensure((size_t)nr * Bd.G * ldp * sizeof(double2)));
     CK(O.npart.ensure((size_t)nr * G * sizeof(double)));
-    CK(O.npart1.ensure((size_t)nr * G * sizeof(double)));
+    const int Gu = oupdate_df_grid(n);          // partials of the double-FP32 first-pass update
+    CK(O.npart1.ensure((size_t)nr * std::max(G, Gu) * sizeof(double)));
     const bool r32 = prm->outer_reorth32 != 0;
     // the double-FP32 first pass pairs with the guarded FP32 second pass (its coefficients are
     // what that guard tests); with the FP64 second pass both passes stay FP64
@@ -1657,9 +1659,16 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                    launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                          // h1 = V^H w
                 KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
             }
-            if (df) {     // FP64 update w' = w - V h1 (24 B, 3 FMAs), then h2 = V^H w' in double-FP32 (16 B)
-                KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
-                   launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, nullptr, O.npart1.as<double>(), s));
+            int g1 = G;   // norm partials of w' = w - V h1
+            if (df) {     // update w' = w - V h1, then h2 = V^H w' in double-FP32 (16 B)
+                if (ctx->outer_udf) {   // double-FP32 update from the hi/lo copies: 16 B, ≈ 48 FP32 instructions
+                    g1 = Gu;
+                    KL(F_OUDF, fa * (nv * 16 + 32) * n, fa * 48 * nv * n,
+                       launch_oupdate_df(B, V32, V32L, j + 1, O.h1.as<double2>(), w, O.npart1.as<double>(), s));
+                } else {                // FP64 Gauss form: 24 B, 3 FMAs
+                    KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
+                       launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, nullptr, O.npart1.as<double>(), s));
+                }
                 KL(F_ODF, fa * (nv * 16 + 16) * n, fa * 48 * nv * n,
                    launch_odots_df(Bd, V32, V32L, j + 1, w, O.part.as<double2>(), s));
                 KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
@@ -1670,7 +1679,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
             }
             if (r32)   // FP32 correction from the FP32 basis copy (guarded; FP64 fallback inside)
                 KL(F_OREORTH, fa * (nv * 8 + 2 * 16) * n, fa * 8 * nv * n,
-                   launch_oupdate2(B, V, V32, j + 1, O.h2.as<double2>(), w, O.npart1.as<double>(),
+                   launch_oupdate2(B, V, V32, j + 1, O.h2.as<double2>(), w, O.npart1.as<double>(), g1,
                                    O.npart.as<double>(), 1, O.fallbacks.as<int>(), s));
             else
                 KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
@@ -2018,6 +2027,7 @@ hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value) {
     if (key == HDD_OPT_COARSE_LOOKAHEAD) ctx->coarse_la = value;
     else if (key == HDD_OPT_FUSED_INNER) ctx->fused_inner = value;
     else if (key == HDD_OPT_OUTER_DOTS_DF) ctx->outer_df = value;
+    else if (key == HDD_OPT_OUTER_UPDATE_DF) ctx->outer_udf = value;
     else FAIL(HDD_ERR_INVALID_ARG, "unknown option %d", key);
     return HDD_OK;
 }

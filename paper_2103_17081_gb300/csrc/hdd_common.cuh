@@ -295,8 +295,12 @@ void launch_odots(const OuterBatch &B, const double2 *V, int nv, const double2 *
 void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2 *h, double2 *w,
                     double2 *part_dots, double *part_norm, cudaStream_t s);
 void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
-                     double2 *w, const double *npart1, double *part_norm, int allow32, int *fallbacks,
+                     double2 *w, const double *npart1, int g1, double *part_norm, int allow32, int *fallbacks,
                      cudaStream_t s);
+// first CGS pass update in double-FP32 from the hi/lo FP32 basis; norm partials on its own grid
+int oupdate_df_grid(long long n);
+void launch_oupdate_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const double2 *h,
+                       double2 *w, double *part_norm, cudaStream_t s);
 void launch_fill_test(long long n, unsigned long long seed, double2 *x, cudaStream_t s);
 void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s);
 void launch_oreduce(const OuterBatch &B, const double2 *part, int nv, double2 *out, cudaStream_t s);

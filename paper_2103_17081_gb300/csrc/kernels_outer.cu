@@ -409,9 +409,10 @@ k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__
     }
 }
 
-// Second CGS pass, w_r -= V_r h2_r, then the partial ||w_r||².  After an FP64 first pass the
-// coefficients h2 = V^H w' are rounding-error sized, so the correction V h2 is tiny next to w'.
-// When Σ_l (|Re h2_l| + |Im h2_l|) <= 2^-34 ||w'_r|| (||w'_r||² = Σ npart1) the correction is
+// Second CGS pass, w_r -= V_r h2_r, then the partial ||w_r||².  After the first pass (FP64 or
+// double-FP32) the coefficients h2 = V^H w' are rounding-error sized, so the correction V h2 is
+// tiny next to w'.  When Σ_l (|Re h2_l| + |Im h2_l|) <= 2^-34 ||w'_r|| (||w'_r||² = the sum of
+// the g1 partials npart1 of RHS r) the correction is
 // formed in FP32 from the FP32 copy V32 of the basis: products and partial sums over 32 vectors
 // in FP32 (one chain per element), widened to FP64 between partial sums, subtracted from w' in
 // FP64.  Its error is then at most about 2^-19 Σ|h2| <= 2^-53 ||w'_r|| in the 2-norm
@@ -420,20 +421,20 @@ k_oupdate(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__
 // (fixed-order sums), so all chunks of one RHS take the same path.
 __global__ void __launch_bounds__(OT2)
 k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict__ V32, int nv,
-           const double2 *__restrict__ h, double2 *__restrict__ w, const double *__restrict__ npart1,
+           const double2 *__restrict__ h, double2 *__restrict__ w, const double *__restrict__ npart1, int g1,
            double *__restrict__ part_norm, int allow32, int *__restrict__ fallbacks) {
     extern __shared__ double2 hs[];
     __shared__ double red[OT2 / 32];
     __shared__ int use32_s;
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
-    V += r * B.n; w += r * B.n; h += (long long)r * B.ldp; npart1 += (long long)r * B.G;
+    V += r * B.n; w += r * B.n; h += (long long)r * B.ldp; npart1 += (long long)r * g1;
     if (V32) V32 += r * B.n32;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
         double a = 0.0, q2 = 0.0;
         for (int l = lane; l < nv; l += 32) a += fabs(h[l].x) + fabs(h[l].y);
-        for (int q = lane; q < B.G; q += 32) q2 += npart1[q];
+        for (int q = lane; q < g1; q += 32) q2 += npart1[q];
         for (int o = 16; o > 0; o >>= 1) { a += shfl_xor(a, o); q2 += shfl_xor(q2, o); }
         if (lane == 0) {
             const int u = allow32 && V32 && a <= ldexp(sqrt(q2), -34);
@@ -495,6 +496,79 @@ k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict
         }
     }
     block_sum_store(nrm, red, part_norm + (long long)r * B.G + blockIdx.x);
+}
+
+// First CGS pass update w_r -= Σ_l h_{r,l} V_{r,l} in double-FP32 arithmetic from the hi/lo FP32
+// copies of the basis (V = Vh + Vl to 2^-48 relative), then the partial ||w_r||² of the updated
+// vector (one partial per CTA of this kernel's own grid).  Each coefficient is split once per
+// CTA into (hi, lo) FP32 pairs; every real product v·h is formed as in the dot products (df_acc:
+// exact product of the high parts, the two cross terms, a two-sum into a (hi, lo) FP32
+// accumulator); the accumulators are widened to FP64 after every block of 32 basis vectors and
+// the FP64 total is subtracted from w.  Per block the sum carries at most 2^-48 |S_b| +
+// (32·2^-24)² Σ_b |v_l h_l| (Ogita, Rump & Oishi's bound for the compensated sum, the final
+// rounding to FP32 replaced by the widening), i.e. 3.6e-12 Σ|v_l h_l| in the worst case and
+// about 32·2^-48 typically, against nv·2^-53 Σ|v_l h_l| for the FP64 Gauss-form update
+// (1.4e-13 at nv = 1270).  The second CGS pass removes the basis components of that error;
+// what is left perturbs the next basis vector far below the outer tolerance.  The pass reads 16 B
+// per basis vector and element and runs on the FP32 pipe (≈ 48 instructions per vector and
+// element), where the FP64 update is bound by the FP64 pipe.  Thread q of the grid takes the
+// element pair (2q, 2q + 1) with 16-byte loads; an odd last pair reads the padding entry of
+// its RHS (n32 = n + (n & 1)) and drops it.
+constexpr int OTU = 256;
+__global__ void __launch_bounds__(OTU, 3)
+k_oupdate_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int nv,
+             const double2 *__restrict__ h, double2 *__restrict__ w, double *__restrict__ part_norm) {
+    extern __shared__ float4 hq[];              // (Re hi, Re lo, Im hi, Im lo) of h_l
+    __shared__ double red[OTU / 32];
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    Vh += r * B.n32; Vl += r * B.n32; w += r * B.n; h += (long long)r * B.ldp;
+    for (int l = threadIdx.x; l < nv; l += OTU) {
+        const double2 v = h[l];
+        const float rh = (float)v.x, ih = (float)v.y;
+        hq[l] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+    }
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * OTU + threadIdx.x, i = 2 * p;
+    double nrm = 0.0;
+    if (i < B.n) {
+        const bool two = i + 1 < B.n;
+        const float4 *hp = reinterpret_cast<const float4 *>(Vh) + p;
+        const float4 *lp = reinterpret_cast<const float4 *>(Vl) + p;
+        const long long ld4 = B.ld32 / 2;
+        double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+        for (int l0 = 0; l0 < nv; l0 += 32) {
+            const int l1 = l0 + 32 < nv ? l0 + 32 : nv;
+            float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, bxh = 0.f, bxl = 0.f, byh = 0.f, byl = 0.f;
+#pragma unroll 4
+            for (int l = l0; l < l1; l++) {
+                const float4 vh = hp[(long long)l * ld4], vl = lp[(long long)l * ld4];
+                const float4 c = hq[l];
+                // v·h = (vr hr - vi hi) + i (vr hi + vi hr) for elements a = (x, y) and b = (z, w)
+                df_acc(axh, axl, vh.x, vl.x, c.x, c.y);
+                df_acc(axh, axl, -vh.y, -vl.y, c.z, c.w);
+                df_acc(ayh, ayl, vh.x, vl.x, c.z, c.w);
+                df_acc(ayh, ayl, vh.y, vl.y, c.x, c.y);
+                df_acc(bxh, bxl, vh.z, vl.z, c.x, c.y);
+                df_acc(bxh, bxl, -vh.w, -vl.w, c.z, c.w);
+                df_acc(byh, byl, vh.z, vl.z, c.z, c.w);
+                df_acc(byh, byl, vh.w, vl.w, c.x, c.y);
+            }
+            ax += (double)axh + (double)axl; ay += (double)ayh + (double)ayl;
+            bx += (double)bxh + (double)bxl; by += (double)byh + (double)byl;
+        }
+        double2 xa = w[i];
+        xa.x -= ax; xa.y -= ay;
+        w[i] = xa;
+        nrm = fma(xa.x, xa.x, xa.y * xa.y);
+        if (two) {
+            double2 xb = w[i + 1];
+            xb.x -= bx; xb.y -= by;
+            w[i + 1] = xb;
+            nrm = fma(xb.x, xb.x, fma(xb.y, xb.y, nrm));
+        }
+    }
+    block_sum_store(nrm, red, part_norm + (long long)r * gridDim.x + blockIdx.x);
 }
 
 // Partial ||x_r||² per CTA: part[r][cta].
@@ -777,11 +851,17 @@ void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2
                     double2 *part_dots, double *part_norm, cudaStream_t s) {
     k_oupdate<<<dim3(B.G, B.nrhs), OT, (size_t)nv * 3 * sizeof(double), s>>>(B, V, nv, h, w, part_dots, part_norm);
 }
+int oupdate_df_grid(long long n) { return (int)(((n + 1) / 2 + OTU - 1) / OTU); }
+void launch_oupdate_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const double2 *h,
+                       double2 *w, double *part_norm, cudaStream_t s) {
+    k_oupdate_df<<<dim3(oupdate_df_grid(B.n), B.nrhs), OTU, (size_t)nv * sizeof(float4), s>>>(B, Vh, Vl, nv, h, w,
+                                                                                          part_norm);
+}
 void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
-                     double2 *w, const double *npart1, double *part_norm, int allow32, int *fallbacks,
+                     double2 *w, const double *npart1, int g1, double *part_norm, int allow32, int *fallbacks,
                      cudaStream_t s) {
-    k_oupdate2<<<dim3(B.G, B.nrhs), OT2, (size_t)nv * sizeof(double2), s>>>(B, V, V32, nv, h, w, npart1, part_norm,
-                                                                           allow32, fallbacks);
+    k_oupdate2<<<dim3(B.G, B.nrhs), OT2, (size_t)nv * sizeof(double2), s>>>(B, V, V32, nv, h, w, npart1, g1,
+                                                                           part_norm, allow32, fallbacks);
 }
 void launch_onorm(const OuterBatch &B, const double2 *x, double *part, cudaStream_t s) {
     k_onorm<<<dim3(B.G, B.nrhs), OT, 0, s>>>(B, x, part);
@@ -820,6 +900,7 @@ cudaError_t set_outer_smem_limits(size_t bytes) {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_oupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_oupdate2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_oupdate_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_otrisolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_oaxpy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     return cudaSuccess;

@@ -252,7 +252,7 @@ class Solver:
     def launch_count(self) -> int:
         return int(self._L.hdd_launch_count(self._h))
 
-    OPTIONS = {"coarse_lookahead": 1, "fused_inner": 2, "outer_dots_df": 3}
+    OPTIONS = {"coarse_lookahead": 1, "fused_inner": 2, "outer_dots_df": 3, "outer_update_df": 4}
 
     def set_option(self, name: str, value: int):
         """Implementation choice of this context (hdd_set_option): "coarse_lookahead" selects
