@@ -367,13 +367,19 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 /* 32 basis vectors (1, the default: 16 bytes per basis entry on the FP32 pipe; worst-case      */
 /* error 3.6e-12 Σ|v h| against 1.4e-13 for the FP64 sum at 1270 vectors, removed from the      */
 /* basis directions by the second pass) or in FP64 (0).  Hessenberg entries, norms, w and the   */
-/* solution stay FP64.  outer_reorth32 = 0 runs every outer step in FP64 whatever these say.    */
+/* solution stay FP64.  HDD_OPT_OUTER_DCGS2 (5): with both double-FP32 options, the outer      */
+/* Arnoldi uses delayed CGS2 (Świrydowicz et al., low-synchronisation Gram-Schmidt): the second */
+/* pass of basis vector j runs fused with the first pass of step j+1, so a step makes two passes */
+/* over the basis instead of four (1, the default), or the plain CGS2 above (0); both compute   */
+/* the same FGMRES iteration up to rounding.  outer_reorth32 = 0 runs every outer step in FP64 */
+/* (plain CGS2) whatever these say.                                                            */
 /* HDD_ERR_INVALID_ARG for an unknown key or a value other than 0 or 1.  Takes effect from the  */
 /* next call that solves.                                                                       */
 #define HDD_OPT_COARSE_LOOKAHEAD 1
 #define HDD_OPT_FUSED_INNER 2
 #define HDD_OPT_OUTER_DOTS_DF 3
 #define HDD_OPT_OUTER_UPDATE_DF 4
+#define HDD_OPT_OUTER_DCGS2 5
 hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value);
 
 /* ---------------------------------------------------------------------------------------- */

@@ -112,6 +112,7 @@ struct CnnState {            // learned warm start: parameters, Adam moments, ac
 struct OuterWork {
     DevMem V, V32, V32L, D, Z, w, r, H, cs, sn, g, Wq, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
     DevMem fallbacks;
+    DevMem part2, invs, err, close;             // delayed CGS2: second dot partials, 1/σ, breakdown, end-of-cycle mask
 };
 
 }  // namespace
@@ -165,6 +166,7 @@ struct hdd_ctx {
     int fused_inner = 1;                       // HDD_OPT_FUSED_INNER
     int outer_df = 1;                          // HDD_OPT_OUTER_DOTS_DF
     int outer_udf = 1;                         // HDD_OPT_OUTER_UPDATE_DF
+    int outer_dcgs = 1;                        // HDD_OPT_OUTER_DCGS2
     int step_C[2] = {-1, -1};                  // fused-step cluster size per inner precision (0: off, -1: unplanned)
     size_t step_smem[2] = {0, 0};
     bool poisoned = false;                     // a device wait gave up with work in flight
@@ -1561,6 +1563,17 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     if (df) CK(O.V32L.ensure((size_t)(R + 1) * B.ld32 * sizeof(float2)));
     float2 *V32 = r32 ? O.V32.as<float2>() : nullptr;
     float2 *V32L = df ? O.V32L.as<float2>() : nullptr;
+    // delayed CGS2 (two passes over the basis per step) with the double-FP32 dots and update
+    const bool dc = df && ctx->outer_udf && ctx->outer_dcgs;
+    const int Gc = oupdate_dcgs_grid(n);        // partials of its update
+    if (dc) {
+        CK(O.part2.ensure((size_t)nr * G * ldp * sizeof(double2)));
+        CK(O.invs.ensure(nr * sizeof(double)));
+        CK(O.err.ensure(sizeof(int)));
+        CK(O.close.ensure(nr * sizeof(int)));
+        CK(O.npart1.ensure((size_t)nr * std::max(std::max(G, Gu), Gc) * sizeof(double)));
+        CK(cudaMemsetAsync(O.err.p, 0, sizeof(int), s));
+    }
     CK(O.fallbacks.ensure(sizeof(int)));
     CK(cudaMemsetAsync(O.fallbacks.p, 0, sizeof(int), s));
     CK(O.hn.ensure(nr * sizeof(double))); CK(O.flag.ensure(nr * sizeof(int))); CK(O.beta.ensure(nr * sizeof(double)));
@@ -1646,68 +1659,123 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
             for (int r = 0; r < nr; r++) nact += act[r];
             const double nv = j + 1, fa = nact;
             KL(F_OMISC, 2.0 * fa * n * 16, 0, launch_gstencil(ctx->st, ctx->N, zj, w, nullptr, nr, dact, s));  // w = A z_j
-            // CGS2 flops as executed: dots and update 6 per (vector, element) each (three FMAs,
-            // Gauss form); bytes: V (16 B) and d (8 B) per vector and element for each pass over
-            // the basis (k_oupdate with dots makes two: the update, then the dots of the updated
-            // w), and w
-            if (df) {     // 16 B (hi + lo FP32) per vector and element; 4 real products of ~12 FP32 ops
-                KL(F_ODF, fa * (nv * 16 + 16) * n, fa * 48 * nv * n,
-                   launch_odots_df(Bd, V32, V32L, j + 1, w, O.part.as<double2>(), s));             // h1 = V^H w
-                KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
-            } else {
-                KL(F_OCGS, fa * (nv * 24 + 16) * n, fa * 6 * nv * n,
-                   launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                          // h1 = V^H w
-                KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
-            }
-            int g1 = G;   // norm partials of w' = w - V h1
-            if (df) {     // update w' = w - V h1, then h2 = V^H w' in double-FP32 (16 B)
-                if (ctx->outer_udf) {   // double-FP32 update from the hi/lo copies: 16 B, ≈ 48 FP32 instructions
-                    g1 = Gu;
-                    KL(F_OUDF, fa * (nv * 16 + 32) * n, fa * 48 * nv * n,
-                       launch_oupdate_df(B, V32, V32L, j + 1, O.h1.as<double2>(), w, O.npart1.as<double>(), s));
-                } else {                // FP64 Gauss form: 24 B, 3 FMAs
-                    KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
-                       launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, nullptr, O.npart1.as<double>(), s));
+            if (dc) {
+                // delayed CGS2: one double-FP32 pass for V^H ṽ_j and V^H w (slots 0..j), the
+                // per-RHS completion of column j-1, one pass writing v_j and w', the tentative
+                // stopping test of column j, then ṽ_{j+1} = w'/ν_{j+1} into slot j+1
+                double2 *P1 = O.h2.as<double2>(), *P2 = O.h1.as<double2>();
+                if (j == 0) {
+                    KL(F_ODF, fa * 32.0 * n, fa * 48.0 * n,
+                       launch_odots_df(Bd, V32, V32L, 1, w, O.part.as<double2>(), s));
+                    KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), 1, P2, s));
+                } else {
+                    KL(F_ODF, fa * (nv * 16 + 32) * n, fa * 96 * nv * n,
+                       launch_odots2_df(B, V32, V32L, j + 1, V32 + (long long)j * B.ld32, V32L + (long long)j * B.ld32,
+                                        w, O.part.as<double2>(), O.part2.as<double2>(), s));
+                    KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, P1, s));
+                    KL(F_OMISC, 0, 0, launch_oreduce(B, O.part2.as<double2>(), j + 1, P2, s));
                 }
-                KL(F_ODF, fa * (nv * 16 + 16) * n, fa * 48 * nv * n,
-                   launch_odots_df(Bd, V32, V32L, j + 1, w, O.part.as<double2>(), s));
-                KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
+                KL(F_OMISC, 0, 0,
+                   launch_dcgs_col(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(),
+                                   O.Wq.as<double2>(), j, P1, P2, O.hn.as<double>(), O.invs.as<double>(),
+                                   O.fnorm.as<double>(), O.hist.as<double>(), hstride, total, O.err.as<int>(), s));
+                // bytes: hi/lo of slots 0..j-1, slot j read and rewritten (FP64, Re - Im, hi/lo), w
+                // read and written; ≈ 56 FP32 instructions per basis vector and element
+                KL(F_OUDF, fa * ((nv - 1) * 16 + 16 + 40 + 32) * n, fa * 56 * (nv - 1) * n,
+                   launch_oupdate_dcgs(B, V32, V32L, j, j > 0 ? 1 : 0, V + (long long)j * B.ld,
+                                       O.D.as<double>() + (long long)j * B.ld, V32 + (long long)j * B.ld32,
+                                       V32L + (long long)j * B.ld32, P1, P2, O.invs.as<double>(), w,
+                                       O.npart1.as<double>(), s));
+                KL(F_OMISC, 0, 0,
+                   launch_dcgs_tent(B, O.H.as<double2>(), O.g.as<double2>(), O.Wq.as<double2>(), j,
+                                    O.npart1.as<double>(), Gc, O.fnorm.as<double>(), prm->outer_tol,
+                                    O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>(), hstride, total, s));
+                KL(F_OMISC, 2.0 * fa * n * 16 + fa * n * 16.0, 0,
+                   launch_oscale(B, V + (long long)(j + 1) * B.ld, V32 + (long long)(j + 1) * B.ld32,
+                                 V32L + (long long)(j + 1) * B.ld32, O.D.as<double>() + (long long)(j + 1) * B.ld, w,
+                                 O.hn.as<double>(), s));
             } else {
-                KL(F_OCGS, fa * (nv * 48 + 32) * n, fa * 12 * nv * n,
-                   launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
-                KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
+                // CGS2 flops as executed: dots and update 6 per (vector, element) each (three FMAs,
+                // Gauss form); bytes: V (16 B) and d (8 B) per vector and element for each pass over
+                // the basis (k_oupdate with dots makes two: the update, then the dots of the updated
+                // w), and w
+                if (df) {     // 16 B (hi + lo FP32) per vector and element; 4 real products of ~12 FP32 ops
+                    KL(F_ODF, fa * (nv * 16 + 16) * n, fa * 48 * nv * n,
+                       launch_odots_df(Bd, V32, V32L, j + 1, w, O.part.as<double2>(), s));             // h1 = V^H w
+                    KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
+                } else {
+                    KL(F_OCGS, fa * (nv * 24 + 16) * n, fa * 6 * nv * n,
+                       launch_odots(B, V, j + 1, w, O.part.as<double2>(), s));                          // h1 = V^H w
+                    KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h1.as<double2>(), s));
+                }
+                int g1 = G;   // norm partials of w' = w - V h1
+                if (df) {     // update w' = w - V h1, then h2 = V^H w' in double-FP32 (16 B)
+                    if (ctx->outer_udf) {   // double-FP32 update from the hi/lo copies: 16 B, ≈ 48 FP32 instructions
+                        g1 = Gu;
+                        KL(F_OUDF, fa * (nv * 16 + 32) * n, fa * 48 * nv * n,
+                           launch_oupdate_df(B, V32, V32L, j + 1, O.h1.as<double2>(), w, O.npart1.as<double>(), s));
+                    } else {                // FP64 Gauss form: 24 B, 3 FMAs
+                        KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
+                           launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, nullptr, O.npart1.as<double>(), s));
+                    }
+                    KL(F_ODF, fa * (nv * 16 + 16) * n, fa * 48 * nv * n,
+                       launch_odots_df(Bd, V32, V32L, j + 1, w, O.part.as<double2>(), s));
+                    KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
+                } else {
+                    KL(F_OCGS, fa * (nv * 48 + 32) * n, fa * 12 * nv * n,
+                       launch_oupdate(B, V, j + 1, O.h1.as<double2>(), w, O.part.as<double2>(), O.npart1.as<double>(), s));
+                    KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, O.h2.as<double2>(), s));
+                }
+                if (r32)   // FP32 correction from the FP32 basis copy (guarded; FP64 fallback inside)
+                    KL(F_OREORTH, fa * (nv * 8 + 2 * 16) * n, fa * 8 * nv * n,
+                       launch_oupdate2(B, V, V32, j + 1, O.h2.as<double2>(), w, O.npart1.as<double>(), g1,
+                                       O.npart.as<double>(), 1, O.fallbacks.as<int>(), s));
+                else
+                    KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
+                       launch_oupdate(B, V, j + 1, O.h2.as<double2>(), w, nullptr, O.npart.as<double>(), s));
+                KL(F_OMISC, 0, 0,
+                   launch_ogivens(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(),
+                                  O.Wq.as<double2>(), j,
+                                  O.h1.as<double2>(), O.h2.as<double2>(), O.npart.as<double>(), O.fnorm.as<double>(),
+                                  prm->outer_tol, O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>(), hstride,
+                                  total, s));
+                KL(F_OMISC, 2.0 * fa * n * 16 + (r32 ? fa * n * 8.0 : 0.0) + (df ? fa * n * 8.0 : 0.0), 0,
+                   launch_oscale(B, V + (long long)(j + 1) * B.ld, r32 ? V32 + (long long)(j + 1) * B.ld32 : nullptr,
+                                 df ? V32L + (long long)(j + 1) * B.ld32 : nullptr,
+                                 O.D.as<double>() + (long long)(j + 1) * B.ld, w, O.hn.as<double>(), s));
             }
-            if (r32)   // FP32 correction from the FP32 basis copy (guarded; FP64 fallback inside)
-                KL(F_OREORTH, fa * (nv * 8 + 2 * 16) * n, fa * 8 * nv * n,
-                   launch_oupdate2(B, V, V32, j + 1, O.h2.as<double2>(), w, O.npart1.as<double>(), g1,
-                                   O.npart.as<double>(), 1, O.fallbacks.as<int>(), s));
-            else
-                KL(F_OCGS, fa * (nv * 24 + 32) * n, fa * 6 * nv * n,
-                   launch_oupdate(B, V, j + 1, O.h2.as<double2>(), w, nullptr, O.npart.as<double>(), s));
-            KL(F_OMISC, 0, 0,
-               launch_ogivens(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(),
-                              O.Wq.as<double2>(), j,
-                              O.h1.as<double2>(), O.h2.as<double2>(), O.npart.as<double>(), O.fnorm.as<double>(),
-                              prm->outer_tol, O.hn.as<double>(), O.flag.as<int>(), O.hist.as<double>(), hstride,
-                              total, s));
-            KL(F_OMISC, 2.0 * fa * n * 16 + (r32 ? fa * n * 8.0 : 0.0) + (df ? fa * n * 8.0 : 0.0), 0,
-               launch_oscale(B, V + (long long)(j + 1) * B.ld, r32 ? V32 + (long long)(j + 1) * B.ld32 : nullptr,
-                             df ? V32L + (long long)(j + 1) * B.ld32 : nullptr,
-                             O.D.as<double>() + (long long)(j + 1) * B.ld, w, O.hn.as<double>(), s));
             CKL();
             total++;
             std::vector<int> flags(nr);
+            int berr = 0;
             CK(cudaMemcpyAsync(flags.data(), O.flag.p, nr * sizeof(int), cudaMemcpyDeviceToHost, s));
+            if (dc) CK(cudaMemcpyAsync(&berr, O.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             ctx->prof.harvest();
+            if (berr) FAIL(HDD_ERR_NONFINITE, "outer orthogonalisation: a pending basis vector lost half its norm");
             bool changed = false, more = false;
+            std::vector<int> closev(nr, 0);
             for (int r = 0; r < nr; r++) {
                 if (!act[r]) continue;
                 its[r]++;
                 kcols[r] = j + 1;
-                if (!flags[r]) { act[r] = 0; changed = true; } else more = true;
+                if (!flags[r]) { act[r] = 0; changed = true; closev[r] = 1; } else more = true;
             }
-            if (!more || total >= prm->outer_maxit) break;
+            const bool stop = !more || total >= prm->outer_maxit || j == R - 1;
+            if (dc) {   // the cycle ends for these RHS: commit the rotation of their tentative column j
+                bool anyc = false;
+                for (int r = 0; r < nr; r++) {
+                    if (stop && act[r]) closev[r] = 1;
+                    anyc = anyc || closev[r];
+                }
+                if (anyc) {
+                    CK(cudaMemcpyAsync(O.close.p, closev.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s));
+                    KL(F_OMISC, 0, 0, launch_dcgs_close(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(),
+                                                        O.g.as<double2>(), O.Wq.as<double2>(), j, O.close.as<int>(), s));
+                    CKL();
+                }
+            }
+            if (stop) break;
             if (changed && (st = push_active()) != HDD_OK) return st;
         }
         // x_r += Z_r y_r, y_r = H_r⁻¹ g_r, for every RHS that ran in this cycle
@@ -2028,6 +2096,7 @@ hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value) {
     else if (key == HDD_OPT_FUSED_INNER) ctx->fused_inner = value;
     else if (key == HDD_OPT_OUTER_DOTS_DF) ctx->outer_df = value;
     else if (key == HDD_OPT_OUTER_UPDATE_DF) ctx->outer_udf = value;
+    else if (key == HDD_OPT_OUTER_DCGS2) ctx->outer_dcgs = value;
     else FAIL(HDD_ERR_INVALID_ARG, "unknown option %d", key);
     return HDD_OK;
 }

@@ -299,6 +299,21 @@ void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, i
                      cudaStream_t s);
 // first CGS pass update in double-FP32 from the hi/lo FP32 basis; norm partials on its own grid
 int oupdate_df_grid(long long n);
+// delayed CGS2: fused dots of the pending vector and w, per-RHS coefficient kernels, fused update
+int oupdate_dcgs_grid(long long n);
+void launch_odots2_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const float2 *x1h,
+                      const float2 *x1l, const double2 *w, double2 *part1, double2 *part2, cudaStream_t s);
+void launch_dcgs_col(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,
+                     const double2 *P1, double2 *P2, const double *hn, double *invs, const double *fnorm,
+                     double *hist, int hstride, int it, int *err, cudaStream_t s);
+void launch_dcgs_tent(const OuterBatch &B, double2 *H, double2 *g, double2 *Wq, int j, const double *npart, int gp,
+                      const double *fnorm, double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
+                      cudaStream_t s);
+void launch_dcgs_close(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,
+                       const int *close, cudaStream_t s);
+void launch_oupdate_dcgs(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int j, int corr, double2 *Vj,
+                         double *Dj, float2 *Vjh, float2 *Vjl, const double2 *acoef, const double2 *bcoef,
+                         const double *invs, double2 *w, double *part_norm, cudaStream_t s);
 void launch_oupdate_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const double2 *h,
                        double2 *w, double *part_norm, cudaStream_t s);
 void launch_fill_test(long long n, unsigned long long seed, double2 *x, cudaStream_t s);

@@ -513,7 +513,8 @@ k_oupdate2(OuterBatch B, const double2 *__restrict__ V, const float2 *__restrict
 // per basis vector and element and runs on the FP32 pipe (≈ 48 instructions per vector and
 // element), where the FP64 update is bound by the FP64 pipe.  Thread q of the grid takes the
 // element pair (2q, 2q + 1) with 16-byte loads; an odd last pair reads the padding entry of
-// its RHS (n32 = n + (n & 1)) and drops it.
+// its RHS (n32 = n + (n & 1)) and drops it.  The CTA size (≤ OTU) is chosen so that the grid
+// fills whole waves of resident CTAs (oupdate_df_plan).
 constexpr int OTU = 256;
 __global__ void __launch_bounds__(OTU, 3)
 k_oupdate_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int nv,
@@ -523,13 +524,13 @@ k_oupdate_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restri
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     Vh += r * B.n32; Vl += r * B.n32; w += r * B.n; h += (long long)r * B.ldp;
-    for (int l = threadIdx.x; l < nv; l += OTU) {
+    for (int l = threadIdx.x; l < nv; l += blockDim.x) {
         const double2 v = h[l];
         const float rh = (float)v.x, ih = (float)v.y;
         hq[l] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
     }
     __syncthreads();
-    const long long p = (long long)blockIdx.x * OTU + threadIdx.x, i = 2 * p;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x, i = 2 * p;
     double nrm = 0.0;
     if (i < B.n) {
         const bool two = i + 1 < B.n;
@@ -537,25 +538,37 @@ k_oupdate_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restri
         const float4 *lp = reinterpret_cast<const float4 *>(Vl) + p;
         const long long ld4 = B.ld32 / 2;
         double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+        float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, bxh = 0.f, bxl = 0.f, byh = 0.f, byl = 0.f;
+        // v·h = (vr hr - vi hi) + i (vr hi + vi hr) for elements a = (x, y) and b = (z, w)
+        auto acc = [&](const float4 vh, const float4 vl, const float4 c) {
+            df_acc(axh, axl, vh.x, vl.x, c.x, c.y);
+            df_acc(axh, axl, -vh.y, -vl.y, c.z, c.w);
+            df_acc(ayh, ayl, vh.x, vl.x, c.z, c.w);
+            df_acc(ayh, ayl, vh.y, vl.y, c.x, c.y);
+            df_acc(bxh, bxl, vh.z, vl.z, c.x, c.y);
+            df_acc(bxh, bxl, -vh.w, -vl.w, c.z, c.w);
+            df_acc(byh, byl, vh.z, vl.z, c.z, c.w);
+            df_acc(byh, byl, vh.w, vl.w, c.x, c.y);
+        };
         for (int l0 = 0; l0 < nv; l0 += 32) {
             const int l1 = l0 + 32 < nv ? l0 + 32 : nv;
-            float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, bxh = 0.f, bxl = 0.f, byh = 0.f, byl = 0.f;
-#pragma unroll 4
-            for (int l = l0; l < l1; l++) {
-                const float4 vh = hp[(long long)l * ld4], vl = lp[(long long)l * ld4];
-                const float4 c = hq[l];
-                // v·h = (vr hr - vi hi) + i (vr hi + vi hr) for elements a = (x, y) and b = (z, w)
-                df_acc(axh, axl, vh.x, vl.x, c.x, c.y);
-                df_acc(axh, axl, -vh.y, -vl.y, c.z, c.w);
-                df_acc(ayh, ayl, vh.x, vl.x, c.z, c.w);
-                df_acc(ayh, ayl, vh.y, vl.y, c.x, c.y);
-                df_acc(bxh, bxl, vh.z, vl.z, c.x, c.y);
-                df_acc(bxh, bxl, -vh.w, -vl.w, c.z, c.w);
-                df_acc(byh, byl, vh.z, vl.z, c.z, c.w);
-                df_acc(byh, byl, vh.w, vl.w, c.x, c.y);
+            int l = l0;
+            // groups of four vectors: the eight 16-byte loads of a group are issued before its
+            // arithmetic (the pass is bound by bytes in flight)
+            for (; l + 4 <= l1; l += 4) {
+                float4 vh[4], vl[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    vh[u] = hp[(long long)(l + u) * ld4];
+                    vl[u] = lp[(long long)(l + u) * ld4];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) acc(vh[u], vl[u], hq[l + u]);
             }
+            for (; l < l1; l++) acc(hp[(long long)l * ld4], lp[(long long)l * ld4], hq[l]);
             ax += (double)axh + (double)axl; ay += (double)ayh + (double)ayl;
             bx += (double)bxh + (double)bxl; by += (double)byh + (double)byl;
+            axh = axl = ayh = ayl = bxh = bxl = byh = byl = 0.f;
         }
         double2 xa = w[i];
         xa.x -= ax; xa.y -= ay;
@@ -681,6 +694,371 @@ k_ogivens(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs, double
         Wq[l] = make_double2(-(sr.x * wl.x + sr.y * wl.y), -(sr.x * wl.y - sr.y * wl.x));
     }
     if (tid == 0) Wq[j + 1] = make_double2(c, 0.0);
+}
+
+// ------------------------------------------------------------------------------------------
+// Delayed CGS2 (the low-synchronisation classical Gram-Schmidt of Świrydowicz, Langou, Ananthan,
+// Yang & Thomas, Numer. Linear Algebra Appl. 2021, applied to the flexible Arnoldi process).  At
+// outer step j the basis slot j holds the pending vector ṽ_j = w'_{j-1}/ν_j: the previous step's
+// first-pass result, normalised but not yet reorthogonalised, and column j-1 of H holds that
+// step's first-pass coefficients with the tentative subdiagonal ν_j.  The preconditioner is
+// applied to ṽ_j (FGMRES allows any z_j: the Arnoldi relation A Z = V H only needs the final
+// orthonormal V), and one pass over the basis then forms both
+//   a = V_{<j}^H ṽ_j, d = ṽ_j^H ṽ_j     (the second pass of vector j, delayed by one step)
+//   b = V_{<j}^H w,   c = ṽ_j^H w       (the first pass of the new vector w = A z_j).
+// With σ = sqrt(d - |a|²) the final v_j = (ṽ_j - V_{<j} a)/σ, column j-1 becomes
+// h + ν_j a with subdiagonal ν_j σ, and v_j^H w = (c - a^H b)/σ; one more pass over the basis
+// writes v_j and w' = w - V_{<j} b - v_j (v_j^H w) together.  Two passes per step instead of
+// four; the stopping test runs on the tentative column j (its rotation is committed a step later,
+// or at once when the cycle ends, the column then keeping its first-pass coefficients).
+// ------------------------------------------------------------------------------------------
+
+// Warp q forms the partial dots of vectors l = q, q + 8, ... with the two staged vectors s1, s2
+// (double-FP32, as warp_dots_df; four element groups per pass, the next group's basis loads
+// issued before the current group's arithmetic).
+__device__ __forceinline__ void warp_dots2_df(const float2 *__restrict__ Vh, const float2 *__restrict__ Vl,
+                                              long long ld32, int nv, const float4 *__restrict__ s1,
+                                              const float4 *__restrict__ s2, long long b, int len,
+                                              double2 *__restrict__ part1, double2 *__restrict__ part2, int ldp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = warp; l < nv; l += OT / 32) {
+        const float2 *hp = Vh + (long long)l * ld32 + b, *lp = Vl + (long long)l * ld32 + b;
+        float ah[4][2], al[4][2], bh[4][2], bl[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int c = 0; c < 2; c++) ah[u][c] = al[u][c] = bh[u][c] = bl[u][c] = 0.f;
+        auto step = [&](int u, float2 h, float2 q, float4 x, float4 y) {
+            // conj(v)·x = (vr xr + vi xi) + i (vr xi - vi xr), the same for y
+            df_acc(ah[u][0], al[u][0], h.x, q.x, x.x, x.y);
+            df_acc(ah[u][1], al[u][1], h.x, q.x, x.z, x.w);
+            df_acc(ah[u][0], al[u][0], h.y, q.y, x.z, x.w);
+            df_acc(ah[u][1], al[u][1], -h.y, -q.y, x.x, x.y);
+            df_acc(bh[u][0], bl[u][0], h.x, q.x, y.x, y.y);
+            df_acc(bh[u][1], bl[u][1], h.x, q.x, y.z, y.w);
+            df_acc(bh[u][0], bl[u][0], h.y, q.y, y.z, y.w);
+            df_acc(bh[u][1], bl[u][1], -h.y, -q.y, y.x, y.y);
+        };
+        const int full = len & ~127;
+        float2 vh[4], vl[4];
+        int i = lane;
+        if (i < full) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) { vh[u] = hp[i + 32 * u]; vl[u] = lp[i + 32 * u]; }
+        }
+        for (; i < full; i += 128) {
+            float2 nh[4], nl[4];
+            const bool more = i + 128 < full;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                nh[u] = more ? hp[i + 128 + 32 * u] : make_float2(0.f, 0.f);
+                nl[u] = more ? lp[i + 128 + 32 * u] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) step(u, vh[u], vl[u], s1[i + 32 * u], s2[i + 32 * u]);
+#pragma unroll
+            for (int u = 0; u < 4; u++) { vh[u] = nh[u]; vl[u] = nl[u]; }
+        }
+        for (i = full + lane; i < len; i += 32) step(0, hp[i], lp[i], s1[i], s2[i]);
+#pragma unroll
+        for (int u = 1; u < 4; u++)
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                df_add(ah[0][c], al[0][c], ah[u][c], al[u][c]);
+                df_add(bh[0][c], bl[0][c], bh[u][c], bl[u][c]);
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const float x1 = __shfl_xor_sync(0xffffffffu, ah[0][c], o), x2 = __shfl_xor_sync(0xffffffffu, al[0][c], o);
+                const float y1 = __shfl_xor_sync(0xffffffffu, bh[0][c], o), y2 = __shfl_xor_sync(0xffffffffu, bl[0][c], o);
+                df_add(ah[0][c], al[0][c], x1, x2);
+                df_add(bh[0][c], bl[0][c], y1, y2);
+            }
+        }
+        if (lane == 0) {
+            part1[(long long)blockIdx.x * ldp + l] = make_double2((double)ah[0][0] + (double)al[0][0],
+                                                                  (double)ah[0][1] + (double)al[0][1]);
+            part2[(long long)blockIdx.x * ldp + l] = make_double2((double)bh[0][0] + (double)bl[0][0],
+                                                                  (double)bh[0][1] + (double)bl[0][1]);
+        }
+    }
+}
+
+// Partials part1[r][cta][l] = Σ conj(V_l) x1 and part2[r][cta][l] = Σ conj(V_l) w for l < nv
+// (x1: hi/lo copies of a basis slot; w: FP64).  Dynamic shared memory: 2 · chunk float4.
+__global__ void __launch_bounds__(OT, 2)
+k_odots2_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int nv,
+            const float2 *__restrict__ x1h, const float2 *__restrict__ x1l, const double2 *__restrict__ w,
+            double2 *__restrict__ part1, double2 *__restrict__ part2) {
+    extern __shared__ float4 st2[];
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    Vh += r * B.n32; Vl += r * B.n32; x1h += r * B.n32; x1l += r * B.n32; w += r * B.n;
+    part1 += (long long)r * B.G * B.ldp; part2 += (long long)r * B.G * B.ldp;
+    long long b, e;
+    chunk_of(B.n, b, e);
+    const int len = (int)(e > b ? e - b : 0);
+    float4 *s1 = st2, *s2 = st2 + len;
+    for (int i = threadIdx.x; i < len; i += OT) {
+        const float2 h = x1h[b + i], q = x1l[b + i];
+        s1[i] = make_float4(h.x, q.x, h.y, q.y);
+        const double2 x = w[b + i];
+        const float rh = (float)x.x, ih = (float)x.y;
+        s2[i] = make_float4(rh, (float)(x.x - (double)rh), ih, (float)(x.y - (double)ih));
+    }
+    __syncthreads();
+    warp_dots2_df(Vh, Vl, B.ld32, nv, s1, s2, b, len, part1, part2, B.ldp);
+}
+
+// Block reductions of the small per-RHS kernels (OG threads)
+__device__ __forceinline__ double og_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int q = 0; q < OG / 32; q++) s += red[q];
+    return s;
+}
+
+// Rotation j of one RHS from the unrotated column hc (rows 0..j) and its subdiagonal hn: the
+// rotated entry (Q_jᵀ h)_j = W_j · h, then cs, sn, g and W_{j+1} (commit) or only the residual
+// estimate |g_{j+1}| (commit == false).  Returns |g_{j+1}| to every thread.
+__device__ double givens_step(const double2 *__restrict__ hc, double hn, int j, double *cs, double2 *sn,
+                              double2 *g, double2 *Wq, bool commit, double *red) {
+    __shared__ double c_s, res_s;
+    __shared__ double2 s_s;
+    double dx = 0.0, dy = 0.0;
+    for (int l = threadIdx.x; l <= j; l += OG) {
+        const double2 hv = hc[l], wl = Wq[l];
+        dx = fma(wl.x, hv.x, fma(-wl.y, hv.y, dx));
+        dy = fma(wl.x, hv.y, fma(wl.y, hv.x, dy));
+    }
+    const double bx = og_sum(dx, red), by = og_sum(dy, red);
+    if (threadIdx.x == 0) {
+        double c; double2 sr, rr;
+        zgivens(make_double2(bx, by), make_double2(hn, 0.0), c, sr, rr);
+        const double2 gj = g[j];
+        const double2 g1 = make_double2(-(sr.x * gj.x + sr.y * gj.y), -(sr.x * gj.y - sr.y * gj.x));
+        res_s = hypot(g1.x, g1.y);
+        c_s = c; s_s = sr;
+        if (commit) {
+            cs[j] = c; sn[j] = sr;
+            g[j + 1] = g1;
+            g[j] = make_double2(c * gj.x, c * gj.y);
+        }
+    }
+    __syncthreads();
+    const double res = res_s;
+    if (commit) {
+        const double c = c_s;
+        const double2 sr = s_s;
+        for (int l = threadIdx.x; l <= j; l += OG) {             // W_{j+1} = [-conj(s_j) W_j, c_j]
+            const double2 wl = Wq[l];
+            Wq[l] = make_double2(-(sr.x * wl.x + sr.y * wl.y), -(sr.x * wl.y - sr.y * wl.x));
+        }
+        if (threadIdx.x == 0) Wq[j + 1] = make_double2(c, 0.0);
+        __syncthreads();
+    }
+    return res;
+}
+
+// Delayed CGS2 coefficients of step j for every active RHS (one CTA each).  P1 = V^H ṽ_j and
+// P2 = V^H w over slots 0..j (reduced).  For j >= 1: column j-1 is completed (h += ν_j a,
+// subdiagonal ν_j σ) and its rotation committed (hist[it-1], the final residual estimate after
+// column j-1); invs = 1/σ; P2[j] becomes v_j^H w.  Then P2[0..j] is the first-pass column j,
+// stored in H.  err[0] is set if σ² <= d/4 (the pending vector lost more than half of its norm
+// to the basis, or is not finite): the delayed form then does not hold.
+__global__ void __launch_bounds__(OG)
+k_dcgs_col(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs, double2 *__restrict__ sn,
+           double2 *__restrict__ g, double2 *__restrict__ Wq, int j, const double2 *__restrict__ P1,
+           double2 *__restrict__ P2, const double *__restrict__ hn, double *__restrict__ invs,
+           const double *__restrict__ fnorm, double *__restrict__ hist, int hstride, int it, int *__restrict__ err) {
+    __shared__ double red[OG / 32];
+    __shared__ double2 hj_s;
+    const int r = blockIdx.x;
+    if (B.active && !B.active[r]) return;
+    const int R = B.R;
+    H += (long long)r * (R + 1) * R; cs += (long long)r * R; sn += (long long)r * R;
+    g += (long long)r * (R + 1); Wq += (long long)r * (R + 1);
+    P1 += (long long)r * B.ldp; P2 += (long long)r * B.ldp;
+    double2 *hcol = H + (long long)j * (R + 1);
+    if (j >= 1) {
+        double q2 = 0.0, abx = 0.0, aby = 0.0;
+        for (int l = threadIdx.x; l < j; l += OG) {
+            const double2 a = P1[l], bb = P2[l];
+            q2 = fma(a.x, a.x, fma(a.y, a.y, q2));
+            abx = fma(a.x, bb.x, fma(a.y, bb.y, abx));          // conj(a)·b
+            aby = fma(a.x, bb.y, fma(-a.y, bb.x, aby));
+        }
+        const double aa = og_sum(q2, red), sx = og_sum(abx, red), sy = og_sum(aby, red);
+        const double d = P1[j].x, s2 = d - aa;
+        const bool ok = s2 > 0.25 * d && isfinite(s2);
+        const double sig = ok ? sqrt(s2) : 1.0;
+        const double nu = hn[r];
+        double2 *hp = H + (long long)(j - 1) * (R + 1);
+        for (int l = threadIdx.x; l < j; l += OG) {
+            const double2 a = P1[l];
+            hp[l] = make_double2(fma(nu, a.x, hp[l].x), fma(nu, a.y, hp[l].y));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            hp[j] = make_double2(nu * sig, 0.0);
+            const double2 c = P2[j];
+            hj_s = make_double2((c.x - sx) / sig, (c.y - sy) / sig);
+            invs[r] = 1.0 / sig;
+            if (!ok) atomicExch(err, 1);
+        }
+        __syncthreads();
+        const double res = givens_step(hp, nu * sig, j - 1, cs, sn, g, Wq, true, red);
+        if (threadIdx.x == 0) {
+            hist[(long long)r * hstride + it - 1] = res / fnorm[r];
+            P2[j] = hj_s;
+        }
+        __syncthreads();
+    }
+    for (int l = threadIdx.x; l <= j; l += OG) hcol[l] = P2[l];
+}
+
+// Tentative stopping test of step j: ν_{j+1} = ||w'|| (gp partials per RHS) as the subdiagonal
+// of the first-pass column j, the residual estimate |g_{j+1}| that rotation j would give
+// (nothing committed); flag[r] = 1 while it exceeds tol·||f_r|| and ν_{j+1} > 0.
+__global__ void __launch_bounds__(OG)
+k_dcgs_tent(OuterBatch B, double2 *__restrict__ H, double2 *__restrict__ g, double2 *__restrict__ Wq, int j,
+            const double *__restrict__ npart, int gp, const double *__restrict__ fnorm, double tol,
+            double *__restrict__ hn_out, int *__restrict__ flag, double *__restrict__ hist, int hstride, int it) {
+    __shared__ double red[OG / 32];
+    const int r = blockIdx.x;
+    if (B.active && !B.active[r]) return;
+    const int R = B.R;
+    H += (long long)r * (R + 1) * R; g += (long long)r * (R + 1); Wq += (long long)r * (R + 1);
+    npart += (long long)r * gp;
+    double s = 0.0;
+    for (int q = threadIdx.x; q < gp; q += OG) s += npart[q];
+    const double nu = sqrt(og_sum(s, red));
+    double2 *hcol = H + (long long)j * (R + 1);
+    const double res = givens_step(hcol, nu, j, nullptr, nullptr, g, Wq, false, red);
+    if (threadIdx.x == 0) {
+        hcol[j + 1] = make_double2(nu, 0.0);
+        hn_out[r] = nu;
+        hist[(long long)r * hstride + it] = res / fnorm[r];
+        flag[r] = (res > tol * fnorm[r] && nu > 0.0) ? 1 : 0;
+    }
+}
+
+// End of a cycle for the RHS with close[r] = 1: rotation j of the first-pass column j (its
+// subdiagonal ν_{j+1} in H) committed; the column keeps its first-pass coefficients.
+__global__ void __launch_bounds__(OG)
+k_dcgs_close(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs, double2 *__restrict__ sn,
+             double2 *__restrict__ g, double2 *__restrict__ Wq, int j, const int *__restrict__ close) {
+    __shared__ double red[OG / 32];
+    const int r = blockIdx.x;
+    if (!close[r]) return;
+    const int R = B.R;
+    H += (long long)r * (R + 1) * R; cs += (long long)r * R; sn += (long long)r * R;
+    g += (long long)r * (R + 1); Wq += (long long)r * (R + 1);
+    const double2 *hcol = H + (long long)j * (R + 1);
+    givens_step(hcol, hcol[j + 1].x, j, cs, sn, g, Wq, true, red);
+}
+
+// Delayed CGS2 update of step j, one element pair per thread (as k_oupdate_df):
+//   v_j = (ṽ_j - Σ_{l<j} V_l a_l)·invs   (corr = 1; slot j rewritten in FP64, Re - Im and hi/lo)
+//   w'  = w - Σ_{l<j} V_l b_l - v_j b_j   (b_j = v_j^H w)
+// The sums run over the hi/lo copies of slots 0..j-1: Σ V_l b_l in double-FP32 widened to FP64
+// every 32 vectors (as k_oupdate_df); Σ V_l a_l in FP32 from the high parts (the coefficients a
+// are rounding-error sized, so its error is far below the FP64 rounding of ṽ_j), widened every 32
+// vectors.  corr = 0 (step 0): v_0 is final and only read.  Then the partial ||w'||².
+// Dynamic shared memory: j · (float4 + float2).
+__global__ void __launch_bounds__(OTU, 2)
+k_oupdate_dcgs(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int j, int corr,
+               double2 *__restrict__ Vj, double *__restrict__ Dj, float2 *__restrict__ Vjh, float2 *__restrict__ Vjl,
+               const double2 *__restrict__ acoef, const double2 *__restrict__ bcoef, const double *__restrict__ invs,
+               double2 *__restrict__ w, double *__restrict__ part_norm) {
+    extern __shared__ float4 dq[];
+    float4 *bq = dq;                                      // (Re hi, Re lo, Im hi, Im lo) of b_l
+    float2 *aq = reinterpret_cast<float2 *>(dq + j);      // a_l in FP32
+    __shared__ double red[OTU / 32];
+    const int r = blockIdx.y;
+    if (B.active && !B.active[r]) return;
+    Vh += r * B.n32; Vl += r * B.n32; w += r * B.n; Vj += r * B.n; Dj += r * B.n;
+    Vjh += r * B.n32; Vjl += r * B.n32;
+    acoef += (long long)r * B.ldp; bcoef += (long long)r * B.ldp;
+    for (int l = threadIdx.x; l < j; l += blockDim.x) {
+        const double2 v = bcoef[l];
+        const float rh = (float)v.x, ih = (float)v.y;
+        bq[l] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+        aq[l] = corr ? make_float2((float)acoef[l].x, (float)acoef[l].y) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const double2 hj = bcoef[j];
+    const double is = corr ? invs[r] : 1.0;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x, i = 2 * p;
+    double nrm = 0.0;
+    if (i < B.n) {
+        const bool two = i + 1 < B.n;
+        const float4 *hp = reinterpret_cast<const float4 *>(Vh) + p;
+        const float4 *lp = reinterpret_cast<const float4 *>(Vl) + p;
+        const long long ld4 = B.ld32 / 2;
+        double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;        // Σ V b (elements a, b of the pair)
+        double cx = 0.0, cy = 0.0, ex = 0.0, ey = 0.0;        // Σ V a
+        float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, bxh = 0.f, bxl = 0.f, byh = 0.f, byl = 0.f;
+        float cxf = 0.f, cyf = 0.f, exf = 0.f, eyf = 0.f;
+        auto acc = [&](const float4 vh, const float4 vl, const float4 c, const float2 a) {
+            df_acc(axh, axl, vh.x, vl.x, c.x, c.y);
+            df_acc(axh, axl, -vh.y, -vl.y, c.z, c.w);
+            df_acc(ayh, ayl, vh.x, vl.x, c.z, c.w);
+            df_acc(ayh, ayl, vh.y, vl.y, c.x, c.y);
+            df_acc(bxh, bxl, vh.z, vl.z, c.x, c.y);
+            df_acc(bxh, bxl, -vh.w, -vl.w, c.z, c.w);
+            df_acc(byh, byl, vh.z, vl.z, c.z, c.w);
+            df_acc(byh, byl, vh.w, vl.w, c.x, c.y);
+            cxf = fmaf(vh.x, a.x, fmaf(-vh.y, a.y, cxf));
+            cyf = fmaf(vh.x, a.y, fmaf(vh.y, a.x, cyf));
+            exf = fmaf(vh.z, a.x, fmaf(-vh.w, a.y, exf));
+            eyf = fmaf(vh.z, a.y, fmaf(vh.w, a.x, eyf));
+        };
+        for (int l0 = 0; l0 < j; l0 += 32) {
+            const int l1 = l0 + 32 < j ? l0 + 32 : j;
+            int l = l0;
+            for (; l + 4 <= l1; l += 4) {
+                float4 vh[4], vl[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    vh[u] = hp[(long long)(l + u) * ld4];
+                    vl[u] = lp[(long long)(l + u) * ld4];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) acc(vh[u], vl[u], bq[l + u], aq[l + u]);
+            }
+            for (; l < l1; l++) acc(hp[(long long)l * ld4], lp[(long long)l * ld4], bq[l], aq[l]);
+            ax += (double)axh + (double)axl; ay += (double)ayh + (double)ayl;
+            bx += (double)bxh + (double)bxl; by += (double)byh + (double)byl;
+            cx += (double)cxf; cy += (double)cyf; ex += (double)exf; ey += (double)eyf;
+            axh = axl = ayh = ayl = bxh = bxl = byh = byl = 0.f;
+            cxf = cyf = exf = eyf = 0.f;
+        }
+        auto finish = [&](long long k, double sbx, double sby, double sax, double say) {
+            double2 v = Vj[k];
+            if (corr) {
+                v = make_double2((v.x - sax) * is, (v.y - say) * is);
+                Vj[k] = v;
+                Dj[k] = v.x - v.y;
+                const float2 hi = make_float2((float)v.x, (float)v.y);
+                Vjh[k] = hi;
+                Vjl[k] = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+            }
+            double2 x = w[k];
+            x.x -= sbx + (v.x * hj.x - v.y * hj.y);
+            x.y -= sby + (v.x * hj.y + v.y * hj.x);
+            w[k] = x;
+            return fma(x.x, x.x, x.y * x.y);
+        };
+        nrm = finish(i, ax, ay, cx, cy);
+        if (two) nrm += finish(i + 1, bx, by, ex, ey);
+    }
+    block_sum_store(nrm, red, part_norm + (long long)r * gridDim.x + blockIdx.x);
 }
 
 // End of a cycle: the triangular factor of every RHS's Hessenberg matrix, column k < kcols[r]
@@ -851,11 +1229,77 @@ void launch_oupdate(const OuterBatch &B, const double2 *V, int nv, const double2
                     double2 *part_dots, double *part_norm, cudaStream_t s) {
     k_oupdate<<<dim3(B.G, B.nrhs), OT, (size_t)nv * 3 * sizeof(double), s>>>(B, V, nv, h, w, part_dots, part_norm);
 }
-int oupdate_df_grid(long long n) { return (int)(((n + 1) / 2 + OTU - 1) / OTU); }
+// CTA size and grid of a one-element-pair-per-thread update kernel for vectors of n entries: of
+// the sizes 256, 224, ..., 128 threads the one whose grid leaves the least idle in the last wave
+// of resident CTAs (occupancy from the compiled register count), the largest on ties.
+struct PairPlan { long long n = -1; int threads = OTU, grid = 1; };
+template <typename K>
+static void pair_plan(K kern, PairPlan &c, long long n, int &threads, int &grid) {
+    if (n != c.n) {
+        const long long P = (n + 1) / 2;
+        int dev = 0, nsm = 152;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 152;
+        double best = -1.0;
+        c.threads = OTU;
+        c.grid = (int)((P + OTU - 1) / OTU);
+        for (int t = OTU; t >= 128; t -= 32) {
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, t, 32 * 1024) != cudaSuccess || occ < 1)
+                continue;
+            const long long R = (long long)occ * nsm, g = (P + t - 1) / t, waves = (g + R - 1) / R;
+            const double eff = (double)P / ((double)waves * (double)R * t);
+            if (eff > best + 1e-9) { best = eff; c.threads = t; c.grid = (int)(g > 0 ? g : 1); }
+        }
+        c.n = n;
+    }
+    threads = c.threads;
+    grid = c.grid;
+}
+static PairPlan plan_udf, plan_dcgs;
+int oupdate_df_grid(long long n) {
+    int t = 0, g = 0;
+    pair_plan(k_oupdate_df, plan_udf, n, t, g);
+    return g;
+}
+int oupdate_dcgs_grid(long long n) {
+    int t = 0, g = 0;
+    pair_plan(k_oupdate_dcgs, plan_dcgs, n, t, g);
+    return g;
+}
 void launch_oupdate_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const double2 *h,
                        double2 *w, double *part_norm, cudaStream_t s) {
-    k_oupdate_df<<<dim3(oupdate_df_grid(B.n), B.nrhs), OTU, (size_t)nv * sizeof(float4), s>>>(B, Vh, Vl, nv, h, w,
-                                                                                          part_norm);
+    int t = 0, g = 0;
+    pair_plan(k_oupdate_df, plan_udf, B.n, t, g);
+    k_oupdate_df<<<dim3(g, B.nrhs), t, (size_t)nv * sizeof(float4), s>>>(B, Vh, Vl, nv, h, w, part_norm);
+}
+void launch_odots2_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const float2 *x1h,
+                      const float2 *x1l, const double2 *w, double2 *part1, double2 *part2, cudaStream_t s) {
+    const long long chunk = (B.n + B.G - 1) / B.G;
+    k_odots2_df<<<dim3(B.G, B.nrhs), OT, (size_t)(2 * chunk) * sizeof(float4), s>>>(B, Vh, Vl, nv, x1h, x1l, w,
+                                                                                    part1, part2);
+}
+void launch_dcgs_col(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,
+                     const double2 *P1, double2 *P2, const double *hn, double *invs, const double *fnorm,
+                     double *hist, int hstride, int it, int *err, cudaStream_t s) {
+    k_dcgs_col<<<B.nrhs, OG, 0, s>>>(B, H, cs, sn, g, Wq, j, P1, P2, hn, invs, fnorm, hist, hstride, it, err);
+}
+void launch_dcgs_tent(const OuterBatch &B, double2 *H, double2 *g, double2 *Wq, int j, const double *npart, int gp,
+                      const double *fnorm, double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
+                      cudaStream_t s) {
+    k_dcgs_tent<<<B.nrhs, OG, 0, s>>>(B, H, g, Wq, j, npart, gp, fnorm, tol, hn_out, flag, hist, hstride, it);
+}
+void launch_dcgs_close(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,
+                       const int *close, cudaStream_t s) {
+    k_dcgs_close<<<B.nrhs, OG, 0, s>>>(B, H, cs, sn, g, Wq, j, close);
+}
+void launch_oupdate_dcgs(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int j, int corr, double2 *Vj,
+                         double *Dj, float2 *Vjh, float2 *Vjl, const double2 *acoef, const double2 *bcoef,
+                         const double *invs, double2 *w, double *part_norm, cudaStream_t s) {
+    int t = 0, g = 0;
+    pair_plan(k_oupdate_dcgs, plan_dcgs, B.n, t, g);
+    k_oupdate_dcgs<<<dim3(g, B.nrhs), t, (size_t)j * (sizeof(float4) + sizeof(float2)), s>>>(
+        B, Vh, Vl, j, corr, Vj, Dj, Vjh, Vjl, acoef, bcoef, invs, w, part_norm);
 }
 void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
                      double2 *w, const double *npart1, int g1, double *part_norm, int allow32, int *fallbacks,
@@ -901,6 +1345,7 @@ cudaError_t set_outer_smem_limits(size_t bytes) {
     if ((e = cudaFuncSetAttribute(k_oupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_oupdate2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_oupdate_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_oupdate_dcgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_otrisolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_oaxpy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
     return cudaSuccess;
