@@ -278,7 +278,8 @@ hdd_status hdd_autotune(hdd_ctx *ctx, const hdd_solve_params *prm, void *stream,
 /*   op 5: out = R_j in        (global → fine; `in` is a global vector)                      */
 /*   op 6: out = A_j⁻¹ in      (fine → fine, direct solve; needs hdd_setup_exact)            */
 /* prec: 64 runs the fine arithmetic of ops 0, 1, 2, 4 in complex64 (inputs rounded to FP32, */
-/* outputs widened back), 128 in complex128. */
+/* outputs widened back) and the banded solves of ops 3 and 6 in double-FP32 arithmetic (the  */
+/* form the complex64 inner iteration uses, HDD_OPT_COARSE_DF); 128: complex128 / FP64. */
 hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void *out_dev,
                         void *stream);
 
@@ -372,7 +373,10 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 /* pass of basis vector j runs fused with the first pass of step j+1, so a step makes two passes */
 /* over the basis instead of four (1, the default), or the plain CGS2 above (0); both compute   */
 /* the same FGMRES iteration up to rounding.  outer_reorth32 = 0 runs every outer step in FP64 */
-/* (plain CGS2) whatever these say.                                                            */
+/* (plain CGS2) whatever these say.  HDD_OPT_COARSE_DF (6): the coarse solves E_j⁻¹ of the    */
+/* complex64 inner iteration run in double-FP32 arithmetic on the FP32 pipe (1, the default:    */
+/* operators as (hi, lo) FP32 pairs, 2^-48 relative, forward error about κ(E_j)·2^-48) or in   */
+/* FP64 (0).  Complex128 inner solves and the direct local solve always use FP64.              */
 /* HDD_ERR_INVALID_ARG for an unknown key or a value other than 0 or 1.  Takes effect from the  */
 /* next call that solves.                                                                       */
 #define HDD_OPT_COARSE_LOOKAHEAD 1
@@ -380,6 +384,7 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 #define HDD_OPT_OUTER_DOTS_DF 3
 #define HDD_OPT_OUTER_UPDATE_DF 4
 #define HDD_OPT_OUTER_DCGS2 5
+#define HDD_OPT_COARSE_DF 6
 hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value);
 
 /* ---------------------------------------------------------------------------------------- */

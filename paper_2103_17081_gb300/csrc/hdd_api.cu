@@ -38,13 +38,13 @@ struct SubBox {
 };
 
 struct FactorSet {            // banded FP64 factors of one matrix per shape, blocked solve form
-    DevMem M, P, Meta, table;
+    DevMem M, Mdf, P, Meta, table;  // Mdf: the operators M as (hi, lo) FP32 pairs (double-FP32 solve)
     std::vector<BlockFactor> h;
     std::vector<double> fma_col;    // FP64 FMAs of one real column by banded substitution, per shape
     BlockSolveCfg cfg;              // shared-memory plan of the blocked solve
     bool re2 = false;               // factors of real-equivalent systems (complex matrices)
     bool ready = false;
-    void clear() { M.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); cfg = BlockSolveCfg{}; re2 = false; ready = false; }
+    void clear() { M.release(); Mdf.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); cfg = BlockSolveCfg{}; re2 = false; ready = false; }
 };
 
 template <typename R> struct InnerWork {   // inner GMRES buffers for one precision
@@ -58,13 +58,13 @@ template <typename R> struct InnerWork {   // inner GMRES buffers for one precis
 // Kernel families timed by the profiler (CUDA events around every launch on the launching
 // stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
 enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, F_STEP, F_ODF,
-           F_CGRID, F_OUDF, NFAM };
+           F_CGRID, F_OUDF, F_CDF, NFAM };
 const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
                               "local_cgs2_update", "local_givens_normalize", "local_misc",
                               "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn",
                               "outer_reorth_fp32", "local_arnoldi_step", "outer_dots_df32",
-                              "two_level_grid_coarse", "outer_update_df32"};
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 0, 0, 0};
+                              "two_level_grid_coarse", "outer_update_df32", "coarse_solve_df32"};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 0, 0, 0, 2};
 
 struct Prof {
     bool on = false;
@@ -167,6 +167,7 @@ struct hdd_ctx {
     int outer_df = 1;                          // HDD_OPT_OUTER_DOTS_DF
     int outer_udf = 1;                         // HDD_OPT_OUTER_UPDATE_DF
     int outer_dcgs = 1;                        // HDD_OPT_OUTER_DCGS2
+    int coarse_df = 1;                         // HDD_OPT_COARSE_DF
     int step_C[2] = {-1, -1};                  // fused-step cluster size per inner precision (0: off, -1: unplanned)
     size_t step_smem[2] = {0, 0};
     bool poisoned = false;                     // a device wait gave up with work in flight
@@ -372,6 +373,9 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
                                F.Meta.as<int4>() + F.h[q].meta_off, F.M.as<double>(), s);
         CKL();
     }
+    CK(F.Mdf.ensure((size_t)std::max(mo, 1LL) * sizeof(float2)));
+    launch_ops_to_df(mo, F.M.as<double>(), F.Mdf.as<float2>(), s);
+    CKL();
     CK(F.table.ensure(ns * sizeof(BlockFactor)));
     CK(cudaMemcpyAsync(F.table.p, F.h.data(), ns * sizeof(BlockFactor), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -384,34 +388,39 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
     return HDD_OK;
 }
 
-// FP64 banded solve of every flagged task; `nact` tasks are expected to be flagged (profiling).
+// Banded solve of every flagged task (FP64; with df, in double-FP32 arithmetic on the FP32 pipe
+// where the look-ahead kernel serves); `nact` tasks are expected to be flagged (profiling).
 void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *out, bool fine,
-                const int *flag, cudaStream_t s, int nact = -1) {
+                const int *flag, cudaStream_t s, int nact = -1, bool df = false) {
     const int nt = (int)ctx->h_tasks.size();
     double fl = 0;
     for (int q = 0; q < nt; q++) fl += F.fma_col[ctx->h_tasks[q].shape];
     // 2 flops per FMA, over 2 real columns (or the one column of a real-equivalent factor)
     fl = (F.re2 ? 2.0 : 4.0) * fl * (nact < 0 ? 1.0 : (double)nact / nt);
-    Launch L(ctx, F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
     BlockSolveCfg cfg = F.cfg;
     cfg.lookahead = ctx->coarse_la;
+    df = df && cfg.lookahead && cfg.la_ring >= 3;
+    Launch L(ctx, df ? F_CDF : F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
     launch_block_solve(ctx->d_tasks.as<Task>(), nt, F.table.as<BlockFactor>(), F.M.as<double>(),
-                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, cfg, F.re2 ? 1 : 0, s);
+                       F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, cfg, F.re2 ? 1 : 0, s,
+                       df ? F.Mdf.as<float2>() : nullptr);
 }
 
 // Two coarse solves per flagged task in one launch: in[0, ldc) and in[ldc, 2·ldc) into the same
 // halves of out (the doubled task table); `flag` (if not null) must cover 2·ntasks entries.
 void band_solve2(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *out, const int *flag,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool df = false) {
     const int nt = (int)ctx->h_tasks.size();
     double fl = 0;
     for (int q = 0; q < nt; q++) fl += F.fma_col[ctx->h_tasks[q].shape];
     fl = 2.0 * (F.re2 ? 2.0 : 4.0) * fl;
-    Launch L(ctx, F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
     BlockSolveCfg cfg = F.cfg;
     cfg.lookahead = ctx->coarse_la;
+    df = df && cfg.lookahead && cfg.la_ring >= 3;
+    Launch L(ctx, df ? F_CDF : F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
     launch_block_solve(ctx->d_tasks2.as<Task>(), 2 * nt, F.table.as<BlockFactor>(), F.M.as<double>(),
-                       F.P.as<int>(), F.Meta.as<int4>(), in, out, 0, flag, cfg, F.re2 ? 1 : 0, s);
+                       F.P.as<int>(), F.Meta.as<int4>(), in, out, 0, flag, cfg, F.re2 ? 1 : 0, s,
+                       df ? F.Mdf.as<float2>() : nullptr);
 }
 
 // ---- learned warm start ---------------------------------------------------------------------
@@ -700,6 +709,8 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
     const int *ones = ctx->d_ones.as<int>();
     const R tol = (R)prm->inner_tol;
     const int maxit = prm->inner_maxit;
+    // the complex64 inner iteration takes its coarse solves in double-FP32 (HDD_OPT_COARSE_DF)
+    const bool cdf = sizeof(R) == 4 && ctx->coarse_df;
 
     const int *all = mask ? mask : ones;
     KL(F_LMISC, ld * (16 + cs), 0, launch_restrict<R>(a, v, ctx->nglob, f, mask, s));
@@ -713,7 +724,7 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
         CK(cudaMemsetAsync(u, 0, ld * sizeof(c2<R>), s));
         // first cycle from ũ = 0: r0 = P f̃ = f̃ - A Z E⁻¹ Zᵀ f̃, and ref = ||P f̃||
         KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, y, 0, mask, s));
-        band_solve(ctx, ctx->E, y, sc, false, mask, s);
+        band_solve(ctx, ctx->E, y, sc, false, mask, s, -1, cdf);
         KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, sc, V, nullptr, 0, p3, mask, s));
     } else {
         // learned initial guess ũ₀ = σ·CNN(f̃/σ) (tensor-core inference); ref = ||P f̃|| and
@@ -735,7 +746,7 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
         KL(F_LMISC, 3 * ld * cs, 0, launch_local_A<R>(a, u, t, f, mask, s));
         KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, f, yy, 0, mask, s));
         KL(F_ZT, ld * cs + ldc * 16, 0, launch_zt<R>(a, t, yy + ldc, 0, mask, s));
-        band_solve2(ctx, ctx->E, yy, ss, m2, s);
+        band_solve2(ctx, ctx->E, yy, ss, m2, s, cdf);
         CK(cudaMemcpyAsync(sc, ss + ldc, ldc * sizeof(double2), cudaMemcpyDeviceToDevice, s));
         KL(F_PS, 2 * ld * cs + ldc * 16, 0, launch_prolong_stencil<R>(a, 1, f, ss, x, nullptr, 0, p3, mask, s));
         KL(F_LMISC, 0, 0, launch_set_ref<R>(a, S, p3, mask, s));
@@ -762,7 +773,7 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
             const double fa = (double)nact / nt;            // fraction of tasks still iterating
             double2 *si = sc + (long long)(i + 1) * ldc;  // E⁻¹ Zᵀ A v_i, kept for the completion
             if (stepC > 0) {
-                band_solve(ctx, ctx->E, y, si, false, ain, s, nact);
+                band_solve(ctx, ctx->E, y, si, false, ain, s, nact, cdf);
                 CK(cudaMemsetAsync(aout, 0, nt * sizeof(int), s));
                 CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
                 // algorithmic bytes of the fused schedule: 3 passes over V_0..V_i, v_i, v_{i+1}
@@ -771,7 +782,7 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
                    CK(launch_arnoldi_step<R>(a, stepC, i, RST, V, si, y, S, ain, aout, cnt, tol, maxit, step_sm, s)));
             } else {
                 KL(F_ZT, fa * (ld * cs + ldc * 16), 0, launch_zt<R>(a, vi, y, 1, ain, s));
-                band_solve(ctx, ctx->E, y, si, false, ain, s, nact);
+                band_solve(ctx, ctx->E, y, si, false, ain, s, nact, cdf);
                 KL(F_PS, fa * ((i + 3) * ld * cs + ldc * 16), fa * 8.0 * (i + 1) * ld,
                    launch_prolong_stencil<R>(a, 0, vi, si, vn, V, i + 1, p1, ain, s));
                 KL(F_CGS, fa * (i + 3) * ld * cs, fa * 16.0 * (i + 1) * ld,
@@ -800,7 +811,7 @@ hdd_status inner_ras(hdd_ctx *ctx, const double2 *v, double2 *z, const hdd_solve
         // restart: r = P(f̃ - A ũ) → v0
         KL(F_LMISC, 0, 0, launch_local_A<R>(a, u, t, f, rs, s));
         KL(F_ZT, 0, 0, launch_zt<R>(a, t, y, 0, rs, s));
-        band_solve(ctx, ctx->E, y, sc, false, rs, s, nrs);
+        band_solve(ctx, ctx->E, y, sc, false, rs, s, nrs, cdf);
         KL(F_PS, 0, 0, launch_prolong_stencil<R>(a, 1, t, sc, V, nullptr, 0, p3, rs, s));
         CK(cudaMemsetAsync(act[cur], 0, nt * sizeof(int), s));
         CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
@@ -2097,6 +2108,7 @@ hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value) {
     else if (key == HDD_OPT_OUTER_DOTS_DF) ctx->outer_df = value;
     else if (key == HDD_OPT_OUTER_UPDATE_DF) ctx->outer_udf = value;
     else if (key == HDD_OPT_OUTER_DCGS2) ctx->outer_dcgs = value;
+    else if (key == HDD_OPT_COARSE_DF) ctx->coarse_df = value;
     else FAIL(HDD_ERR_INVALID_ARG, "unknown option %d", key);
     return HDD_OK;
 }
@@ -2147,8 +2159,14 @@ hdd_status hdd_local_op(hdd_ctx *ctx, int op, int prec, const void *in_dev, void
     const long long ld = ctx->ld, ldc = ctx->ldc;
     const double2 *in = (const double2 *)in_dev;
     double2 *out = (double2 *)out_dev;
-    if (op == 3) { band_solve(ctx, ctx->E, in, out, false, nullptr, s); CKL(); CK(cudaStreamSynchronize(s)); return HDD_OK; }
-    if (op == 6) { band_solve(ctx, ctx->Aex, in, out, true, nullptr, s); CKL(); CK(cudaStreamSynchronize(s)); return HDD_OK; }
+    if (op == 3) {
+        band_solve(ctx, ctx->E, in, out, false, nullptr, s, -1, prec == 64);
+        CKL(); CK(cudaStreamSynchronize(s)); return HDD_OK;
+    }
+    if (op == 6) {
+        band_solve(ctx, ctx->Aex, in, out, true, nullptr, s, -1, prec == 64);
+        CKL(); CK(cudaStreamSynchronize(s)); return HDD_OK;
+    }
     auto run = [&](auto tag) -> hdd_status {
         using R = decltype(tag);
         LocalArgs<R> a = local_args<R>(ctx);

@@ -18,6 +18,40 @@ namespace hdd {
 // ------------------------------------------------------------------------------------------
 // complex helpers (storage as float2 / double2)
 // ------------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------------
+// double-FP32 ("df") arithmetic on the FP32 pipe: a value is an unevaluated pair (hi, lo) of
+// FP32 numbers.  df_acc adds the product (xh + xl)(yh + yl) to the accumulator (sh, sl): the
+// product of the high parts exactly (p + e, e = fma(xh, yh, -p)), the two cross terms, and a
+// Knuth two-sum of p into sh (the compensated dot product of Ogita, Rump & Oishi, SIAM J. Sci.
+// Comput. 2005, on split inputs).  The _rn intrinsics keep the compiler from contracting the
+// error-free steps into fused multiply-adds.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void df_acc(float &sh, float &sl, float xh, float xl, float yh, float yl) {
+    const float p = __fmul_rn(xh, yh);
+    const float e = fmaf(xh, yh, -p);                 // exact: xh·yh = p + e
+    const float c = fmaf(xh, yl, fmaf(xl, yh, e));
+    const float t = __fadd_rn(sh, p);                 // two-sum: sh + p = t + err exactly
+    const float bb = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, c));
+}
+
+// (sh, sl) += (bh, bl): two-sum of the high parts, the low parts added
+__device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl) {
+    const float t = __fadd_rn(sh, bh);
+    const float bb = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(bh, bb));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, bl));
+}
+
+// the FP64 value x as a pair (hi, lo) with hi + lo = x to about 2^-48 relative
+__device__ __forceinline__ float2 df_split(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
 template <typename R> struct C2;
 template <> struct C2<float> { using T = float2; };
 template <> struct C2<double> { using T = double2; };
@@ -237,9 +271,13 @@ struct BlockSolveCfg {       // shared-memory plan of the blocked solve over a s
 };
 // re2 = 0: real factors, Re and Im of the complex vector solved as two columns; re2 = 1: factors
 // of real-equivalent systems (order 2m), the complex vector read as one real column
+// Mdf (may be null): the operators as (hi, lo) FP32 pairs; given, the look-ahead kernel runs in
+// double-FP32 arithmetic on the FP32 pipe (k_block_solve_la_df)
 void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
                         const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
-                        int use_fine, const int *flag, const BlockSolveCfg &cfg, int re2, cudaStream_t s);
+                        int use_fine, const int *flag, const BlockSolveCfg &cfg, int re2, cudaStream_t s,
+                        const float2 *Mdf = nullptr);
+void launch_ops_to_df(long long n, const double *M, float2 *Mdf, cudaStream_t s);
 cudaError_t set_block_solve_smem(BlockSolveCfg &cfg);
 
 // learned warm start (kernels_cnn.cu)

@@ -735,6 +735,222 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
     cp_async_wait_n<0>();
 }
 
+// ------------------------------------------------------------------------------------------
+// Double-FP32 form of the look-ahead blocked solve, for the coarse solves of the complex64 inner
+// iteration.  GB300's FP64 pipe issues two FMAs per clock per SM, so k_block_solve_la is bound by
+// it (the chain warp's eight FMAs per lane occupy one sub-partition's FP64 unit for ~512 cycles
+// per block).  Here the same block operators, converted once to (hi, lo) FP32 pairs (Mdf, the
+// offsets of Mall in 8-byte entries), are applied with df_acc on the FP32 pipe: every product
+// exact in its high parts, sums by two-sum, windows, partial sums and the working vector kept as
+// pairs (the input split once at the start, the result widened to FP64 once at the end: on GB300
+// an FP64 conversion of a warp costs as much as an FP64 FMA, so none stays inside the sweeps).  The operators carry 2^-48 relative error instead
+// of 2^-53, so the solve's forward error grows to about κ(E)·2^-48 (4e-10 at κ = 1e5), far
+// below what inner solves to a relative tolerance of 1e-2 in complex64 arithmetic need; the
+// complex128 inner solves and the direct local solve keep k_block_solve_la.  Schedule, ring,
+// windows and shared-memory layout are those of k_block_solve_la (a pair takes the 8 bytes of a
+// double).
+// ------------------------------------------------------------------------------------------
+template <int RING, bool RE2>
+__global__ void __launch_bounds__(LA_T, 2)
+k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restrict__ shapes,
+                    const float2 *__restrict__ Mdf, const int *__restrict__ Pall,
+                    const int4 *__restrict__ Meta, const double2 *__restrict__ in,
+                    double2 *__restrict__ out, int use_fine, const int *__restrict__ flag, int maxK,
+                    int cwy, int cwx) {
+    static_assert(RING >= 3, "the look-ahead needs blocks J and J+1 resident while J+2 loads");
+    static_assert(LA_BW == 7, "chain_row adds the seven bulk partials in four accumulators");
+    extern __shared__ double smd[];
+    __shared__ float2 part[2][LA_BW][BNB];
+    __shared__ int sw[RING];
+    constexpr int STR = RE2 ? 1 : 2;
+    const int t = RE2 ? (int)blockIdx.x : (int)(blockIdx.x >> 1), comp = RE2 ? 0 : (int)(blockIdx.x & 1);
+    if (flag && !flag[t]) return;
+    const Task T = tasks[t];
+    const BlockFactor F = shapes[T.shape];
+    const long long off = use_fine ? T.foff : T.coff;
+    const int m = F.m, nbk = F.nblk;
+    const int slot = la_slot(maxK);
+    float2 *CY = reinterpret_cast<float2 *>(smd + RING * slot), *CX = CY + cwy;
+    const int *perm = Pall + F.perm_off;
+    const int4 *meta = Meta + F.meta_off;
+    const double *inr = reinterpret_cast<const double *>(in + off) + comp;
+    double *outr = reinterpret_cast<double *>(out + off) + comp;
+    // during the solve every 8-byte slot of the output holds the entry as a (hi, lo) pair: the
+    // inputs are split once here, the block inputs travel as pairs, the outputs are widened to
+    // FP64 once at the end (no FP64-pipe conversion inside the sweeps)
+    float2 *od = reinterpret_cast<float2 *>(outr);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = lane >> 1, half = lane & 1;
+    const int q = (warp - 1) * 2 + half;
+    const int bt = tid - 32;
+    auto load_block = [&](long long src_off, int K, int buf, int J) {
+        if (bt < 0) return;
+        double *dst = smd + buf * slot;
+        const float2 *src = Mdf + src_off;
+        const int nchunk = BNB * K / 2;                  // 16-byte chunks (two pairs each)
+        for (int c = bt; c < nchunk; c += LA_T - 32) cp_async16(dst + 2 * c, src + 2 * c);
+        if (bt < BNB) {
+            const int i = J * BNB + bt;
+            cp_async8_zfill(dst + BNB * maxK + bt, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
+        }
+    };
+    for (int i = tid; i < m; i += LA_T) od[STR * (long long)i] = df_split(inr[STR * (long long)perm[i]]);
+    for (int i = tid; i < cwy; i += LA_T) CY[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < cwx; i += LA_T) CX[i] = make_float2(0.f, 0.f);
+    __threadfence_block();
+    __syncthreads();
+
+    // columns [k0, k1) of the block in slot sp (row stride K) for this bulk lane's row: diagonal
+    // columns k < BNB take the block's inputs (pairs), panel column p = k - BNB the window
+    auto bulk_row = [&](const double *sp, int K, int k0, int k1, const float2 *win, int pbase, int mask) {
+        const float2 *Mr = reinterpret_cast<const float2 *>(sp) + row * K;
+        const float2 *a = reinterpret_cast<const float2 *>(sp + BNB * maxK);
+        float sh = 0.f, sl = 0.f;
+        int k = q;
+        for (; k < BNB; k += LA_BL) {
+            const float2 mk = Mr[k], x = a[k];
+            df_acc(sh, sl, mk.x, mk.y, x.x, x.y);
+        }
+        if (k < k0) k += ((k0 - k + LA_BL - 1) / LA_BL) * LA_BL;
+        for (; k < k1; k += LA_BL) {
+            const float2 mk = Mr[k], x = win[(pbase + k - BNB) & mask];
+            df_acc(sh, sl, mk.x, mk.y, x.x, x.y);
+        }
+        const float oh = __shfl_xor_sync(0xffffffffu, sh, 1), ol = __shfl_xor_sync(0xffffffffu, sl, 1);
+        df_add(sh, sl, oh, ol);
+        return make_float2(sh, sl);
+    };
+    // warp 0: block J from the bulk partials (parity par) and the recent panel columns [p0, p1),
+    // four pair accumulators seeded by the lane's partials, combined by a two-level tree
+    auto chain_row = [&](const double *sp, int K, int p0, int p1, const float2 *win, int pbase, int mask,
+                         int par) {
+        const float2 *Mr = reinterpret_cast<const float2 *>(sp) + row * K + BNB;
+        float2 a0 = part[par][half][row], a1 = part[par][half + 2][row], a2 = part[par][half + 4][row];
+        float2 a3 = half == 0 ? part[par][6][row] : make_float2(0.f, 0.f);
+        auto madd = [&](float2 &acc, int p) {
+            const float2 mk = Mr[p], x = win[(pbase + p) & mask];
+            df_acc(acc.x, acc.y, mk.x, mk.y, x.x, x.y);
+        };
+        int p = p0 + half;
+        for (; p + 6 < p1; p += 8) { madd(a0, p); madd(a1, p + 2); madd(a2, p + 4); madd(a3, p + 6); }
+        if (p < p1) madd(a0, p);
+        if (p + 2 < p1) madd(a1, p + 2);
+        if (p + 4 < p1) madd(a2, p + 4);
+        df_add(a0.x, a0.y, a1.x, a1.y);
+        df_add(a2.x, a2.y, a3.x, a3.y);
+        df_add(a0.x, a0.y, a2.x, a2.y);
+        const float oh = __shfl_xor_sync(0xffffffffu, a0.x, 1), ol = __shfl_xor_sync(0xffffffffu, a0.y, 1);
+        df_add(a0.x, a0.y, oh, ol);
+        return a0;
+    };
+
+    // ---- forward: y_J = M_J [(Pb)_J ; y_{J-w_J..J}] ----
+    int4 mnext = make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < RING - 1; u++) {
+        if (u < nbk) {
+            const int4 mt = meta[u];
+            load_block(mt.x, BNB + mt.y, u, u);
+            if (tid == 32) sw[u] = mt.y;
+        }
+        cp_async_commit();
+    }
+    if (RING - 1 < nbk) mnext = meta[RING - 1];
+    cp_async_wait_n<RING - 2>();
+    __syncthreads();
+    if (warp > 0) {
+        const int w0 = sw[0], nold = w0 > BNB ? w0 - BNB : 0;
+        const float2 v = bulk_row(smd, BNB + w0, BNB, BNB + nold, CY, -w0, cwy - 1);
+        if (half == 0) part[0][warp - 1][row] = v;
+    }
+    for (int J = 0; J < nbk; J++) {
+        cp_async_wait_n<RING - 3>();
+        __syncthreads();
+        if (J + RING - 1 < nbk) {
+            const int buf = (J + RING - 1) % RING;
+            load_block(mnext.x, BNB + mnext.y, buf, J + RING - 1);
+            if (tid == 32) sw[buf] = mnext.y;
+        }
+        cp_async_commit();
+        if (J + RING < nbk) mnext = meta[J + RING];
+        if (warp == 0) {
+            const int wJ = sw[J % RING];
+            const int p0 = wJ > BNB ? wJ - BNB : 0;
+            const float2 v = chain_row(smd + (J % RING) * slot, BNB + wJ, p0, wJ, CY, J * BNB - wJ, cwy - 1, J & 1);
+            if (half == 0) {
+                const int i = J * BNB + row;
+                CY[i & (cwy - 1)] = v;
+                if (i < m) od[STR * (long long)i] = v;
+            }
+        } else if (J + 1 < nbk) {
+            const int Jn = J + 1, w1 = sw[Jn % RING], nold = w1 > BNB ? w1 - BNB : 0;
+            const float2 v = bulk_row(smd + (Jn % RING) * slot, BNB + w1, BNB, BNB + nold, CY, Jn * BNB - w1, cwy - 1);
+            if (half == 0) part[Jn & 1][warp - 1][row] = v;
+        }
+    }
+    cp_async_wait_n<0>();
+    __threadfence_block();
+    __syncthreads();
+
+    // ---- backward: x_J = M_J [y_J ; x_{J+1..J+w_J}] ----
+#pragma unroll
+    for (int u = 0; u < RING - 1; u++) {
+        const int J = nbk - 1 - u;
+        if (J >= 0) {
+            const int4 mt = meta[J];
+            load_block(mt.z, BNB + mt.w, u, J);
+            if (tid == 32) sw[u] = mt.w;
+        }
+        cp_async_commit();
+    }
+    mnext = nbk - RING >= 0 ? meta[nbk - RING] : make_int4(0, 0, 0, 0);
+    cp_async_wait_n<RING - 2>();
+    __syncthreads();
+    if (warp > 0) {
+        const int J = nbk - 1, w0 = sw[0];
+        const float2 v = bulk_row(smd, BNB + w0, 2 * BNB, BNB + w0, CX, (J + 1) * BNB, cwx - 1);
+        if (half == 0) part[0][warp - 1][row] = v;
+    }
+    for (int k = 0; k < nbk; k++) {
+        const int J = nbk - 1 - k;
+        cp_async_wait_n<RING - 3>();
+        __syncthreads();
+        if (J - (RING - 1) >= 0) {
+            const int buf = (k + RING - 1) % RING;
+            load_block(mnext.z, BNB + mnext.w, buf, J - (RING - 1));
+            if (tid == 32) sw[buf] = mnext.w;
+        }
+        cp_async_commit();
+        if (J - RING >= 0) mnext = meta[J - RING];
+        if (warp == 0) {
+            const int wJ = sw[k % RING];
+            const float2 v = chain_row(smd + (k % RING) * slot, BNB + wJ, 0, wJ < BNB ? wJ : BNB, CX, (J + 1) * BNB,
+                                       cwx - 1, k & 1);
+            if (half == 0) {
+                const int i = J * BNB + row;
+                CX[i & (cwx - 1)] = v;
+                if (i < m) od[STR * (long long)i] = v;
+            }
+        } else if (J - 1 >= 0) {
+            const int kn = k + 1, Jn = J - 1, w1 = sw[kn % RING];
+            const float2 v = bulk_row(smd + (kn % RING) * slot, BNB + w1, 2 * BNB, BNB + w1, CX, (Jn + 1) * BNB,
+                                      cwx - 1);
+            if (half == 0) part[kn & 1][warp - 1][row] = v;
+        }
+    }
+    cp_async_wait_n<0>();
+    __syncthreads();
+    for (int i = tid; i < m; i += LA_T) {
+        const float2 v = od[STR * (long long)i];
+        outr[STR * (long long)i] = (double)v.x + (double)v.y;
+    }
+}
+
+__global__ void k_ops_to_df(long long n, const double *__restrict__ M, float2 *__restrict__ Mdf) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        Mdf[i] = df_split(M[i]);
+}
+
 void launch_assemble_E(const Stencil &st, int nx, int ny, int kl, int ku, double *ab, cudaStream_t s) {
     long long tot = (long long)(nx / 2) * (ny / 2) * 25;
     k_assemble_E<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(st, nx, ny, kl, ku, ab);
@@ -757,6 +973,11 @@ void launch_band_lu(int nmat, const int *m, const int *kl, const int *ku, double
                     int *const *piv, int *info, cudaStream_t s) {
     k_band_lu<<<nmat, 512, 0, s>>>(m, kl, ku, ab, piv, info);
 }
+void launch_ops_to_df(long long n, const double *M, float2 *Mdf, cudaStream_t s) {
+    long long g = (n + 255) / 256;
+    if (g > 8 * 152) g = 8 * 152;
+    k_ops_to_df<<<(int)(g > 0 ? g : 1), 256, 0, s>>>(n, M, Mdf);
+}
 void launch_factor_prepare(int m, int kl, int ku, const double *ab, const int *piv, int KLW,
                            double *Lp, int *lext, int *uext, int *perm, int *err, cudaStream_t s) {
     k_perm<<<1, 32, 0, s>>>(m, piv, perm);
@@ -778,10 +999,14 @@ static size_t la_smem(const BlockSolveCfg &c, int ring) {
 
 template <int RING, bool RE2>
 static void la_launch(int grid, const BlockSolveCfg &c, const Task *tasks, const BlockFactor *shapes,
-                      const double *Mall, const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
-                      int use_fine, const int *flag, cudaStream_t s) {
-    k_block_solve_la<RING, RE2><<<grid, LA_T, la_smem(c, RING), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
-                                                                      use_fine, flag, c.maxK, c.cwy, c.cwx);
+                      const double *Mall, const float2 *Mdf, const int *Pall, const int4 *Meta, const double2 *in,
+                      double2 *out, int use_fine, const int *flag, cudaStream_t s) {
+    if (Mdf)
+        k_block_solve_la_df<RING, RE2><<<grid, LA_T, la_smem(c, RING), s>>>(tasks, shapes, Mdf, Pall, Meta, in, out,
+                                                                             use_fine, flag, c.maxK, c.cwy, c.cwx);
+    else
+        k_block_solve_la<RING, RE2><<<grid, LA_T, la_smem(c, RING), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
+                                                                          use_fine, flag, c.maxK, c.cwy, c.cwx);
 }
 
 static int sm_count() {
@@ -796,21 +1021,23 @@ static int sm_count() {
 
 void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes, const double *Mall,
                         const int *Pall, const int4 *Meta, const double2 *in, double2 *out,
-                        int use_fine, const int *flag, const BlockSolveCfg &c, int re2, cudaStream_t s) {
+                        int use_fine, const int *flag, const BlockSolveCfg &c, int re2, cudaStream_t s,
+                        const float2 *Mdf) {
     const int chains = re2 ? ntasks : 2 * ntasks;
+    if (!(c.lookahead && c.la_ring >= 3)) Mdf = nullptr;    // the double-FP32 form exists as look-ahead only
     if (c.lookahead && c.la_ring >= 3) {
         // the deepest ring that fits, unless there are more chains than SMs and a ring of 4 lets
         // two CTAs share an SM (many chains: throughput over latency)
         int ring = c.la_ring;
         if (ring > 4 && chains > sm_count() && 2 * (la_smem(c, 4) + 4096) <= 228 * 1024) ring = 4;
         if (re2) {
-            if (ring == 6) la_launch<6, true>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
-            else if (ring == 4) la_launch<4, true>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
-            else la_launch<3, true>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
+            if (ring == 6) la_launch<6, true>(chains, c, tasks, shapes, Mall, Mdf, Pall, Meta, in, out, use_fine, flag, s);
+            else if (ring == 4) la_launch<4, true>(chains, c, tasks, shapes, Mall, Mdf, Pall, Meta, in, out, use_fine, flag, s);
+            else la_launch<3, true>(chains, c, tasks, shapes, Mall, Mdf, Pall, Meta, in, out, use_fine, flag, s);
         } else {
-            if (ring == 6) la_launch<6, false>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
-            else if (ring == 4) la_launch<4, false>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
-            else la_launch<3, false>(chains, c, tasks, shapes, Mall, Pall, Meta, in, out, use_fine, flag, s);
+            if (ring == 6) la_launch<6, false>(chains, c, tasks, shapes, Mall, Mdf, Pall, Meta, in, out, use_fine, flag, s);
+            else if (ring == 4) la_launch<4, false>(chains, c, tasks, shapes, Mall, Mdf, Pall, Meta, in, out, use_fine, flag, s);
+            else la_launch<3, false>(chains, c, tasks, shapes, Mall, Mdf, Pall, Meta, in, out, use_fine, flag, s);
         }
         return;
     }
@@ -832,12 +1059,16 @@ void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes
 }
 
 template <int RING, bool RE2> static cudaError_t la_attr(size_t lim, size_t &static_bytes) {
-    cudaFuncAttributes a;
+    cudaFuncAttributes a, b;
     cudaError_t e = cudaFuncGetAttributes(&a, k_block_solve_la<RING, RE2>);
     if (e != cudaSuccess) return e;
-    static_bytes = std::max(static_bytes, a.sharedSizeBytes);
-    return cudaFuncSetAttribute(k_block_solve_la<RING, RE2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(lim - a.sharedSizeBytes));
+    if ((e = cudaFuncGetAttributes(&b, k_block_solve_la_df<RING, RE2>)) != cudaSuccess) return e;
+    static_bytes = std::max(static_bytes, std::max(a.sharedSizeBytes, b.sharedSizeBytes));
+    if ((e = cudaFuncSetAttribute(k_block_solve_la<RING, RE2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(lim - a.sharedSizeBytes))) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_block_solve_la_df<RING, RE2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(lim - b.sharedSizeBytes));
 }
 
 // Ring depth 4 if its shared memory fits the per-CTA limit, else 2; error if not even that fits.

@@ -210,25 +210,6 @@ k_odots(OuterBatch B, const double2 *__restrict__ V, int nv, const double2 *__re
 // ------------------------------------------------------------------------------------------
 struct WStageDF { float4 w[OCH]; };        // (Re hi, Re lo, Im hi, Im lo) per element
 
-__device__ __forceinline__ void df_acc(float &sh, float &sl, float xh, float xl, float yh, float yl) {
-    const float p = __fmul_rn(xh, yh);
-    const float e = fmaf(xh, yh, -p);                 // exact: xh·yh = p + e
-    const float c = fmaf(xh, yl, fmaf(xl, yh, e));
-    const float t = __fadd_rn(sh, p);                 // two-sum: sh + p = t + err exactly
-    const float bb = __fsub_rn(t, sh);
-    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
-    sh = t;
-    sl = __fadd_rn(sl, __fadd_rn(err, c));
-}
-
-// (sh, sl) += (bh, bl): two-sum of the high parts, the low parts added
-__device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl) {
-    const float t = __fadd_rn(sh, bh);
-    const float bb = __fsub_rn(t, sh);
-    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(bh, bb));
-    sh = t;
-    sl = __fadd_rn(sl, __fadd_rn(err, bl));
-}
 
 // w (FP64) split per element into (Re hi, Re lo, Im hi, Im lo) for the double-FP32 dots
 __device__ __forceinline__ void stage_w_df(WStageDF &ws, int i, double2 x) {

@@ -252,7 +252,7 @@ class Solver:
     def launch_count(self) -> int:
         return int(self._L.hdd_launch_count(self._h))
 
-    OPTIONS = {"coarse_lookahead": 1, "fused_inner": 2, "outer_dots_df": 3, "outer_update_df": 4, "outer_dcgs2": 5}
+    OPTIONS = {"coarse_lookahead": 1, "fused_inner": 2, "outer_dots_df": 3, "outer_update_df": 4, "outer_dcgs2": 5, "coarse_df": 6}
 
     def set_option(self, name: str, value: int):
         """Implementation choice of this context (hdd_set_option): "coarse_lookahead" selects
@@ -260,7 +260,8 @@ class Solver:
         Arnoldi step (1) or the separate kernels (0); "outer_dots_df" the outer CGS dot products
         in double-FP32 arithmetic (1) or in FP64 (0); "outer_update_df" the first-pass update in
         double-FP32 (1) or FP64 (0); "outer_dcgs2" the delayed CGS2 outer Arnoldi (1) or plain
-        CGS2 (0)."""
+        CGS2 (0); "coarse_df" the complex64 inner iteration's coarse solves in double-FP32 (1) or
+        FP64 (0)."""
         self._check(self._L.hdd_set_option(self._h, self.OPTIONS[name], int(value)), "hdd_set_option")
         return self
 

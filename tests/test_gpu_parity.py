@@ -86,9 +86,10 @@ def test_local_operators(oracle_mod, w, prec):
         xg = xg.astype(np.complex64).astype(np.complex128)
     outs = {op: s.local_op(op, _to_dev(x), prec).cpu().numpy()
             for op, x in [("A", xf), ("Z", xc), ("Zt", xf), ("R", xg), ("PA", xf)]}
-    if prec == 128:
-        outs["Einv"] = s.local_op("Einv", _to_dev(xc)).cpu().numpy()
-        outs["Ainv"] = s.local_op("Ainv", _to_dev(xf)).cpu().numpy()
+    # banded solves: FP64 (prec 128) or double-FP32 on the FP32 pipe (prec 64, the complex64 inner
+    # iteration's coarse solve: operators to 2^-48, so the bar is 2^5 x looser at equal κ)
+    outs["Einv"] = s.local_op("Einv", _to_dev(xc), prec).cpu().numpy()
+    outs["Ainv"] = s.local_op("Ainv", _to_dev(xf), prec).cpu().numpy()
     for q in range(p.nsub):
         F, Cc = slice(fo[q], fo[q + 1]), slice(co[q], co[q + 1])
         assert _rel(outs["A"][F], p.sub_apply_A(q, xf[F])) < tol
@@ -100,9 +101,9 @@ def test_local_operators(oracle_mod, w, prec):
             assert _rel(outs["PA"][F], p.sub_apply_PA(q, xf[F])) < 1e-11
         else:
             assert _close(outs["PA"][F], p.sub_apply_PA(q, xf[F]), 1e-4)
-        if prec == 128:
-            assert _rel(outs["Einv"][Cc], p.coarse_solve(q, xc[Cc])) < 1e-11
-            assert _rel(outs["Ainv"][F], p.sub_solve_exact(q, xf[F])) < 1e-10
+        ebar, abar = (1e-11, 1e-10) if prec == 128 else (1e-9, 1e-8)
+        assert _close(outs["Einv"][Cc], p.coarse_solve(q, xc[Cc]), ebar)
+        assert _close(outs["Ainv"][F], p.sub_solve_exact(q, xf[F]), abar)
 
 
 @pytest.mark.parametrize("prec,tol", [(128, 1e-1), (128, 1e-2), (128, 1e-6), (64, 1e-1), (64, 1e-2),
@@ -467,12 +468,12 @@ def test_fused_step_and_lookahead_solve_match_separate_kernels(oracle_mod, bc, p
     # the coarse operator itself: both block-solve kernels against the oracle
     fo, co = s.offsets()
     xc = W.random_complex_fast(co[-1], 6)
-    for la in (0, 1):
+    for la, cprec, bar in ((0, 128, 1e-11), (1, 128, 1e-11), (1, 64, 1e-9)):
         s.set_option("coarse_lookahead", la)
-        e = s.local_op("Einv", _to_dev(xc)).cpu().numpy()
+        e = s.local_op("Einv", _to_dev(xc), cprec).cpu().numpy()
         for q in range(p.nsub):
             Cc = slice(co[q], co[q + 1])
-            assert _rel(e[Cc], p.coarse_solve(q, xc[Cc])) < 1e-11, (la, q)
+            assert _close(e[Cc], p.coarse_solve(q, xc[Cc]), bar), (la, cprec, q)
     s.set_option("coarse_lookahead", 1)
 
 
