@@ -351,8 +351,8 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
                 if (c - ue[c] <= r1) { wu = c - r1; break; }
             wl += wl & 1; wu += wu & 1;
             int4 e;
-            e.x = (int)(base + so); e.y = wl; so += (long long)BNB * (BNB + wl);
-            e.z = (int)(base + so); e.w = wu; so += (long long)BNB * (BNB + wu);
+            e.x = (int)(base + so); e.y = wl; so += (long long)BNB * op_stride(wl);
+            e.z = (int)(base + so); e.w = wu; so += (long long)BNB * op_stride(wu);
             meta.push_back(e);
             b.wl = std::max(b.wl, wl); b.wu = std::max(b.wu, wu);
         }
@@ -360,7 +360,7 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
         double fm = 0;
         for (int j = 0; j < m[q]; j++) fm += std::min(kl[q], m[q] - 1 - j) + ue[j];
         F.fma_col[q] = fm;
-        F.cfg.maxK = std::max(F.cfg.maxK, BNB + std::max(b.wl, b.wu));
+        F.cfg.maxK = std::max(F.cfg.maxK, std::max(op_stride(b.wl), op_stride(b.wu)));
         while (F.cfg.cwy < BNB + b.wl) F.cfg.cwy = F.cfg.cwy ? 2 * F.cfg.cwy : BNB;
         while (F.cfg.cwx < BNB + b.wu) F.cfg.cwx = F.cfg.cwx ? 2 * F.cfg.cwx : BNB;
     }

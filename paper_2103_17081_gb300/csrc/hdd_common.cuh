@@ -162,6 +162,14 @@ struct BlockFactor {        // FP64 banded LU with partial pivoting in blocked s
                            // offsets in doubles from the start of the operator array
 };
 constexpr int BNB = 16;    // rows per block of the blocked banded solve
+// Row stride of a block operator with panel width w (BNB + w columns), padded with zeros to
+// ≡ 2 (mod 16) entries: the 8-byte reads of a warp's 16 rows x 2 lanes then fall in distinct
+// shared-memory banks whatever the panel width (an unpadded width ≡ 0 mod 16 put every row on
+// the same banks).
+__host__ __device__ __forceinline__ int op_stride(int w) {
+    const int K = BNB + w;
+    return K + ((2 - K) & 15);
+}
 
 constexpr int MAX_RESTART = 64;       // inner GMRES restart bound (Hessenberg in registers/smem)
 constexpr int FINE_ROWS = 8;          // default fine rows per fine tile (hdd_autotune may change it)
@@ -263,7 +271,7 @@ void launch_factor_prepare(int m, int kl, int ku, const double *ab, const int *p
 void launch_block_operators(int m, int kl, int ku, const double *ab, int KLW, const double *Lp,
                             const int4 *meta, double *Mall, cudaStream_t s);
 struct BlockSolveCfg {       // shared-memory plan of the blocked solve over a set of factors
-    int maxK = 0;          // widest operator row: BNB + panel width
+    int maxK = 0;          // widest operator row stride: op_stride(panel width)
     int cwy = 0, cwx = 0;  // circular y / x windows, powers of two >= BNB + widest left / right panel
     int ring = 0;          // operator ring depth (4 or 2), chosen by set_block_solve_smem
     int la_ring = 0;       // ring of the look-ahead kernel (6, 4 or 3; 0 if it does not fit)

@@ -283,13 +283,13 @@ __global__ void k_uext(int m, int kl, int ku, const double *__restrict__ ab, int
     uext[c] = e;
 }
 
-// Forward block operators: one CTA per block J, M_J row-major BNB x (BNB + w_J) at meta[J].x,
-// w_J = meta[J].y the width of block J's left panel.
+// Forward block operators: one CTA per block J, M_J row-major BNB x (BNB + w_J) at meta[J].x
+// (row stride op_stride(w_J)), w_J = meta[J].y the width of block J's left panel.
 __global__ void k_block_fwd(int m, int KLW, const double *__restrict__ Lp, const int4 *__restrict__ meta,
                             double *__restrict__ Mall) {
     __shared__ double Li[BNB][BNB];
     const int J = blockIdx.x, r0 = J * BNB;
-    const int WL = meta[J].y, K = BNB + WL;
+    const int WL = meta[J].y, K = BNB + WL, KS = op_stride(WL);
     double *MJ = Mall + meta[J].x;
     auto Lv = [&](int r, int c) -> double {            // permuted L(r, c), r > c
         if (c < 0 || r >= m || c >= m) return 0.0;
@@ -309,10 +309,11 @@ __global__ void k_block_fwd(int m, int KLW, const double *__restrict__ Lp, const
         for (int r = 0; r < BNB; r++) Li[r][c] = x[r];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < BNB * K; e += blockDim.x) {
-        const int r = e / K, cc = e % K;
+    for (int e = threadIdx.x; e < BNB * KS; e += blockDim.x) {
+        const int r = e / KS, cc = e % KS;
         double v;
         if (cc < BNB) v = Li[r][cc];
+        else if (cc >= K) v = 0.0;                         // row padding
         else {
             const int col = r0 - WL + (cc - BNB);          // global column of the panel entry
             double acc = 0.0;
@@ -324,12 +325,12 @@ __global__ void k_block_fwd(int m, int KLW, const double *__restrict__ Lp, const
 }
 
 // Backward block operators from the row-band U: M_J = [U_JJ⁻¹ | -U_JJ⁻¹ U_J], BNB x (BNB + w_J)
-// at meta[J].z with w_J = meta[J].w.
+// at meta[J].z (row stride op_stride(w_J)) with w_J = meta[J].w.
 __global__ void k_block_bwd(int m, int kl, int ku, const double *__restrict__ ab,
                             const int4 *__restrict__ meta, double *__restrict__ Mall) {
     __shared__ double Ui[BNB][BNB];
     const int J = blockIdx.x, r0 = J * BNB;
-    const int WU = meta[J].w, K = BNB + WU;
+    const int WU = meta[J].w, K = BNB + WU, KS = op_stride(WU);
     const int W = 2 * kl + ku + 1;
     double *MJ = Mall + meta[J].z;
     auto Uv = [&](int r, int c) -> double {            // U(r, c), c >= r
@@ -350,10 +351,11 @@ __global__ void k_block_bwd(int m, int kl, int ku, const double *__restrict__ ab
         for (int r = 0; r < BNB; r++) Ui[r][c] = x[r];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < BNB * K; e += blockDim.x) {
-        const int r = e / K, cc = e % K;
+    for (int e = threadIdx.x; e < BNB * KS; e += blockDim.x) {
+        const int r = e / KS, cc = e % KS;
         double v;
         if (cc < BNB) v = Ui[r][cc];
+        else if (cc >= K) v = 0.0;                         // row padding
         else {
             const int col = r0 + BNB + (cc - BNB);
             double acc = 0.0;
@@ -469,7 +471,7 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
     for (int u = 0; u < RING - 1; u++) {
         if (u < nbk) {
             const int4 mt = meta[u];
-            load_block(mt.x, BNB + mt.y, u, u);
+            load_block(mt.x, op_stride(mt.y), u, u);
             if (tid == 0) sw[u] = mt.y;
         }
         cp_async_commit();
@@ -480,14 +482,14 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
         __syncthreads();
         if (J + RING - 1 < nbk) {
             const int buf = (J + RING - 1) % RING;
-            load_block(mnext.x, BNB + mnext.y, buf, J + RING - 1);
+            load_block(mnext.x, op_stride(mnext.y), buf, J + RING - 1);
             if (tid == 0) sw[buf] = mnext.y;
         }
         cp_async_commit();
         if (J + RING < nbk) mnext = meta[J + RING];
         const int wJ = sw[J % RING];
         const double *Mb = sm + (J % RING) * slot;
-        const double v = block_row_dot(Mb + row * (BNB + wJ), BNB + wJ, Mb + BNB * maxK, CY, J * BNB - wJ,
+        const double v = block_row_dot(Mb + row * op_stride(wJ), BNB + wJ, Mb + BNB * maxK, CY, J * BNB - wJ,
                                        cwy - 1, part);
         if (part == 0) {
             const int i = J * BNB + row;
@@ -504,7 +506,7 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
         const int J = nbk - 1 - u;
         if (J >= 0) {
             const int4 mt = meta[J];
-            load_block(mt.z, BNB + mt.w, u, J);
+            load_block(mt.z, op_stride(mt.w), u, J);
             if (tid == 0) sw[u] = mt.w;
         }
         cp_async_commit();
@@ -516,14 +518,14 @@ k_block_solve(const Task *__restrict__ tasks, const BlockFactor *__restrict__ sh
         __syncthreads();
         if (J - (RING - 1) >= 0) {
             const int buf = (k + RING - 1) % RING;
-            load_block(mnext.z, BNB + mnext.w, buf, J - (RING - 1));
+            load_block(mnext.z, op_stride(mnext.w), buf, J - (RING - 1));
             if (tid == 0) sw[buf] = mnext.w;
         }
         cp_async_commit();
         if (J - RING >= 0) mnext = meta[J - RING];
         const int wJ = sw[k % RING];
         const double *Mb = sm + (k % RING) * slot;
-        const double v = block_row_dot(Mb + row * (BNB + wJ), BNB + wJ, Mb + BNB * maxK, CX, (J + 1) * BNB,
+        const double v = block_row_dot(Mb + row * op_stride(wJ), BNB + wJ, Mb + BNB * maxK, CX, (J + 1) * BNB,
                                        cwx - 1, part);
         if (part == 0) {
             const int i = J * BNB + row;
@@ -639,22 +641,26 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
     };
 
     // ---- forward: y_J = M_J [(Pb)_J ; y_{J-w_J..J}] ----
-    int4 mnext = make_int4(0, 0, 0, 0);
+    // metadata of the blocks three prefetches ahead, in a register queue: each global load has
+    // three steps to arrive before the copy it addresses is issued
+    int4 mq0 = make_int4(0, 0, 0, 0), mq1 = mq0, mq2 = mq0;
 #pragma unroll
     for (int u = 0; u < RING - 1; u++) {
         if (u < nbk) {
             const int4 mt = meta[u];
-            load_block(mt.x, BNB + mt.y, u, u);
+            load_block(mt.x, op_stride(mt.y), u, u);
             if (tid == 32) sw[u] = mt.y;
         }
         cp_async_commit();
     }
-    if (RING - 1 < nbk) mnext = meta[RING - 1];
+    if (RING - 1 < nbk) mq0 = meta[RING - 1];
+    if (RING < nbk) mq1 = meta[RING];
+    if (RING + 1 < nbk) mq2 = meta[RING + 1];
     cp_async_wait_n<RING - 2>();                           // block 0 resident
     __syncthreads();
     if (warp > 0) {                                        // bulk part of block 0
         const int w0 = sw[0], nold = w0 > BNB ? w0 - BNB : 0;
-        const double v = bulk_row(sm, BNB + w0, BNB, BNB + nold, CY, -w0, cwy - 1);
+        const double v = bulk_row(sm, op_stride(w0), BNB, BNB + nold, CY, -w0, cwy - 1);
         if (half == 0) part[0][warp - 1][row] = v;
     }
     for (int J = 0; J < nbk; J++) {
@@ -662,15 +668,16 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
         __syncthreads();
         if (J + RING - 1 < nbk) {                          // into the slot block J-1 used
             const int buf = (J + RING - 1) % RING;
-            load_block(mnext.x, BNB + mnext.y, buf, J + RING - 1);
-            if (tid == 32) sw[buf] = mnext.y;
+            load_block(mq0.x, op_stride(mq0.y), buf, J + RING - 1);
+            if (tid == 32) sw[buf] = mq0.y;
         }
         cp_async_commit();
-        if (J + RING < nbk) mnext = meta[J + RING];
+        mq0 = mq1; mq1 = mq2;
+        if (J + RING + 2 < nbk) mq2 = meta[J + RING + 2];
         if (warp == 0) {
             const int wJ = sw[J % RING];
             const int p0 = wJ > BNB ? wJ - BNB : 0;
-            const double v = chain_row(sm + (J % RING) * slot, BNB + wJ, p0, wJ, CY, J * BNB - wJ, cwy - 1, J & 1);
+            const double v = chain_row(sm + (J % RING) * slot, op_stride(wJ), p0, wJ, CY, J * BNB - wJ, cwy - 1, J & 1);
             if (half == 0) {
                 const int i = J * BNB + row;
                 CY[i & (cwy - 1)] = v;
@@ -678,7 +685,7 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
             }
         } else if (J + 1 < nbk) {
             const int Jn = J + 1, w1 = sw[Jn % RING], nold = w1 > BNB ? w1 - BNB : 0;
-            const double v = bulk_row(sm + (Jn % RING) * slot, BNB + w1, BNB, BNB + nold, CY, Jn * BNB - w1, cwy - 1);
+            const double v = bulk_row(sm + (Jn % RING) * slot, op_stride(w1), BNB, BNB + nold, CY, Jn * BNB - w1, cwy - 1);
             if (half == 0) part[Jn & 1][warp - 1][row] = v;
         }
     }
@@ -692,17 +699,19 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
         const int J = nbk - 1 - u;
         if (J >= 0) {
             const int4 mt = meta[J];
-            load_block(mt.z, BNB + mt.w, u, J);
+            load_block(mt.z, op_stride(mt.w), u, J);
             if (tid == 32) sw[u] = mt.w;
         }
         cp_async_commit();
     }
-    mnext = nbk - RING >= 0 ? meta[nbk - RING] : make_int4(0, 0, 0, 0);
+    mq0 = nbk - RING >= 0 ? meta[nbk - RING] : make_int4(0, 0, 0, 0);
+    mq1 = nbk - RING - 1 >= 0 ? meta[nbk - RING - 1] : make_int4(0, 0, 0, 0);
+    mq2 = nbk - RING - 2 >= 0 ? meta[nbk - RING - 2] : make_int4(0, 0, 0, 0);
     cp_async_wait_n<RING - 2>();
     __syncthreads();
     if (warp > 0) {                                        // bulk part of block nbk-1
         const int J = nbk - 1, w0 = sw[0];
-        const double v = bulk_row(sm, BNB + w0, 2 * BNB, BNB + w0, CX, (J + 1) * BNB, cwx - 1);
+        const double v = bulk_row(sm, op_stride(w0), 2 * BNB, BNB + w0, CX, (J + 1) * BNB, cwx - 1);
         if (half == 0) part[0][warp - 1][row] = v;
     }
     for (int k = 0; k < nbk; k++) {                        // sweep position k: block J = nbk-1-k
@@ -711,14 +720,15 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
         __syncthreads();
         if (J - (RING - 1) >= 0) {
             const int buf = (k + RING - 1) % RING;
-            load_block(mnext.z, BNB + mnext.w, buf, J - (RING - 1));
-            if (tid == 32) sw[buf] = mnext.w;
+            load_block(mq0.z, op_stride(mq0.w), buf, J - (RING - 1));
+            if (tid == 32) sw[buf] = mq0.w;
         }
         cp_async_commit();
-        if (J - RING >= 0) mnext = meta[J - RING];
+        mq0 = mq1; mq1 = mq2;
+        if (J - RING - 2 >= 0) mq2 = meta[J - RING - 2];
         if (warp == 0) {
             const int wJ = sw[k % RING];
-            const double v = chain_row(sm + (k % RING) * slot, BNB + wJ, 0, wJ < BNB ? wJ : BNB, CX, (J + 1) * BNB,
+            const double v = chain_row(sm + (k % RING) * slot, op_stride(wJ), 0, wJ < BNB ? wJ : BNB, CX, (J + 1) * BNB,
                                        cwx - 1, k & 1);
             if (half == 0) {
                 const int i = J * BNB + row;
@@ -727,7 +737,7 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
             }
         } else if (J - 1 >= 0) {
             const int kn = k + 1, Jn = J - 1, w1 = sw[kn % RING];
-            const double v = bulk_row(sm + (kn % RING) * slot, BNB + w1, 2 * BNB, BNB + w1, CX, (Jn + 1) * BNB,
+            const double v = bulk_row(sm + (kn % RING) * slot, op_stride(w1), 2 * BNB, BNB + w1, CX, (Jn + 1) * BNB,
                                       cwx - 1);
             if (half == 0) part[kn & 1][warp - 1][row] = v;
         }
@@ -750,17 +760,22 @@ k_block_solve_la(const Task *__restrict__ tasks, const BlockFactor *__restrict__
 // windows and shared-memory layout are those of k_block_solve_la (a pair takes the 8 bytes of a
 // double).
 // ------------------------------------------------------------------------------------------
+// 16 warps: warp 0 runs the chain alone on its sub-partition (warps are issued by the
+// sub-partition of index warp mod 4); warps 4, 8 and 12 share that sub-partition and only issue
+// the block copies; the other 12 warps sum the bulk of the next block.
+constexpr int LAD_T = 512;
+constexpr int LAD_BW = 12;                 // bulk warps
+constexpr int LAD_BL = 2 * LAD_BW;         // bulk lanes per row (24)
 template <int RING, bool RE2>
-__global__ void __launch_bounds__(LA_T, 2)
+__global__ void __launch_bounds__(LAD_T, 1)
 k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restrict__ shapes,
                     const float2 *__restrict__ Mdf, const int *__restrict__ Pall,
                     const int4 *__restrict__ Meta, const double2 *__restrict__ in,
                     double2 *__restrict__ out, int use_fine, const int *__restrict__ flag, int maxK,
                     int cwy, int cwx) {
     static_assert(RING >= 3, "the look-ahead needs blocks J and J+1 resident while J+2 loads");
-    static_assert(LA_BW == 7, "chain_row adds the seven bulk partials in four accumulators");
     extern __shared__ double smd[];
-    __shared__ float2 part[2][LA_BW][BNB];
+    __shared__ float2 part[2][LAD_BW][BNB];
     __shared__ int sw[RING];
     constexpr int STR = RE2 ? 1 : 2;
     const int t = RE2 ? (int)blockIdx.x : (int)(blockIdx.x >> 1), comp = RE2 ? 0 : (int)(blockIdx.x & 1);
@@ -781,22 +796,24 @@ k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restric
     float2 *od = reinterpret_cast<float2 *>(outr);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = lane >> 1, half = lane & 1;
-    const int q = (warp - 1) * 2 + half;
+    const bool bulkw = warp > 0 && (warp & 3) != 0;
+    const int wb = warp - 1 - (warp >> 2);                 // bulk warp index 0..11 (if bulkw)
+    const int q = wb * 2 + half;
     const int bt = tid - 32;
     auto load_block = [&](long long src_off, int K, int buf, int J) {
         if (bt < 0) return;
         double *dst = smd + buf * slot;
         const float2 *src = Mdf + src_off;
         const int nchunk = BNB * K / 2;                  // 16-byte chunks (two pairs each)
-        for (int c = bt; c < nchunk; c += LA_T - 32) cp_async16(dst + 2 * c, src + 2 * c);
+        for (int c = bt; c < nchunk; c += LAD_T - 32) cp_async16(dst + 2 * c, src + 2 * c);
         if (bt < BNB) {
             const int i = J * BNB + bt;
             cp_async8_zfill(dst + BNB * maxK + bt, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
         }
     };
-    for (int i = tid; i < m; i += LA_T) od[STR * (long long)i] = df_split(inr[STR * (long long)perm[i]]);
-    for (int i = tid; i < cwy; i += LA_T) CY[i] = make_float2(0.f, 0.f);
-    for (int i = tid; i < cwx; i += LA_T) CX[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < m; i += LAD_T) od[STR * (long long)i] = df_split(inr[STR * (long long)perm[i]]);
+    for (int i = tid; i < cwy; i += LAD_T) CY[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < cwx; i += LAD_T) CX[i] = make_float2(0.f, 0.f);
     __threadfence_block();
     __syncthreads();
 
@@ -807,12 +824,12 @@ k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restric
         const float2 *a = reinterpret_cast<const float2 *>(sp + BNB * maxK);
         float sh = 0.f, sl = 0.f;
         int k = q;
-        for (; k < BNB; k += LA_BL) {
+        for (; k < BNB; k += LAD_BL) {
             const float2 mk = Mr[k], x = a[k];
             df_acc(sh, sl, mk.x, mk.y, x.x, x.y);
         }
-        if (k < k0) k += ((k0 - k + LA_BL - 1) / LA_BL) * LA_BL;
-        for (; k < k1; k += LA_BL) {
+        if (k < k0) k += ((k0 - k + LAD_BL - 1) / LAD_BL) * LAD_BL;
+        for (; k < k1; k += LAD_BL) {
             const float2 mk = Mr[k], x = win[(pbase + k - BNB) & mask];
             df_acc(sh, sl, mk.x, mk.y, x.x, x.y);
         }
@@ -825,8 +842,16 @@ k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restric
     auto chain_row = [&](const double *sp, int K, int p0, int p1, const float2 *win, int pbase, int mask,
                          int par) {
         const float2 *Mr = reinterpret_cast<const float2 *>(sp) + row * K + BNB;
-        float2 a0 = part[par][half][row], a1 = part[par][half + 2][row], a2 = part[par][half + 4][row];
-        float2 a3 = half == 0 ? part[par][6][row] : make_float2(0.f, 0.f);
+        // lane half h seeds the four accumulators with the partials h, h + 2, ... round-robin
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll
+        for (int w = 0; 2 * w < LAD_BW; w++) {
+            const int src = 2 * w + half;
+            if (src >= LAD_BW) break;
+            const float2 pv = part[par][src][row];
+            float2 &acc = (w & 3) == 0 ? a0 : (w & 3) == 1 ? a1 : (w & 3) == 2 ? a2 : a3;
+            df_add(acc.x, acc.y, pv.x, pv.y);
+        }
         auto madd = [&](float2 &acc, int p) {
             const float2 mk = Mr[p], x = win[(pbase + p) & mask];
             df_acc(acc.x, acc.y, mk.x, mk.y, x.x, x.y);
@@ -845,47 +870,52 @@ k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restric
     };
 
     // ---- forward: y_J = M_J [(Pb)_J ; y_{J-w_J..J}] ----
-    int4 mnext = make_int4(0, 0, 0, 0);
+    // metadata of the blocks three prefetches ahead, in a register queue: each global load has
+    // three steps to arrive before the copy it addresses is issued
+    int4 mq0 = make_int4(0, 0, 0, 0), mq1 = mq0, mq2 = mq0;
 #pragma unroll
     for (int u = 0; u < RING - 1; u++) {
         if (u < nbk) {
             const int4 mt = meta[u];
-            load_block(mt.x, BNB + mt.y, u, u);
+            load_block(mt.x, op_stride(mt.y), u, u);
             if (tid == 32) sw[u] = mt.y;
         }
         cp_async_commit();
     }
-    if (RING - 1 < nbk) mnext = meta[RING - 1];
+    if (RING - 1 < nbk) mq0 = meta[RING - 1];
+    if (RING < nbk) mq1 = meta[RING];
+    if (RING + 1 < nbk) mq2 = meta[RING + 1];
     cp_async_wait_n<RING - 2>();
     __syncthreads();
-    if (warp > 0) {
+    if (bulkw) {
         const int w0 = sw[0], nold = w0 > BNB ? w0 - BNB : 0;
-        const float2 v = bulk_row(smd, BNB + w0, BNB, BNB + nold, CY, -w0, cwy - 1);
-        if (half == 0) part[0][warp - 1][row] = v;
+        const float2 v = bulk_row(smd, op_stride(w0), BNB, BNB + nold, CY, -w0, cwy - 1);
+        if (half == 0) part[0][wb][row] = v;
     }
     for (int J = 0; J < nbk; J++) {
         cp_async_wait_n<RING - 3>();
         __syncthreads();
         if (J + RING - 1 < nbk) {
             const int buf = (J + RING - 1) % RING;
-            load_block(mnext.x, BNB + mnext.y, buf, J + RING - 1);
-            if (tid == 32) sw[buf] = mnext.y;
+            load_block(mq0.x, op_stride(mq0.y), buf, J + RING - 1);
+            if (tid == 32) sw[buf] = mq0.y;
         }
         cp_async_commit();
-        if (J + RING < nbk) mnext = meta[J + RING];
+        mq0 = mq1; mq1 = mq2;
+        if (J + RING + 2 < nbk) mq2 = meta[J + RING + 2];
         if (warp == 0) {
             const int wJ = sw[J % RING];
             const int p0 = wJ > BNB ? wJ - BNB : 0;
-            const float2 v = chain_row(smd + (J % RING) * slot, BNB + wJ, p0, wJ, CY, J * BNB - wJ, cwy - 1, J & 1);
+            const float2 v = chain_row(smd + (J % RING) * slot, op_stride(wJ), p0, wJ, CY, J * BNB - wJ, cwy - 1, J & 1);
             if (half == 0) {
                 const int i = J * BNB + row;
                 CY[i & (cwy - 1)] = v;
                 if (i < m) od[STR * (long long)i] = v;
             }
-        } else if (J + 1 < nbk) {
+        } else if (bulkw && J + 1 < nbk) {
             const int Jn = J + 1, w1 = sw[Jn % RING], nold = w1 > BNB ? w1 - BNB : 0;
-            const float2 v = bulk_row(smd + (Jn % RING) * slot, BNB + w1, BNB, BNB + nold, CY, Jn * BNB - w1, cwy - 1);
-            if (half == 0) part[Jn & 1][warp - 1][row] = v;
+            const float2 v = bulk_row(smd + (Jn % RING) * slot, op_stride(w1), BNB, BNB + nold, CY, Jn * BNB - w1, cwy - 1);
+            if (half == 0) part[Jn & 1][wb][row] = v;
         }
     }
     cp_async_wait_n<0>();
@@ -898,18 +928,20 @@ k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restric
         const int J = nbk - 1 - u;
         if (J >= 0) {
             const int4 mt = meta[J];
-            load_block(mt.z, BNB + mt.w, u, J);
+            load_block(mt.z, op_stride(mt.w), u, J);
             if (tid == 32) sw[u] = mt.w;
         }
         cp_async_commit();
     }
-    mnext = nbk - RING >= 0 ? meta[nbk - RING] : make_int4(0, 0, 0, 0);
+    mq0 = nbk - RING >= 0 ? meta[nbk - RING] : make_int4(0, 0, 0, 0);
+    mq1 = nbk - RING - 1 >= 0 ? meta[nbk - RING - 1] : make_int4(0, 0, 0, 0);
+    mq2 = nbk - RING - 2 >= 0 ? meta[nbk - RING - 2] : make_int4(0, 0, 0, 0);
     cp_async_wait_n<RING - 2>();
     __syncthreads();
-    if (warp > 0) {
+    if (bulkw) {
         const int J = nbk - 1, w0 = sw[0];
-        const float2 v = bulk_row(smd, BNB + w0, 2 * BNB, BNB + w0, CX, (J + 1) * BNB, cwx - 1);
-        if (half == 0) part[0][warp - 1][row] = v;
+        const float2 v = bulk_row(smd, op_stride(w0), 2 * BNB, BNB + w0, CX, (J + 1) * BNB, cwx - 1);
+        if (half == 0) part[0][wb][row] = v;
     }
     for (int k = 0; k < nbk; k++) {
         const int J = nbk - 1 - k;
@@ -917,30 +949,31 @@ k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restric
         __syncthreads();
         if (J - (RING - 1) >= 0) {
             const int buf = (k + RING - 1) % RING;
-            load_block(mnext.z, BNB + mnext.w, buf, J - (RING - 1));
-            if (tid == 32) sw[buf] = mnext.w;
+            load_block(mq0.z, op_stride(mq0.w), buf, J - (RING - 1));
+            if (tid == 32) sw[buf] = mq0.w;
         }
         cp_async_commit();
-        if (J - RING >= 0) mnext = meta[J - RING];
+        mq0 = mq1; mq1 = mq2;
+        if (J - RING - 2 >= 0) mq2 = meta[J - RING - 2];
         if (warp == 0) {
             const int wJ = sw[k % RING];
-            const float2 v = chain_row(smd + (k % RING) * slot, BNB + wJ, 0, wJ < BNB ? wJ : BNB, CX, (J + 1) * BNB,
+            const float2 v = chain_row(smd + (k % RING) * slot, op_stride(wJ), 0, wJ < BNB ? wJ : BNB, CX, (J + 1) * BNB,
                                        cwx - 1, k & 1);
             if (half == 0) {
                 const int i = J * BNB + row;
                 CX[i & (cwx - 1)] = v;
                 if (i < m) od[STR * (long long)i] = v;
             }
-        } else if (J - 1 >= 0) {
+        } else if (bulkw && J - 1 >= 0) {
             const int kn = k + 1, Jn = J - 1, w1 = sw[kn % RING];
-            const float2 v = bulk_row(smd + (kn % RING) * slot, BNB + w1, 2 * BNB, BNB + w1, CX, (Jn + 1) * BNB,
+            const float2 v = bulk_row(smd + (kn % RING) * slot, op_stride(w1), 2 * BNB, BNB + w1, CX, (Jn + 1) * BNB,
                                       cwx - 1);
-            if (half == 0) part[kn & 1][warp - 1][row] = v;
+            if (half == 0) part[kn & 1][wb][row] = v;
         }
     }
     cp_async_wait_n<0>();
     __syncthreads();
-    for (int i = tid; i < m; i += LA_T) {
+    for (int i = tid; i < m; i += LAD_T) {
         const float2 v = od[STR * (long long)i];
         outr[STR * (long long)i] = (double)v.x + (double)v.y;
     }
@@ -1002,7 +1035,7 @@ static void la_launch(int grid, const BlockSolveCfg &c, const Task *tasks, const
                       const double *Mall, const float2 *Mdf, const int *Pall, const int4 *Meta, const double2 *in,
                       double2 *out, int use_fine, const int *flag, cudaStream_t s) {
     if (Mdf)
-        k_block_solve_la_df<RING, RE2><<<grid, LA_T, la_smem(c, RING), s>>>(tasks, shapes, Mdf, Pall, Meta, in, out,
+        k_block_solve_la_df<RING, RE2><<<grid, LAD_T, la_smem(c, RING), s>>>(tasks, shapes, Mdf, Pall, Meta, in, out,
                                                                              use_fine, flag, c.maxK, c.cwy, c.cwx);
     else
         k_block_solve_la<RING, RE2><<<grid, LA_T, la_smem(c, RING), s>>>(tasks, shapes, Mall, Pall, Meta, in, out,
