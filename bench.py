@@ -30,6 +30,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "time-to-solution at rel-res 1e-6 (k=200, 20 ppwl); subdomain-solve GB/s vs peak"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TINSTR = 152 * 128 * 2.070e9 / 1e12    # 152 SMs x 128 FP32 lanes x 2.07 GHz (instructions)
 L2_FLUSH_BYTES = 512 << 20                      # > 129 MB L2
 # DRAM bytes (read + written) per algorithmic byte of a kernel family, from one ncu capture of its
 # kernels at outer iteration 200 of the k=200 solve (profiles/); their traffic grows with the
@@ -364,17 +365,26 @@ def run_gpu(args):
     per_launch_ms = dom["ms"] / max(1, dom["launches"])
     fp64_frac = dom["flops"] / (dom["ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
     hbm_frac = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9 / hbm
+    # double-FP32 families count FP32 instructions as their work (12 per product of pairs)
+    fp32_frac = dom["flops"] / (dom["ms"] * 1e-3) / 1e12 / FP32_PEAK_TINSTR
     if dom["bound"] == "fp64" and fp64_frac >= hbm_frac:      # the roof it sits closer to binds
         ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom["name"],
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (measured 1.19)",
                 "hbm_frac": hbm_frac}
+    elif dom["bound"] == "fp32" and fp32_frac >= hbm_frac:
+        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TINSTR, "unit": "T FP32 instructions/s",
+                "frac": ach / FP32_PEAK_TINSTR, "traffic": None, "kernel": dom["name"],
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                "hbm_frac": hbm_frac}
     else:
         ach = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": None, "kernel": dom["name"], "peak_source": hbm_src,
-                "fp64_frac": fp64_frac if dom["bound"] == "fp64" else None}
+                "fp64_frac": fp64_frac if dom["bound"] == "fp64" else None,
+                "fp32_instr_frac": fp32_frac if dom["bound"] == "fp32" else None}
     roof["launches"] = dom["launches"]
     roof["ms_per_launch"] = per_launch_ms
     df = any(d["name"] == "outer_dots_df32" and d["launches"] for d in prof)

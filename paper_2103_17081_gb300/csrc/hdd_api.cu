@@ -64,7 +64,8 @@ const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_pr
                               "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn",
                               "outer_reorth_fp32", "local_arnoldi_step", "outer_dots_df32",
                               "two_level_grid_coarse", "outer_update_df32", "coarse_solve_df32"};
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 0, 0, 0, 2};
+// (2: FP32 pipe; for the double-FP32 families the flop counts are FP32 instructions)
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 2, 0, 2, 2};
 
 struct Prof {
     bool on = false;
@@ -400,7 +401,8 @@ void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *ou
     BlockSolveCfg cfg = F.cfg;
     cfg.lookahead = ctx->coarse_la;
     df = df && cfg.lookahead && cfg.la_ring >= 3;
-    Launch L(ctx, df ? F_CDF : F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
+    // double-FP32: 12 FP32 instructions per product of pairs, i.e. 6 per counted flop
+    Launch L(ctx, df ? F_CDF : F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, df ? 6.0 * fl : fl, s);
     launch_block_solve(ctx->d_tasks.as<Task>(), nt, F.table.as<BlockFactor>(), F.M.as<double>(),
                        F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, cfg, F.re2 ? 1 : 0, s,
                        df ? F.Mdf.as<float2>() : nullptr);
@@ -417,7 +419,7 @@ void band_solve2(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *o
     BlockSolveCfg cfg = F.cfg;
     cfg.lookahead = ctx->coarse_la;
     df = df && cfg.lookahead && cfg.la_ring >= 3;
-    Launch L(ctx, df ? F_CDF : F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, fl, s);
+    Launch L(ctx, df ? F_CDF : F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, df ? 6.0 * fl : fl, s);
     launch_block_solve(ctx->d_tasks2.as<Task>(), 2 * nt, F.table.as<BlockFactor>(), F.M.as<double>(),
                        F.P.as<int>(), F.Meta.as<int4>(), in, out, 0, flag, cfg, F.re2 ? 1 : 0, s,
                        df ? F.Mdf.as<float2>() : nullptr);

@@ -952,7 +952,7 @@ k_dcgs_close(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs, dou
 // are rounding-error sized, so its error is far below the FP64 rounding of ṽ_j), widened every 32
 // vectors.  corr = 0 (step 0): v_0 is final and only read.  Then the partial ||w'||².
 // Dynamic shared memory: j · (float4 + float2).
-__global__ void __launch_bounds__(OTU, 2)
+__global__ void __launch_bounds__(OTU, 3)
 k_oupdate_dcgs(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int j, int corr,
                double2 *__restrict__ Vj, double *__restrict__ Dj, float2 *__restrict__ Vjh, float2 *__restrict__ Vjl,
                const double2 *__restrict__ acoef, const double2 *__restrict__ bcoef, const double *__restrict__ invs,
