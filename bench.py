@@ -31,6 +31,8 @@ import workloads as W  # noqa: E402
 METRIC = "time-to-solution at rel-res 1e-6 (k=200, 20 ppwl); subdomain-solve GB/s vs peak"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TINSTR = 152 * 128 * 2.070e9 / 1e12    # 152 SMs x 128 FP32 lanes x 2.07 GHz (instructions)
+# the library's default outer Arnoldi: delayed CGS2 with double-FP32 dots and updates
+OUTER_DF = "dcgs2-df32"
 L2_FLUSH_BYTES = 512 << 20                      # > 129 MB L2
 # DRAM bytes (read + written) per algorithmic byte of a kernel family, from one ncu capture of its
 # kernels at outer iteration 200 of the k=200 solve (profiles/); their traffic grows with the
@@ -42,8 +44,10 @@ TRAFFIC_PER_ALG = {
     ("outer_cgs2_fp64", False): (1.982693 + 4.043380) / (1.976274 + 3.952547),
     # k_oupdate without dots (double-FP32 dots on): 2.0608 + 0.0061 GB against 1.9828 GB
     ("outer_cgs2_fp64", True): (2.060811 + 0.006137) / ((201 * 24 + 32) * 408321 / 1e9),
-    # k_odots_df (both passes): 1.3205 + 0.0046 GB against 1.3197 GB
-    ("outer_dots_df32", True): (1.320545 + 0.004604) / ((201 * 16 + 16) * 408321 / 1e9),
+    # k_odots2_df (delayed CGS2, step 199): 1.3201 + 0.0051 GB against 1.3197 GB
+    ("outer_dots_df32", True): (1.320112 + 0.005139) / ((200 * 16 + 32) * 408321 / 1e9),
+    # k_oupdate_dcgs (step 199): 1.3134 + 0.0189 GB against 1.3360 GB
+    ("outer_update_df32", True): (1.313391 + 0.018886) / ((199 * 16 + 88) * 408321 / 1e9),
 }
 
 
@@ -336,7 +340,7 @@ def run_gpu(args):
                            "outer_its": fst["outer_its"], "inner_its_avg": round(fst["inner_its_avg"], 3),
                            "rel_res_true": fst["rel_res_true"], "err_vs_oracle": oracle_error(w, x),
                            "inner_prec": fkw["inner_prec"],
-                           "outer_reorth": "fp32-guarded" if fkw["outer_reorth32"] else "fp64",
+                           "outer": OUTER_DF if fkw["outer_reorth32"] else "cgs2-fp64",
                            "warm_start": bool(fkw.get("warm_start", 0))}
             if params:
                 forms[name]["params"] = os.path.relpath(params, ROOT)
@@ -411,7 +415,7 @@ def run_gpu(args):
             "data": "synthetic",
             "config": {**workload_config(w), "inner_prec": args.prec,
                        "l2": "flushed between timed steps (512 MB write)",
-                       "warm_start": bool(args.warm_start), "outer_reorth": "fp64" if args.fp64_reorth else "fp32-guarded",
+                       "warm_start": bool(args.warm_start), "outer": "cgs2-fp64" if args.fp64_reorth else OUTER_DF,
                        "tiles": tiles or {"fine_rows": 8, "coarse_rows": 4},
                        "parallelism": "replicas" if ws > 1 else "single"},
             "solve": {"outer_its": stats["outer_its"], "inner_its_avg": round(stats["inner_its_avg"], 3),
