@@ -200,6 +200,13 @@ def time_form(s, f, x, kw, steps, warmup, flush, stream):
     return statistics.mean(ts), st
 
 
+def apply_options(s, opts):
+    """--option NAME=VALUE pairs: implementation choices of the solver (hdd_set_option)."""
+    for o in opts:
+        name, _, val = o.partition("=")
+        s.set_option(name.strip(), int(val))
+
+
 def workload_config(w) -> dict:
     """Keys that define the workload; both arms report them identically."""
     return {"workload": w.name, "k": w.k, "N": w.N, "ppwl": round(w.ppwl, 2),
@@ -249,6 +256,7 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     w = W.make(args.workload, seed=rank)          # independent replica per rank
     s = Solver.from_workload(w, device=dev)
+    apply_options(s, args.option)
     f = s.build_rhs_batch(w.rhs) if w.nrhs > 1 else s.build_rhs(w.rhs[0])
     x = s.empty(f.numel())
     kw = dict(outer_tol=w.outer_tol, inner_tol=w.inner_tol, inner_prec=args.prec,
@@ -417,7 +425,8 @@ def run_gpu(args):
                        "l2": "flushed between timed steps (512 MB write)",
                        "warm_start": bool(args.warm_start), "outer": "cgs2-fp64" if args.fp64_reorth else OUTER_DF,
                        "tiles": tiles or {"fine_rows": 8, "coarse_rows": 4},
-                       "parallelism": "replicas" if ws > 1 else "single"},
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       **({"options": list(args.option)} if args.option else {})},
             "solve": {"outer_its": stats["outer_its"], "inner_its_avg": round(stats["inner_its_avg"], 3),
                       "rel_res_true": rel, "status": stats["status_code"], "err_vs_oracle": err},
             "forms": forms,
@@ -451,6 +460,7 @@ def run_ras_dense(args):
 
     w = W.make(args.workload)
     s = Solver.from_workload(w)
+    apply_options(s, args.option)
     if args.autotune:
         s.autotune(inner_tol=w.inner_tol, inner_prec=args.prec)
     n = s.n
@@ -502,6 +512,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample-its", type=int, default=400)
     ap.add_argument("--full-outer-its", type=int, default=0)
+    ap.add_argument("--option", action="append", default=[],
+                    help="NAME=VALUE: a hdd_set_option choice of the solver (Solver.OPTIONS), repeatable")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form-steps", type=int, default=2,
                     help="timed solves of each other form (plain FP64, warm start); 0 skips them")

@@ -377,6 +377,9 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 /* complex64 inner iteration run in double-FP32 arithmetic on the FP32 pipe (1, the default:    */
 /* operators as (hi, lo) FP32 pairs, 2^-48 relative, forward error about κ(E_j)·2^-48) or in   */
 /* FP64 (0).  Complex128 inner solves and the direct local solve always use FP64.              */
+/* HDD_OPT_COARSE_SPIKE (7): those double-FP32 solves split each banded solve over 2 or 4 SMs   */
+/* (the SPIKE algorithm on the blocked operators, spike matrices formed at hdd_setup_deflation  */
+/* in FP64 by the host) when the active chains leave SMs free (1, the default) or not (0).     */
 /* HDD_ERR_INVALID_ARG for an unknown key or a value other than 0 or 1.  Takes effect from the  */
 /* next call that solves.                                                                       */
 #define HDD_OPT_COARSE_LOOKAHEAD 1
@@ -385,6 +388,7 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 #define HDD_OPT_OUTER_UPDATE_DF 4
 #define HDD_OPT_OUTER_DCGS2 5
 #define HDD_OPT_COARSE_DF 6
+#define HDD_OPT_COARSE_SPIKE 7
 hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value);
 
 /* ---------------------------------------------------------------------------------------- */

@@ -39,12 +39,16 @@ struct SubBox {
 
 struct FactorSet {            // banded FP64 factors of one matrix per shape, blocked solve form
     DevMem M, Mdf, P, Meta, table;  // Mdf: the operators M as (hi, lo) FP32 pairs (double-FP32 solve)
+    DevMem G, spk;                  // SPIKE plans: spike matrices (pairs), SpikeInfo level-major
+    int spike_level[SPIKE_LEVELS] = {0, 0};   // level L (P = 2, 4) available for every shape
+    int spike_levels_built = 0;
     std::vector<BlockFactor> h;
     std::vector<double> fma_col;    // FP64 FMAs of one real column by banded substitution, per shape
     BlockSolveCfg cfg;              // shared-memory plan of the blocked solve
     bool re2 = false;               // factors of real-equivalent systems (complex matrices)
     bool ready = false;
-    void clear() { M.release(); Mdf.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); cfg = BlockSolveCfg{}; re2 = false; ready = false; }
+    void clear() { G.release(); spk.release(); spike_level[0] = spike_level[1] = 0; spike_levels_built = 0;
+                   M.release(); Mdf.release(); P.release(); Meta.release(); table.release(); h.clear(); fma_col.clear(); cfg = BlockSolveCfg{}; re2 = false; ready = false; }
 };
 
 template <typename R> struct InnerWork {   // inner GMRES buffers for one precision
@@ -58,14 +62,15 @@ template <typename R> struct InnerWork {   // inner GMRES buffers for one precis
 // Kernel families timed by the profiler (CUDA events around every launch on the launching
 // stream).  bound: 0 = memory (HBM bytes), 1 = FP64 arithmetic.
 enum Fam { F_ZT, F_COARSE, F_PS, F_CGS, F_GIVENS, F_LMISC, F_OCGS, F_OMISC, F_CNN, F_OREORTH, F_STEP, F_ODF,
-           F_CGRID, F_OUDF, F_CDF, NFAM };
+           F_CGRID, F_OUDF, F_CDF, F_CSPK, NFAM };
 const char *kFamName[NFAM] = {"local_stencil_zt", "coarse_solve_fp64", "local_prolong_stencil_dots",
                               "local_cgs2_update", "local_givens_normalize", "local_misc",
                               "outer_cgs2_fp64", "outer_misc_fp64", "warm_start_cnn",
                               "outer_reorth_fp32", "local_arnoldi_step", "outer_dots_df32",
-                              "two_level_grid_coarse", "outer_update_df32", "coarse_solve_df32"};
+                              "two_level_grid_coarse", "outer_update_df32", "coarse_solve_df32",
+                              "coarse_solve_df32_spike"};
 // (2: FP32 pipe; for the double-FP32 families the flop counts are FP32 instructions)
-const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 2, 0, 2, 2};
+const int kFamBound[NFAM] = {0, 1, 0, 0, 0, 0, 1, 0, 2, 0, 0, 2, 0, 2, 2, 2};
 
 struct Prof {
     bool on = false;
@@ -157,6 +162,7 @@ struct hdd_ctx {
     OuterWork ow;
     CnnState cnn;
     DevMem tmp_a, tmp_b, tmp_c;                // staging for test hooks
+    DevMem d_alist;                            // active tasks of a SPIKE coarse solve, compacted
     int *h_counter = nullptr;                  // pinned
     DevMem d_counter;
     std::vector<double> hist;
@@ -169,6 +175,7 @@ struct hdd_ctx {
     int outer_udf = 1;                         // HDD_OPT_OUTER_UPDATE_DF
     int outer_dcgs = 1;                        // HDD_OPT_OUTER_DCGS2
     int coarse_df = 1;                         // HDD_OPT_COARSE_DF
+    int coarse_spike = 1;                      // HDD_OPT_COARSE_SPIKE
     int step_C[2] = {-1, -1};                  // fused-step cluster size per inner precision (0: off, -1: unplanned)
     size_t step_smem[2] = {0, 0};
     bool poisoned = false;                     // a device wait gave up with work in flight
@@ -253,6 +260,124 @@ hdd_status read_counter(hdd_ctx *ctx, cudaStream_t s, int *out) {
 
 // E_j (or A_j) factors for every distinct shape, FP64, on the device: banded LU with partial
 // pivoting, then the blocked solve operators.
+// ---- SPIKE plans of a factor set (the double-FP32 coarse solve split over P parts) ----------
+// Forward / backward sweeps of blocks [J0, J1) of one shape emulated in FP64 on the host with the
+// device's own block operators, for W unit window vectors at once (zero inputs): Y holds rows
+// [ybase, ybase + ny) of the sweep's vector, W values per row (row-major, row = vector index).
+static void emu_fwd_cols(const double *M, const int4 *meta, int J0, int J1, int W, long long ybase,
+                         std::vector<double> &Y) {
+    std::vector<double> acc((size_t)BNB * W);
+    for (int J = J0; J < J1; J++) {
+        const int4 mt = meta[J];
+        const int w = mt.y, Ks = op_stride(w);
+        const double *MJ = M + mt.x;
+        std::fill(acc.begin(), acc.end(), 0.0);
+        for (int r = 0; r < BNB; r++) {
+            const double *row = MJ + (size_t)r * Ks + BNB;
+            double *a = acc.data() + (size_t)r * W;
+            for (int c = 0; c < w; c++) {
+                const double mv = row[c];
+                if (mv == 0.0) continue;
+                const double *yr = Y.data() + (size_t)((long long)J * BNB - w + c - ybase) * W;
+                for (int k = 0; k < W; k++) a[k] += mv * yr[k];
+            }
+        }
+        std::copy(acc.begin(), acc.end(), Y.begin() + (size_t)((long long)J * BNB - ybase) * W);
+    }
+}
+static void emu_bwd_cols(const double *M, const int4 *meta, int J0, int J1, int W, long long xbase,
+                         std::vector<double> &X) {
+    std::vector<double> acc((size_t)BNB * W);
+    for (int J = J1 - 1; J >= J0; J--) {
+        const int4 mt = meta[J];
+        const int w = mt.w, Ks = op_stride(w);
+        const double *MJ = M + mt.z;
+        std::fill(acc.begin(), acc.end(), 0.0);
+        for (int r = 0; r < BNB; r++) {
+            const double *row = MJ + (size_t)r * Ks + BNB;
+            double *a = acc.data() + (size_t)r * W;
+            for (int c = 0; c < w; c++) {
+                const double mv = row[c];
+                if (mv == 0.0) continue;
+                const double *xr = X.data() + (size_t)((long long)(J + 1) * BNB + c - xbase) * W;
+                for (int k = 0; k < W; k++) a[k] += mv * xr[k];
+            }
+        }
+        std::copy(acc.begin(), acc.end(), X.begin() + (size_t)((long long)J * BNB - xbase) * W);
+    }
+}
+
+// Spike matrices for P = 2 and 4 (SpikeInfo): parts of equal block counts, available for a shape
+// when every part has at least max(wf, wb) + 16 rows, the last part starts before row m - wb and
+// both windows fit the kernel's staging (SPIKE_WMAX).  Gf_p[:, k] is the forward response of part
+// p to the unit value at row r_p - wf + k; Gb_p[:, k] the backward response of part p to the unit
+// value at row r_{p+1} + k (column-major, stored as (hi, lo) FP32 pairs).
+hdd_status build_spikes(hdd_ctx *ctx, FactorSet &F, const std::vector<int4> &meta, long long mo) {
+    const int ns = (int)F.h.size();
+    std::vector<double> M((size_t)std::max(mo, 1LL));
+    CK(cudaMemcpy(M.data(), F.M.p, (size_t)mo * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<SpikeInfo> tab((size_t)ns * SPIKE_LEVELS);
+    std::vector<float2> Gall;
+    auto put = [&](const std::vector<double> &Y, long long ybase, int W, long long r0, int np) {
+        const long long o = (long long)Gall.size();
+        Gall.resize(Gall.size() + (size_t)np * W);
+        for (int k = 0; k < W; k++)
+            for (int i = 0; i < np; i++) {
+                const double v = Y[(size_t)(r0 + i - ybase) * W + k];
+                const float hi = (float)v;
+                Gall[(size_t)o + (size_t)k * np + i] = make_float2(hi, (float)(v - (double)hi));
+            }
+        return o;
+    };
+    for (int L = 0; L < SPIKE_LEVELS; L++) F.spike_level[L] = 1;
+    for (int q = 0; q < ns; q++) {
+        const BlockFactor &b = F.h[q];
+        const int4 *mt = meta.data() + b.meta_off;
+        const int nbk = b.nblk, m = b.m, wf = b.wl, wb = b.wu;
+        for (int L = 0; L < SPIKE_LEVELS; L++) {
+            SpikeInfo &S = tab[(size_t)q * SPIKE_LEVELS + L];
+            std::memset(&S, 0, sizeof(S));
+            const int P = L == 0 ? 2 : 4;
+            bool ok = wf >= 1 && wb >= 1 && wf <= SPIKE_WMAX && wb <= SPIKE_WMAX;
+            for (int p = 0; p <= P; p++) S.B[p] = (int)(((long long)p * nbk) / P);
+            for (int p = 0; p < P && ok; p++)
+                if ((S.B[p + 1] - S.B[p]) * BNB < std::max(wf, wb) + BNB) ok = false;
+            if (ok && (long long)S.B[P - 1] * BNB + wb > m) ok = false;
+            if (!ok) { F.spike_level[L] = 0; continue; }
+            S.P = P; S.wf = wf; S.wb = wb;
+            for (int p = 1; p < P; p++) {             // forward spikes
+                const long long r0 = (long long)S.B[p] * BNB, r1 = (long long)S.B[p + 1] * BNB;
+                const long long ybase = r0 - wf;
+                std::vector<double> Y((size_t)(r1 - ybase) * wf, 0.0);
+                for (int k = 0; k < wf; k++) Y[(size_t)k * wf + k] = 1.0;
+                emu_fwd_cols(M.data(), mt, S.B[p], S.B[p + 1], wf, ybase, Y);
+                S.gf[p] = put(Y, ybase, wf, r0, (int)(r1 - r0));
+            }
+            for (int p = 0; p + 1 < P; p++) {         // backward spikes
+                const long long r0 = (long long)S.B[p] * BNB, r1 = (long long)S.B[p + 1] * BNB;
+                std::vector<double> X((size_t)(r1 + wb + BNB - r0) * wb, 0.0);
+                for (int k = 0; k < wb; k++)
+                    if (r1 + k < (long long)nbk * BNB) X[(size_t)(r1 + k - r0) * wb + k] = 1.0;
+                emu_bwd_cols(M.data(), mt, S.B[p], S.B[p + 1], wb, r0, X);
+                S.gb[p] = put(X, r0, wb, r0, (int)(r1 - r0));
+            }
+        }
+    }
+    F.spike_levels_built = 0;
+    for (int L = 0; L < SPIKE_LEVELS; L++) F.spike_levels_built += F.spike_level[L];
+    if (F.spike_levels_built == 0) return HDD_OK;
+    CK(F.G.ensure(std::max<size_t>(Gall.size(), 1) * sizeof(float2)));
+    CK(cudaMemcpy(F.G.p, Gall.data(), Gall.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(F.spk.ensure(tab.size() * sizeof(SpikeInfo)));
+    // level-major on the device: the table of level L is ns consecutive entries
+    std::vector<SpikeInfo> dev(tab.size());
+    for (int L = 0; L < SPIKE_LEVELS; L++)
+        for (int q = 0; q < ns; q++) dev[(size_t)L * ns + q] = tab[(size_t)q * SPIKE_LEVELS + L];
+    CK(cudaMemcpy(F.spk.p, dev.data(), dev.size() * sizeof(SpikeInfo), cudaMemcpyHostToDevice));
+    (void)ctx;
+    return HDD_OK;
+}
+
 hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s) {
     F.clear();
     const int ns = (int)ctx->shapes.size();
@@ -377,6 +502,18 @@ hdd_status build_factors(hdd_ctx *ctx, FactorSet &F, bool coarse, cudaStream_t s
     CK(F.Mdf.ensure((size_t)std::max(mo, 1LL) * sizeof(float2)));
     launch_ops_to_df(mo, F.M.as<double>(), F.Mdf.as<float2>(), s);
     CKL();
+    // SPIKE plans of the coarse factors (their double-FP32 solves), where the host emulation that
+    // forms the spike matrices stays cheap (about m·(wf² + wb²) multiply-adds per shape)
+    if (coarse && ctx->coarse_spike) {
+        CK(cudaStreamSynchronize(s));
+        double cost = 0.0;
+        for (int q = 0; q < ns; q++)
+            cost += (double)F.h[q].m * ((double)F.h[q].wl * F.h[q].wl + (double)F.h[q].wu * F.h[q].wu);
+        if (cost <= 1.5e9) {
+            hdd_status sst = build_spikes(ctx, F, meta, mo);
+            if (sst != HDD_OK) return sst;
+        }
+    }
     CK(F.table.ensure(ns * sizeof(BlockFactor)));
     CK(cudaMemcpyAsync(F.table.p, F.h.data(), ns * sizeof(BlockFactor), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -401,8 +538,36 @@ void band_solve(hdd_ctx *ctx, const FactorSet &F, const double2 *in, double2 *ou
     BlockSolveCfg cfg = F.cfg;
     cfg.lookahead = ctx->coarse_la;
     df = df && cfg.lookahead && cfg.la_ring >= 3;
+    // SPIKE: each chain split over P parts (a cluster of P CTAs) while every part still gets an
+    // SM of its own (two CTAs sharing an SM take as long as the unsplit chain); P = 4, else 2,
+    // else the one-CTA solve
+    int P = 0, lev = 0;
+    if (df && ctx->coarse_spike && F.spike_levels_built && cfg.spike_ok) {
+        const int act = nact < 0 ? nt : nact;
+        const int chains = (F.re2 ? 1 : 2) * act;      // one cluster per active chain
+        if (F.spike_level[1] && chains <= cfg.spike_cap[1]) { P = 4; lev = 1; }
+        else if (F.spike_level[0] && chains <= cfg.spike_cap[0]) { P = 2; lev = 0; }
+    }
     // double-FP32: 12 FP32 instructions per product of pairs, i.e. 6 per counted flop
-    Launch L(ctx, df ? F_CDF : F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, df ? 6.0 * fl : fl, s);
+    Launch L(ctx, P ? F_CSPK : df ? F_CDF : F_COARSE, F.re2 ? fl * 4.0 : fl * 2.0, df ? 6.0 * fl : fl, s);
+    if (P) {
+        // clusters for the active chains only: the flagged tasks compacted into a list first
+        // (a grid over every task would put the active clusters behind the inactive ones in
+        // waves of co-resident clusters)
+        const int *list = nullptr;
+        int ntl = nt;
+        if (flag && nact >= 0 && ctx->d_alist.ensure((size_t)std::max(nt, 1) * sizeof(int)) == cudaSuccess) {
+            launch_compact_flags(nt, flag, ctx->d_alist.as<int>(), s);
+            ctx->prof.launches++;
+            list = ctx->d_alist.as<int>();
+            ntl = nact;
+        }
+        if (ntl == 0) return;
+        if (launch_block_solve_spike(P, ctx->d_tasks.as<Task>(), ntl, F.table.as<BlockFactor>(), F.Mdf.as<float2>(),
+                                     F.P.as<int>(), F.Meta.as<int4>(), F.spk.as<SpikeInfo>() + (size_t)lev * F.h.size(),
+                                     F.G.as<float2>(), in, out, fine ? 1 : 0, flag, list, cfg, F.re2 ? 1 : 0, s))
+            return;
+    }
     launch_block_solve(ctx->d_tasks.as<Task>(), nt, F.table.as<BlockFactor>(), F.M.as<double>(),
                        F.P.as<int>(), F.Meta.as<int4>(), in, out, fine ? 1 : 0, flag, cfg, F.re2 ? 1 : 0, s,
                        df ? F.Mdf.as<float2>() : nullptr);
@@ -2111,6 +2276,7 @@ hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value) {
     else if (key == HDD_OPT_OUTER_UPDATE_DF) ctx->outer_udf = value;
     else if (key == HDD_OPT_OUTER_DCGS2) ctx->outer_dcgs = value;
     else if (key == HDD_OPT_COARSE_DF) ctx->coarse_df = value;
+    else if (key == HDD_OPT_COARSE_SPIKE) ctx->coarse_spike = value;
     else FAIL(HDD_ERR_INVALID_ARG, "unknown option %d", key);
     return HDD_OK;
 }

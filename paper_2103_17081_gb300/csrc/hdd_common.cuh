@@ -276,6 +276,8 @@ struct BlockSolveCfg {       // shared-memory plan of the blocked solve over a s
     int ring = 0;          // operator ring depth (4 or 2), chosen by set_block_solve_smem
     int la_ring = 0;       // ring of the look-ahead kernel (6, 4 or 3; 0 if it does not fit)
     int lookahead = 1;     // use the look-ahead kernel when la_ring > 0
+    int spike_ok = 0;      // ring of the SPIKE kernels (6, 4 or 3; 0 if none fits)
+    int spike_cap[2] = {0, 0};  // clusters of 2 / of 4 co-resident with that ring
 };
 // re2 = 0: real factors, Re and Im of the complex vector solved as two columns; re2 = 1: factors
 // of real-equivalent systems (order 2m), the complex vector read as one real column
@@ -286,6 +288,34 @@ void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes
                         int use_fine, const int *flag, const BlockSolveCfg &cfg, int re2, cudaStream_t s,
                         const float2 *Mdf = nullptr);
 void launch_ops_to_df(long long n, const double *M, float2 *Mdf, cudaStream_t s);
+
+// SPIKE partition of one factor's blocked solve (Polizzi & Sameh's SPIKE algorithm for banded
+// systems, on the blocked operators): the block range [0, nblk) split into P parts solved at
+// once by a cluster of P CTAs, each part with zero values outside it; the exact solution follows
+// from the local ones through the spike matrices of the parts' couplings:
+//   forward  y_p = g_p + Gf_p t_p,  t_p = y[r_p - wf, r_p)        (parts p >= 1),
+//   backward x_p = l_p + Gb_p h_p,  h_p = x[r_{p+1}, r_{p+1} + wb)   (parts p <= P-2),
+// with r_p = 16·B[p]; the boundary values t_p, h_p chain through the parts' boundary rows.
+constexpr int SPIKE_PMAX = 4;          // most parts
+constexpr int SPIKE_WMAX = 512;        // widest window the kernel stages (wf, wb)
+constexpr int SPIKE_LEVELS = 2;        // P = 2 and P = 4
+struct SpikeInfo {
+    int P;                             // parts (0: this level is not available for the shape)
+    int wf, wb;                        // forward / backward window widths (widest panels)
+    int B[SPIKE_PMAX + 1];             // first block of each part; B[P] = nblk
+    long long gf[SPIKE_PMAX];          // part p >= 1: offset (pairs) of Gf_p, 16·(B[p+1]-B[p]) x wf
+    long long gb[SPIKE_PMAX];          // part p <= P-2: offset of Gb_p, 16·(B[p+1]-B[p]) x wb
+};
+// The double-FP32 look-ahead solve with a cluster of P = spikes[shape].P CTAs per chain
+// (spikes: the table of the level used, one SpikeInfo per shape; G: the spike matrices as
+// (hi, lo) pairs) over the chains of the ntasks tasks list[0 .. ntasks) (list null: tasks
+// 0 .. ntasks).  Returns false (nothing launched) if the plan does not fit.
+bool launch_block_solve_spike(int P, const Task *tasks, int ntasks, const BlockFactor *shapes,
+                              const float2 *Mdf, const int *Pall, const int4 *Meta, const SpikeInfo *spikes,
+                              const float2 *G, const double2 *in, double2 *out, int use_fine, const int *flag,
+                              const int *list, const BlockSolveCfg &cfg, int re2, cudaStream_t s);
+// list[0 .. count) = indices of the nonzero flags in order (count = number of nonzero flags)
+void launch_compact_flags(int n, const int *flag, int *list, cudaStream_t s);
 cudaError_t set_block_solve_smem(BlockSolveCfg &cfg);
 
 // learned warm start (kernels_cnn.cu)

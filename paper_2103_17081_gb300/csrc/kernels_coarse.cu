@@ -979,6 +979,337 @@ k_block_solve_la_df(const Task *__restrict__ tasks, const BlockFactor *__restric
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// SPIKE form of the double-FP32 look-ahead solve (SpikeInfo, hdd_common.cuh).  One cluster of P
+// CTAs per chain; CTA p sweeps the blocks [B[p], B[p+1]) of both triangular solves with the
+// schedule of k_block_solve_la_df (8 warps: the chain in warp 0, the next block's bulk in warps
+// 1-7) and zero window values outside its part.  The parts then exchange boundary values through
+// the output vector (written before a cluster barrier) and correct:
+//   forward:  t_1 = g_0[tail], t_{q+1} = g_q[tail] + Gf_q[tail rows] t_q,  y_p = g_p + Gf_p t_p;
+//   backward: h_{P-2} = l_{P-1}[head], h_{q-1} = l_q[head] + Gb_q[head rows] h_q,  x_p = l_p + Gb_p h_p.
+// Each CTA forms the boundary chain up to its own part itself (a few small dense products), so
+// the phases need four cluster barriers.  Spike matrices are column-major per part (rows of the
+// part contiguous), so that threads over rows read them coalesced.  All arithmetic in pairs.
+// ------------------------------------------------------------------------------------------
+constexpr int SPK_T = 256;
+constexpr int SPK_BW = SPK_T / 32 - 1;    // bulk warps (7)
+constexpr int SPK_BL = 2 * SPK_BW;        // bulk lanes per row (14)
+
+__device__ __forceinline__ void spk_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+template <int RING, bool RE2>
+__global__ void __launch_bounds__(SPK_T, 1)
+k_block_solve_spike_df(const Task *__restrict__ tasks, const BlockFactor *__restrict__ shapes,
+                       const float2 *__restrict__ Mdf, const int *__restrict__ Pall,
+                       const int4 *__restrict__ Meta, const SpikeInfo *__restrict__ spikes,
+                       const float2 *__restrict__ G, const double2 *__restrict__ in,
+                       double2 *__restrict__ out, int use_fine, const int *__restrict__ flag,
+                       const int *__restrict__ list, int maxK, int cwy, int cwx, int P) {
+    static_assert(RING >= 3, "the look-ahead needs blocks J and J+1 resident while J+2 loads");
+    extern __shared__ double smd[];
+    __shared__ float2 part[2][SPK_BW][BNB];
+    __shared__ int sw[RING];
+    __shared__ float2 tb[2][SPIKE_WMAX];
+    constexpr int STR = RE2 ? 1 : 2;
+    // clusters over the active chains only (list: the active tasks in order, or null = every task)
+    const int chain = (int)blockIdx.x / P, rank = (int)blockIdx.x % P;
+    const int tl = RE2 ? chain : chain >> 1, comp = RE2 ? 0 : (chain & 1);
+    const int t = list ? list[tl] : tl;
+    if (t < 0) return;                               // past the compacted count (every CTA of the cluster)
+    if (flag && !flag[t]) return;                    // every CTA of the cluster shares the chain
+    const Task T = tasks[t];
+    const BlockFactor F = shapes[T.shape];
+    const SpikeInfo SP = spikes[T.shape];
+    const long long off = use_fine ? T.foff : T.coff;
+    const int m = F.m;
+    const int J0 = SP.B[rank], J1 = SP.B[rank + 1], nb = J1 - J0;
+    const int r0 = J0 * BNB, r1 = J1 * BNB, rend = r1 < m ? r1 : m;
+    const int slot = la_slot(maxK);
+    float2 *CY = reinterpret_cast<float2 *>(smd + RING * slot), *CX = CY + cwy;
+    const int *perm = Pall + F.perm_off;
+    const int4 *meta = Meta + F.meta_off;
+    const double *inr = reinterpret_cast<const double *>(in + off) + comp;
+    double *outr = reinterpret_cast<double *>(out + off) + comp;
+    float2 *od = reinterpret_cast<float2 *>(outr);   // entries as (hi, lo) pairs during the solve
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = lane >> 1, half = lane & 1;
+    const int q = (warp - 1) * 2 + half;
+    const int bt = tid - 32;
+    auto load_block = [&](long long src_off, int K, int buf, int J) {
+        if (bt < 0) return;
+        double *dst = smd + buf * slot;
+        const float2 *src = Mdf + src_off;
+        const int nchunk = BNB * K / 2;
+        for (int c = bt; c < nchunk; c += SPK_T - 32) cp_async16(dst + 2 * c, src + 2 * c);
+        if (bt < BNB) {
+            const int i = J * BNB + bt;
+            cp_async8_zfill(dst + BNB * maxK + bt, i < m ? outr + STR * (long long)i : outr, i < m ? 8 : 0);
+        }
+    };
+    for (int i = r0 + tid; i < rend; i += SPK_T) od[STR * (long long)i] = df_split(inr[STR * (long long)perm[i]]);
+    for (int i = tid; i < cwy; i += SPK_T) CY[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < cwx; i += SPK_T) CX[i] = make_float2(0.f, 0.f);
+    __threadfence_block();
+    __syncthreads();
+
+    auto bulk_row = [&](const double *sp, int K, int k0, int k1, const float2 *win, int pbase, int mask) {
+        const float2 *Mr = reinterpret_cast<const float2 *>(sp) + row * K;
+        const float2 *a = reinterpret_cast<const float2 *>(sp + BNB * maxK);
+        float sh = 0.f, sl = 0.f;
+        int k = q;
+        for (; k < BNB; k += SPK_BL) {
+            const float2 mk = Mr[k], x = a[k];
+            df_acc(sh, sl, mk.x, mk.y, x.x, x.y);
+        }
+        if (k < k0) k += ((k0 - k + SPK_BL - 1) / SPK_BL) * SPK_BL;
+        for (; k < k1; k += SPK_BL) {
+            const float2 mk = Mr[k], x = win[(pbase + k - BNB) & mask];
+            df_acc(sh, sl, mk.x, mk.y, x.x, x.y);
+        }
+        const float oh = __shfl_xor_sync(0xffffffffu, sh, 1), ol = __shfl_xor_sync(0xffffffffu, sl, 1);
+        df_add(sh, sl, oh, ol);
+        return make_float2(sh, sl);
+    };
+    auto chain_row = [&](const double *sp, int K, int p0, int p1, const float2 *win, int pbase, int mask,
+                         int par) {
+        const float2 *Mr = reinterpret_cast<const float2 *>(sp) + row * K + BNB;
+        // lane half 0 seeds with the partials of bulk warps 0, 2, 4, 6; half 1 with 1, 3, 5
+        float2 a0 = part[par][half][row], a1 = part[par][half + 2][row], a2 = part[par][half + 4][row];
+        float2 a3 = half == 0 ? part[par][6][row] : make_float2(0.f, 0.f);
+        auto madd = [&](float2 &acc, int p) {
+            const float2 mk = Mr[p], x = win[(pbase + p) & mask];
+            df_acc(acc.x, acc.y, mk.x, mk.y, x.x, x.y);
+        };
+        int p = p0 + half;
+        for (; p + 6 < p1; p += 8) { madd(a0, p); madd(a1, p + 2); madd(a2, p + 4); madd(a3, p + 6); }
+        if (p < p1) madd(a0, p);
+        if (p + 2 < p1) madd(a1, p + 2);
+        if (p + 4 < p1) madd(a2, p + 4);
+        df_add(a0.x, a0.y, a1.x, a1.y);
+        df_add(a2.x, a2.y, a3.x, a3.y);
+        df_add(a0.x, a0.y, a2.x, a2.y);
+        const float oh = __shfl_xor_sync(0xffffffffu, a0.x, 1), ol = __shfl_xor_sync(0xffffffffu, a0.y, 1);
+        df_add(a0.x, a0.y, oh, ol);
+        return a0;
+    };
+
+    // acc += Σ_{k<n} g[k·ld] x[k] in pairs, the spike entries loaded eight at a time ahead of
+    // their arithmetic (they come from L2; one dependent sum would wait on every load)
+    auto gdot = [&](float2 acc, const float2 *g, long long ld, const float2 *x, int n) {
+        int k = 0;
+        for (; k + 8 <= n; k += 8) {
+            float2 gv[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) gv[u] = g[(long long)(k + u) * ld];
+#pragma unroll
+            for (int u = 0; u < 8; u++) df_acc(acc.x, acc.y, gv[u].x, gv[u].y, x[k + u].x, x[k + u].y);
+        }
+        for (; k < n; k++) {
+            const float2 gv = g[(long long)k * ld];
+            df_acc(acc.x, acc.y, gv.x, gv.y, x[k].x, x[k].y);
+        }
+        return acc;
+    };
+
+    // ---- forward local sweep over the part's blocks: g_p (window values below r0 are zero) ----
+    int4 mq0 = make_int4(0, 0, 0, 0), mq1 = mq0, mq2 = mq0;
+#pragma unroll
+    for (int u = 0; u < RING - 1; u++) {
+        if (u < nb) {
+            const int4 mt = meta[J0 + u];
+            load_block(mt.x, op_stride(mt.y), u, J0 + u);
+            if (tid == 32) sw[u] = mt.y;
+        }
+        cp_async_commit();
+    }
+    if (RING - 1 < nb) mq0 = meta[J0 + RING - 1];
+    if (RING < nb) mq1 = meta[J0 + RING];
+    if (RING + 1 < nb) mq2 = meta[J0 + RING + 1];
+    cp_async_wait_n<RING - 2>();
+    __syncthreads();
+    if (warp > 0) {
+        const int w0 = sw[0], nold = w0 > BNB ? w0 - BNB : 0;
+        const float2 v = bulk_row(smd, op_stride(w0), BNB, BNB + nold, CY, r0 - w0, cwy - 1);
+        if (half == 0) part[0][warp - 1][row] = v;
+    }
+    for (int k = 0; k < nb; k++) {
+        const int J = J0 + k;
+        cp_async_wait_n<RING - 3>();
+        __syncthreads();
+        if (k + RING - 1 < nb) {
+            const int buf = (k + RING - 1) % RING;
+            load_block(mq0.x, op_stride(mq0.y), buf, J + RING - 1);
+            if (tid == 32) sw[buf] = mq0.y;
+        }
+        cp_async_commit();
+        mq0 = mq1; mq1 = mq2;
+        if (k + RING + 2 < nb) mq2 = meta[J + RING + 2];
+        if (warp == 0) {
+            const int wJ = sw[k % RING];
+            const int p0 = wJ > BNB ? wJ - BNB : 0;
+            const float2 v = chain_row(smd + (k % RING) * slot, op_stride(wJ), p0, wJ, CY, J * BNB - wJ, cwy - 1, k & 1);
+            if (half == 0) {
+                const int i = J * BNB + row;
+                CY[i & (cwy - 1)] = v;
+                if (i < m) od[STR * (long long)i] = v;
+            }
+        } else if (k + 1 < nb) {
+            const int kn = k + 1, Jn = J + 1, w1 = sw[kn % RING], nold = w1 > BNB ? w1 - BNB : 0;
+            const float2 v = bulk_row(smd + (kn % RING) * slot, op_stride(w1), BNB, BNB + nold, CY, Jn * BNB - w1, cwy - 1);
+            if (half == 0) part[kn & 1][warp - 1][row] = v;
+        }
+    }
+    cp_async_wait_n<0>();
+    __threadfence();
+    __syncthreads();
+    spk_cluster_sync();                              // (1) every part's g is written
+
+    // ---- forward boundary values t_rank (parts >= 1) from the parts' local solutions ----
+    const int wf = SP.wf, wb = SP.wb;
+    float2 *tcur = tb[0], *tnext = tb[1];
+    if (rank >= 1) {
+        const int ra = SP.B[1] * BNB - wf;            // tail rows of part 0: [r_1 - wf, r_1)
+        for (int k = tid; k < wf; k += SPK_T) tcur[k] = od[STR * (long long)(ra + k)];
+        __syncthreads();
+        for (int qq = 1; qq < rank; qq++) {           // t_{qq+1} = g_qq[tail] + Gf_qq[tail rows] t_qq
+            const int rq = SP.B[qq] * BNB, nq = (SP.B[qq + 1] - SP.B[qq]) * BNB;
+            const float2 *Gq = G + SP.gf[qq];
+            for (int kk = tid; kk < wf; kk += SPK_T) {
+                const int il = nq - wf + kk;          // local row of the tail entry
+                tnext[kk] = gdot(od[STR * (long long)(rq + il)], Gq + il, nq, tcur, wf);
+            }
+            __syncthreads();
+            float2 *sx = tcur; tcur = tnext; tnext = sx;
+        }
+    }
+    spk_cluster_sync();                              // (2) every part has read the g it needs
+    if (rank >= 1) {                                 // y_p = g_p + Gf_p t_p
+        const int np = r1 - r0;
+        const float2 *Gp = G + SP.gf[rank];
+        for (int i = r0 + tid; i < rend; i += SPK_T)
+            od[STR * (long long)i] = gdot(od[STR * (long long)i], Gp + (i - r0), np, tcur, wf);
+    }
+    __threadfence_block();
+    __syncthreads();
+
+    // ---- backward local sweep: l_p (window values from r1 on are zero) ----
+#pragma unroll
+    for (int u = 0; u < RING - 1; u++) {
+        const int J = J1 - 1 - u;
+        if (J >= J0) {
+            const int4 mt = meta[J];
+            load_block(mt.z, op_stride(mt.w), u, J);
+            if (tid == 32) sw[u] = mt.w;
+        }
+        cp_async_commit();
+    }
+    mq0 = J1 - RING >= J0 ? meta[J1 - RING] : make_int4(0, 0, 0, 0);
+    mq1 = J1 - RING - 1 >= J0 ? meta[J1 - RING - 1] : make_int4(0, 0, 0, 0);
+    mq2 = J1 - RING - 2 >= J0 ? meta[J1 - RING - 2] : make_int4(0, 0, 0, 0);
+    cp_async_wait_n<RING - 2>();
+    __syncthreads();
+    if (warp > 0) {
+        const int w0 = sw[0];
+        const float2 v = bulk_row(smd, op_stride(w0), 2 * BNB, BNB + w0, CX, r1, cwx - 1);
+        if (half == 0) part[0][warp - 1][row] = v;
+    }
+    for (int k = 0; k < nb; k++) {
+        const int J = J1 - 1 - k;
+        cp_async_wait_n<RING - 3>();
+        __syncthreads();
+        if (J - (RING - 1) >= J0) {
+            const int buf = (k + RING - 1) % RING;
+            load_block(mq0.z, op_stride(mq0.w), buf, J - (RING - 1));
+            if (tid == 32) sw[buf] = mq0.w;
+        }
+        cp_async_commit();
+        mq0 = mq1; mq1 = mq2;
+        if (J - RING - 2 >= J0) mq2 = meta[J - RING - 2];
+        if (warp == 0) {
+            const int wJ = sw[k % RING];
+            const float2 v = chain_row(smd + (k % RING) * slot, op_stride(wJ), 0, wJ < BNB ? wJ : BNB, CX,
+                                       (J + 1) * BNB, cwx - 1, k & 1);
+            if (half == 0) {
+                const int i = J * BNB + row;
+                CX[i & (cwx - 1)] = v;
+                if (i < m) od[STR * (long long)i] = v;
+            }
+        } else if (J - 1 >= J0) {
+            const int kn = k + 1, Jn = J - 1, w1 = sw[kn % RING];
+            const float2 v = bulk_row(smd + (kn % RING) * slot, op_stride(w1), 2 * BNB, BNB + w1, CX, (Jn + 1) * BNB,
+                                      cwx - 1);
+            if (half == 0) part[kn & 1][warp - 1][row] = v;
+        }
+    }
+    cp_async_wait_n<0>();
+    __threadfence();
+    __syncthreads();
+    spk_cluster_sync();                              // (3) every part's l is written
+
+    // ---- backward boundary values h_rank (parts <= P-2) ----
+    if (rank <= P - 2) {
+        const int ra = SP.B[P - 1] * BNB;             // head rows of the last part (final as solved)
+        for (int k = tid; k < wb; k += SPK_T)
+            tcur[k] = ra + k < m ? od[STR * (long long)(ra + k)] : make_float2(0.f, 0.f);
+        __syncthreads();
+        for (int qq = P - 2; qq > rank; qq--) {       // h_{qq-1} = l_qq[head] + Gb_qq[head rows] h_qq
+            const int rq = SP.B[qq] * BNB, nq = (SP.B[qq + 1] - SP.B[qq]) * BNB;
+            const float2 *Gq = G + SP.gb[qq];
+            for (int kk = tid; kk < wb; kk += SPK_T) {
+                tnext[kk] = gdot(od[STR * (long long)(rq + kk)], Gq + kk, nq, tcur, wb);
+            }
+            __syncthreads();
+            float2 *sx = tcur; tcur = tnext; tnext = sx;
+        }
+    }
+    spk_cluster_sync();                              // (4) every part has read the l it needs
+    if (rank <= P - 2) {                             // x_p = l_p + Gb_p h_p
+        const int np = r1 - r0;
+        const float2 *Gp = G + SP.gb[rank];
+        for (int i = r0 + tid; i < rend; i += SPK_T)
+            od[STR * (long long)i] = gdot(od[STR * (long long)i], Gp + (i - r0), np, tcur, wb);
+    }
+    __syncthreads();
+    for (int i = r0 + tid; i < rend; i += SPK_T) {
+        const float2 v = od[STR * (long long)i];
+        outr[STR * (long long)i] = (double)v.x + (double)v.y;
+    }
+}
+
+// list[0 .. count) = the indices i < n with flag[i] != 0, in increasing order, list[count .. n) =
+// -1 (one CTA of 1024 threads: ballots within warps, a scan of the warp counts per chunk)
+__global__ void __launch_bounds__(1024) k_compact_flags(int n, const int *__restrict__ flag, int *__restrict__ list) {
+    __shared__ int wc[32];
+    __shared__ int base_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) base_s = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += 1024) {
+        const int i = c0 + tid;
+        const bool on = i < n && flag[i] != 0;
+        const unsigned b = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) wc[warp] = __popc(b);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < 32; w++) {
+            if (w < warp) before += wc[w];
+            total += wc[w];
+        }
+        const int base = base_s;
+        if (on) list[base + before + __popc(b & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        if (tid == 0) base_s = base + total;
+        __syncthreads();
+    }
+    for (int i = base_s + tid; i < n; i += 1024) list[i] = -1;      // past the count: no task
+}
+void launch_compact_flags(int n, const int *flag, int *list, cudaStream_t s) {
+    k_compact_flags<<<1, 1024, 0, s>>>(n, flag, list);
+}
+
 __global__ void k_ops_to_df(long long n, const double *__restrict__ M, float2 *__restrict__ Mdf) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         Mdf[i] = df_split(M[i]);
@@ -1091,6 +1422,61 @@ void launch_block_solve(const Task *tasks, int ntasks, const BlockFactor *shapes
                                                                         use_fine, flag, c.maxK, c.cwy, c.cwx);
 }
 
+// SPIKE launches: clusters of P CTAs, one CTA per SM, the ring of the look-ahead kernel (6, 4 or 3)
+template <int RING, bool RE2>
+static cudaError_t spk_launch(int P, int grid, const BlockSolveCfg &c, const Task *tasks, const BlockFactor *shapes,
+                              const float2 *Mdf, const int *Pall, const int4 *Meta, const SpikeInfo *spikes,
+                              const float2 *G, const double2 *in, double2 *out, int use_fine, const int *flag,
+                              const int *list, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(SPK_T);
+    cfg.dynamicSmemBytes = la_smem(c, RING);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_block_solve_spike_df<RING, RE2>, tasks, shapes, Mdf, Pall, Meta, spikes, G, in,
+                              out, use_fine, flag, list, c.maxK, c.cwy, c.cwx, P);
+}
+template <bool RE2>
+static cudaError_t spk_launch_ring(int P, int grid, const BlockSolveCfg &c, const Task *tasks,
+                                   const BlockFactor *shapes, const float2 *Mdf, const int *Pall, const int4 *Meta,
+                                   const SpikeInfo *spikes, const float2 *G, const double2 *in, double2 *out,
+                                   int use_fine, const int *flag, const int *list, cudaStream_t s) {
+    if (c.spike_ok >= 6)
+        return spk_launch<6, RE2>(P, grid, c, tasks, shapes, Mdf, Pall, Meta, spikes, G, in, out, use_fine, flag, list, s);
+    if (c.spike_ok >= 4)
+        return spk_launch<4, RE2>(P, grid, c, tasks, shapes, Mdf, Pall, Meta, spikes, G, in, out, use_fine, flag, list, s);
+    return spk_launch<3, RE2>(P, grid, c, tasks, shapes, Mdf, Pall, Meta, spikes, G, in, out, use_fine, flag, list, s);
+}
+
+bool launch_block_solve_spike(int P, const Task *tasks, int ntasks, const BlockFactor *shapes,
+                              const float2 *Mdf, const int *Pall, const int4 *Meta, const SpikeInfo *spikes,
+                              const float2 *G, const double2 *in, double2 *out, int use_fine, const int *flag,
+                              const int *list, const BlockSolveCfg &c, int re2, cudaStream_t s) {
+    if (P < 2 || P > SPIKE_PMAX || !c.spike_ok || ntasks < 1) return false;
+    const int chains = re2 ? ntasks : 2 * ntasks;
+    const cudaError_t e = re2 ? spk_launch_ring<true>(P, chains * P, c, tasks, shapes, Mdf, Pall, Meta, spikes, G, in,
+                                                      out, use_fine, flag, list, s)
+                              : spk_launch_ring<false>(P, chains * P, c, tasks, shapes, Mdf, Pall, Meta, spikes, G, in,
+                                                       out, use_fine, flag, list, s);
+    if (e != cudaSuccess) cudaGetLastError();      // a refused launch configuration: the caller falls back
+    return e == cudaSuccess;
+}
+
+template <int RING, bool RE2> static cudaError_t spk_attr(size_t lim, size_t &static_bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_block_solve_spike_df<RING, RE2>);
+    if (e != cudaSuccess) return e;
+    static_bytes = std::max(static_bytes, a.sharedSizeBytes);
+    return cudaFuncSetAttribute(k_block_solve_spike_df<RING, RE2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(lim - a.sharedSizeBytes));
+}
 template <int RING, bool RE2> static cudaError_t la_attr(size_t lim, size_t &static_bytes) {
     cudaFuncAttributes a, b;
     cudaError_t e = cudaFuncGetAttributes(&a, k_block_solve_la<RING, RE2>);
@@ -1138,6 +1524,41 @@ cudaError_t set_block_solve_smem(BlockSolveCfg &c) {
     c.la_ring = 0;
     for (int r : {6, 4, 3})
         if (la_smem(c, r) + st <= lim) { c.la_ring = r; break; }
+    // the SPIKE kernels (one CTA per SM): the deepest ring of 6, 4, 3 that fits (spike_ok = ring)
+    size_t sst = 0;
+    if ((e = spk_attr<6, false>(lim, sst)) != cudaSuccess) return e;
+    if ((e = spk_attr<6, true>(lim, sst)) != cudaSuccess) return e;
+    if ((e = spk_attr<4, false>(lim, sst)) != cudaSuccess) return e;
+    if ((e = spk_attr<4, true>(lim, sst)) != cudaSuccess) return e;
+    if ((e = spk_attr<3, false>(lim, sst)) != cudaSuccess) return e;
+    if ((e = spk_attr<3, true>(lim, sst)) != cudaSuccess) return e;
+    c.spike_ok = 0;
+    for (int r : {6, 4, 3})
+        if (la_smem(c, r) + sst <= lim) { c.spike_ok = r; break; }
+    // clusters of 2 and of 4 the device co-schedules with that ring (a cluster lives in one GPC,
+    // so this is below #SMs / P): more active chains than this would run in a second wave
+    c.spike_cap[0] = c.spike_cap[1] = 0;
+    if (c.spike_ok) {
+        for (int L = 0; L < 2; L++) {
+            cudaLaunchConfig_t cf = {};
+            cf.gridDim = dim3(L == 0 ? 2u : 4u);
+            cf.blockDim = dim3(SPK_T);
+            cf.dynamicSmemBytes = la_smem(c, c.spike_ok);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = L == 0 ? 2u : 4u;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cf.attrs = at;
+            cf.numAttrs = 1;
+            int n = 0;
+            const cudaError_t qe = c.spike_ok >= 6 ? cudaOccupancyMaxActiveClusters(&n, k_block_solve_spike_df<6, false>, &cf)
+                                 : c.spike_ok >= 4 ? cudaOccupancyMaxActiveClusters(&n, k_block_solve_spike_df<4, false>, &cf)
+                                                   : cudaOccupancyMaxActiveClusters(&n, k_block_solve_spike_df<3, false>, &cf);
+            if (qe != cudaSuccess) { cudaGetLastError(); n = 0; }
+            c.spike_cap[L] = n;
+        }
+    }
     return cudaSuccess;
 }
 
