@@ -380,6 +380,13 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 /* HDD_OPT_COARSE_SPIKE (7): those double-FP32 solves split each banded solve over 2 or 4 SMs   */
 /* (the SPIKE algorithm on the blocked operators, spike matrices formed at hdd_setup_deflation  */
 /* in FP64 by the host) when the active chains leave SMs free (1, the default) or not (0).     */
+/* HDD_OPT_OUTER_DOTS_BIASED (8): with delayed CGS2, the first-pass dot products V^H w of its  */
+/* fused pass keep every high accumulator offset by a power of two above four times the sum    */
+/* it will take (bounded from the largest |entry| of each basis vector and of the chunk of w), */
+/* so one fma and one exact subtraction replace the two-sum: a quarter fewer FP32 instructions */
+/* in the pass, those dots within a few 1e-12 of Σ|v w| instead of about 1e-15 (1, the        */
+/* default: the delayed second pass, which keeps the two-sum, measures and removes what the   */
+/* first pass left) or the two-sum for both (0).                                              */
 /* HDD_ERR_INVALID_ARG for an unknown key or a value other than 0 or 1.  Takes effect from the  */
 /* next call that solves.                                                                       */
 #define HDD_OPT_COARSE_LOOKAHEAD 1
@@ -389,6 +396,7 @@ long long hdd_launch_count(const hdd_ctx *ctx);
 #define HDD_OPT_OUTER_DCGS2 5
 #define HDD_OPT_COARSE_DF 6
 #define HDD_OPT_COARSE_SPIKE 7
+#define HDD_OPT_OUTER_DOTS_BIASED 8
 hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value);
 
 /* ---------------------------------------------------------------------------------------- */

@@ -119,6 +119,7 @@ struct OuterWork {
     DevMem V, V32, V32L, D, Z, w, r, H, cs, sn, g, Wq, h1, h2, part, npart, npart1, hn, flag, hist, beta, y, fnorm, act, kcols;
     DevMem fallbacks;
     DevMem part2, invs, err, close;             // delayed CGS2: second dot partials, 1/σ, breakdown, end-of-cycle mask
+    DevMem vmax;                                // delayed CGS2: max |hi part| per basis slot (bias of the dots)
 };
 
 }  // namespace
@@ -176,6 +177,7 @@ struct hdd_ctx {
     int outer_dcgs = 1;                        // HDD_OPT_OUTER_DCGS2
     int coarse_df = 1;                         // HDD_OPT_COARSE_DF
     int coarse_spike = 1;                      // HDD_OPT_COARSE_SPIKE
+    int outer_bias = 1;                        // HDD_OPT_OUTER_DOTS_BIASED
     int step_C[2] = {-1, -1};                  // fused-step cluster size per inner precision (0: off, -1: unplanned)
     size_t step_smem[2] = {0, 0};
     bool poisoned = false;                     // a device wait gave up with work in flight
@@ -1747,6 +1749,7 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
     if (dc) {
         CK(O.part2.ensure((size_t)nr * G * ldp * sizeof(double2)));
         CK(O.invs.ensure(nr * sizeof(double)));
+        CK(O.vmax.ensure((size_t)nr * ldp * sizeof(unsigned)));
         CK(O.err.ensure(sizeof(int)));
         CK(O.close.ensure(nr * sizeof(int)));
         CK(O.npart1.ensure((size_t)nr * std::max(std::max(G, Gu), Gc) * sizeof(double)));
@@ -1847,23 +1850,27 @@ hdd_status hdd_solve(hdd_ctx *ctx, const void *f_dev, void *x_dev, const hdd_sol
                        launch_odots_df(Bd, V32, V32L, 1, w, O.part.as<double2>(), s));
                     KL(F_OMISC, 0, 0, launch_oreduce(Bd, O.part.as<double2>(), 1, P2, s));
                 } else {
-                    KL(F_ODF, fa * (nv * 16 + 32) * n, fa * 96 * nv * n,
-                       launch_odots2_df(B, V32, V32L, j + 1, V32 + (long long)j * B.ld32, V32L + (long long)j * B.ld32,
-                                        w, O.part.as<double2>(), O.part2.as<double2>(), s));
+                    // two compensated complex dot products per basis vector and element: 96 FP32
+                    // instructions with the two-sum, 72 with the first pass's biased accumulators
+                    KL(F_ODF, fa * (nv * 16 + 32) * n, fa * (ctx->outer_bias ? 72 : 96) * nv * n,
+                       CK(launch_odots2_df(B, V32, V32L, j + 1, V32 + (long long)j * B.ld32,
+                                           V32L + (long long)j * B.ld32, w, O.part.as<double2>(),
+                                           O.part2.as<double2>(), O.vmax.as<unsigned>(), ctx->outer_bias, s)));
                     KL(F_OMISC, 0, 0, launch_oreduce(B, O.part.as<double2>(), j + 1, P1, s));
                     KL(F_OMISC, 0, 0, launch_oreduce(B, O.part2.as<double2>(), j + 1, P2, s));
                 }
                 KL(F_OMISC, 0, 0,
                    launch_dcgs_col(B, O.H.as<double2>(), O.cs.as<double>(), O.sn.as<double2>(), O.g.as<double2>(),
                                    O.Wq.as<double2>(), j, P1, P2, O.hn.as<double>(), O.invs.as<double>(),
-                                   O.fnorm.as<double>(), O.hist.as<double>(), hstride, total, O.err.as<int>(), s));
+                                   O.fnorm.as<double>(), O.hist.as<double>(), hstride, total, O.err.as<int>(),
+                                   O.vmax.as<unsigned>(), s));
                 // bytes: hi/lo of slots 0..j-1, slot j read and rewritten (FP64, Re - Im, hi/lo), w
                 // read and written; ≈ 56 FP32 instructions per basis vector and element
                 KL(F_OUDF, fa * ((nv - 1) * 16 + 16 + 40 + 32) * n, fa * 56 * (nv - 1) * n,
                    launch_oupdate_dcgs(B, V32, V32L, j, j > 0 ? 1 : 0, V + (long long)j * B.ld,
                                        O.D.as<double>() + (long long)j * B.ld, V32 + (long long)j * B.ld32,
                                        V32L + (long long)j * B.ld32, P1, P2, O.invs.as<double>(), w,
-                                       O.npart1.as<double>(), s));
+                                       O.npart1.as<double>(), O.vmax.as<unsigned>(), s));
                 KL(F_OMISC, 0, 0,
                    launch_dcgs_tent(B, O.H.as<double2>(), O.g.as<double2>(), O.Wq.as<double2>(), j,
                                     O.npart1.as<double>(), Gc, O.fnorm.as<double>(), prm->outer_tol,
@@ -2277,6 +2284,7 @@ hdd_status hdd_set_option(hdd_ctx *ctx, int key, int value) {
     else if (key == HDD_OPT_OUTER_DCGS2) ctx->outer_dcgs = value;
     else if (key == HDD_OPT_COARSE_DF) ctx->coarse_df = value;
     else if (key == HDD_OPT_COARSE_SPIKE) ctx->coarse_spike = value;
+    else if (key == HDD_OPT_OUTER_DOTS_BIASED) ctx->outer_bias = value;
     else FAIL(HDD_ERR_INVALID_ARG, "unknown option %d", key);
     return HDD_OK;
 }

@@ -37,6 +37,28 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, float xh, float xl,
     sl = __fadd_rn(sl, __fadd_rn(err, c));
 }
 
+// The same sum with a biased high accumulator (6 instructions instead of 12).  sh starts at a
+// power of two M >= 4 Σ|xh·yh| over every product the accumulator will take, so it stays within
+// [3M/4, 5M/4]: t = fl(sh + xh·yh) (one fma) and q = t - sh is exact (Sterbenz), and the part of
+// the product that t did not absorb, xh·yh - q, is formed by a second fma and added to sl with
+// the cross terms.  That remainder is below ulp(M) and is itself rounded once (error <= 2^-24
+// ulp(M)), so a sum of T products carries at most about T·2^-47·M more error than df_acc, i.e.
+// a few 1e-12 of T·max|xh|·max|yh| when M is the bound's power of two.  The caller subtracts M
+// (exact) when it is done.
+__device__ __forceinline__ void df_acc_biased(float &sh, float &sl, float xh, float xl, float yh, float yl) {
+    const float t = fmaf(xh, yh, sh);
+    const float q = __fsub_rn(t, sh);
+    sl = __fadd_rn(sl, fmaf(xh, yh, -q));
+    sl = fmaf(xh, yl, sl);
+    sl = fmaf(xl, yh, sl);
+    sh = t;
+}
+// smallest power of two >= max(y, 2^-100) for finite y >= 0 (the bias M of df_acc_biased)
+__device__ __forceinline__ float pow2_ceil(float y) {
+    y = fmaxf(y, 0x1p-100f);
+    return __uint_as_float((__float_as_uint(y) + 0x007FFFFFu) & 0xFF800000u);
+}
+
 // (sh, sl) += (bh, bl): two-sum of the high parts, the low parts added
 __device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl) {
     const float t = __fadd_rn(sh, bh);
@@ -377,11 +399,12 @@ void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, i
 int oupdate_df_grid(long long n);
 // delayed CGS2: fused dots of the pending vector and w, per-RHS coefficient kernels, fused update
 int oupdate_dcgs_grid(long long n);
-void launch_odots2_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const float2 *x1h,
-                      const float2 *x1l, const double2 *w, double2 *part1, double2 *part2, cudaStream_t s);
+cudaError_t launch_odots2_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const float2 *x1h,
+                             const float2 *x1l, const double2 *w, double2 *part1, double2 *part2,
+                             const unsigned *vmax, int bias, cudaStream_t s);
 void launch_dcgs_col(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,
                      const double2 *P1, double2 *P2, const double *hn, double *invs, const double *fnorm,
-                     double *hist, int hstride, int it, int *err, cudaStream_t s);
+                     double *hist, int hstride, int it, int *err, unsigned *vmax, cudaStream_t s);
 void launch_dcgs_tent(const OuterBatch &B, double2 *H, double2 *g, double2 *Wq, int j, const double *npart, int gp,
                       const double *fnorm, double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
                       cudaStream_t s);
@@ -389,7 +412,7 @@ void launch_dcgs_close(const OuterBatch &B, double2 *H, double *cs, double2 *sn,
                        const int *close, cudaStream_t s);
 void launch_oupdate_dcgs(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int j, int corr, double2 *Vj,
                          double *Dj, float2 *Vjh, float2 *Vjl, const double2 *acoef, const double2 *bcoef,
-                         const double *invs, double2 *w, double *part_norm, cudaStream_t s);
+                         const double *invs, double2 *w, double *part_norm, unsigned *vmax, cudaStream_t s);
 void launch_oupdate_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const double2 *h,
                        double2 *w, double *part_norm, cudaStream_t s);
 void launch_fill_test(long long n, unsigned long long seed, double2 *x, cudaStream_t s);

@@ -696,29 +696,50 @@ k_ogivens(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs, double
 
 // Warp q forms the partial dots of vectors l = q, q + 8, ... with the two staged vectors s1, s2
 // (double-FP32, as warp_dots_df; four element groups per pass, the next group's basis loads
-// issued before the current group's arithmetic).
+// issued before the current group's arithmetic).  BIAS: the dots with w (s2, the first pass of
+// the new vector) take the biased sums of df_acc_biased (6 FP32 instructions per product instead
+// of 12).  Their error (a few 1e-12 of Σ|v w| instead of about 1e-15) needs no care: the first
+// pass only has to leave w' nearly orthogonal to V, and the delayed second pass measures what it
+// left, V^H ṽ, exactly and adds it to the column (the Arnoldi relation w = V h + ν σ v holds
+// whatever the first-pass coefficients were).  The dots with s1 (that second pass, which sets
+// the orthogonality of the basis) keep the two-sum.  The bias of vector l is the power of two
+// M >= 4·T·vm_l·xm, T = 2·(len/128 + 4) the products one accumulator takes (len/128 whole
+// groups plus at most four tail elements, two products each per component), vm_l >= |hi part|
+// of every entry of V_l (vms[l] for the final slots, recorded by the update that wrote them; the
+// chunk maximum of s1 for the last slot, which is s1) and xm the chunk maximum of w's hi parts.
+template <bool BIAS>
 __device__ __forceinline__ void warp_dots2_df(const float2 *__restrict__ Vh, const float2 *__restrict__ Vl,
                                               long long ld32, int nv, const float4 *__restrict__ s1,
                                               const float4 *__restrict__ s2, long long b, int len,
-                                              double2 *__restrict__ part1, double2 *__restrict__ part2, int ldp) {
+                                              double2 *__restrict__ part1, double2 *__restrict__ part2, int ldp,
+                                              const float *__restrict__ vms, float xm1, float xm2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float Tb = 4.001f * (float)(2 * ((len >> 7) + 4));
     for (int l = warp; l < nv; l += OT / 32) {
         const float2 *hp = Vh + (long long)l * ld32 + b, *lp = Vl + (long long)l * ld32 + b;
+        const float M2 = BIAS ? pow2_ceil(Tb * (l < nv - 1 ? vms[l] : xm1) * xm2) : 0.f;
         float ah[4][2], al[4][2], bh[4][2], bl[4][2];
 #pragma unroll
         for (int u = 0; u < 4; u++)
 #pragma unroll
-            for (int c = 0; c < 2; c++) ah[u][c] = al[u][c] = bh[u][c] = bl[u][c] = 0.f;
+            for (int c = 0; c < 2; c++) { ah[u][c] = al[u][c] = bl[u][c] = 0.f; bh[u][c] = M2; }
+        auto acc1 = [](float &sh, float &sl, float xh, float xl, float yh, float yl) {
+            df_acc(sh, sl, xh, xl, yh, yl);
+        };
+        auto acc2 = [](float &sh, float &sl, float xh, float xl, float yh, float yl) {
+            if (BIAS) df_acc_biased(sh, sl, xh, xl, yh, yl);
+            else df_acc(sh, sl, xh, xl, yh, yl);
+        };
         auto step = [&](int u, float2 h, float2 q, float4 x, float4 y) {
             // conj(v)·x = (vr xr + vi xi) + i (vr xi - vi xr), the same for y
-            df_acc(ah[u][0], al[u][0], h.x, q.x, x.x, x.y);
-            df_acc(ah[u][1], al[u][1], h.x, q.x, x.z, x.w);
-            df_acc(ah[u][0], al[u][0], h.y, q.y, x.z, x.w);
-            df_acc(ah[u][1], al[u][1], -h.y, -q.y, x.x, x.y);
-            df_acc(bh[u][0], bl[u][0], h.x, q.x, y.x, y.y);
-            df_acc(bh[u][1], bl[u][1], h.x, q.x, y.z, y.w);
-            df_acc(bh[u][0], bl[u][0], h.y, q.y, y.z, y.w);
-            df_acc(bh[u][1], bl[u][1], -h.y, -q.y, y.x, y.y);
+            acc1(ah[u][0], al[u][0], h.x, q.x, x.x, x.y);
+            acc1(ah[u][1], al[u][1], h.x, q.x, x.z, x.w);
+            acc1(ah[u][0], al[u][0], h.y, q.y, x.z, x.w);
+            acc1(ah[u][1], al[u][1], -h.y, -q.y, x.x, x.y);
+            acc2(bh[u][0], bl[u][0], h.x, q.x, y.x, y.y);
+            acc2(bh[u][1], bl[u][1], h.x, q.x, y.z, y.w);
+            acc2(bh[u][0], bl[u][0], h.y, q.y, y.z, y.w);
+            acc2(bh[u][1], bl[u][1], -h.y, -q.y, y.x, y.y);
         };
         const int full = len & ~127;
         float2 vh[4], vl[4];
@@ -741,6 +762,12 @@ __device__ __forceinline__ void warp_dots2_df(const float2 *__restrict__ Vh, con
             for (int u = 0; u < 4; u++) { vh[u] = nh[u]; vl[u] = nl[u]; }
         }
         for (i = full + lane; i < len; i += 32) step(0, hp[i], lp[i], s1[i], s2[i]);
+        if (BIAS) {            // remove the bias: sh in [3M/4, 5M/4], so sh - M is exact
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) bh[u][c] = __fsub_rn(bh[u][c], M2);
+        }
 #pragma unroll
         for (int u = 1; u < 4; u++)
 #pragma unroll
@@ -767,12 +794,16 @@ __device__ __forceinline__ void warp_dots2_df(const float2 *__restrict__ Vh, con
 }
 
 // Partials part1[r][cta][l] = Σ conj(V_l) x1 and part2[r][cta][l] = Σ conj(V_l) w for l < nv
-// (x1: hi/lo copies of a basis slot; w: FP64).  Dynamic shared memory: 2 · chunk float4.
+// (x1: hi/lo copies of basis slot nv-1; w: FP64).  vmax[r·ldp + l], l < nv-1: max |hi part| of
+// slot l as float bits (BIAS only).  Dynamic shared memory: 2 · chunk float4, then nv - 1 floats
+// (BIAS).
+template <bool BIAS>
 __global__ void __launch_bounds__(OT, 2)
 k_odots2_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int nv,
             const float2 *__restrict__ x1h, const float2 *__restrict__ x1l, const double2 *__restrict__ w,
-            double2 *__restrict__ part1, double2 *__restrict__ part2) {
+            double2 *__restrict__ part1, double2 *__restrict__ part2, const unsigned *__restrict__ vmax) {
     extern __shared__ float4 st2[];
+    __shared__ float mx[2][OT / 32];
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     Vh += r * B.n32; Vl += r * B.n32; x1h += r * B.n32; x1l += r * B.n32; w += r * B.n;
@@ -780,16 +811,35 @@ k_odots2_df(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restric
     long long b, e;
     chunk_of(B.n, b, e);
     const int len = (int)(e > b ? e - b : 0);
+    const long long chunk = (B.n + gridDim.x - 1) / gridDim.x;
     float4 *s1 = st2, *s2 = st2 + len;
+    float *vms = reinterpret_cast<float *>(st2 + 2 * chunk);
+    float m1 = 0.f, m2 = 0.f;
     for (int i = threadIdx.x; i < len; i += OT) {
         const float2 h = x1h[b + i], q = x1l[b + i];
         s1[i] = make_float4(h.x, q.x, h.y, q.y);
         const double2 x = w[b + i];
         const float rh = (float)x.x, ih = (float)x.y;
         s2[i] = make_float4(rh, (float)(x.x - (double)rh), ih, (float)(x.y - (double)ih));
+        m1 = fmaxf(m1, fmaxf(fabsf(h.x), fabsf(h.y)));
+        m2 = fmaxf(m2, fmaxf(fabsf(rh), fabsf(ih)));
+    }
+    float xm1 = 0.f, xm2 = 0.f;
+    if (BIAS) {
+        vmax += (long long)r * B.ldp;
+        for (int l = threadIdx.x; l < nv - 1; l += OT) vms[l] = __uint_as_float(vmax[l]);
+        for (int o = 16; o > 0; o >>= 1) {
+            m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+            m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        }
+        if ((threadIdx.x & 31) == 0) { mx[0][threadIdx.x >> 5] = m1; mx[1][threadIdx.x >> 5] = m2; }
     }
     __syncthreads();
-    warp_dots2_df(Vh, Vl, B.ld32, nv, s1, s2, b, len, part1, part2, B.ldp);
+    if (BIAS) {
+#pragma unroll
+        for (int q = 0; q < OT / 32; q++) { xm1 = fmaxf(xm1, mx[0][q]); xm2 = fmaxf(xm2, mx[1][q]); }
+    }
+    warp_dots2_df<BIAS>(Vh, Vl, B.ld32, nv, s1, s2, b, len, part1, part2, B.ldp, vms, xm1, xm2);
 }
 
 // Block reductions of the small per-RHS kernels (OG threads)
@@ -851,16 +901,19 @@ __device__ double givens_step(const double2 *__restrict__ hc, double hn, int j, 
 // subdiagonal ν_j σ) and its rotation committed (hist[it-1], the final residual estimate after
 // column j-1); invs = 1/σ; P2[j] becomes v_j^H w.  Then P2[0..j] is the first-pass column j,
 // stored in H.  err[0] is set if σ² <= d/4 (the pending vector lost more than half of its norm
-// to the basis, or is not finite): the delayed form then does not hold.
+// to the basis, or is not finite): the delayed form then does not hold.  vmax[r·ldp + j] (the
+// largest |hi part| of slot j, recorded by the update of this step) is cleared.
 __global__ void __launch_bounds__(OG)
 k_dcgs_col(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs, double2 *__restrict__ sn,
            double2 *__restrict__ g, double2 *__restrict__ Wq, int j, const double2 *__restrict__ P1,
            double2 *__restrict__ P2, const double *__restrict__ hn, double *__restrict__ invs,
-           const double *__restrict__ fnorm, double *__restrict__ hist, int hstride, int it, int *__restrict__ err) {
+           const double *__restrict__ fnorm, double *__restrict__ hist, int hstride, int it, int *__restrict__ err,
+           unsigned *__restrict__ vmax) {
     __shared__ double red[OG / 32];
     __shared__ double2 hj_s;
     const int r = blockIdx.x;
     if (B.active && !B.active[r]) return;
+    if (threadIdx.x == 0) vmax[(long long)r * B.ldp + j] = 0u;
     const int R = B.R;
     H += (long long)r * (R + 1) * R; cs += (long long)r * R; sn += (long long)r * R;
     g += (long long)r * (R + 1); Wq += (long long)r * (R + 1);
@@ -950,17 +1003,20 @@ k_dcgs_close(OuterBatch B, double2 *__restrict__ H, double *__restrict__ cs, dou
 // The sums run over the hi/lo copies of slots 0..j-1: Σ V_l b_l in double-FP32 widened to FP64
 // every 32 vectors (as k_oupdate_df); Σ V_l a_l in FP32 from the high parts (the coefficients a
 // are rounding-error sized, so its error is far below the FP64 rounding of ṽ_j), widened every 32
-// vectors.  corr = 0 (step 0): v_0 is final and only read.  Then the partial ||w'||².
+// vectors.  corr = 0 (step 0): v_0 is final and only read.  Then the partial ||w'||², and the
+// largest |hi part| of the final v_j (an atomic maximum on float bits into vmax[r·ldp + j],
+// which k_dcgs_col cleared) for the biased dot products of the later steps.
 // Dynamic shared memory: j · (float4 + float2).
 __global__ void __launch_bounds__(OTU, 3)
 k_oupdate_dcgs(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int j, int corr,
                double2 *__restrict__ Vj, double *__restrict__ Dj, float2 *__restrict__ Vjh, float2 *__restrict__ Vjl,
                const double2 *__restrict__ acoef, const double2 *__restrict__ bcoef, const double *__restrict__ invs,
-               double2 *__restrict__ w, double *__restrict__ part_norm) {
+               double2 *__restrict__ w, double *__restrict__ part_norm, unsigned *__restrict__ vmax) {
     extern __shared__ float4 dq[];
     float4 *bq = dq;                                      // (Re hi, Re lo, Im hi, Im lo) of b_l
     float2 *aq = reinterpret_cast<float2 *>(dq + j);      // a_l in FP32
     __shared__ double red[OTU / 32];
+    __shared__ float redm[OTU / 32];
     const int r = blockIdx.y;
     if (B.active && !B.active[r]) return;
     Vh += r * B.n32; Vl += r * B.n32; w += r * B.n; Vj += r * B.n; Dj += r * B.n;
@@ -977,6 +1033,7 @@ k_oupdate_dcgs(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__rest
     const double is = corr ? invs[r] : 1.0;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x, i = 2 * p;
     double nrm = 0.0;
+    float vm = 0.f;
     if (i < B.n) {
         const bool two = i + 1 < B.n;
         const float4 *hp = reinterpret_cast<const float4 *>(Vh) + p;
@@ -1022,14 +1079,18 @@ k_oupdate_dcgs(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__rest
         }
         auto finish = [&](long long k, double sbx, double sby, double sax, double say) {
             double2 v = Vj[k];
+            float2 hi;
             if (corr) {
                 v = make_double2((v.x - sax) * is, (v.y - say) * is);
                 Vj[k] = v;
                 Dj[k] = v.x - v.y;
-                const float2 hi = make_float2((float)v.x, (float)v.y);
+                hi = make_float2((float)v.x, (float)v.y);
                 Vjh[k] = hi;
                 Vjl[k] = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+            } else {
+                hi = Vjh[k];
             }
+            vm = fmaxf(vm, fmaxf(fabsf(hi.x), fabsf(hi.y)));
             double2 x = w[k];
             x.x -= sbx + (v.x * hj.x - v.y * hj.y);
             x.y -= sby + (v.x * hj.y + v.y * hj.x);
@@ -1039,7 +1100,13 @@ k_oupdate_dcgs(OuterBatch B, const float2 *__restrict__ Vh, const float2 *__rest
         nrm = finish(i, ax, ay, cx, cy);
         if (two) nrm += finish(i + 1, bx, by, ex, ey);
     }
-    block_sum_store(nrm, red, part_norm + (long long)r * gridDim.x + blockIdx.x);
+    for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+    if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = vm;
+    block_sum_store(nrm, red, part_norm + (long long)r * gridDim.x + blockIdx.x);   // syncs before its sum
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); q++) vm = fmaxf(vm, redm[q]);
+        atomicMax(vmax + (long long)r * B.ldp + j, __float_as_uint(vm));
+    }
 }
 
 // End of a cycle: the triangular factor of every RHS's Hessenberg matrix, column k < kcols[r]
@@ -1254,16 +1321,28 @@ void launch_oupdate_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, 
     pair_plan(k_oupdate_df, plan_udf, B.n, t, g);
     k_oupdate_df<<<dim3(g, B.nrhs), t, (size_t)nv * sizeof(float4), s>>>(B, Vh, Vl, nv, h, w, part_norm);
 }
-void launch_odots2_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const float2 *x1h,
-                      const float2 *x1l, const double2 *w, double2 *part1, double2 *part2, cudaStream_t s) {
+cudaError_t launch_odots2_df(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int nv, const float2 *x1h,
+                             const float2 *x1l, const double2 *w, double2 *part1, double2 *part2,
+                             const unsigned *vmax, int bias, cudaStream_t s) {
     const long long chunk = (B.n + B.G - 1) / B.G;
-    k_odots2_df<<<dim3(B.G, B.nrhs), OT, (size_t)(2 * chunk) * sizeof(float4), s>>>(B, Vh, Vl, nv, x1h, x1l, w,
-                                                                                    part1, part2);
+    const size_t smem = (size_t)(2 * chunk) * sizeof(float4) + (bias ? (size_t)nv * sizeof(float) : 0);
+    static size_t set[2] = {48 * 1024, 48 * 1024};
+    bias = bias ? 1 : 0;
+    void (*const kern[2])(OuterBatch, const float2 *, const float2 *, int, const float2 *, const float2 *,
+                          const double2 *, double2 *, double2 *, const unsigned *) = {k_odots2_df<false>,
+                                                                                      k_odots2_df<true>};
+    if (smem > set[bias]) {
+        cudaError_t e = cudaFuncSetAttribute(kern[bias], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set[bias] = smem;
+    }
+    kern[bias]<<<dim3(B.G, B.nrhs), OT, smem, s>>>(B, Vh, Vl, nv, x1h, x1l, w, part1, part2, vmax);
+    return cudaSuccess;
 }
 void launch_dcgs_col(const OuterBatch &B, double2 *H, double *cs, double2 *sn, double2 *g, double2 *Wq, int j,
                      const double2 *P1, double2 *P2, const double *hn, double *invs, const double *fnorm,
-                     double *hist, int hstride, int it, int *err, cudaStream_t s) {
-    k_dcgs_col<<<B.nrhs, OG, 0, s>>>(B, H, cs, sn, g, Wq, j, P1, P2, hn, invs, fnorm, hist, hstride, it, err);
+                     double *hist, int hstride, int it, int *err, unsigned *vmax, cudaStream_t s) {
+    k_dcgs_col<<<B.nrhs, OG, 0, s>>>(B, H, cs, sn, g, Wq, j, P1, P2, hn, invs, fnorm, hist, hstride, it, err, vmax);
 }
 void launch_dcgs_tent(const OuterBatch &B, double2 *H, double2 *g, double2 *Wq, int j, const double *npart, int gp,
                       const double *fnorm, double tol, double *hn_out, int *flag, double *hist, int hstride, int it,
@@ -1276,11 +1355,11 @@ void launch_dcgs_close(const OuterBatch &B, double2 *H, double *cs, double2 *sn,
 }
 void launch_oupdate_dcgs(const OuterBatch &B, const float2 *Vh, const float2 *Vl, int j, int corr, double2 *Vj,
                          double *Dj, float2 *Vjh, float2 *Vjl, const double2 *acoef, const double2 *bcoef,
-                         const double *invs, double2 *w, double *part_norm, cudaStream_t s) {
+                         const double *invs, double2 *w, double *part_norm, unsigned *vmax, cudaStream_t s) {
     int t = 0, g = 0;
     pair_plan(k_oupdate_dcgs, plan_dcgs, B.n, t, g);
     k_oupdate_dcgs<<<dim3(g, B.nrhs), t, (size_t)j * (sizeof(float4) + sizeof(float2)), s>>>(
-        B, Vh, Vl, j, corr, Vj, Dj, Vjh, Vjl, acoef, bcoef, invs, w, part_norm);
+        B, Vh, Vl, j, corr, Vj, Dj, Vjh, Vjl, acoef, bcoef, invs, w, part_norm, vmax);
 }
 void launch_oupdate2(const OuterBatch &B, const double2 *V, const float2 *V32, int nv, const double2 *h,
                      double2 *w, const double *npart1, int g1, double *part_norm, int allow32, int *fallbacks,

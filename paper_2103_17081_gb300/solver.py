@@ -252,7 +252,8 @@ class Solver:
     def launch_count(self) -> int:
         return int(self._L.hdd_launch_count(self._h))
 
-    OPTIONS = {"coarse_lookahead": 1, "fused_inner": 2, "outer_dots_df": 3, "outer_update_df": 4, "outer_dcgs2": 5, "coarse_df": 6, "coarse_spike": 7}
+    OPTIONS = {"coarse_lookahead": 1, "fused_inner": 2, "outer_dots_df": 3, "outer_update_df": 4, "outer_dcgs2": 5,
+               "coarse_df": 6, "coarse_spike": 7, "outer_dots_biased": 8}
 
     def set_option(self, name: str, value: int):
         """Implementation choice of this context (hdd_set_option): "coarse_lookahead" selects
@@ -262,7 +263,9 @@ class Solver:
         double-FP32 (1) or FP64 (0); "outer_dcgs2" the delayed CGS2 outer Arnoldi (1) or plain
         CGS2 (0); "coarse_df" the complex64 inner iteration's coarse solves in double-FP32 (1) or
         FP64 (0); "coarse_spike" those solves split over 2 or 4 SMs (SPIKE) when SMs are free (1)
-        or not (0; takes effect at the next hdd_setup_deflation)."""
+        or not (0; takes effect at the next hdd_setup_deflation); "outer_dots_biased" the delayed
+        CGS2 first-pass dot products with biased accumulators (1: half their FP32 instructions,
+        a few 1e-12 of Σ|v w|; the second pass removes what they leave) or with the two-sum (0)."""
         self._check(self._L.hdd_set_option(self._h, self.OPTIONS[name], int(value)), "hdd_set_option")
         return self
 

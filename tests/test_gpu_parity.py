@@ -276,13 +276,15 @@ def test_outer_fp32_reorthogonalisation_matches_fp64(wname):
 
 
 @pytest.mark.parametrize("wname", ["tiny", "k100"])
-@pytest.mark.parametrize("update_df,dcgs2", [(0, 0), (1, 0), (1, 1)])
-def test_outer_double_fp32_first_pass_matches_fp64(wname, update_df, dcgs2):
+@pytest.mark.parametrize("update_df,dcgs2,bias", [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 1, 1)])
+def test_outer_double_fp32_first_pass_matches_fp64(wname, update_df, dcgs2, bias):
     """The outer CGS2's dot products (both passes) in double-FP32 arithmetic (hi/lo FP32 basis,
     error-free products and sums), with the first-pass update in FP64 (update_df 0) or in
     double-FP32 as well (1, widened to FP64 every 32 vectors), and in the delayed CGS2 form (dcgs2
     1: the second pass of each basis vector fused with the next step's first pass, two passes over
-    the basis per step), give the FP64 iteration: with complex128 inner solves, residual histories
+    the basis per step; bias 1: its first-pass dots with biased accumulators, a few 1e-12 of
+    Σ|v w|, corrected by the second pass), give
+    the FP64 iteration: with complex128 inner solves, residual histories
     equal to 1e-6 while the residual is above 1e-4, the same outer count within one (a different
     rounding order can move the stop across the tolerance: 19 against 20 on the tiny workload),
     solutions within 1e-5 of each other (the complex128 whole-solve bar), and the guarded FP32
@@ -297,9 +299,11 @@ def test_outer_double_fp32_first_pass_matches_fp64(wname, update_df, dcgs2):
     s.set_option("outer_dots_df", 1)
     s.set_option("outer_update_df", update_df)
     s.set_option("outer_dcgs2", dcgs2)
+    s.set_option("outer_dots_biased", bias)
     xdf, stdf = s.solve(f, inner_prec=128, outer_reorth32=1)
     s.set_option("outer_update_df", 1)
     s.set_option("outer_dcgs2", 1)
+    s.set_option("outer_dots_biased", 1)
     assert stdf["outer_reorth_fp64"] == 0 and st64["outer_reorth_fp64"] == 0
     assert abs(stdf["outer_its"] - st64["outer_its"]) <= 1
     assert _close(xdf.cpu().numpy(), x64.cpu().numpy(), 1e-5)
