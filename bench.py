@@ -44,8 +44,9 @@ TRAFFIC_PER_ALG = {
     ("outer_cgs2_fp64", False): (1.982693 + 4.043380) / (1.976274 + 3.952547),
     # k_oupdate without dots (double-FP32 dots on): 2.0608 + 0.0061 GB against 1.9828 GB
     ("outer_cgs2_fp64", True): (2.060811 + 0.006137) / ((201 * 24 + 32) * 408321 / 1e9),
-    # k_odots2_df (delayed CGS2, step 199): 1.3201 + 0.0051 GB against 1.3197 GB
-    ("outer_dots_df32", True): (1.320112 + 0.005139) / ((200 * 16 + 32) * 408321 / 1e9),
+    # k_odots2_df<1> (delayed CGS2 with biased first-pass dots, step 199): 1.3200 + 0.0052 GB
+    # against 1.3197 GB
+    ("outer_dots_df32", True): (1.320033 + 0.005162) / ((200 * 16 + 32) * 408321 / 1e9),
     # k_oupdate_dcgs (step 199): 1.3134 + 0.0189 GB against 1.3360 GB
     ("outer_update_df32", True): (1.313391 + 0.018886) / ((199 * 16 + 88) * 408321 / 1e9),
 }

@@ -106,6 +106,47 @@ def test_local_operators(oracle_mod, w, prec):
         assert _close(outs["Ainv"][F], p.sub_solve_exact(q, xf[F]), abar)
 
 
+# coarse boxes wide enough for the SPIKE split into 4 parts (each part wider than the band plus
+# one block): 2x2 subdomains, and 3x2 with three box widths
+SPIKE_CASES = [W.custom(40.0, 100, 2, 2, name="spike2x2"),
+               W.custom(50.0, 128, 3, 2, Sy=2, ifx=[0, 40, 90, 128], name="spike_ragged")]
+
+
+def _family_launches(s):
+    return {d["name"]: d["launches"] for d in s.profile_stats()}
+
+
+@pytest.mark.parametrize("w", SPIKE_CASES, ids=lambda w: w.name)
+def test_coarse_solve_spike_split_matches_oracle(oracle_mod, w):
+    """The double-FP32 coarse solve E_j⁻¹ split over a cluster of 4 SMs per chain (SPIKE: the
+    parts swept at once, then the boundary chain and the corrections through spike matrices formed
+    at set-up) against the oracle's banded LU of every E_j, and against the unsplit kernel of a
+    context set up with the split off: all within the double-FP32 bar of the local operators
+    (1e-9).  The profiler shows which kernel family ran."""
+    from paper_2103_17081_gb300 import Solver
+    s, p = _pair(oracle_mod, w)
+    fo, co = s.offsets()
+    xc = W.random_complex_fast(co[-1], 6).astype(np.complex64).astype(np.complex128)
+    s.profile(True)
+    ys = s.local_op("Einv", _to_dev(xc), 64).cpu().numpy()
+    fam = _family_launches(s)
+    s.profile(False)
+    assert fam.get("coarse_solve_df32_spike", 0) == 1 and fam.get("coarse_solve_df32", 0) == 0, fam
+    u = Solver.from_workload(w, deflation=False)
+    u.set_option("coarse_spike", 0).setup_deflation()
+    u.profile(True)
+    yu = u.local_op("Einv", _to_dev(xc), 64).cpu().numpy()
+    fam = _family_launches(u)
+    u.profile(False)
+    assert fam.get("coarse_solve_df32", 0) == 1 and fam.get("coarse_solve_df32_spike", 0) == 0, fam
+    for q in range(p.nsub):
+        Cc = slice(co[q], co[q + 1])
+        yo = p.coarse_solve(q, xc[Cc])
+        assert _close(ys[Cc], yo, 1e-9), (q, _rel(ys[Cc], yo))
+        assert _close(yu[Cc], yo, 1e-9), (q, _rel(yu[Cc], yo))
+        assert _close(ys[Cc], yu[Cc], 1e-9)
+
+
 @pytest.mark.parametrize("prec,tol", [(128, 1e-1), (128, 1e-2), (128, 1e-6), (64, 1e-1), (64, 1e-2),
                                       (64, 1e-4)])
 def test_ras_apply_matches_oracle(oracle_mod, prec, tol):
