@@ -21,6 +21,19 @@ def test_header_matches_binding():
     assert sorted(SYMBOLS) == _declared()
 
 
+def test_option_keys_match_binding_and_library():
+    """Every HDD_OPT_* key include/hdd.h defines is in the binding's OPTIONS table under its
+    lower-case name with the same value, and hdd_set_option handles it."""
+    src = open(os.path.join(ROOT, "include", "hdd.h")).read()
+    keys = {name.lower(): int(v) for name, v in re.findall(r"#define HDD_OPT_([A-Z0-9_]+)\s+(\d+)", src)}
+    assert keys, "no option keys found in the header"
+    from paper_2103_17081_gb300 import Solver
+    assert Solver.OPTIONS == keys
+    api = open(os.path.join(ROOT, "paper_2103_17081_gb300", "csrc", "hdd_api.cu")).read()
+    for name in keys:
+        assert re.search(r"key == HDD_OPT_%s\)" % name.upper(), api), name
+
+
 def test_library_builds_and_exports_all_symbols():
     from paper_2103_17081_gb300 import build
     path = build.build()
