@@ -1326,15 +1326,22 @@ cudaError_t launch_odots2_df(const OuterBatch &B, const float2 *Vh, const float2
                              const unsigned *vmax, int bias, cudaStream_t s) {
     const long long chunk = (B.n + B.G - 1) / B.G;
     const size_t smem = (size_t)(2 * chunk) * sizeof(float4) + (bias ? (size_t)nv * sizeof(float) : 0);
-    static size_t set[2] = {48 * 1024, 48 * 1024};
+    // the largest dynamic shared memory requested so far, per device and variant (the attribute
+    // is set on the current device)
+    constexpr int MAXDEV = 64;
+    static size_t set[MAXDEV][2];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
     bias = bias ? 1 : 0;
     void (*const kern[2])(OuterBatch, const float2 *, const float2 *, int, const float2 *, const float2 *,
                           const double2 *, double2 *, double2 *, const unsigned *) = {k_odots2_df<false>,
                                                                                       k_odots2_df<true>};
-    if (smem > set[bias]) {
-        cudaError_t e = cudaFuncSetAttribute(kern[bias], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024 && smem > set[dev][bias]) {
+        e = cudaFuncSetAttribute(kern[bias], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        set[bias] = smem;
+        set[dev][bias] = smem;
     }
     kern[bias]<<<dim3(B.G, B.nrhs), OT, smem, s>>>(B, Vh, Vl, nv, x1h, x1l, w, part1, part2, vmax);
     return cudaSuccess;
